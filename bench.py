@@ -1,0 +1,354 @@
+#!/usr/bin/env python3
+"""Benchmark of the downsampling hot path on GB300.
+
+Workload (one step): MinMax and M4, n_out = 2000, over one series of
+n = 10^9 float32 random-walk values (cumsum of N(0,1) steps) with int64
+sorted, non-equidistant x (0 then a cumsum of geometric(0.5) gaps).  Inputs
+are drawn on the device with a seeded generator and stay resident in HBM; at
+4 GB of y (8 GB of x) they are far larger than the 129 MB L2, so no flush is
+needed between steps.
+
+Metric: input GB/s = algorithmic input bytes / time, where a step's bytes are
+n*4 for each of the two algorithms plus the x reads of the bin-edge searches
+((nb+1)*ceil(log2 n)*8 per algorithm).  The line also reports the roofline of
+the dominant kernel (the streaming argmin/argmax, n*4 bytes per launch, timed
+by CUDA events on its stream), an end-to-end figure through the public API
+with pinned host buffers, and the CPU oracle timed on a bounded sample.
+
+--impl reference times the CPU oracle itself on the host cores (the paper's
+own implementation is CPU code that is not available here).
+Under torchrun each rank runs an independent series (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+N_DEFAULT = 10 ** 9
+N_OUT = 2000
+ALGOS = ("minmax", "m4")
+METRIC = "input GB/s and % of GB300 HBM peak per algorithm"
+WORKLOAD = ("single series n=1e9 float32 random walk with int64 sorted non-equidistant x "
+            "(geometric(0.5) gaps), n_out=2000, MinMax + M4")
+FALLBACK_HBM = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--n", type=int, default=N_DEFAULT)
+    ap.add_argument("--cpu-sample", type=int, default=250_000_000)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def step_bytes(n, n_out=N_OUT, x_itemsize=8):
+    per = {}
+    for algo in ALGOS:
+        nb = n_out // (2 if algo == "minmax" else 4)
+        per[algo] = n * 4 + (nb + 1) * math.ceil(math.log2(max(n, 2))) * x_itemsize
+    return per
+
+
+def hbm_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM, "fallback"
+
+
+def kernel_traffic():
+    """DRAM bytes per launch from the committed ncu summary, only while the
+    kernel source still matches the one profiled."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "argminmax_traffic.json")) as f:
+            rec = json.load(f)
+        src = open(os.path.join(ROOT, "paper_2307_05389_gb300", "csrc", "argminmax.cu"), "rb").read()
+        if hashlib.sha256(src).hexdigest() != rec.get("source_sha256"):
+            return None
+        return rec.get("dram_bytes_per_launch_full_size")
+    except Exception:
+        return None
+
+
+# ----------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        import torch
+        self.path = tempfile.mktemp(prefix="tsds_clocks_", suffix=".csv")
+        sel = []
+        try:
+            u = str(torch.cuda.get_device_properties(device_index).uuid)
+            sel = ["--id=" + (u if u.startswith("GPU-") else "GPU-" + u)]
+        except Exception:
+            sel = []
+        self.proc = None
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", *sel, f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            p = [t.strip() for t in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax.append(float(p[2]))
+                power.append(float(p[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm), "power_w_max": max(power) if power else None}
+
+
+# ----------------------------------------------------------------------------- reference arm
+
+def run_reference(args, rank):
+    import numpy as np
+
+    import oracle
+    from paper_2307_05389_gb300 import inputs
+    if rank != 0:
+        return
+    n = min(args.cpu_sample, args.n) // 5          # one step of the reference: a bounded sample
+    y = inputs.random_walk(n, "float32", seed=2)
+    x = inputs.geometric_x(n, seed=2)
+    oracle.build()
+    for _ in range(args.warmup):
+        for algo in ALGOS:
+            oracle.downsample(algo, x, y, N_OUT)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for algo in ALGOS:
+            oracle.downsample(algo, x, y, N_OUT)
+    dt = time.perf_counter() - t0
+    per = step_bytes(n)
+    gbs = sum(per.values()) * args.steps / dt / 1e9
+    sample = f"first {n} points of the workload (numpy default_rng seed 2), MinMax + M4, single-threaded C oracle"
+    line = {"impl": "reference", "metric": METRIC, "value": gbs, "unit": "GB/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "n_sample": n, "n_out": N_OUT},
+            "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": gbs, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- native arm
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    import numpy as np
+    import torch
+
+    import paper_2307_05389_gb300 as pkg
+    from paper_2307_05389_gb300 import binding, inputs
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    pkg.load()
+
+    n = args.n
+    y = inputs.random_walk_cuda(n, "float32", seed=2 + rank, device=dev)
+    x = inputs.geometric_x_cuda(n, seed=2 + rank, device=dev)
+    outs = {a: torch.empty(N_OUT, dtype=torch.int64, device=dev) for a in ALGOS}
+    cnts = {a: torch.empty(1, dtype=torch.int64, device=dev) for a in ALGOS}
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()               # drop the generators' temporaries
+    stream = torch.cuda.current_stream(dev)
+    sp = binding.ctypes.c_void_p(stream.cuda_stream)
+    fns = {"minmax": binding.tsds_minmax, "m4": binding.tsds_m4}
+
+    def call(algo):
+        r = fns[algo](x.data_ptr(), binding.DTYPES["int64"], y.data_ptr(), binding.DTYPES["float32"], n, N_OUT,
+                      0, outs[algo].data_ptr(), cnts[algo].data_ptr(), sp)
+        if r != 0:
+            raise RuntimeError(binding.last_error())
+
+    def step():
+        for a in ALGOS:
+            call(a)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+
+    # ---- timed region: K steps, CUDA events on the launching stream
+    clocks = ClockSampler(local)
+    time.sleep(0.2)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    pkg.tsds_timing_read()                 # drop anything recorded before
+    pkg.tsds_timing_enable(True)
+    launches0 = pkg.tsds_kernel_launches()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    launches = pkg.tsds_kernel_launches() - launches0
+    pkg.tsds_timing_enable(False)
+    ms = ev0.elapsed_time(ev1)
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    kern_ms, kern_launches = pkg.tsds_timing_read()
+    t = torch.tensor([ms], device=dev)
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+
+    per = step_bytes(n)
+    total_bytes = sum(per.values()) * args.steps * world
+    value = total_bytes / (ms_max / 1e3) / 1e9
+    peak, peak_src = hbm_peak()
+    kern_avg_ms = kern_ms / max(kern_launches, 1)
+    achieved = n * 4 / (kern_avg_ms / 1e3) / 1e9
+
+    # ---- per-algorithm breakdown (whole call and streaming kernel)
+    per_algo = {}
+    for a in ALGOS:
+        reps = max(10, args.steps // 4)
+        pkg.tsds_timing_read()
+        pkg.tsds_timing_enable(True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            call(a)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        pkg.tsds_timing_enable(False)
+        km, kl = pkg.tsds_timing_read()
+        call_ms = e0.elapsed_time(e1) / reps
+        per_algo[a] = {"call_ms": call_ms, "call_GBps": per[a] / (call_ms / 1e3) / 1e9,
+                       "kernel_ms": km / max(kl, 1), "kernel_GBps": n * 4 / (km / max(kl, 1) / 1e3) / 1e9,
+                       "pct_of_hbm_peak": 100.0 * per[a] / (call_ms / 1e3) / 1e9 / peak}
+
+    # ---- end to end through the public API with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        yh = y.cpu().pin_memory()
+        xh = x.cpu().pin_memory()
+        yd, xd = torch.empty_like(y), torch.empty_like(x)
+        pkg.downsample_host(ALGOS, yh, N_OUT, x=xh, y_dev=yd, x_dev=xd)   # warm-up
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        d2h = 0
+        for _ in range(args.e2e_steps):
+            res = pkg.downsample_host(ALGOS, yh, N_OUT, x=xh, y_dev=yd, x_dev=xd)
+            d2h = sum(r.numel() * 8 + 8 for r in res)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        tt = torch.tensor([dt], device=dev)
+        if dist:
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        dt = float(tt.item())
+        e2e = {"value": sum(per.values()) * args.e2e_steps * world / dt / 1e9, "unit": "GB/s",
+               "h2d_bytes_per_step": int(yh.numel() * 4 + xh.numel() * 8), "d2h_bytes_per_step": int(d2h),
+               "api": "paper_2307_05389_gb300.downsample_host"}
+        del yh, xh, yd, xd
+
+    # ---- CPU oracle on a bounded sample (rank 0)
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        import oracle
+        oracle.build()
+        ns = min(args.cpu_sample, n)
+        ys = y[:ns].cpu().numpy()
+        xs = x[:ns].cpu().numpy()
+        t0 = time.perf_counter()
+        for a in ALGOS:
+            oracle.downsample(a, xs, ys, N_OUT)
+        dt = time.perf_counter() - t0
+        cpu = {"value": sum(step_bytes(ns).values()) / dt / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
+               "sample": f"first {ns} points of the same series and x, MinMax + M4 once each ({dt:.1f} s)"}
+
+    # ---- output check of the timed results against each other (counts)
+    counts = {a: int(cnts[a].item()) for a in ALGOS}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "impl": "native",
+            "config": {"workload": WORKLOAD, "n": n, "n_out": N_OUT, "algorithms": list(ALGOS),
+                       "x": "int64", "y": "float32", "l2": "inputs larger than L2 (4 GB y, 8 GB x); no flush",
+                       "parallelism": f"{world} independent series (one per GPU)" if world > 1 else "single GPU"},
+            "pct_of_hbm_peak": 100.0 * value / world / peak,
+            "per_algo": per_algo,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": kernel_traffic(),
+                         "kernel": "tsds::k_argminmax (streaming per-bin argmin/argmax)",
+                         "bytes_per_launch": n * 4, "launches_timed": kern_launches,
+                         "peak_source": f"{peak_src} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"},
+            "clocks": clk,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+            "gpu_launches": launches,
+            "selected": counts,
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

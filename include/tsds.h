@@ -1,0 +1,142 @@
+/*
+ * tsds.h -- C ABI of the GB300 time-series downsampling library.
+ *
+ * The library computes, on one NVIDIA GB300 GPU, the index selections of the
+ * downsampling algorithms offered by "tsdownsample: high-performance time
+ * series downsampling for scalable visualization" (arXiv 2307.05389):
+ * MinMax, M4, LTTB and MinMaxLTTB.  Each call mirrors the paper's interface
+ * downsample([x], y, n_out) -> indices (Section 2.3), returning int64 indices
+ * of the selected points in increasing order.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Pointers named x, y, out and out_count are CUDA device pointers owned by
+ *    the caller.  The library never frees them, never keeps them past the
+ *    call's completion on the stream and never copies y or x.
+ *  - y holds n elements of y_dtype; x is NULL (equally spaced points, Section
+ *    2.3) or holds n elements of x_dtype sorted non-decreasing (not checked).
+ *    Both must be aligned to their element size.
+ *  - out must have room for n_out indices (for MinMaxLTTB also n_out); when
+ *    n_out >= n it receives 0..n-1 and needs room for n.  *out_count (a device
+ *    int64) receives the number of indices written.  With x, empty bins select
+ *    nothing, so MinMax and M4 may return fewer than n_out indices (Section
+ *    2.3 footnote).
+ *  - Calls are asynchronous on `stream` (a cudaStream_t passed as void*;
+ *    NULL selects the legacy default stream).  Scratch memory is taken from a
+ *    library-owned, stream-ordered pool on the current device and returned to
+ *    it in stream order; tsds_shutdown releases the pool.
+ *  - Status codes are returned, never exceptions.  TSDS_EINVAL leaves out and
+ *    out_count untouched.  tsds_last_error() describes the last failure of
+ *    the calling thread.
+ *
+ * Semantics (the paper states the interface and the argmin/argmax loop,
+ * Section 2.1 Listing 1; it does not define bins or LTTB buckets, so the
+ * library fixes these readings):
+ *  - MinMax uses n_out/2 bins, M4 n_out/4 bins.  Without x, bin i starts at
+ *    ceil(i*(n-1)/nb); with x, bin i starts at the first point whose x
+ *    reaches x_0 + i*(x_{n-1}-x_0)/nb (exact integer arithmetic for integer x,
+ *    binary64 with each operation rounded to nearest for floating x).  The
+ *    last bin ends at n.
+ *  - Per bin MinMax selects {argmin, argmax}, M4 {first, argmin, argmax,
+ *    last}; each bin's selections are emitted once each, in increasing order.
+ *    Ties go to the lowest index; -0 equals +0; float16 compares as the value
+ *    it encodes.
+ *  - TSDS_NAN_PROPAGATE: a bin holding a NaN selects its first NaN as argmin
+ *    and argmax.  TSDS_NAN_IGNORE: NaNs are skipped; an all-NaN bin selects
+ *    its first index.
+ *  - LTTB keeps the first and last point and picks one point in each of
+ *    n_out-2 buckets over the interior (bucket j covers points
+ *    [1+floor(j(m-2)/B), 1+floor((j+1)(m-2)/B))), maximising the doubled
+ *    triangle area |(xa-xm)(yb-ya) - (xa-xb)(ym-ya)| in binary64 with every
+ *    operation rounded and no fused multiply-add, where a is the previous
+ *    pick and (xm, ym) the next bucket's mean (index-order binary64 sums
+ *    divided by the count) or, after the last bucket, the last point.  x is
+ *    the point's x converted to binary64, or its index.
+ */
+#ifndef TSDS_H
+#define TSDS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* The eleven element types of the paper's ArgMinMax (Section 2.1). */
+typedef enum {
+  TSDS_I8 = 0, TSDS_I16 = 1, TSDS_I32 = 2, TSDS_I64 = 3,
+  TSDS_U8 = 4, TSDS_U16 = 5, TSDS_U32 = 6, TSDS_U64 = 7,
+  TSDS_F16 = 8, TSDS_F32 = 9, TSDS_F64 = 10
+} tsds_dtype;
+
+typedef enum { TSDS_NAN_PROPAGATE = 0, TSDS_NAN_IGNORE = 1 } tsds_nan_mode;
+
+typedef enum {
+  TSDS_OK = 0,
+  TSDS_EINVAL = 1,    /* an argument outside what the algorithm defines */
+  TSDS_ENOMEM = 2,    /* the scratch pool could not grow */
+  TSDS_ECUDA = 3,     /* a CUDA runtime call or kernel launch failed */
+  TSDS_ETIMEOUT = 4,  /* a bounded device-side wait ran out */
+  TSDS_EINTERNAL = 5  /* a device-side consistency check failed */
+} tsds_status;
+
+/* MinMax (Section 1; per-bin argmin/argmax of Section 2.1).
+ * n >= 0; n_out even and >= 2.  Selects at most n_out indices. */
+tsds_status tsds_minmax(const void* x, tsds_dtype x_dtype, const void* y, tsds_dtype y_dtype,
+                        int64_t n, int64_t n_out, tsds_nan_mode nan, int64_t* out,
+                        int64_t* out_count, void* stream);
+
+/* M4 (Section 1): first, argmin, argmax and last of each bin.
+ * n >= 0; n_out a positive multiple of 4. */
+tsds_status tsds_m4(const void* x, tsds_dtype x_dtype, const void* y, tsds_dtype y_dtype,
+                    int64_t n, int64_t n_out, tsds_nan_mode nan, int64_t* out,
+                    int64_t* out_count, void* stream);
+
+/* LTTB (Section 1; sequential over buckets, Table 1 caption).
+ * n >= 0; n_out >= 3.  Selects exactly min(n, n_out) indices. */
+tsds_status tsds_lttb(const void* x, tsds_dtype x_dtype, const void* y, tsds_dtype y_dtype,
+                      int64_t n, int64_t n_out, tsds_nan_mode nan, int64_t* out,
+                      int64_t* out_count, void* stream);
+
+/* MinMaxLTTB (Section 1): MinMax over the interior points 1..n-2 with
+ * 2*floor(n_out*minmax_ratio/2) selections, plus the first and last point,
+ * then LTTB over those points (with their original x or index).
+ * n >= 0; n_out >= 3; minmax_ratio >= 1.  Selects min(n, n_out) indices
+ * unless the preselection itself returns fewer than n_out points. */
+tsds_status tsds_minmaxlttb(const void* x, tsds_dtype x_dtype, const void* y,
+                            tsds_dtype y_dtype, int64_t n, int64_t n_out,
+                            int64_t minmax_ratio, tsds_nan_mode nan, int64_t* out,
+                            int64_t* out_count, void* stream);
+
+/* Message for the calling thread's last failed call ("" if none). */
+const char* tsds_last_error(void);
+
+/* Releases the scratch pools of every device the library touched.  Work
+ * still queued on streams must have completed.  Later calls re-create them. */
+void tsds_shutdown(void);
+
+/* Library version, "major.minor.patch". */
+const char* tsds_version(void);
+
+/* ---- tracing (the paper reports median wall times, Section 4; these give
+ * the device-side view of the same work). */
+
+/* Number of CUDA kernels this library has launched in the process so far. */
+int64_t tsds_kernel_launches(void);
+
+/* on != 0: every later MinMax/M4 streaming argmin/argmax launch (also the
+ * MinMaxLTTB preselection) is bracketed by two CUDA events recorded on the
+ * call's stream.  Recording adds no synchronisation. */
+void tsds_timing_enable(int on);
+
+/* Waits for the launches recorded since the previous read, writes the sum of
+ * their device durations in milliseconds to *total_ms (may be NULL) and their
+ * number to *launches (may be NULL), and forgets them.  TSDS_ECUDA if an
+ * event query fails. */
+tsds_status tsds_timing_read(double* total_ms, int64_t* launches);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TSDS_H */

@@ -1,1 +1,30 @@
+"""GB300-native downsampling for line-chart visualisation: MinMax, M4, LTTB and
+MinMaxLTTB (the algorithms of tsdownsample, arXiv 2307.05389) as hand-written
+sm_103a CUDA kernels behind a C ABI (include/tsds.h).
 
+``binding`` holds the ctypes entry points (same names as the C ABI) and the
+torch-facing ``downsample`` / ``*Downsampler`` helpers; ``inputs`` draws the
+seeded synthetic series used by the tests and the benchmark.
+"""
+from .binding import (  # noqa: F401
+    DTYPES,
+    M4Downsampler,
+    LTTBDownsampler,
+    MinMaxDownsampler,
+    MinMaxLTTBDownsampler,
+    NAN_MODES,
+    TsdsError,
+    downsample,
+    downsample_host,
+    last_error,
+    load,
+    tsds_lttb,
+    tsds_m4,
+    tsds_minmax,
+    tsds_minmaxlttb,
+    tsds_shutdown,
+    tsds_version,
+    tsds_kernel_launches,
+    tsds_timing_enable,
+    tsds_timing_read,
+)

@@ -1,0 +1,227 @@
+"""ctypes binding of libtsds.so (the C ABI in include/tsds.h).
+
+The functions named like the C entry points take raw device pointers and
+return the tsds_status code; ``downsample`` and the ``*Downsampler`` classes
+marshal torch tensors onto them.  Every step of the computation runs in the
+library's CUDA kernels; there is no CPU path, and a missing library raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libtsds.so")
+
+DTYPES = {
+    "int8": 0, "int16": 1, "int32": 2, "int64": 3,
+    "uint8": 4, "uint16": 5, "uint32": 6, "uint64": 7,
+    "float16": 8, "float32": 9, "float64": 10,
+}
+NAN_MODES = {"propagate": 0, "ignore": 1}
+STATUS = {0: "TSDS_OK", 1: "TSDS_EINVAL", 2: "TSDS_ENOMEM", 3: "TSDS_ECUDA", 4: "TSDS_ETIMEOUT",
+          5: "TSDS_EINTERNAL"}
+
+ENTRY_POINTS = ["tsds_minmax", "tsds_m4", "tsds_lttb", "tsds_minmaxlttb", "tsds_last_error",
+                "tsds_shutdown", "tsds_version"]
+
+_lib = None
+
+
+class TsdsError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+def load(path: str = LIB_PATH):
+    """Load libtsds.so (built by paper_2307_05389_gb300.build) and declare its symbols."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with `python -m paper_2307_05389_gb300.build`")
+    lib = ctypes.CDLL(path)
+    p, i64, c_int = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+    for name in ("tsds_minmax", "tsds_m4", "tsds_lttb"):
+        f = getattr(lib, name)
+        f.argtypes = [p, c_int, p, c_int, i64, i64, c_int, p, p, p]
+        f.restype = c_int
+    lib.tsds_minmaxlttb.argtypes = [p, c_int, p, c_int, i64, i64, i64, c_int, p, p, p]
+    lib.tsds_minmaxlttb.restype = c_int
+    lib.tsds_last_error.argtypes = []
+    lib.tsds_last_error.restype = ctypes.c_char_p
+    lib.tsds_shutdown.argtypes = []
+    lib.tsds_shutdown.restype = None
+    lib.tsds_version.argtypes = []
+    lib.tsds_version.restype = ctypes.c_char_p
+    lib.tsds_kernel_launches.argtypes = []
+    lib.tsds_kernel_launches.restype = i64
+    lib.tsds_timing_enable.argtypes = [c_int]
+    lib.tsds_timing_enable.restype = None
+    lib.tsds_timing_read.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)]
+    lib.tsds_timing_read.restype = c_int
+    _lib = lib
+    return lib
+
+
+def tsds_kernel_launches() -> int:
+    return int(load().tsds_kernel_launches())
+
+
+def tsds_timing_enable(on: bool) -> None:
+    load().tsds_timing_enable(1 if on else 0)
+
+
+def tsds_timing_read():
+    """(total device milliseconds, launches) of the timed streaming launches since the last read."""
+    ms = ctypes.c_double()
+    k = ctypes.c_int64()
+    r = load().tsds_timing_read(ctypes.byref(ms), ctypes.byref(k))
+    if r != 0:
+        raise TsdsError(r, last_error())
+    return ms.value, k.value
+
+
+def last_error() -> str:
+    return load().tsds_last_error().decode()
+
+
+# ----------------------------------------------------------------------------- raw entry points
+
+def tsds_minmax(x, x_dtype, y, y_dtype, n, n_out, nan, out, out_count, stream):
+    return load().tsds_minmax(x, x_dtype, y, y_dtype, n, n_out, nan, out, out_count, stream)
+
+
+def tsds_m4(x, x_dtype, y, y_dtype, n, n_out, nan, out, out_count, stream):
+    return load().tsds_m4(x, x_dtype, y, y_dtype, n, n_out, nan, out, out_count, stream)
+
+
+def tsds_lttb(x, x_dtype, y, y_dtype, n, n_out, nan, out, out_count, stream):
+    return load().tsds_lttb(x, x_dtype, y, y_dtype, n, n_out, nan, out, out_count, stream)
+
+
+def tsds_minmaxlttb(x, x_dtype, y, y_dtype, n, n_out, minmax_ratio, nan, out, out_count, stream):
+    return load().tsds_minmaxlttb(x, x_dtype, y, y_dtype, n, n_out, minmax_ratio, nan, out, out_count, stream)
+
+
+def tsds_shutdown():
+    load().tsds_shutdown()
+
+
+def tsds_version() -> str:
+    return load().tsds_version().decode()
+
+
+# ----------------------------------------------------------------------------- torch marshalling
+
+def _torch_dtype_name(t) -> str:
+    name = str(t.dtype).replace("torch.", "")
+    if name not in DTYPES:
+        raise TypeError(f"unsupported dtype {t.dtype}")
+    return name
+
+
+def out_capacity(algo: str, n: int, n_out: int) -> int:
+    return max(1, n if n_out >= n else n_out)
+
+
+def downsample(algo, y, n_out, x=None, nan="propagate", minmax_ratio=4, out=None, out_count=None,
+               stream=None, sync=True):
+    """Indices selected by `algo` ("minmax", "m4", "lttb", "minmaxlttb") on y (and x).
+
+    y and x are 1-D CUDA tensors (contiguous).  With sync=True the result is
+    trimmed to the selected count (one device-to-host read of the count);
+    with sync=False the call only enqueues work and returns (out, out_count)
+    device tensors.  Errors raise TsdsError with the library's message."""
+    import torch
+    if not (y.is_cuda and y.dim() == 1 and y.is_contiguous()):
+        raise ValueError("y must be a contiguous 1-D CUDA tensor")
+    n = y.shape[0]
+    if x is not None:
+        if not (x.is_cuda and x.dim() == 1 and x.is_contiguous() and x.shape[0] == n):
+            raise ValueError("x must be a contiguous 1-D CUDA tensor as long as y")
+    dev = y.device
+    if out is None:
+        out = torch.empty(out_capacity(algo, n, n_out), dtype=torch.int64, device=dev)
+    if out_count is None:
+        out_count = torch.empty(1, dtype=torch.int64, device=dev)
+    st = stream if stream is not None else torch.cuda.current_stream(dev)
+    xp = x.data_ptr() if x is not None else None
+    xd = DTYPES[_torch_dtype_name(x)] if x is not None else 0
+    args = (xp, xd, y.data_ptr(), DTYPES[_torch_dtype_name(y)], n, n_out)
+    tail = (NAN_MODES[nan], out.data_ptr(), out_count.data_ptr(), ctypes.c_void_p(st.cuda_stream))
+    with torch.cuda.device(dev):
+        if algo == "minmax":
+            r = tsds_minmax(*args, *tail)
+        elif algo == "m4":
+            r = tsds_m4(*args, *tail)
+        elif algo == "lttb":
+            r = tsds_lttb(*args, *tail)
+        elif algo == "minmaxlttb":
+            r = tsds_minmaxlttb(*args, minmax_ratio, *tail)
+        else:
+            raise ValueError(f"unknown algorithm {algo!r}")
+    if r != 0:
+        raise TsdsError(r, last_error())
+    if not sync:
+        return out, out_count
+    k = int(out_count.item())
+    return out[:k]
+
+
+def downsample_host(algos, y, n_out, x=None, nan="propagate", minmax_ratio=4, device="cuda",
+                    y_dev=None, x_dev=None):
+    """Host-buffer form: copies y (and x) from host memory to the device once
+    (asynchronously when the host tensors are pinned), runs each algorithm in
+    `algos` on the GPU and copies each index list back.  Returns a list of
+    CPU int64 tensors.  y_dev / x_dev may supply preallocated device buffers
+    to copy into."""
+    import torch
+    st = torch.cuda.current_stream(device)
+    yd = y_dev if y_dev is not None else torch.empty_like(y, device=device)
+    yd.copy_(y, non_blocking=True)
+    xd = None
+    if x is not None:
+        xd = x_dev if x_dev is not None else torch.empty_like(x, device=device)
+        xd.copy_(x, non_blocking=True)
+    res = []
+    for algo in algos:
+        out, cnt = downsample(algo, yd, n_out, x=xd, nan=nan, minmax_ratio=minmax_ratio, stream=st, sync=False)
+        k = int(cnt.item())
+        res.append(out[:k].cpu())
+    return res
+
+
+class _Downsampler:
+    """Class interface in the shape of the paper's (Section 2.3):
+    ``Downsampler().downsample([x], y, n_out=..., **kwargs)``."""
+    algo = ""
+
+    def downsample(self, *args, n_out, nan="propagate", **kw):
+        if len(args) == 1:
+            x, y = None, args[0]
+        elif len(args) == 2:
+            x, y = args
+        else:
+            raise TypeError("downsample([x], y, n_out=...)")
+        return downsample(self.algo, y, n_out, x=x, nan=nan, **kw)
+
+
+class MinMaxDownsampler(_Downsampler):
+    algo = "minmax"
+
+
+class M4Downsampler(_Downsampler):
+    algo = "m4"
+
+
+class LTTBDownsampler(_Downsampler):
+    algo = "lttb"
+
+
+class MinMaxLTTBDownsampler(_Downsampler):
+    algo = "minmaxlttb"
+
+    def downsample(self, *args, n_out, minmax_ratio=4, nan="propagate", **kw):
+        return super().downsample(*args, n_out=n_out, nan=nan, minmax_ratio=minmax_ratio, **kw)

@@ -1,0 +1,313 @@
+// api.cu -- the C ABI (include/tsds.h): argument checks, the per-device
+// stream-ordered scratch pool, and the launch sequence of each algorithm.
+#include <cuda_runtime.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <atomic>
+#include <map>
+#include <mutex>
+#include <vector>
+
+#include "internal.h"
+#include "lttb.h"
+
+namespace tsds {
+
+// ---------------------------------------------------------------- errors
+
+static thread_local char g_err[512] = "";
+
+tsds_status fail(tsds_status s, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof g_err, fmt, ap);
+  va_end(ap);
+  return s;
+}
+
+#define TSDS_CK(call)                                                                    \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess) {                                                             \
+      if (e_ == cudaErrorMemoryAllocation)                                               \
+        return fail(TSDS_ENOMEM, "%s: %s", #call, cudaGetErrorString(e_));               \
+      return fail(TSDS_ECUDA, "%s: %s", #call, cudaGetErrorString(e_));                  \
+    }                                                                                    \
+  } while (0)
+
+// ---------------------------------------------------------------- per-device state
+
+struct DevState {
+  cudaMemPool_t pool = nullptr;
+  int sm_count = 0;
+};
+static std::mutex g_mu;
+static std::map<int, DevState> g_dev;
+
+static DevState* dev_state(cudaError_t* err) {
+  int d = 0;
+  *err = cudaGetDevice(&d);
+  if (*err != cudaSuccess) return nullptr;
+  std::lock_guard<std::mutex> lk(g_mu);
+  DevState& s = g_dev[d];
+  if (!s.pool) {
+    cudaMemPoolProps props;
+    memset(&props, 0, sizeof props);
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = d;
+    *err = cudaMemPoolCreate(&s.pool, &props);
+    if (*err != cudaSuccess) { s.pool = nullptr; return nullptr; }
+    uint64_t keep = ~0ull;   // keep freed blocks cached for the next call
+    cudaMemPoolSetAttribute(s.pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    *err = cudaDeviceGetAttribute(&s.sm_count, cudaDevAttrMultiProcessorCount, d);
+    if (*err != cudaSuccess) return nullptr;
+  }
+  return &s;
+}
+
+int device_sm_count() {
+  cudaError_t e;
+  DevState* s = dev_state(&e);
+  return s ? s->sm_count : 148;
+}
+
+cudaError_t scratch_alloc(Scratch& s, size_t bytes, cudaStream_t st) {
+  cudaError_t e;
+  DevState* d = dev_state(&e);
+  if (!d) return e;
+  s.st = st;
+  if (bytes == 0) bytes = 256;
+  return cudaMallocFromPoolAsync(&s.p, bytes, d->pool, st);
+}
+
+// ---------------------------------------------------------------- tracing
+
+static std::atomic<long long> g_launches{0};
+static std::atomic<int> g_timing{0};
+struct TimedLaunch {
+  cudaEvent_t a, b;
+};
+static std::mutex g_tmu;
+static std::vector<TimedLaunch> g_timed;
+static std::vector<cudaEvent_t> g_free_events;
+
+void note_launch(int kernels) { g_launches.fetch_add(kernels, std::memory_order_relaxed); }
+bool timing_on() { return g_timing.load(std::memory_order_relaxed) != 0; }
+
+static cudaEvent_t take_event() {
+  std::lock_guard<std::mutex> lk(g_tmu);
+  if (!g_free_events.empty()) {
+    cudaEvent_t e = g_free_events.back();
+    g_free_events.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+void timing_begin(cudaStream_t st, void** token) {
+  *token = nullptr;
+  if (!timing_on()) return;
+  cudaEvent_t a = take_event();
+  if (a && cudaEventRecord(a, st) == cudaSuccess) *token = a;
+}
+
+void timing_end(cudaStream_t st, void* token) {
+  if (!token) return;
+  cudaEvent_t b = take_event();
+  if (!b) return;
+  cudaEventRecord(b, st);
+  std::lock_guard<std::mutex> lk(g_tmu);
+  g_timed.push_back(TimedLaunch{static_cast<cudaEvent_t>(token), b});
+}
+
+static size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// ---------------------------------------------------------------- argument checks
+
+static tsds_status check_common(const void* x, int x_dtype, const void* y, int y_dtype, int64_t n,
+                                int nan, const int64_t* out, const int64_t* out_count) {
+  if (n < 0) return fail(TSDS_EINVAL, "n must be >= 0 (got %lld)", (long long)n);
+  if (!dtype_valid(y_dtype)) return fail(TSDS_EINVAL, "unknown y dtype %d", y_dtype);
+  if (x && !dtype_valid(x_dtype)) return fail(TSDS_EINVAL, "unknown x dtype %d", x_dtype);
+  if (nan != TSDS_NAN_PROPAGATE && nan != TSDS_NAN_IGNORE) return fail(TSDS_EINVAL, "unknown NaN mode %d", nan);
+  if (n > 0 && !y) return fail(TSDS_EINVAL, "y is NULL");
+  if (!out_count) return fail(TSDS_EINVAL, "out_count is NULL");
+  if (n > 0 && !out) return fail(TSDS_EINVAL, "out is NULL");
+  if (y && (reinterpret_cast<uintptr_t>(y) % dtype_size((tsds_dtype)y_dtype)) != 0)
+    return fail(TSDS_EINVAL, "y is not aligned to its element size");
+  if (x && (reinterpret_cast<uintptr_t>(x) % dtype_size((tsds_dtype)x_dtype)) != 0)
+    return fail(TSDS_EINVAL, "x is not aligned to its element size");
+  return TSDS_OK;
+}
+
+// ---------------------------------------------------------------- MinMax / M4
+
+// Scratch layout of one binned call.
+struct BinnedLayout {
+  size_t edges, res, cnt, work, first, last, total, zero_begin, zero_bytes;
+};
+
+static BinnedLayout binned_layout(int64_t nb, int64_t windows) {
+  BinnedLayout L;
+  size_t o = 0;
+  L.edges = o; o = align_up(o + (size_t)(nb + 1) * 8, 256);
+  L.res = o;   o = align_up(o + (size_t)nb * 16, 256);
+  L.cnt = o;   o = align_up(o + (size_t)nb * 4, 256);
+  L.work = o;  o = align_up(o + sizeof(WorkCounters), 256);
+  L.first = o; o = align_up(o + (size_t)windows * sizeof(Piece), 256);
+  L.last = o;  o = align_up(o + (size_t)windows * sizeof(Piece), 256);
+  L.total = o;
+  L.zero_begin = L.cnt;
+  L.zero_bytes = L.first - L.cnt;
+  return L;
+}
+
+// The MinMax/M4 pipeline on one series with nb bins, writing to out/out_count
+// with idx_bias added to every index.
+tsds_status run_binned_series(const void* x, tsds_dtype x_dtype, const void* y, tsds_dtype y_dtype,
+                              int64_t n, int64_t nb, tsds_nan_mode nan, Algo algo, int64_t* out,
+                              int64_t* out_count, int64_t idx_bias, cudaStream_t st) {
+  const int64_t welems = window_elems(y_dtype);
+  const int64_t windows = (n + welems - 1) / welems;
+  const BinnedLayout L = binned_layout(nb, windows);
+  Scratch s;
+  TSDS_CK(scratch_alloc(s, L.total, st));
+  char* base = static_cast<char*>(s.p);
+  TSDS_CK(cudaMemsetAsync(base + L.zero_begin, 0, L.zero_bytes, st));
+  SeriesDev S;
+  S.y = y;
+  S.x = x;
+  S.n = n;
+  S.nb = nb;
+  S.edges = reinterpret_cast<int64_t*>(base + L.edges);
+  S.res = reinterpret_cast<int64_t*>(base + L.res);
+  S.cnt = reinterpret_cast<uint32_t*>(base + L.cnt);
+  S.win_base = 0;
+  S.out = out;
+  S.out_count = out_count;
+  S.idx_bias = idx_bias;
+  TSDS_CK(launch_edges(nullptr, 1, &S, x != nullptr, x_dtype, nb, st));
+  void* tok;
+  timing_begin(st, &tok);
+  TSDS_CK(launch_argminmax(nullptr, 1, S, nullptr, windows, reinterpret_cast<Piece*>(base + L.first),
+                           reinterpret_cast<Piece*>(base + L.last), reinterpret_cast<WorkCounters*>(base + L.work),
+                           y_dtype, nan, st));
+  timing_end(st, tok);
+  TSDS_CK(launch_emit(nullptr, 1, S, algo, st));
+  return TSDS_OK;
+}
+
+static tsds_status run_binned(Algo algo, const void* x, tsds_dtype x_dtype, const void* y,
+                              tsds_dtype y_dtype, int64_t n, int64_t n_out, tsds_nan_mode nan,
+                              int64_t* out, int64_t* out_count, void* stream) {
+  g_err[0] = 0;
+  tsds_status s = check_common(x, x_dtype, y, y_dtype, n, nan, out, out_count);
+  if (s != TSDS_OK) return s;
+  const int per_bin = algo == ALGO_MINMAX ? 2 : 4;
+  if (n_out < per_bin || n_out % per_bin != 0)
+    return fail(TSDS_EINVAL, "%s needs n_out to be a positive multiple of %d (got %lld)",
+                algo == ALGO_MINMAX ? "MinMax" : "M4", per_bin, (long long)n_out);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (n == 0) {
+    TSDS_CK(cudaMemsetAsync(out_count, 0, sizeof(int64_t), st));
+    return TSDS_OK;
+  }
+  if (n_out >= n) {
+    TSDS_CK(launch_iota(out, n, out_count, st));
+    return TSDS_OK;
+  }
+  return run_binned_series(x, x_dtype, y, y_dtype, n, n_out / per_bin, nan, algo, out, out_count, 0, st);
+}
+
+}  // namespace tsds
+
+using namespace tsds;
+
+extern "C" {
+
+tsds_status tsds_minmax(const void* x, tsds_dtype x_dtype, const void* y, tsds_dtype y_dtype,
+                        int64_t n, int64_t n_out, tsds_nan_mode nan, int64_t* out,
+                        int64_t* out_count, void* stream) {
+  return run_binned(ALGO_MINMAX, x, x_dtype, y, y_dtype, n, n_out, nan, out, out_count, stream);
+}
+
+tsds_status tsds_m4(const void* x, tsds_dtype x_dtype, const void* y, tsds_dtype y_dtype,
+                    int64_t n, int64_t n_out, tsds_nan_mode nan, int64_t* out,
+                    int64_t* out_count, void* stream) {
+  return run_binned(ALGO_M4, x, x_dtype, y, y_dtype, n, n_out, nan, out, out_count, stream);
+}
+
+tsds_status tsds_lttb(const void* x, tsds_dtype x_dtype, const void* y, tsds_dtype y_dtype,
+                      int64_t n, int64_t n_out, tsds_nan_mode nan, int64_t* out,
+                      int64_t* out_count, void* stream) {
+  g_err[0] = 0;
+  tsds_status s = check_common(x, x_dtype, y, y_dtype, n, nan, out, out_count);
+  if (s != TSDS_OK) return s;
+  if (n_out < 3) return fail(TSDS_EINVAL, "LTTB needs n_out >= 3 (got %lld)", (long long)n_out);
+  return run_lttb(x, x_dtype, y, y_dtype, n, n_out, nan, out, out_count, static_cast<cudaStream_t>(stream));
+}
+
+tsds_status tsds_minmaxlttb(const void* x, tsds_dtype x_dtype, const void* y, tsds_dtype y_dtype,
+                            int64_t n, int64_t n_out, int64_t minmax_ratio, tsds_nan_mode nan,
+                            int64_t* out, int64_t* out_count, void* stream) {
+  g_err[0] = 0;
+  tsds_status s = check_common(x, x_dtype, y, y_dtype, n, nan, out, out_count);
+  if (s != TSDS_OK) return s;
+  if (n_out < 3) return fail(TSDS_EINVAL, "MinMaxLTTB needs n_out >= 3 (got %lld)", (long long)n_out);
+  if (minmax_ratio < 1) return fail(TSDS_EINVAL, "minmax_ratio must be >= 1 (got %lld)", (long long)minmax_ratio);
+  if (minmax_ratio > (INT64_MAX / 4) / n_out) return fail(TSDS_EINVAL, "n_out * minmax_ratio overflows");
+  return run_minmaxlttb(x, x_dtype, y, y_dtype, n, n_out, minmax_ratio, nan, out, out_count,
+                        static_cast<cudaStream_t>(stream));
+}
+
+const char* tsds_last_error(void) { return g_err; }
+
+void tsds_shutdown(void) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  int cur = 0;
+  cudaGetDevice(&cur);
+  for (auto& kv : g_dev) {
+    if (kv.second.pool) {
+      cudaSetDevice(kv.first);
+      cudaMemPoolDestroy(kv.second.pool);
+    }
+  }
+  g_dev.clear();
+  cudaSetDevice(cur);
+}
+
+const char* tsds_version(void) { return "0.1.0"; }
+
+int64_t tsds_kernel_launches(void) { return g_launches.load(); }
+
+void tsds_timing_enable(int on) { g_timing.store(on ? 1 : 0); }
+
+tsds_status tsds_timing_read(double* total_ms, int64_t* launches) {
+  std::vector<TimedLaunch> done;
+  {
+    std::lock_guard<std::mutex> lk(g_tmu);
+    done.swap(g_timed);
+  }
+  double ms = 0.0;
+  tsds_status st = TSDS_OK;
+  for (auto& t : done) {
+    float f = 0.f;
+    if (cudaEventSynchronize(t.b) != cudaSuccess || cudaEventElapsedTime(&f, t.a, t.b) != cudaSuccess)
+      st = fail(TSDS_ECUDA, "tsds_timing_read: event query failed");
+    ms += f;
+  }
+  {
+    std::lock_guard<std::mutex> lk(g_tmu);
+    for (auto& t : done) { g_free_events.push_back(t.a); g_free_events.push_back(t.b); }
+  }
+  if (total_ms) *total_ms = ms;
+  if (launches) *launches = (int64_t)done.size();
+  return st;
+}
+
+}  // extern "C"

@@ -1,0 +1,144 @@
+// device.cuh -- device helpers shared by the kernels: ordered keys for the
+// (value, index) comparisons, candidate combines and warp searches.
+#pragma once
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+#include "internal.h"
+
+namespace tsds {
+
+constexpr uint64_t kKeyMax = ~0ull;
+constexpr int64_t kIdxNone = INT64_MAX;
+constexpr uint64_t kSign64 = 1ull << 63;
+
+// ---------------------------------------------------------------------------
+// Ordered 64-bit keys.  Every element maps to an unsigned key whose order is
+// the order the selections use (Section 2.1: smallest / largest value, the
+// earliest index on ties), so partial results of any dtype combine with one
+// unsigned comparison plus an index tie-break.
+//
+//   signed ints : sign-extend, flip the top bit (two's complement order).
+//   unsigned    : the value.
+//   floats      : the value widened exactly to binary64; non-negative values
+//                 get the top bit set, negative values are negated as
+//                 integers, which maps -0 and +0 to the same key and keeps
+//                 every finite value and both infinities strictly inside
+//                 (0, 2^64-1).  NaN takes an end key chosen by the NaN mode:
+//                 propagate puts it below everything for argmin and above
+//                 everything for argmax (the first NaN wins both); ignore does
+//                 the opposite (it never wins unless the bin is all NaN).
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ uint64_t f64_bits_key(uint64_t b) {
+  return (b & kSign64) ? (0ull - b) : (b | kSign64);
+}
+// Keys of +inf and -inf: raw keys beyond them are NaNs.
+constexpr uint64_t kKeyPosInf = 0xFFF0000000000000ull;
+constexpr uint64_t kKeyNegInf = 0x0010000000000000ull;
+
+__device__ __forceinline__ bool raw_key_is_nan(uint64_t k) { return k > kKeyPosInf || k < kKeyNegInf; }
+
+template <int NAN_MODE>
+__device__ __forceinline__ uint64_t nan_key_min() { return NAN_MODE == TSDS_NAN_PROPAGATE ? 0ull : kKeyMax; }
+template <int NAN_MODE>
+__device__ __forceinline__ uint64_t nan_key_max() { return NAN_MODE == TSDS_NAN_PROPAGATE ? kKeyMax : 0ull; }
+
+template <int NAN_MODE>
+__device__ __forceinline__ uint64_t fkey_min(double d) {
+  uint64_t k = f64_bits_key((uint64_t)__double_as_longlong(d));
+  return raw_key_is_nan(k) ? nan_key_min<NAN_MODE>() : k;
+}
+template <int NAN_MODE>
+__device__ __forceinline__ uint64_t fkey_max(double d) {
+  uint64_t k = f64_bits_key((uint64_t)__double_as_longlong(d));
+  return raw_key_is_nan(k) ? nan_key_max<NAN_MODE>() : k;
+}
+
+__device__ __forceinline__ uint64_t skey(int64_t v) { return (uint64_t)v ^ kSign64; }
+__device__ __forceinline__ uint64_t ukey(uint64_t v) { return v; }
+
+// ---------------------------------------------------------------------------
+// Candidates: (key, index) for the minimum and the maximum.  The identity
+// element is (max key, no index) for the minimum and (0, no index) for the
+// maximum, so an empty lane never wins.
+// ---------------------------------------------------------------------------
+struct Cand {
+  uint64_t kmin;
+  int64_t imin;
+  uint64_t kmax;
+  int64_t imax;
+};
+
+__device__ __forceinline__ void cand_init(Cand& c) {
+  c.kmin = kKeyMax; c.imin = kIdxNone; c.kmax = 0; c.imax = kIdxNone;
+}
+__device__ __forceinline__ void cand_merge_min(Cand& c, uint64_t k, int64_t i) {
+  if (k < c.kmin || (k == c.kmin && i < c.imin)) { c.kmin = k; c.imin = i; }
+}
+__device__ __forceinline__ void cand_merge_max(Cand& c, uint64_t k, int64_t i) {
+  if (k > c.kmax || (k == c.kmax && i < c.imax)) { c.kmax = k; c.imax = i; }
+}
+__device__ __forceinline__ void cand_merge(Cand& c, const Cand& o) {
+  cand_merge_min(c, o.kmin, o.imin);
+  cand_merge_max(c, o.kmax, o.imax);
+}
+__device__ __forceinline__ void cand_warp_reduce(Cand& c) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    Cand t;
+    t.kmin = __shfl_xor_sync(0xffffffffu, c.kmin, o);
+    t.imin = __shfl_xor_sync(0xffffffffu, c.imin, o);
+    t.kmax = __shfl_xor_sync(0xffffffffu, c.kmax, o);
+    t.imax = __shfl_xor_sync(0xffffffffu, c.imax, o);
+    cand_merge(c, t);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Warp-cooperative search: the first j in [lo, hi) with pred(j) true, for a
+// predicate that is false then true along j; hi when none.  Each round the
+// 32 lanes probe 32 evenly spaced positions, so a range of n shrinks to one
+// in about log32(n) dependent rounds.  All lanes return the same value.
+// ---------------------------------------------------------------------------
+template <class Pred>
+__device__ __forceinline__ int64_t warp_lower_bound(int64_t lo, int64_t hi, Pred pred) {
+  const int lane = threadIdx.x & 31;
+  while (lo < hi) {
+    int64_t len = hi - lo;
+    int64_t step = (len + 31) / 32;      // probes lo, lo+step, ... cover [lo, hi)
+    int64_t q = lo + (int64_t)lane * step;
+    bool valid = q < hi;
+    bool p = valid && pred(q);
+    unsigned m = __ballot_sync(0xffffffffu, p);
+    unsigned vm = __ballot_sync(0xffffffffu, valid);
+    if (m == 0) {
+      // everything probed is false: answer is after the last probe
+      int last = 31 - __clz(vm);
+      lo = lo + (int64_t)last * step + 1;
+    } else {
+      int f = __ffs(m) - 1;
+      int64_t qf = lo + (int64_t)f * step;
+      if (f == 0) return qf;             // pred(lo) holds
+      // answer in (q_{f-1}, q_f]
+      lo = lo + (int64_t)(f - 1) * step + 1;
+      hi = qf;
+      if (step == 1) return qf;
+      // pred(hi) is known true: search [lo, hi) and fall back to hi
+    }
+  }
+  return hi;
+}
+
+// Load helpers -------------------------------------------------------------
+template <class T>
+__device__ __forceinline__ T ldg_elem(const T* p) { return __ldg(p); }
+template <>
+__device__ __forceinline__ __half ldg_elem<__half>(const __half* p) {
+  unsigned short s = __ldg(reinterpret_cast<const unsigned short*>(p));
+  return __ushort_as_half(s);
+}
+
+__device__ __forceinline__ uint4 ldg_vec(const uint4* p) { return __ldg(p); }
+
+}  // namespace tsds

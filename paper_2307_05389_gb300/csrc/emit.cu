@@ -1,0 +1,96 @@
+// emit.cu -- turns per-bin selections into the output index list.
+//
+// MinMax emits {argmin, argmax} of each non-empty bin and M4 emits {first,
+// argmin, argmax, last} (Section 1); each bin's selections are written once
+// each, in increasing order, and bins follow each other, so the output is
+// strictly increasing.  Empty bins (possible with gaps in x) emit nothing,
+// which is why fewer than n_out indices can come back (Section 2.3 footnote).
+// One CTA per series: per-thread runs of bins, a block-wide exclusive scan of
+// their counts, then a second pass that writes.
+#include "device.cuh"
+#include "internal.h"
+
+namespace tsds {
+
+constexpr int kEmitThreads = 1024;
+
+template <int ALGO>
+__device__ __forceinline__ int bin_select(const SeriesDev& S, int64_t b, int64_t (&v)[4]) {
+  const int64_t lo = __ldg(S.edges + b), hi = __ldg(S.edges + b + 1);
+  if (hi <= lo) return 0;
+  const int64_t mn = S.res[2 * b], mx = S.res[2 * b + 1];
+  int k = 0;
+  if (ALGO == ALGO_MINMAX) {
+    v[0] = min(mn, mx); v[1] = max(mn, mx);
+    k = v[0] == v[1] ? 1 : 2;
+  } else {
+    // sort {lo, mn, mx, hi-1}: lo is the smallest and hi-1 the largest
+    int64_t a = min(mn, mx), c = max(mn, mx);
+    int64_t t[4] = {lo, a, c, hi - 1};
+    k = 0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      if (k == 0 || t[i] != v[k - 1]) v[k++] = t[i];
+  }
+  return k;
+}
+
+template <int ALGO>
+__global__ void __launch_bounds__(kEmitThreads) k_emit(const SeriesDev* __restrict__ sd, SeriesDev single) {
+  const SeriesDev S = sd ? sd[blockIdx.x] : single;
+  const int64_t nb = S.nb;
+  if (nb <= 0) return;
+  __shared__ int64_t warp_tot[kEmitThreads / 32];
+  __shared__ int64_t total_sh;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t per = (nb + blockDim.x - 1) / blockDim.x;
+  const int64_t b0 = min((int64_t)tid * per, nb), b1 = min(b0 + per, nb);
+  int64_t v[4];
+  int64_t local = 0;
+  for (int64_t b = b0; b < b1; ++b) local += bin_select<ALGO>(S, b, v);
+  // block exclusive scan of `local`
+  int64_t incl = local;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int64_t t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  if (lane == 31) warp_tot[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    const int nw = blockDim.x >> 5;
+    int64_t wv = lane < nw ? warp_tot[lane] : 0;
+    int64_t wi = wv;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int64_t t = __shfl_up_sync(0xffffffffu, wi, o);
+      if (lane >= o) wi += t;
+    }
+    if (lane < nw) warp_tot[lane] = wi - wv;   // exclusive prefix of warp totals
+    if (lane == nw - 1) total_sh = wi;
+  }
+  __syncthreads();
+  int64_t off = warp_tot[warp] + incl - local;
+  for (int64_t b = b0; b < b1; ++b) {
+    const int k = bin_select<ALGO>(S, b, v);
+    for (int i = 0; i < k; ++i) S.out[off + i] = v[i] + S.idx_bias;
+    off += k;
+  }
+  if (tid == 0 && S.out_count) *S.out_count = total_sh;
+}
+
+cudaError_t launch_emit(const SeriesDev* s_dev, int count, const SeriesDev& single, Algo algo,
+                        cudaStream_t st) {
+  const SeriesDev* arr = (count > 1 || s_dev) ? s_dev : nullptr;
+  int64_t threads = kEmitThreads;
+  if (!arr && single.nb < 1024) threads = ((single.nb + 31) / 32) * 32;
+  if (threads < 32) threads = 32;
+  note_launch();
+  if (algo == ALGO_MINMAX)
+    k_emit<ALGO_MINMAX><<<count, (unsigned)threads, 0, st>>>(arr, single);
+  else
+    k_emit<ALGO_M4><<<count, (unsigned)threads, 0, st>>>(arr, single);
+  return cudaGetLastError();
+}
+
+}  // namespace tsds

@@ -1,0 +1,104 @@
+// internal.h -- structures shared by the host runtime and the kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/tsds.h"
+
+namespace tsds {
+
+// Bytes of y one warp claims at a time in the streaming argmin/argmax pass.
+constexpr int64_t kWindowBytes = 64 * 1024;
+constexpr int kStreamThreads = 256;   // 8 warps per CTA
+
+enum Algo : int { ALGO_MINMAX = 0, ALGO_M4 = 1 };
+
+// One series as the binned kernels see it.  For a single call there is one;
+// the batched launch passes an array.
+struct SeriesDev {
+  const void* y;
+  const void* x;
+  int64_t n;          // points
+  int64_t nb;         // bins (0: the series returns every index)
+  int64_t* edges;     // nb+1 bin starts, edges[nb] = n
+  int64_t* res;       // 2*nb: per-bin argmin, argmax (global indices of this series)
+  uint32_t* cnt;      // nb: pieces of the bin finished so far (zero between calls)
+  int64_t win_base;   // first window of this series in the launch's window numbering
+  int64_t* out;       // output indices
+  int64_t* out_count; // device count
+  int64_t idx_bias;   // added to every index written (1 for the MinMaxLTTB interior)
+};
+
+// Partial argmin/argmax of one bin piece: ordered 64-bit keys plus indices.
+struct Piece {
+  uint64_t kmin;
+  int64_t imin;
+  uint64_t kmax;
+  int64_t imax;
+};
+
+struct WorkCounters {
+  unsigned long long next_window;
+  unsigned long long pad[7];
+};
+
+inline int64_t dtype_size(tsds_dtype d) {
+  switch (d) {
+    case TSDS_I8: case TSDS_U8: return 1;
+    case TSDS_I16: case TSDS_U16: case TSDS_F16: return 2;
+    case TSDS_I32: case TSDS_U32: case TSDS_F32: return 4;
+    default: return 8;
+  }
+}
+inline bool dtype_valid(int d) { return d >= TSDS_I8 && d <= TSDS_F64; }
+inline bool dtype_is_float(tsds_dtype d) { return d == TSDS_F16 || d == TSDS_F32 || d == TSDS_F64; }
+
+inline int64_t window_elems(tsds_dtype y_dtype) { return kWindowBytes / dtype_size(y_dtype); }
+
+// ---- launchers (each returns the launch's cudaError_t)
+
+// Bin starts for every series in `s` (count series, array in device memory
+// or, for count == 1, also usable by value).
+cudaError_t launch_edges(const SeriesDev* s_dev, int count, const SeriesDev* s_host_single,
+                         bool has_x, tsds_dtype x_dtype, int64_t max_nb, cudaStream_t st);
+
+// Window -> series map for a batched launch.
+cudaError_t launch_window_map(const SeriesDev* s_dev, int count, int32_t* win_series,
+                              tsds_dtype y_dtype, cudaStream_t st);
+
+// The streaming per-bin argmin/argmax pass.
+cudaError_t launch_argminmax(const SeriesDev* s_dev, int count, const SeriesDev& single,
+                             const int32_t* win_series, int64_t total_windows,
+                             Piece* first_piece, Piece* last_piece, WorkCounters* work,
+                             tsds_dtype y_dtype, tsds_nan_mode nan, cudaStream_t st);
+
+// Per-bin selections -> compacted, sorted output and count.
+cudaError_t launch_emit(const SeriesDev* s_dev, int count, const SeriesDev& single, Algo algo,
+                        cudaStream_t st);
+
+// out[i] = i + offset for i < n, *count = n.
+cudaError_t launch_iota(int64_t* out, int64_t n, int64_t* count, cudaStream_t st);
+
+int device_sm_count();
+
+// Counts every kernel this library launches (reported by tsds_kernel_launches).
+void note_launch(int kernels = 1);
+
+// Kernel timing (tsds_timing_enable): when on, the streaming argmin/argmax
+// launches are bracketed by CUDA events on their stream.
+bool timing_on();
+void timing_begin(cudaStream_t st, void** token);
+void timing_end(cudaStream_t st, void* token);
+
+// Scratch memory taken from the library's per-device pool in stream order and
+// handed back in stream order when the owning call has queued its launches.
+struct Scratch {
+  void* p = nullptr;
+  cudaStream_t st = nullptr;
+  ~Scratch() {
+    if (p) cudaFreeAsync(p, st);
+  }
+};
+cudaError_t scratch_alloc(Scratch& s, size_t bytes, cudaStream_t st);
+
+}  // namespace tsds

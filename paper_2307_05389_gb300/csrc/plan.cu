@@ -1,0 +1,147 @@
+// plan.cu -- bin planning: bin start indices for MinMax / M4 (and the
+// MinMaxLTTB preselection), the batched window map and the n_out >= n copy.
+//
+// The paper's tsdownsample generates bin indices "using a search sorted
+// approach" (Section 2.2).  Bin i of nb starts at
+//   no x        : ceil(i*(n-1)/nb)                      (index arithmetic)
+//   integer x   : first j with (x_j-x_0)*nb >= i*(x_{n-1}-x_0)   (exact, 128-bit)
+//   floating x  : first j with x_j >= x_0 + ((x_{n-1}-x_0)*i)/nb (binary64,
+//                 each operation rounded to nearest, no fused multiply-add)
+// and the last bin ends at n.  For x = 0..n-1 the three rules agree, which is
+// the paper's "equally sampled x gives the same output as no x" (Section 2.2).
+#include "device.cuh"
+#include "internal.h"
+
+namespace tsds {
+
+typedef unsigned __int128 u128;
+
+__global__ void k_edges_index(const SeriesDev* sd, SeriesDev single, int count) {
+  const SeriesDev& S = count == 1 && sd == nullptr ? single : sd[blockIdx.y];
+  const int64_t nb = S.nb;
+  if (nb <= 0) return;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= nb; i += (int64_t)gridDim.x * blockDim.x) {
+    int64_t v;
+    if (i == nb) {
+      v = S.n;
+    } else {
+      u128 num = (u128)i * (u128)(S.n - 1);
+      v = (int64_t)((num + (u128)nb - 1) / (u128)nb);
+    }
+    S.edges[i] = v;
+  }
+}
+
+template <class X>
+struct XInt {
+  static constexpr bool is_signed = (X)(-1) < (X)0;
+  __device__ static u128 off(const X* x, int64_t j, X x0) {
+    X v = __ldg(x + j);
+    if (is_signed) return (u128)((__int128)(int64_t)v - (__int128)(int64_t)x0);
+    return (u128)((uint64_t)v - (uint64_t)x0);
+  }
+};
+
+template <class X>
+__device__ __forceinline__ double x_as_f64(const X* x, int64_t j) { return (double)__ldg(x + j); }
+template <>
+__device__ __forceinline__ double x_as_f64<__half>(const __half* x, int64_t j) {
+  return (double)__half2float(ldg_elem<__half>(x + j));
+}
+
+template <class X, bool FLOATX>
+__global__ void k_edges_x(const SeriesDev* sd, SeriesDev single, int count) {
+  const SeriesDev& S = count == 1 && sd == nullptr ? single : sd[blockIdx.y];
+  const int64_t nb = S.nb;
+  if (nb <= 0) return;
+  const X* x = static_cast<const X*>(S.x);
+  const int64_t n = S.n;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t warps_total = (int64_t)gridDim.x * (blockDim.x >> 5);
+  if (blockIdx.x == 0 && threadIdx.x == 0) { S.edges[0] = 0; S.edges[nb] = n; }
+  for (int64_t i = 1 + (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; i < nb; i += warps_total) {
+    int64_t e;
+    if constexpr (FLOATX) {
+      double x0 = x_as_f64<X>(x, 0);
+      double xl = x_as_f64<X>(x, n - 1);
+      double span = __dsub_rn(xl, x0);
+      double edge = __dadd_rn(x0, __ddiv_rn(__dmul_rn(span, (double)i), (double)nb));
+      e = warp_lower_bound(0, n, [&](int64_t j) { return x_as_f64<X>(x, j) >= edge; });
+    } else {
+      X x0 = __ldg(x);
+      u128 span = XInt<X>::off(x, n - 1, x0);
+      u128 rhs = (u128)i * span;
+      e = warp_lower_bound(0, n, [&](int64_t j) { return XInt<X>::off(x, j, x0) * (u128)nb >= rhs; });
+    }
+    if (lane == 0) S.edges[i] = e;
+  }
+}
+
+cudaError_t launch_edges(const SeriesDev* s_dev, int count, const SeriesDev* s_host_single,
+                         bool has_x, tsds_dtype x_dtype, int64_t max_nb, cudaStream_t st) {
+  SeriesDev single = s_host_single ? *s_host_single : SeriesDev{};
+  const SeriesDev* arr = s_host_single ? nullptr : s_dev;
+  if (max_nb <= 0) return cudaSuccess;
+  if (!has_x) {
+    int threads = 256;
+    int64_t blocks = (max_nb + 1 + threads - 1) / threads;
+    if (blocks > 65535) blocks = 65535;
+    dim3 grid((unsigned)blocks, (unsigned)count);
+    note_launch();
+    k_edges_index<<<grid, threads, 0, st>>>(arr, single, count);
+    return cudaGetLastError();
+  }
+  int threads = 256;   // 8 warps, one edge each
+  int64_t blocks = (max_nb + 7) / 8;
+  if (blocks < 1) blocks = 1;
+  if (blocks > 65535) blocks = 65535;
+  dim3 grid((unsigned)blocks, (unsigned)count);
+  note_launch();
+  switch (x_dtype) {
+    case TSDS_I8: k_edges_x<int8_t, false><<<grid, threads, 0, st>>>(arr, single, count); break;
+    case TSDS_I16: k_edges_x<int16_t, false><<<grid, threads, 0, st>>>(arr, single, count); break;
+    case TSDS_I32: k_edges_x<int32_t, false><<<grid, threads, 0, st>>>(arr, single, count); break;
+    case TSDS_I64: k_edges_x<int64_t, false><<<grid, threads, 0, st>>>(arr, single, count); break;
+    case TSDS_U8: k_edges_x<uint8_t, false><<<grid, threads, 0, st>>>(arr, single, count); break;
+    case TSDS_U16: k_edges_x<uint16_t, false><<<grid, threads, 0, st>>>(arr, single, count); break;
+    case TSDS_U32: k_edges_x<uint32_t, false><<<grid, threads, 0, st>>>(arr, single, count); break;
+    case TSDS_U64: k_edges_x<uint64_t, false><<<grid, threads, 0, st>>>(arr, single, count); break;
+    case TSDS_F16: k_edges_x<__half, true><<<grid, threads, 0, st>>>(arr, single, count); break;
+    case TSDS_F32: k_edges_x<float, true><<<grid, threads, 0, st>>>(arr, single, count); break;
+    case TSDS_F64: k_edges_x<double, true><<<grid, threads, 0, st>>>(arr, single, count); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+__global__ void k_window_map(const SeriesDev* sd, int32_t* win_series, int64_t welems) {
+  const SeriesDev& S = sd[blockIdx.x];
+  if (S.nb <= 0) return;
+  int64_t k = (S.n + welems - 1) / welems;
+  for (int64_t w = threadIdx.x; w < k; w += blockDim.x) win_series[S.win_base + w] = (int32_t)blockIdx.x;
+}
+
+cudaError_t launch_window_map(const SeriesDev* s_dev, int count, int32_t* win_series,
+                              tsds_dtype y_dtype, cudaStream_t st) {
+  note_launch();
+  k_window_map<<<count, 256, 0, st>>>(s_dev, win_series, window_elems(y_dtype));
+  return cudaGetLastError();
+}
+
+__global__ void k_iota(int64_t* out, int64_t n, int64_t* count) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = i;
+  if (blockIdx.x == 0 && threadIdx.x == 0 && count) *count = n;
+}
+
+cudaError_t launch_iota(int64_t* out, int64_t n, int64_t* count, cudaStream_t st) {
+  int64_t blocks = (n + 255) / 256;
+  if (blocks < 1) blocks = 1;
+  int cap = device_sm_count() * 8;
+  if (blocks > cap) blocks = cap;
+  note_launch();
+  k_iota<<<(unsigned)blocks, 256, 0, st>>>(out, n, count);
+  return cudaGetLastError();
+}
+
+}  // namespace tsds

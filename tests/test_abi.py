@@ -1,0 +1,83 @@
+"""The C ABI library loads and exports every entry point include/tsds.h
+declares; host-side argument checks answer without a GPU (CPU only)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_2307_05389_gb300 as pkg
+from paper_2307_05389_gb300 import binding
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADERS = [os.path.join(ROOT, "include", f) for f in os.listdir(os.path.join(ROOT, "include")) if f.endswith(".h")]
+
+
+def declared_functions():
+    names = set()
+    for h in HEADERS:
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        for m in re.finditer(r"\b(tsds_[a-z0-9_]+)\s*\(", text):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    return pkg.load()
+
+
+def test_header_declares_the_survey_entry_points():
+    names = declared_functions()
+    for n in ("tsds_minmax", "tsds_m4", "tsds_lttb", "tsds_minmaxlttb", "tsds_last_error", "tsds_shutdown"):
+        assert n in names
+
+
+@pytest.mark.parametrize("name", declared_functions())
+def test_symbol_exported(lib, name):
+    assert hasattr(lib, name), f"{name} declared in include/ but not exported"
+
+
+def test_binding_names_match_abi():
+    for n in ("tsds_minmax", "tsds_m4", "tsds_lttb", "tsds_minmaxlttb", "tsds_shutdown", "tsds_version"):
+        assert callable(getattr(pkg, n))
+
+
+def test_version(lib):
+    assert re.match(r"^\d+\.\d+\.\d+$", pkg.tsds_version())
+
+
+def _call(fn, n, n_out, y=1 << 20, out=1 << 21, cnt=1 << 22, x=None, x_dtype=0, y_dtype=9, nan=0):
+    return fn(x, x_dtype, y, y_dtype, n, n_out, nan, out, cnt, None)
+
+
+@pytest.mark.parametrize("fn,n_out", [(binding.tsds_minmax, 3), (binding.tsds_minmax, 0), (binding.tsds_m4, 6),
+                                      (binding.tsds_m4, 2), (binding.tsds_lttb, 2)])
+def test_invalid_n_out_is_rejected_on_the_host(lib, fn, n_out):
+    assert _call(fn, 100, n_out) == 1
+    assert "n_out" in pkg.last_error()
+
+
+def test_other_invalid_arguments(lib):
+    assert _call(binding.tsds_minmax, -1, 10) == 1                   # n < 0
+    assert _call(binding.tsds_minmax, 10, 10, y=None) == 1           # y NULL
+    assert _call(binding.tsds_minmax, 10, 10, y_dtype=11) == 1       # unknown dtype
+    assert _call(binding.tsds_minmax, 10, 10, x=1 << 20, x_dtype=-1) == 1
+    assert _call(binding.tsds_minmax, 10, 10, nan=2) == 1
+    assert _call(binding.tsds_minmax, 10, 10, cnt=None) == 1
+    assert _call(binding.tsds_minmax, 10, 10, y=(1 << 20) + 2) == 1  # misaligned float32
+    assert binding.tsds_minmaxlttb(None, 0, 1 << 20, 9, 100, 10, 0, 0, 1 << 21, 1 << 22, None) == 1
+    assert "minmax_ratio" in pkg.last_error()
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    with pytest.raises(RuntimeError):
+        binding_path = str(tmp_path / "nope.so")
+        saved = binding._lib
+        binding._lib = None
+        try:
+            binding.load(binding_path)
+        finally:
+            binding._lib = saved

@@ -1,0 +1,192 @@
+"""CUDA path vs the CPU oracle, index for index, on seeded inputs.
+
+Sizes span many 64 KB windows (so bins are cut across windows and rejoined)
+and end in ragged tails; cases cover all eleven dtypes, both NaN modes,
+no x / integer x / floating x, unaligned starts, empty bins and the
+degenerate shapes (n = 0, 1, n_out >= n, one bin, one point per bin).
+The bar is bit-exact equality of the int64 index lists."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2307_05389_gb300 import inputs
+
+from gpu_util import call, run
+
+pytestmark = pytest.mark.gpu
+
+INT_DTYPES = ["int8", "int16", "int32", "int64", "uint8", "uint16", "uint32", "uint64"]
+FLOAT_DTYPES = ["float16", "float32", "float64"]
+ALL_DTYPES = INT_DTYPES + FLOAT_DTYPES
+
+
+def check(algo, x, y, n_out, nan="propagate", ratio=4, **kw):
+    got = run(algo, x, y, n_out, nan, ratio, **kw)
+    exp = oracle.downsample(algo, x, y, n_out, nan=nan, minmax_ratio=ratio)
+    if not np.array_equal(got, exp):
+        d = np.flatnonzero(got[:min(len(got), len(exp))] != exp[:min(len(got), len(exp))])
+        first = int(d[0]) if d.size else min(len(got), len(exp))
+        raise AssertionError(f"{algo} n={len(y)} n_out={n_out} nan={nan}: {len(got)} vs {len(exp)} indices, "
+                             f"first difference at {first}: got {got[first:first + 4]} exp {exp[first:first + 4]}")
+
+
+def series(dtype, n, seed, kind="walk"):
+    if kind == "walk":
+        if np.dtype(dtype).kind == "f":
+            return inputs.random_walk(n, dtype, seed)
+        return inputs.quarter_range(n, dtype, seed)
+    if kind == "ties":
+        return inputs.ties_and_specials(n, dtype, seed)
+    raise ValueError(kind)
+
+
+@pytest.mark.parametrize("dtype", ALL_DTYPES)
+@pytest.mark.parametrize("algo", ["minmax", "m4"])
+def test_binned_dtypes_no_x(dtype, algo):
+    n = 1_000_003 if np.dtype(dtype).itemsize == 1 else 300_007
+    for kind in ("walk", "ties"):
+        y = series(dtype, n, seed=11, kind=kind)
+        for n_out in (4, 200, 2000, 40_000):
+            for nan in (("propagate", "ignore") if np.dtype(dtype).kind == "f" else ("propagate",)):
+                check(algo, None, y, n_out, nan)
+
+
+@pytest.mark.parametrize("x_dtype", ["int64", "float64", "int32", "uint64", "float32", "int16", "float16", "uint8"])
+@pytest.mark.parametrize("algo", ["minmax", "m4"])
+def test_binned_with_x(x_dtype, algo):
+    n = 250_001
+    y = inputs.random_walk(n, "float32", seed=3)
+    if x_dtype in ("int16", "float16", "uint8"):
+        # narrow x: sorted values with long runs of equal x (many empty bins)
+        rng = np.random.default_rng(5)
+        hi = 250 if x_dtype == "uint8" else 2000
+        x = np.sort(rng.integers(0, hi, n)).astype(x_dtype)
+    elif np.dtype(x_dtype).kind == "f":
+        x = inputs.exponential_x(n, seed=4).astype(x_dtype)
+        x = np.maximum.accumulate(x)
+    else:
+        x = inputs.geometric_x(n, seed=4).astype(x_dtype)
+        if x_dtype == "uint64":
+            x = x + np.uint64(2 ** 63)
+    for n_out in (4, 400, 4000, 100_000):
+        check(algo, x, y, n_out)
+
+
+def test_equal_x_equals_no_x_on_gpu():
+    y = inputs.random_walk(400_000, "float32", seed=8)
+    for algo in ("minmax", "m4"):
+        ref = run(algo, None, y, 2000)
+        for xd in ("int64", "float64", "uint32"):
+            np.testing.assert_array_equal(run(algo, np.arange(len(y)).astype(xd), y, 2000), ref)
+
+
+@pytest.mark.parametrize("dtype", ["int8", "int16", "float16", "float32", "float64", "uint64"])
+@pytest.mark.parametrize("offset", [1, 3, 7])
+def test_unaligned_start(dtype, offset):
+    y = series(dtype, 123_457, seed=2)
+    for algo in ("minmax", "m4"):
+        check(algo, None, y, 1000, offset=offset)
+
+
+@pytest.mark.parametrize("dtype", FLOAT_DTYPES)
+@pytest.mark.parametrize("nan", ["propagate", "ignore"])
+def test_nan_rich(dtype, nan):
+    rng = np.random.default_rng(9)
+    y = inputs.random_walk(200_000, dtype, seed=9)
+    y[rng.choice(len(y), 3000, replace=False)] = np.nan
+    y[50_000:120_000] = np.nan                     # bins that are all NaN
+    y[rng.choice(len(y), 500, replace=False)] = np.inf
+    y[rng.choice(len(y), 500, replace=False)] = -np.inf
+    for algo in ("minmax", "m4"):
+        for n_out in (8, 100, 3000):
+            check(algo, None, y, n_out, nan)
+
+
+@pytest.mark.parametrize("algo", ["minmax", "m4", "lttb", "minmaxlttb"])
+def test_degenerate_sizes(algo):
+    for n in (0, 1, 2, 3, 4, 5, 7, 8, 9, 17, 33, 100):
+        y = inputs.random_walk(n, "float32", seed=n) if n else np.zeros(0, np.float32)
+        for n_out in (4, 8, 12, 16, 36, 100, 200):
+            check(algo, None, y, n_out)
+
+
+def test_single_bin_and_one_point_bins():
+    y = inputs.random_walk(3_000_001, "float32", seed=1)
+    check("minmax", None, y, 2)          # one bin over 3M points (many windows)
+    check("m4", None, y, 4)
+    y = inputs.random_walk(20_001, "float64", seed=2)
+    check("minmax", None, y, 20_000)     # bins of one or two points
+    check("m4", None, y, 20_000)
+
+
+def test_constant_and_monotone():
+    for dtype in ("int32", "float32", "uint8"):
+        y = np.full(300_000, 7, dtype=dtype)
+        check("minmax", None, y, 100)
+        check("m4", None, y, 100)
+    y = np.arange(300_000, dtype=np.float32)
+    check("minmax", None, y, 100)
+    check("minmax", None, y[::-1].copy(), 100)
+
+
+def test_x_all_equal_and_gaps():
+    n = 100_000
+    y = inputs.random_walk(n, "float32", seed=5)
+    check("minmax", np.zeros(n, np.int64), y, 100)       # one non-empty bin
+    x = np.concatenate([np.arange(n // 2), np.arange(n // 2) + 10 ** 9]).astype(np.int64)
+    check("m4", x, y, 400)                               # a huge gap: most bins empty
+
+
+@pytest.mark.parametrize("dtype", ["float32", "float64", "int16", "uint8", "int64", "float16"])
+@pytest.mark.parametrize("nan", ["propagate", "ignore"])
+def test_lttb(dtype, nan):
+    n = 60_001
+    y = series(dtype, n, seed=21)
+    if np.dtype(dtype).kind == "f":
+        y[::997] = np.nan
+    for n_out in (3, 4, 100, 1000, 30_000):
+        check("lttb", None, y, n_out, nan)
+
+
+@pytest.mark.parametrize("x_dtype", ["int64", "float64", "float32"])
+def test_lttb_with_x(x_dtype):
+    n = 40_000
+    y = inputs.random_walk(n, "float32", seed=22)
+    x = inputs.exponential_x(n, seed=23).astype(x_dtype) if x_dtype != "int64" else inputs.geometric_x(n, seed=23)
+    for n_out in (3, 500, 5000):
+        check("lttb", x, y, n_out)
+
+
+@pytest.mark.parametrize("ratio", [1, 2, 4, 30])
+@pytest.mark.parametrize("nan", ["propagate", "ignore"])
+def test_minmaxlttb(ratio, nan):
+    y = inputs.quantised_nan(156_250, seed=4)
+    for n_out in (3, 100, 4000):
+        check("minmaxlttb", None, y, n_out, nan, ratio)
+    x = inputs.geometric_x(len(y), seed=6)
+    check("minmaxlttb", x, y, 1000, nan, ratio)
+
+
+def test_config1_shape_all_algorithms():
+    y = inputs.random_walk(1_000_000, "float32", seed=0)
+    for algo in ("minmax", "m4", "lttb", "minmaxlttb"):
+        check(algo, None, y, 1000)
+
+
+def test_repeatable_and_stream_ordered():
+    import torch
+    y = inputs.random_walk(500_000, "float32", seed=12)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        a = run("m4", None, y, 4000, stream=s)
+        b = run("m4", None, y, 4000, stream=s)
+    np.testing.assert_array_equal(a, b)
+    np.testing.assert_array_equal(a, oracle.m4(None, y, 4000))
+
+
+def test_invalid_arguments_on_gpu():
+    y = inputs.random_walk(1000, "float32", seed=0)
+    assert call("minmax", None, y, 5)[0] == 1
+    assert call("m4", None, y, 6)[0] == 1
+    assert call("lttb", None, y, 2)[0] == 1
+    assert call("minmaxlttb", None, y, 10, ratio=0)[0] == 1
