@@ -257,7 +257,11 @@ struct Pol64 {
     gmax = hi;
   }
   __device__ static uint64_t bits(T e) {
-    uint64_t b; memcpy(&b, &e, 8); return b;
+    if constexpr (KIND == 2) {
+      return f64_bits(e);   // opaque move: keeps the key arithmetic integer
+    } else {
+      return (uint64_t)e;
+    }
   }
   __device__ static bool better_min(Acc g, Acc r) { return g < r; }
   __device__ static bool better_max(Acc g, Acc r) { return g > r; }

@@ -44,15 +44,26 @@ __device__ __forceinline__ uint64_t nan_key_min() { return NAN_MODE == TSDS_NAN_
 template <int NAN_MODE>
 __device__ __forceinline__ uint64_t nan_key_max() { return NAN_MODE == TSDS_NAN_PROPAGATE ? kKeyMax : 0ull; }
 
+// The bits of a binary64 value as an integer.  The move goes through inline
+// PTX so that the integer operations applied to the bits afterwards stay
+// integer operations: when the compiler saw the sign-bit OR of a
+// reinterpreted double it could carry it out as a floating-point sign
+// operation, which leaves a NaN untouched and broke the NaN keys.
+__device__ __forceinline__ uint64_t f64_bits(double d) {
+  uint64_t b;
+  asm("mov.b64 %0, %1;" : "=l"(b) : "d"(d));
+  return b;
+}
+
 template <int NAN_MODE>
 __device__ __forceinline__ uint64_t fkey_min(double d) {
-  uint64_t k = f64_bits_key((uint64_t)__double_as_longlong(d));
-  return raw_key_is_nan(k) ? nan_key_min<NAN_MODE>() : k;
+  if (isnan(d)) return nan_key_min<NAN_MODE>();
+  return f64_bits_key(f64_bits(d));
 }
 template <int NAN_MODE>
 __device__ __forceinline__ uint64_t fkey_max(double d) {
-  uint64_t k = f64_bits_key((uint64_t)__double_as_longlong(d));
-  return raw_key_is_nan(k) ? nan_key_max<NAN_MODE>() : k;
+  if (isnan(d)) return nan_key_max<NAN_MODE>();
+  return f64_bits_key(f64_bits(d));
 }
 
 __device__ __forceinline__ uint64_t skey(int64_t v) { return (uint64_t)v ^ kSign64; }

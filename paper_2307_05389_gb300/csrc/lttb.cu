@@ -87,7 +87,7 @@ __global__ void k_lttb_means(const double* __restrict__ px, const double* __rest
 template <int NM>
 __device__ __forceinline__ uint64_t area_key(double ar) {
   if (isnan(ar)) return NM == TSDS_NAN_PROPAGATE ? kKeyMax : 0ull;
-  return f64_bits_key((uint64_t)__double_as_longlong(ar));
+  return f64_bits_key(f64_bits(ar));
 }
 
 template <int NM>
