@@ -81,8 +81,10 @@ def kernel_traffic():
     try:
         with open(os.path.join(ROOT, "profiles", "argminmax_traffic.json")) as f:
             rec = json.load(f)
-        src = open(os.path.join(ROOT, "paper_2307_05389_gb300", "csrc", "argminmax.cu"), "rb").read()
-        if hashlib.sha256(src).hexdigest() != rec.get("source_sha256"):
+        h = hashlib.sha256()
+        for s in rec["sources"]:
+            h.update(open(os.path.join(ROOT, s), "rb").read())
+        if h.hexdigest() != rec.get("sources_sha256"):
             return None
         return rec.get("dram_bytes_per_launch_full_size")
     except Exception:
