@@ -108,6 +108,28 @@ tsds_status tsds_minmaxlttb(const void* x, tsds_dtype x_dtype, const void* y,
                             int64_t minmax_ratio, tsds_nan_mode nan, int64_t* out,
                             int64_t* out_count, void* stream);
 
+/* MinMax without allocating (the paper has no counterpart: it exists for
+ * callers of this library that cannot allocate device memory during a call,
+ * e.g. code whose device memory is wholly owned by another allocator, or a
+ * latency-bound redraw loop where cudaMalloc/cudaFree may synchronise the
+ * device).  Same arguments, semantics and results as tsds_minmax, but the
+ * scratch memory is a fixed 8 MiB array compiled into the library (held by
+ * every device that loads the library until the process exits) and the call
+ * makes no allocation of any kind.
+ *  - Size limit: the scratch needs about (n_out/2)*28 + 64*ceil(n*sizeof(y)/65536)
+ *    bytes; a call that needs more than 8 MiB returns TSDS_EINVAL with the
+ *    sizes in tsds_last_error() before touching the device (at n_out = 2000
+ *    about 8 GB of y fit).
+ *  - The first call on a device, with that device current, looks up the
+ *    array's device address (cudaGetSymbolAddress); make that first call
+ *    before any stream capture.
+ *  - Every call shares the one array and clears the parts that must start at
+ *    zero; calls whose work overlaps on the GPU (other streams, other
+ *    threads) race on it and give wrong results.  Serialise them. */
+tsds_status tsds_minmax_noalloc(const void* x, tsds_dtype x_dtype, const void* y,
+                                tsds_dtype y_dtype, int64_t n, int64_t n_out, tsds_nan_mode nan,
+                                int64_t* out, int64_t* out_count, void* stream);
+
 /* Message for the calling thread's last failed call ("" if none). */
 const char* tsds_last_error(void);
 

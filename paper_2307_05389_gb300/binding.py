@@ -55,6 +55,8 @@ def load(path: str = LIB_PATH):
     lib.tsds_shutdown.restype = None
     lib.tsds_version.argtypes = []
     lib.tsds_version.restype = ctypes.c_char_p
+    lib.tsds_minmax_noalloc.argtypes = [p, c_int, p, c_int, i64, i64, c_int, p, p, p]
+    lib.tsds_minmax_noalloc.restype = c_int
     lib.tsds_kernel_launches.argtypes = []
     lib.tsds_kernel_launches.restype = i64
     lib.tsds_timing_enable.argtypes = [c_int]
@@ -103,6 +105,13 @@ def tsds_lttb(x, x_dtype, y, y_dtype, n, n_out, nan, out, out_count, stream):
 
 def tsds_minmaxlttb(x, x_dtype, y, y_dtype, n, n_out, minmax_ratio, nan, out, out_count, stream):
     return load().tsds_minmaxlttb(x, x_dtype, y, y_dtype, n, n_out, minmax_ratio, nan, out, out_count, stream)
+
+
+def tsds_minmax_noalloc(x, x_dtype, y, y_dtype, n, n_out, nan, out, out_count, stream):
+    """MinMax for callers that cannot allocate device memory during a call:
+    scratch comes from a fixed 8 MiB array inside the library (see tsds.h for
+    the size limit and the rule that overlapping calls must be serialised)."""
+    return load().tsds_minmax_noalloc(x, x_dtype, y, y_dtype, n, n_out, nan, out, out_count, stream)
 
 
 def tsds_shutdown():

@@ -509,4 +509,46 @@ cudaError_t launch_argminmax(const SeriesDev* s_dev, int count, const SeriesDev&
 #undef TSDS_LAUNCH
 }
 
+// Single-series launch with the SM count given by the caller instead of the
+// library's per-device state, for the entry point that must not create the
+// library's memory pool (tsds_minmax_noalloc).
+template <class P, int NM>
+static cudaError_t launch_pol_sm(const SeriesDev& single, int64_t total_windows, Piece* fp, Piece* lp,
+                                 WorkCounters* work, int sm_count, cudaStream_t st) {
+  auto kern = k_argminmax<P, NM, false>;
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kStreamThreads, 0) != cudaSuccess || occ < 1)
+    occ = 1;
+  int64_t blocks = (total_windows + kStreamThreads / 32 - 1) / (kStreamThreads / 32);
+  const int64_t cap = (int64_t)sm_count * occ;
+  if (blocks > cap) blocks = cap;
+  if (blocks < 1) blocks = 1;
+  note_launch();
+  kern<<<(unsigned)blocks, kStreamThreads, 0, st>>>(nullptr, single, nullptr, total_windows, fp, lp, work);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_argminmax_sm(const SeriesDev& single, int64_t total_windows, Piece* first_piece,
+                                Piece* last_piece, WorkCounters* work, tsds_dtype y_dtype, tsds_nan_mode nan,
+                                int sm_count, cudaStream_t st) {
+  if (total_windows <= 0) return cudaSuccess;
+  const bool ign = nan == TSDS_NAN_IGNORE;
+#define TSDS_LAUNCH(POL, NM) launch_pol_sm<POL, NM>(single, total_windows, first_piece, last_piece, work, sm_count, st)
+  switch (y_dtype) {
+    case TSDS_I8: return TSDS_LAUNCH(PolSmallInt<int8_t>, 0);
+    case TSDS_U8: return TSDS_LAUNCH(PolSmallInt<uint8_t>, 0);
+    case TSDS_I16: return TSDS_LAUNCH(PolSmallInt<int16_t>, 0);
+    case TSDS_U16: return TSDS_LAUNCH(PolSmallInt<uint16_t>, 0);
+    case TSDS_I32: return TSDS_LAUNCH(PolInt32<int32_t>, 0);
+    case TSDS_U32: return TSDS_LAUNCH(PolInt32<uint32_t>, 0);
+    case TSDS_I64: return TSDS_LAUNCH(PolI64, 0);
+    case TSDS_U64: return TSDS_LAUNCH(PolU64, 0);
+    case TSDS_F16: return ign ? TSDS_LAUNCH(PolF16<1>, 1) : TSDS_LAUNCH(PolF16<0>, 0);
+    case TSDS_F32: return ign ? TSDS_LAUNCH(PolF32<1>, 1) : TSDS_LAUNCH(PolF32<0>, 0);
+    case TSDS_F64: return ign ? TSDS_LAUNCH(PolF64Ign, 1) : TSDS_LAUNCH(PolF64Prop, 0);
+    default: return cudaErrorInvalidValue;
+  }
+#undef TSDS_LAUNCH
+}
+
 }  // namespace tsds
