@@ -55,7 +55,212 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--suite", default=None, choices=["dtypes", "config1", "lttb", "batched"],
+                    help="instead of the headline step, measure one of the other workloads and print one JSON line")
     return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------- other workloads
+
+def _timed_calls(torch, stream, fn, reps):
+    """Median and mean device time (ms) of `fn()` over reps, one event pair each."""
+    times = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    return statistics.median(times), sum(times) / len(times)
+
+
+def _raw_call(binding, algo, x, x_dtype, y, y_dtype, n, n_out, out, cnt, stream, nan=0, ratio=4):
+    sp = binding.ctypes.c_void_p(stream.cuda_stream)
+    xp = x.data_ptr() if x is not None else None
+    xd = binding.DTYPES[x_dtype] if x is not None else 0
+    if algo == "minmaxlttb":
+        r = binding.tsds_minmaxlttb(xp, xd, y.data_ptr(), binding.DTYPES[y_dtype], n, n_out, ratio, nan,
+                                    out.data_ptr(), cnt.data_ptr(), sp)
+    else:
+        fn = {"minmax": binding.tsds_minmax, "m4": binding.tsds_m4, "lttb": binding.tsds_lttb}[algo]
+        r = fn(xp, xd, y.data_ptr(), binding.DTYPES[y_dtype], n, n_out, nan, out.data_ptr(), cnt.data_ptr(), sp)
+    if r != 0:
+        raise RuntimeError(binding.last_error())
+
+
+def suite_dtypes(args):
+    """Config of the paper's Table 1 at 4 GB per dtype: n*itemsize = 4e9, values uniform over a
+    quarter of the dtype range, int64 geometric x, n_out = 2000, MinMax and M4."""
+    import numpy as np
+    import torch
+
+    import paper_2307_05389_gb300 as pkg
+    from paper_2307_05389_gb300 import binding, inputs
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    peak, peak_src = hbm_peak()
+    res = {}
+    x = None
+    x_n = 0
+    out = torch.empty(N_OUT, dtype=torch.int64, device=dev)
+    cnt = torch.empty(1, dtype=torch.int64, device=dev)
+    for d in inputs.DTYPES:
+        size = np.dtype(d).itemsize
+        n = 4_000_000_000 // size
+        y = inputs.quarter_range_cuda(n, d, seed=2, device=dev)
+        if x_n != n:
+            x = None
+            torch.cuda.empty_cache()
+            x = inputs.geometric_x_cuda(n, seed=2, device=dev)
+            x_n = n
+        torch.cuda.synchronize()
+        row = {"n": n}
+        for algo in ALGOS:
+            f = lambda: _raw_call(binding, algo, x, "int64", y, d, n, N_OUT, out, cnt, stream)
+            for _ in range(2):
+                f()
+            pkg.tsds_timing_read()
+            pkg.tsds_timing_enable(True)
+            med, mean = _timed_calls(torch, stream, f, args.steps)
+            pkg.tsds_timing_enable(False)
+            km, kl = pkg.tsds_timing_read()
+            b = step_bytes(n)[algo] - n * 4 + n * size
+            row[algo] = {"call_ms": med, "call_GBps": b / (med / 1e3) / 1e9,
+                         "kernel_GBps": n * size / (km / kl / 1e3) / 1e9,
+                         "pct_of_hbm_peak": 100.0 * b / (med / 1e3) / 1e9 / peak}
+        res[d] = row
+        del y
+        torch.cuda.empty_cache()
+    return {"suite": "dtypes", "metric": METRIC, "unit": "GB/s", "peak": peak, "peak_source": peak_src,
+            "config": {"workload": "per dtype: n*itemsize = 4e9, quarter-range uniform values, int64 geometric x, "
+                                   "n_out=2000, MinMax + M4", "reps": args.steps}, "results": res}
+
+
+def suite_batched(args):
+    """4096 float32 random-walk series, lengths round(10**U(3,7)) (seed 3), n_out uniform in
+    [200, 4000] rounded down to a multiple of 4, no x: one launch sequence per series vs the
+    batched one-shot call vs a resident plan (autotuned launch shape, CUDA graph)."""
+    import numpy as np
+    import torch
+
+    import paper_2307_05389_gb300 as pkg
+    from paper_2307_05389_gb300 import binding, inputs
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    count = 4096
+    lens = inputs.batch_lengths(count, seed=3)
+    n_outs = inputs.batch_n_out(count, seed=3)
+    total = int(lens.sum())
+    walk = inputs.random_walk_cuda(total, "float32", seed=3, device=dev)
+    offs = np.concatenate([[0], np.cumsum(lens)])
+    ys = [walk[int(offs[i]):int(offs[i + 1])] for i in range(count)]
+    torch.cuda.empty_cache()
+    res = {"series": count, "points": total, "GB": total * 4 / 1e9}
+    sp = binding.ctypes.c_void_p(stream.cuda_stream)
+    for algo in ALGOS:
+        outs, counts = binding.batch_buffers(ys, n_outs, dev)
+        fn = binding.tsds_minmax if algo == "minmax" else binding.tsds_m4
+
+        def per_series():
+            for i, y in enumerate(ys):
+                r = fn(None, 0, y.data_ptr(), binding.DTYPES["float32"], y.shape[0], int(n_outs[i]), 0,
+                       outs[i].data_ptr(), counts[i:i + 1].data_ptr(), sp)
+                if r != 0:
+                    raise RuntimeError(binding.last_error())
+
+        def snapshot():
+            torch.cuda.synchronize()
+            c = counts.clone()
+            return c, [o[:int(k)].clone() for o, k in zip(outs, c.tolist())]
+
+        per_series()
+        ref_c, ref_o = snapshot()
+        t_ps, _ = _timed_calls(torch, stream, per_series, 3)
+
+        def batched():
+            binding.downsample_batched(algo, ys, n_outs, outs=outs, counts=counts)
+        counts.fill_(-1)
+        batched()
+        b_c, b_o = snapshot()
+        t_b, _ = _timed_calls(torch, stream, batched, 5)
+
+        plan = binding.Plan(algo, ys, n_outs, graph=True, autotune=True)
+        plan.execute()
+        torch.cuda.synchronize()
+        p_c = plan.counts.clone()
+        p_o = [o[:int(k)].clone() for o, k in zip(plan.outs, p_c.tolist())]
+        t_p, _ = _timed_calls(torch, stream, plan.execute, max(5, args.steps // 10))
+        same = bool(torch.equal(ref_c, b_c) and all(torch.equal(a, b) for a, b in zip(ref_o, b_o)))
+        same_plan = bool(torch.equal(ref_c, p_c) and all(torch.equal(a, b) for a, b in zip(ref_o, p_o)))
+        res[algo] = {"per_series_ms": t_ps, "batched_ms": t_b, "plan_graph_ms": t_p,
+                     "per_series_GBps": total * 4 / (t_ps / 1e3) / 1e9,
+                     "batched_GBps": total * 4 / (t_b / 1e3) / 1e9,
+                     "plan_GBps": total * 4 / (t_p / 1e3) / 1e9,
+                     "speedup_batched": t_ps / t_b, "speedup_plan": t_ps / t_p,
+                     "identical_to_per_series": same and same_plan, "plan": plan.info()}
+        plan.close()
+    peak, peak_src = hbm_peak()
+    return {"suite": "batched", "unit": "ms", "peak": peak, "peak_source": peak_src,
+            "config": {"workload": "4096 float32 random-walk series, lengths log-uniform [1e3, 1e7] (seed 3), "
+                                   "n_out uniform [200, 4000] (multiple of 4), no x; actual total reported"},
+            "results": res}
+
+
+def suite_config1(args):
+    """10^6-point float32 random walk (seed 0), no x, n_out = 1000: latency of each algorithm."""
+    import torch
+
+    from paper_2307_05389_gb300 import binding, inputs
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    n, n_out = 1_000_000, 1000
+    y = torch.from_numpy(inputs.random_walk(n, "float32", seed=0)).to(dev)
+    out = torch.empty(n_out, dtype=torch.int64, device=dev)
+    cnt = torch.empty(1, dtype=torch.int64, device=dev)
+    res = {}
+    for algo in ("minmax", "m4", "lttb", "minmaxlttb"):
+        f = lambda: _raw_call(binding, algo, None, None, y, "float32", n, n_out, out, cnt, stream)
+        for _ in range(5):
+            f()
+        med, mean = _timed_calls(torch, stream, f, max(20, args.steps))
+        res[algo] = {"median_us": med * 1e3, "mean_us": mean * 1e3, "GBps": n * 4 / (med / 1e3) / 1e9}
+    return {"suite": "config1", "unit": "us", "config": {"workload": "n=1e6 float32 random walk (seed 0), no x, "
+            "n_out=1000, minmax_ratio=4; 4 MB is L2-resident: latency, not % of HBM"}, "results": res}
+
+
+def suite_lttb(args):
+    """Plain LTTB on one float64 random walk of 1e7 points and MinMaxLTTB on 64 float64
+    series of 1e8/64 points (random walk quantised to 256 levels, 1 % NaN), n_out = 4000."""
+    import torch
+
+    from paper_2307_05389_gb300 import binding, inputs
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    res = {}
+    n_out = 4000
+    out = torch.empty(n_out, dtype=torch.int64, device=dev)
+    cnt = torch.empty(1, dtype=torch.int64, device=dev)
+    for n, dt in ((10_000_000, "float64"), (10_000_000, "float32"), (1_000_000, "float32")):
+        y = torch.from_numpy(inputs.random_walk(n, dt, seed=4)).to(dev)
+        f = lambda: _raw_call(binding, "lttb", None, None, y, dt, n, n_out, out, cnt, stream)
+        f()
+        med, _ = _timed_calls(torch, stream, f, 3)
+        res[f"lttb_{dt}_{n}"] = {"ms": med, "GBps": n * y.element_size() / (med / 1e3) / 1e9,
+                                 "us_per_bucket": med * 1e3 / (n_out - 2)}
+    series = [torch.from_numpy(inputs.quantised_nan(1_562_500, seed=4 + i)).to(dev) for i in range(64)]
+    for nan, nm in ((0, "propagate"), (1, "ignore")):
+        for r in (2, 4, 30):
+            def f():
+                for s in series:
+                    _raw_call(binding, "minmaxlttb", None, None, s, "float64", s.numel(), n_out, out, cnt, stream,
+                              nan=nan, ratio=r)
+            f()
+            med, _ = _timed_calls(torch, stream, f, 3)
+            res[f"minmaxlttb_r{r}_{nm}"] = {"ms_64_series": med, "GBps": 1e8 * 8 / (med / 1e3) / 1e9}
+    return {"suite": "lttb", "unit": "ms", "config": {"workload": "LTTB: float64/float32 random walks, n_out=4000; "
+            "MinMaxLTTB: 64 x 1.5625e6 float64 quantised to 256 levels with 1% NaN, one call per series"},
+            "results": res}
 
 
 def step_bytes(n, n_out=N_OUT, x_itemsize=8):
@@ -187,6 +392,12 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank)
+        return
+    if args.suite:
+        import paper_2307_05389_gb300 as pkg
+        pkg.load()
+        fn = {"dtypes": suite_dtypes, "config1": suite_config1, "lttb": suite_lttb, "batched": suite_batched}[args.suite]
+        print(json.dumps(fn(args)), flush=True)
         return
 
     import numpy as np

@@ -108,6 +108,64 @@ tsds_status tsds_minmaxlttb(const void* x, tsds_dtype x_dtype, const void* y,
                             int64_t minmax_ratio, tsds_nan_mode nan, int64_t* out,
                             int64_t* out_count, void* stream);
 
+/* ---- Batched form: many series of one dtype in one launch sequence.
+ *
+ * The paper parallelises one series over CPU threads (Section 2.2, the
+ * `parallel` option of Section 2.3).  Here a batch of series shares one
+ * streaming launch: every series' y is cut into windows that the GPU's warps
+ * claim from one counter, whatever series they belong to, so thousands of
+ * small and large series cost one launch sequence instead of one each. */
+
+typedef enum { TSDS_ALGO_MINMAX = 0, TSDS_ALGO_M4 = 1 } tsds_algo;
+
+/* One series of a batch.  x, y, out and out_count are device pointers owned
+ * by the caller, with the same meaning as in tsds_minmax; either every series
+ * of a batch has x or none has.  n_out follows the algorithm's rule. */
+typedef struct {
+  const void* x;
+  const void* y;
+  int64_t n;
+  int64_t n_out;
+  int64_t* out;
+  int64_t* out_count;
+} tsds_series;
+
+/* MinMax or M4 of every series in `series` (a host array of `count`
+ * descriptors), asynchronously on `stream`; each series' indices and count
+ * are exactly those of the single-series call.  1 <= count <= 65535.
+ * Scratch comes from the library's stream-ordered pool.  TSDS_EINVAL names
+ * the offending series. */
+tsds_status tsds_batched(tsds_algo algo, const tsds_series* series, int64_t count,
+                         tsds_dtype x_dtype, tsds_dtype y_dtype, tsds_nan_mode nan, void* stream);
+
+/* A plan keeps a batch's descriptors and scratch resident so the same batch
+ * (same buffers; their contents may change between executions) can be
+ * downsampled again with one call.  Flags: */
+#define TSDS_PLAN_GRAPH 1    /* replay the launch sequence as one CUDA graph */
+#define TSDS_PLAN_AUTOTUNE 2 /* time the candidate window sizes / CTAs per SM on
+                                this batch and keep the fastest; results are
+                                cached per workload class for the process and,
+                                when TSDS_TUNE_CACHE names a file, in that file */
+typedef struct tsds_plan_s* tsds_plan;
+
+/* Creates a plan (allocates its device scratch with cudaMalloc, uploads the
+ * descriptors, autotunes and captures the graph if asked; synchronises
+ * `stream`).  *plan is NULL on failure. */
+tsds_status tsds_plan_create(tsds_plan* plan, tsds_algo algo, const tsds_series* series, int64_t count,
+                             tsds_dtype x_dtype, tsds_dtype y_dtype, tsds_nan_mode nan, int flags,
+                             void* stream);
+
+/* Enqueues one execution of the plan on `stream`.  Executions of one plan
+ * share its scratch: do not let two of them overlap on the GPU. */
+tsds_status tsds_plan_execute(tsds_plan plan, void* stream);
+
+/* The launch shape the plan uses and its sizes (any pointer may be NULL). */
+tsds_status tsds_plan_info(tsds_plan plan, int64_t* window_bytes, int* ctas_per_sm, int64_t* windows,
+                           int64_t* scratch_bytes);
+
+/* Waits for the device to finish queued work, then frees the plan. */
+tsds_status tsds_plan_destroy(tsds_plan plan);
+
 /* MinMax without allocating (the paper has no counterpart: it exists for
  * callers of this library that cannot allocate device memory during a call,
  * e.g. code whose device memory is wholly owned by another allocator, or a

@@ -14,8 +14,16 @@ from .binding import (  # noqa: F401
     MinMaxLTTBDownsampler,
     NAN_MODES,
     TsdsError,
+    Plan,
     downsample,
+    downsample_batched,
     downsample_host,
+    tsds_batched,
+    tsds_minmax_noalloc,
+    tsds_plan_create,
+    tsds_plan_destroy,
+    tsds_plan_execute,
+    tsds_plan_info,
     last_error,
     load,
     tsds_lttb,

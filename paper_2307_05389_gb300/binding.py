@@ -55,6 +55,17 @@ def load(path: str = LIB_PATH):
     lib.tsds_shutdown.restype = None
     lib.tsds_version.argtypes = []
     lib.tsds_version.restype = ctypes.c_char_p
+    lib.tsds_batched.argtypes = [c_int, p, i64, c_int, c_int, c_int, p]
+    lib.tsds_batched.restype = c_int
+    lib.tsds_plan_create.argtypes = [ctypes.POINTER(p), c_int, p, i64, c_int, c_int, c_int, c_int, p]
+    lib.tsds_plan_create.restype = c_int
+    lib.tsds_plan_execute.argtypes = [p, p]
+    lib.tsds_plan_execute.restype = c_int
+    lib.tsds_plan_info.argtypes = [p, ctypes.POINTER(i64), ctypes.POINTER(c_int), ctypes.POINTER(i64),
+                                   ctypes.POINTER(i64)]
+    lib.tsds_plan_info.restype = c_int
+    lib.tsds_plan_destroy.argtypes = [p]
+    lib.tsds_plan_destroy.restype = c_int
     lib.tsds_minmax_noalloc.argtypes = [p, c_int, p, c_int, i64, i64, c_int, p, p, p]
     lib.tsds_minmax_noalloc.restype = c_int
     lib.tsds_kernel_launches.argtypes = []
@@ -112,6 +123,125 @@ def tsds_minmax_noalloc(x, x_dtype, y, y_dtype, n, n_out, nan, out, out_count, s
     scratch comes from a fixed 8 MiB array inside the library (see tsds.h for
     the size limit and the rule that overlapping calls must be serialised)."""
     return load().tsds_minmax_noalloc(x, x_dtype, y, y_dtype, n, n_out, nan, out, out_count, stream)
+
+
+class tsds_series(ctypes.Structure):
+    """One series of a batch (include/tsds.h); pointers are device addresses."""
+    _fields_ = [("x", ctypes.c_void_p), ("y", ctypes.c_void_p), ("n", ctypes.c_int64), ("n_out", ctypes.c_int64),
+                ("out", ctypes.c_void_p), ("out_count", ctypes.c_void_p)]
+
+
+ALGO_CODES = {"minmax": 0, "m4": 1}
+PLAN_GRAPH = 1
+PLAN_AUTOTUNE = 2
+
+
+def tsds_batched(algo, series, count, x_dtype, y_dtype, nan, stream):
+    return load().tsds_batched(algo, series, count, x_dtype, y_dtype, nan, stream)
+
+
+def tsds_plan_create(plan_ref, algo, series, count, x_dtype, y_dtype, nan, flags, stream):
+    return load().tsds_plan_create(plan_ref, algo, series, count, x_dtype, y_dtype, nan, flags, stream)
+
+
+def tsds_plan_execute(plan, stream):
+    return load().tsds_plan_execute(plan, stream)
+
+
+def tsds_plan_info(plan, window_bytes, ctas_per_sm, windows, scratch_bytes):
+    return load().tsds_plan_info(plan, window_bytes, ctas_per_sm, windows, scratch_bytes)
+
+
+def tsds_plan_destroy(plan):
+    return load().tsds_plan_destroy(plan)
+
+
+def _series_array(ys, n_outs, xs, outs, counts):
+    arr = (tsds_series * len(ys))()
+    for i, y in enumerate(ys):
+        arr[i].x = xs[i].data_ptr() if xs is not None else None
+        arr[i].y = y.data_ptr()
+        arr[i].n = y.shape[0]
+        arr[i].n_out = int(n_outs[i])
+        arr[i].out = outs[i].data_ptr()
+        arr[i].out_count = counts[i:i + 1].data_ptr()
+    return arr
+
+
+def batch_buffers(ys, n_outs, device):
+    """Output buffers for a batch: one int64 tensor per series and one count tensor."""
+    import torch
+    outs = [torch.empty(out_capacity("", y.shape[0], int(k)), dtype=torch.int64, device=device)
+            for y, k in zip(ys, n_outs)]
+    counts = torch.empty(len(ys), dtype=torch.int64, device=device)
+    return outs, counts
+
+
+def downsample_batched(algo, ys, n_outs, xs=None, nan="propagate", stream=None, outs=None, counts=None,
+                       y_dtype=None, x_dtype=None):
+    """MinMax/M4 of every CUDA tensor in `ys` in one launch sequence.  Returns
+    (outs, counts) device tensors (outs[i][:counts[i]] are series i's indices)."""
+    import torch
+    dev = ys[0].device
+    if outs is None or counts is None:
+        outs, counts = batch_buffers(ys, n_outs, dev)
+    st = stream if stream is not None else torch.cuda.current_stream(dev)
+    arr = _series_array(ys, n_outs, xs, outs, counts)
+    yd = DTYPES[y_dtype or _torch_dtype_name(ys[0])]
+    xd = DTYPES[x_dtype or _torch_dtype_name(xs[0])] if xs is not None else 0
+    with torch.cuda.device(dev):
+        r = tsds_batched(ALGO_CODES[algo], arr, len(ys), xd, yd, NAN_MODES[nan], ctypes.c_void_p(st.cuda_stream))
+    if r != 0:
+        raise TsdsError(r, last_error())
+    return outs, counts
+
+
+class Plan:
+    """A resident batch (tsds_plan_*): create once, execute many times."""
+
+    def __init__(self, algo, ys, n_outs, xs=None, nan="propagate", graph=True, autotune=False, stream=None,
+                 y_dtype=None, x_dtype=None):
+        import torch
+        self.device = ys[0].device
+        self.outs, self.counts = batch_buffers(ys, n_outs, self.device)
+        self._keep = (ys, xs)
+        st = stream if stream is not None else torch.cuda.current_stream(self.device)
+        arr = _series_array(ys, n_outs, xs, self.outs, self.counts)
+        yd = DTYPES[y_dtype or _torch_dtype_name(ys[0])]
+        xd = DTYPES[x_dtype or _torch_dtype_name(xs[0])] if xs is not None else 0
+        self.handle = ctypes.c_void_p()
+        flags = (PLAN_GRAPH if graph else 0) | (PLAN_AUTOTUNE if autotune else 0)
+        with torch.cuda.device(self.device):
+            r = tsds_plan_create(ctypes.byref(self.handle), ALGO_CODES[algo], arr, len(ys), xd, yd,
+                                 NAN_MODES[nan], flags, ctypes.c_void_p(st.cuda_stream))
+        if r != 0:
+            raise TsdsError(r, last_error())
+
+    def execute(self, stream=None):
+        import torch
+        st = stream if stream is not None else torch.cuda.current_stream(self.device)
+        r = tsds_plan_execute(self.handle, ctypes.c_void_p(st.cuda_stream))
+        if r != 0:
+            raise TsdsError(r, last_error())
+        return self.outs, self.counts
+
+    def info(self):
+        wb, cp, w, sb = ctypes.c_int64(), ctypes.c_int(), ctypes.c_int64(), ctypes.c_int64()
+        r = tsds_plan_info(self.handle, ctypes.byref(wb), ctypes.byref(cp), ctypes.byref(w), ctypes.byref(sb))
+        if r != 0:
+            raise TsdsError(r, last_error())
+        return {"window_bytes": wb.value, "ctas_per_sm": cp.value, "windows": w.value, "scratch_bytes": sb.value}
+
+    def close(self):
+        if self.handle:
+            tsds_plan_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def tsds_shutdown():

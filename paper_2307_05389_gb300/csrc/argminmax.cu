@@ -399,10 +399,9 @@ template <class P, int NM, bool MULTI>
 __global__ void __launch_bounds__(kStreamThreads)
 k_argminmax(const SeriesDev* __restrict__ sd, SeriesDev single, const int32_t* __restrict__ win_series,
             int64_t total_windows, Piece* __restrict__ first_piece, Piece* __restrict__ last_piece,
-            WorkCounters* __restrict__ work) {
+            WorkCounters* __restrict__ work, int64_t welems) {
   using T = typename P::T;
   const int lane = threadIdx.x & 31;
-  const int64_t welems = kWindowBytes / (int64_t)sizeof(T);
   for (;;) {
     unsigned long long wu = 0;
     if (lane == 0) wu = atomicAdd(&work->next_window, 1ull);
@@ -461,7 +460,7 @@ k_argminmax(const SeriesDev* __restrict__ sd, SeriesDev single, const int32_t* _
 template <class P, int NM>
 static cudaError_t launch_pol(const SeriesDev* s_dev, int count, const SeriesDev& single,
                               const int32_t* win_series, int64_t total_windows, Piece* fp, Piece* lp,
-                              WorkCounters* work, cudaStream_t st) {
+                              WorkCounters* work, const StreamConfig& cfg, cudaStream_t st) {
   const bool multi = count > 1 || s_dev != nullptr;
   auto kern = multi ? k_argminmax<P, NM, true> : k_argminmax<P, NM, false>;
   static int per_sm[2] = {0, 0};
@@ -470,13 +469,15 @@ static cudaError_t launch_pol(const SeriesDev* s_dev, int count, const SeriesDev
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kStreamThreads, 0);
     if (e != cudaSuccess || occ < 1) occ = 1;
   }
+  const int per = (cfg.ctas_per_sm > 0 && cfg.ctas_per_sm < occ) ? cfg.ctas_per_sm : occ;
   const int64_t warps_per_block = kStreamThreads / 32;
   int64_t blocks = (total_windows + warps_per_block - 1) / warps_per_block;
-  const int64_t cap = (int64_t)device_sm_count() * occ;
+  const int64_t cap = (int64_t)device_sm_count() * per;
   if (blocks > cap) blocks = cap;
   if (blocks < 1) blocks = 1;
   note_launch();
-  kern<<<(unsigned)blocks, kStreamThreads, 0, st>>>(s_dev, single, win_series, total_windows, fp, lp, work);
+  kern<<<(unsigned)blocks, kStreamThreads, 0, st>>>(s_dev, single, win_series, total_windows, fp, lp, work,
+                                                     cfg.window_bytes / (int64_t)sizeof(typename P::T));
   return cudaGetLastError();
 }
 
@@ -488,10 +489,10 @@ using PolF64Ign = Pol64<2, TSDS_NAN_IGNORE>;
 cudaError_t launch_argminmax(const SeriesDev* s_dev, int count, const SeriesDev& single,
                              const int32_t* win_series, int64_t total_windows,
                              Piece* first_piece, Piece* last_piece, WorkCounters* work,
-                             tsds_dtype y_dtype, tsds_nan_mode nan, cudaStream_t st) {
+                             tsds_dtype y_dtype, tsds_nan_mode nan, cudaStream_t st, const StreamConfig& cfg) {
   if (total_windows <= 0) return cudaSuccess;
   const bool ign = nan == TSDS_NAN_IGNORE;
-#define TSDS_LAUNCH(POL, NM) launch_pol<POL, NM>(s_dev, count, single, win_series, total_windows, first_piece, last_piece, work, st)
+#define TSDS_LAUNCH(POL, NM) launch_pol<POL, NM>(s_dev, count, single, win_series, total_windows, first_piece, last_piece, work, cfg, st)
   switch (y_dtype) {
     case TSDS_I8: return TSDS_LAUNCH(PolSmallInt<int8_t>, 0);
     case TSDS_U8: return TSDS_LAUNCH(PolSmallInt<uint8_t>, 0);
@@ -524,7 +525,8 @@ static cudaError_t launch_pol_sm(const SeriesDev& single, int64_t total_windows,
   if (blocks > cap) blocks = cap;
   if (blocks < 1) blocks = 1;
   note_launch();
-  kern<<<(unsigned)blocks, kStreamThreads, 0, st>>>(nullptr, single, nullptr, total_windows, fp, lp, work);
+  kern<<<(unsigned)blocks, kStreamThreads, 0, st>>>(nullptr, single, nullptr, total_windows, fp, lp, work,
+                                                     kWindowBytes / (int64_t)sizeof(typename P::T));
   return cudaGetLastError();
 }
 

@@ -55,6 +55,12 @@ inline bool dtype_is_float(tsds_dtype d) { return d == TSDS_F16 || d == TSDS_F32
 
 inline int64_t window_elems(tsds_dtype y_dtype) { return kWindowBytes / dtype_size(y_dtype); }
 
+// Launch shape of the streaming pass (the batched plans autotune it).
+struct StreamConfig {
+  int64_t window_bytes = kWindowBytes;  // bytes of y per warp claim: a multiple of 16, >= 4096
+  int ctas_per_sm = 0;                  // 0: as many as fit
+};
+
 // ---- launchers (each returns the launch's cudaError_t)
 
 // Bin starts for every series in `s` (count series, array in device memory
@@ -62,15 +68,19 @@ inline int64_t window_elems(tsds_dtype y_dtype) { return kWindowBytes / dtype_si
 cudaError_t launch_edges(const SeriesDev* s_dev, int count, const SeriesDev* s_host_single,
                          bool has_x, tsds_dtype x_dtype, int64_t max_nb, cudaStream_t st);
 
-// Window -> series map for a batched launch.
+// Window -> series map for a batched launch (window_bytes as in StreamConfig).
 cudaError_t launch_window_map(const SeriesDev* s_dev, int count, int32_t* win_series,
-                              tsds_dtype y_dtype, cudaStream_t st);
+                              tsds_dtype y_dtype, cudaStream_t st, int64_t window_bytes = kWindowBytes);
 
 // The streaming per-bin argmin/argmax pass.
 cudaError_t launch_argminmax(const SeriesDev* s_dev, int count, const SeriesDev& single,
                              const int32_t* win_series, int64_t total_windows,
                              Piece* first_piece, Piece* last_piece, WorkCounters* work,
-                             tsds_dtype y_dtype, tsds_nan_mode nan, cudaStream_t st);
+                             tsds_dtype y_dtype, tsds_nan_mode nan, cudaStream_t st,
+                             const StreamConfig& cfg = StreamConfig());
+
+// Every series with nb == 0 gets 0..n-1 (its n_out >= n) and *out_count = n.
+cudaError_t launch_iota_batched(const SeriesDev* s_dev, int count, cudaStream_t st);
 
 // Per-bin selections -> compacted, sorted output and count.
 cudaError_t launch_emit(const SeriesDev* s_dev, int count, const SeriesDev& single, Algo algo,

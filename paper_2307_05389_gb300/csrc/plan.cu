@@ -122,9 +122,23 @@ __global__ void k_window_map(const SeriesDev* sd, int32_t* win_series, int64_t w
 }
 
 cudaError_t launch_window_map(const SeriesDev* s_dev, int count, int32_t* win_series,
-                              tsds_dtype y_dtype, cudaStream_t st) {
+                              tsds_dtype y_dtype, cudaStream_t st, int64_t window_bytes) {
   note_launch();
-  k_window_map<<<count, 256, 0, st>>>(s_dev, win_series, window_elems(y_dtype));
+  k_window_map<<<count, 256, 0, st>>>(s_dev, win_series, window_bytes / dtype_size(y_dtype));
+  return cudaGetLastError();
+}
+
+// One CTA per series; only series whose n_out >= n (nb == 0) write.
+__global__ void k_iota_batched(const SeriesDev* sd) {
+  const SeriesDev& S = sd[blockIdx.x];
+  if (S.nb != 0) return;
+  for (int64_t i = threadIdx.x; i < S.n; i += blockDim.x) S.out[i] = i + S.idx_bias;
+  if (threadIdx.x == 0) *S.out_count = S.n;
+}
+
+cudaError_t launch_iota_batched(const SeriesDev* s_dev, int count, cudaStream_t st) {
+  note_launch();
+  k_iota_batched<<<count, 256, 0, st>>>(s_dev);
   return cudaGetLastError();
 }
 

@@ -96,44 +96,77 @@ def batch_n_out(count: int, seed: int = 3, lo: int = 200, hi: int = 4000, multip
 
 
 # ----------------------------------------------------------------------------- device-side draws
+# Drawn in chunks of 2^27 elements, each chunk from its own generator seeded
+# with (seed, chunk), so temporaries stay small for 4*10^9-element inputs.
+# Unsigned dtypes come back in the signed dtype of the same width (their
+# values are below the signed maximum, so the bytes are identical); pass the
+# unsigned dtype code to the library.
+
+_CHUNK = 1 << 27
+
+
+def _gen(device, seed, chunk):
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed) * 1_000_003 + int(chunk))
+    return g
+
+
+def _signed_torch_dtype(dtype):
+    import torch
+    dt = np.dtype(dtype)
+    if dt.kind == "u":
+        return getattr(torch, f"int{8 * dt.itemsize}") if dt.itemsize > 1 else torch.uint8
+    return getattr(torch, dtype)
+
 
 def random_walk_cuda(n: int, dtype="float32", seed: int = 0, device="cuda"):
     import torch
-    g = torch.Generator(device=device)
-    g.manual_seed(seed)
-    steps = torch.randn(n, generator=g, device=device, dtype=torch.float32)
-    return torch.cumsum(steps, 0, dtype=torch.float64).to(getattr(torch, dtype))
+    out = torch.empty(n, dtype=_signed_torch_dtype(dtype), device=device)
+    carry = torch.zeros((), dtype=torch.float64, device=device)
+    for c, lo in enumerate(range(0, n, _CHUNK)):
+        hi = min(n, lo + _CHUNK)
+        steps = torch.randn(hi - lo, generator=_gen(device, seed, c), device=device, dtype=torch.float32)
+        w = torch.cumsum(steps, 0, dtype=torch.float64) + carry
+        carry = w[-1].clone()
+        out[lo:hi] = w.to(out.dtype)
+    return out
 
 
 def geometric_x_cuda(n: int, seed: int = 0, p: float = 0.5, device="cuda"):
     import torch
-    g = torch.Generator(device=device)
-    g.manual_seed(seed)
-    gaps = torch.empty(n, dtype=torch.float32, device=device).geometric_(p, generator=g)
-    gaps = gaps.to(torch.int64)
-    gaps[0] = 0
-    return torch.cumsum(gaps, 0)
+    out = torch.empty(n, dtype=torch.int64, device=device)
+    carry = torch.zeros((), dtype=torch.int64, device=device)
+    for c, lo in enumerate(range(0, n, _CHUNK)):
+        hi = min(n, lo + _CHUNK)
+        gaps = torch.empty(hi - lo, dtype=torch.float32, device=device).geometric_(p, generator=_gen(device, seed, c))
+        gaps = gaps.to(torch.int64)
+        if lo == 0:
+            gaps[0] = 0
+        w = torch.cumsum(gaps, 0) + carry
+        carry = w[-1].clone()
+        out[lo:hi] = w
+    return out
 
 
 def quarter_range_cuda(n: int, dtype: str, seed: int = 0, device="cuda"):
     import torch
-    g = torch.Generator(device=device)
-    g.manual_seed(seed)
     dt = np.dtype(dtype)
-    tdt = getattr(torch, dtype)
-    if dt.kind == "f":
-        hi = float(np.finfo(dt).max) / 4
-        u = torch.rand(n, generator=g, device=device, dtype=torch.float64)
-        return (u * (2 * hi) - hi).to(tdt)
-    info = np.iinfo(dt)
-    lo, hi = (info.min // 4, info.max // 4) if dt.kind == "i" else (0, info.max // 4)
-    if dt.itemsize < 8:
-        v = torch.randint(lo, hi + 1, (n,), generator=g, device=device, dtype=torch.int64)
-        return v.to(tdt) if dt.kind == "i" or dt.itemsize < 8 else v
-    # 64-bit: draw 63 random bits and scale into [lo, hi] (uniform up to 2^-63 bias)
-    r = torch.randint(0, 2 ** 62, (n,), generator=g, device=device, dtype=torch.int64)
-    span = hi - lo
-    v = (r.to(torch.float64) / float(2 ** 62) * float(span)).to(torch.int64)
-    if dt.kind == "i":
-        return v + lo
-    return v.view(torch.uint64) if hasattr(torch, "uint64") else v
+    out = torch.empty(n, dtype=_signed_torch_dtype(dtype), device=device)
+    for c, lo in enumerate(range(0, n, _CHUNK)):
+        hi = min(n, lo + _CHUNK)
+        g = _gen(device, seed, c)
+        if dt.kind == "f":
+            top = float(np.finfo(dt).max) / 4
+            u = torch.rand(hi - lo, generator=g, device=device, dtype=torch.float64)
+            out[lo:hi] = (u * (2 * top) - top).to(out.dtype)
+            continue
+        info = np.iinfo(dt)
+        a, b = (info.min // 4, info.max // 4) if dt.kind == "i" else (0, info.max // 4)
+        if dt.itemsize < 8:
+            v = torch.randint(a, b + 1, (hi - lo,), generator=g, device=device, dtype=torch.int64)
+        else:
+            r = torch.randint(0, 2 ** 62, (hi - lo,), generator=g, device=device, dtype=torch.int64)
+            v = (r.to(torch.float64) / float(2 ** 62) * float(b - a)).to(torch.int64) + a
+        out[lo:hi] = v.to(out.dtype)
+    return out
