@@ -167,6 +167,30 @@ def test_minmaxlttb(ratio, nan):
     check("minmaxlttb", x, y, 1000, nan, ratio)
 
 
+@pytest.mark.parametrize("n_out", [3, 60, 2000, 9000])
+def test_lttb_filter_stress(n_out):
+    """Inputs chosen against the FP32 pre-filter of the LTTB chain: exact area
+    ties (small integers), near-collinear points, timestamps ~1e15 (FP32 cannot
+    resolve them), magnitudes beyond its accepted range, and both chain modes
+    (n_out 9000 gives buckets of <= 32 points: the transition table)."""
+    rng = np.random.default_rng(51)
+    n = 40_000
+    cases = []
+    cases.append((None, rng.integers(-3, 4, n).astype(np.float64)))                    # many exact ties
+    t = np.arange(n, dtype=np.float64)
+    cases.append((None, 2.5 * t + 1e-9 * rng.standard_normal(n)))                       # near-collinear
+    cases.append((1e15 + np.cumsum(rng.integers(1, 5, n)).astype(np.float64),
+                  inputs.random_walk(n, "float64", seed=52)))                           # huge x, fine gaps
+    cases.append((None, inputs.random_walk(n, "float64", seed=53) * 1e25))              # beyond the filter range
+    cases.append((None, inputs.random_walk(n, "float64", seed=54) * 1e-25))             # tiny magnitudes
+    y = inputs.random_walk(n, "float64", seed=55)
+    y[rng.choice(n, 50, replace=False)] = np.inf
+    cases.append((None, y))                                                             # infinities
+    for x, y in cases:
+        check("lttb", x, y, n_out)
+        check("lttb", x, y, n_out, "ignore")
+
+
 def test_config1_shape_all_algorithms():
     y = inputs.random_walk(1_000_000, "float32", seed=0)
     for algo in ("minmax", "m4", "lttb", "minmaxlttb"):
