@@ -55,7 +55,7 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--suite", default=None, choices=["dtypes", "config1", "lttb", "batched"],
+    ap.add_argument("--suite", default=None, choices=["dtypes", "config1", "lttb", "batched", "serve"],
                     help="instead of the headline step, measure one of the other workloads and print one JSON line")
     return ap.parse_args()
 
@@ -205,6 +205,101 @@ def suite_batched(args):
             "config": {"workload": "4096 float32 random-walk series, lengths log-uniform [1e3, 1e7] (seed 3), "
                                    "n_out uniform [200, 4000] (multiple of 4), no x; actual total reported"},
             "results": res}
+
+
+def suite_serve(args):
+    """32 resident float32 random walks of 1e8 points with float64 x (cumsum of exponential(1)).
+    Poisson-arriving viewport queries: a series uniformly, a span log-uniform in [1e4, 1e8] points
+    at a uniform start (sent as an x range), n_out from {500, 1000, 2000, 4000}, algorithm from
+    MinMax / M4 / MinMaxLTTB(ratio 4).  Per arrival rate: p50/p99 submission-to-result latency,
+    completed queries/s and GB/s of y inside the ranges; plus the same queries issued one call
+    at a time through the single-series entry points for comparison."""
+    import numpy as np
+    import torch
+
+    from paper_2307_05389_gb300 import binding, inputs
+    dev = torch.device("cuda", 0)
+    nser, n = 32, 100_000_000
+    ys = [inputs.random_walk_cuda(n, "float32", seed=500 + i, device=dev) for i in range(nser)]
+    xs = [inputs.exponential_x_cuda(n, seed=600 + i, device=dev) for i in range(nser)]
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    xh = [x[::1000].cpu().numpy() for x in xs]   # coarse host copy to pick x ranges from
+    rng = np.random.default_rng(5)
+
+    def draw(k):
+        qs = []
+        for _ in range(k):
+            s = int(rng.integers(0, nser))
+            span = int(10 ** rng.uniform(4, 8))
+            start = int(rng.integers(0, n - span + 1))
+            lo_x = float(xh[s][min(start // 1000, len(xh[s]) - 1)])
+            hi_x = float(xh[s][min((start + span) // 1000, len(xh[s]) - 1)])
+            qs.append((s, ["minmax", "m4", "minmaxlttb"][int(rng.integers(0, 3))],
+                       int([500, 1000, 2000, 4000][int(rng.integers(0, 4))]), lo_x, hi_x))
+        return qs
+
+    srv = binding.Server("float32", "float64", streams=4, max_batch=256, memory_budget=8 << 30)
+    ids = [srv.add_series(y, x) for y, x in zip(ys, xs)]
+    res = {}
+    # warm-up (autotune-free path; first batches allocate pinned buffers)
+    for t in [srv.submit(ids[s], a, k, x_range=(l, h)) for s, a, k, l, h in draw(64)]:
+        srv.result(t)
+    for rate in (1e2, 1e3, 1e4, 1e5):
+        count = int(min(max(200, rate * 2.0), 4000))
+        qs = draw(count)
+        gaps = rng.exponential(1.0 / rate, count)
+        srv.reset_stats()
+        t0 = time.perf_counter()
+        due = t0
+        tickets = []
+        for (s, a, k, l, h), g in zip(qs, gaps):
+            due += g
+            while time.perf_counter() < due:
+                pass
+            tickets.append(srv.submit(ids[s], a, k, x_range=(l, h)))
+        for t in tickets:
+            srv.result(t)
+        st = srv.stats()
+        res[f"rate_{int(rate)}"] = {"queries": count, "offered_qps": rate,
+                                    "achieved_qps": st["completed"] / max(st["span_s"], 1e-9),
+                                    "p50_ms": st["p50_us"] / 1e3, "p99_ms": st["p99_us"] / 1e3,
+                                    "mean_ms": st["mean_us"] / 1e3, "batches": st["batches"],
+                                    "GBps": st["bytes"] / max(st["span_s"], 1e-9) / 1e9,
+                                    "mean_points_per_query": st["points"] / max(st["completed"], 1)}
+    # saturation: every query submitted at once
+    qs = draw(2000)
+    srv.reset_stats()
+    tickets = [srv.submit(ids[s], a, k, x_range=(l, h)) for s, a, k, l, h in qs]
+    for t in tickets:
+        srv.result(t)
+    st = srv.stats()
+    res["burst_2000"] = {"achieved_qps": st["completed"] / st["span_s"], "p50_ms": st["p50_us"] / 1e3,
+                         "p99_ms": st["p99_us"] / 1e3, "GBps": st["bytes"] / st["span_s"] / 1e9,
+                         "batches": st["batches"]}
+    srv.close()
+    # the same kind of queries one call at a time (range found by searchsorted on the device)
+    qs = draw(300)
+    stream = torch.cuda.current_stream(dev)
+    out = torch.empty(4096, dtype=torch.int64, device=dev)
+    cnt = torch.empty(1, dtype=torch.int64, device=dev)
+    tot_pts = 0
+    t0 = time.perf_counter()
+    for s, a, k, l, h in qs:
+        lo = int(torch.searchsorted(xs[s], torch.tensor([l], device=dev, dtype=torch.float64)).item())
+        hi = int(torch.searchsorted(xs[s], torch.tensor([h], device=dev, dtype=torch.float64), right=True).item())
+        tot_pts += hi - lo
+        if hi - lo <= 0:
+            continue
+        _raw_call(binding, a, xs[s][lo:hi], "float64", ys[s][lo:hi], "float32", hi - lo, k, out, cnt, stream)
+        int(cnt.item())
+    dt = time.perf_counter() - t0
+    res["one_call_per_query"] = {"queries": len(qs), "qps": len(qs) / dt, "GBps": tot_pts * 4 / dt / 1e9,
+                                 "mean_ms": dt / len(qs) * 1e3}
+    return {"suite": "serve", "unit": "ms", "config": {
+        "workload": "32 x 1e8 float32 random walks, float64 x = cumsum(exponential(1)); Poisson viewport queries, "
+                    "span log-uniform [1e4, 1e8] points, n_out in {500,1000,2000,4000}, MinMax/M4/MinMaxLTTB(4)",
+        "server": {"streams": 4, "max_batch": 256, "memory_budget_GiB": 8}}, "results": res}
 
 
 def suite_config1(args):
@@ -396,7 +491,8 @@ def main():
     if args.suite:
         import paper_2307_05389_gb300 as pkg
         pkg.load()
-        fn = {"dtypes": suite_dtypes, "config1": suite_config1, "lttb": suite_lttb, "batched": suite_batched}[args.suite]
+        fn = {"dtypes": suite_dtypes, "config1": suite_config1, "lttb": suite_lttb, "batched": suite_batched,
+              "serve": suite_serve}[args.suite]
         print(json.dumps(fn(args)), flush=True)
         return
 

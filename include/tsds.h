@@ -166,6 +166,74 @@ tsds_status tsds_plan_info(tsds_plan plan, int64_t* window_bytes, int* ctas_per_
 /* Waits for the device to finish queued work, then frees the plan. */
 tsds_status tsds_plan_destroy(tsds_plan plan);
 
+/* ---- Served form: viewport queries over resident series.
+ *
+ * Interactive exploration re-downsamples the visible range on every zoom or
+ * pan (Section 1).  A server keeps series resident (caller-owned device
+ * memory), accepts queries at any time from any thread, and runs them in
+ * batches on `streams` CUDA streams: whenever a batch finishes, queued
+ * queries join the next batch as far as `max_batch` and the device-memory
+ * budget allow (continuous batching), so a query's result is the same alone
+ * or in a mix.  Results are the indices (into the whole series) that the
+ * single-series call returns on the selected range, copied to host memory. */
+
+#define TSDS_ALGO_MINMAXLTTB 2   /* third algorithm code accepted by the server */
+
+typedef struct {
+  int32_t streams;        /* batches in flight at once, 1..16 (default 2) */
+  int32_t max_batch;      /* queries per batch, 1..4096 (default 256) */
+  int64_t memory_budget;  /* device scratch bytes the in-flight batches may hold (default 1 GiB);
+                             a query larger than the budget runs alone */
+} tsds_server_config;
+
+typedef struct {
+  int64_t series;         /* id from tsds_server_add_series */
+  int32_t algo;           /* TSDS_ALGO_MINMAX, TSDS_ALGO_M4 or TSDS_ALGO_MINMAXLTTB */
+  int32_t nan;            /* tsds_nan_mode */
+  int32_t by_x;           /* 1: points with x_lo <= x <= x (compared as binary64); 0: indices [lo, hi) */
+  int32_t reserved;
+  double x_lo, x_hi;
+  int64_t lo, hi;
+  int64_t n_out;          /* the algorithm's n_out rule applies */
+  int64_t minmax_ratio;   /* MinMaxLTTB only, >= 1 */
+} tsds_query;
+
+typedef struct {
+  int64_t submitted, completed, batches;
+  int64_t points, bytes;  /* points (and bytes of y) inside the completed queries' ranges */
+  double span_s;          /* first submission to last completion */
+  double p50_us, p99_us, mean_us, max_us;  /* submission-to-completion latency */
+} tsds_server_stats;
+
+typedef struct tsds_server_s* tsds_server;
+
+/* Starts a server on the current device (cfg may be NULL for the defaults).
+ * All series of a server share y_dtype and x_dtype (x_dtype is ignored when
+ * the series have no x). */
+tsds_status tsds_server_create(tsds_server* server, const tsds_server_config* cfg, tsds_dtype x_dtype,
+                               tsds_dtype y_dtype);
+
+/* Registers a resident series (device pointers kept until tsds_server_destroy;
+ * x sorted non-decreasing or NULL; every series of a server has x or none). */
+tsds_status tsds_server_add_series(tsds_server server, const void* x, const void* y, int64_t n, int64_t* id);
+
+/* Queues a query; returns at once with a ticket.  Thread-safe. */
+tsds_status tsds_server_submit(tsds_server server, const tsds_query* query, int64_t* ticket);
+
+/* Result of a ticket.  timeout_us: 0 = do not wait, < 0 = wait until done,
+ * > 0 = wait at most that long.  *done = 1 when finished, then the indices
+ * (at most the query's n_out) are copied to `out` (host memory, capacity
+ * `cap`), *count and *latency_us (submission to completion) are set and the
+ * ticket is released. */
+tsds_status tsds_server_result(tsds_server server, int64_t ticket, int64_t timeout_us, int64_t* out, int64_t cap,
+                               int64_t* count, int* done, double* latency_us);
+
+tsds_status tsds_server_stats_get(tsds_server server, tsds_server_stats* stats);
+tsds_status tsds_server_reset_stats(tsds_server server);
+
+/* Finishes queued and running queries, then stops the server. */
+tsds_status tsds_server_destroy(tsds_server server);
+
 /* MinMax without allocating (the paper has no counterpart: it exists for
  * callers of this library that cannot allocate device memory during a call,
  * e.g. code whose device memory is wholly owned by another allocator, or a

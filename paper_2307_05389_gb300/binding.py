@@ -244,6 +244,130 @@ class Plan:
             pass
 
 
+class tsds_query(ctypes.Structure):
+    _fields_ = [("series", ctypes.c_int64), ("algo", ctypes.c_int32), ("nan", ctypes.c_int32),
+                ("by_x", ctypes.c_int32), ("reserved", ctypes.c_int32), ("x_lo", ctypes.c_double),
+                ("x_hi", ctypes.c_double), ("lo", ctypes.c_int64), ("hi", ctypes.c_int64),
+                ("n_out", ctypes.c_int64), ("minmax_ratio", ctypes.c_int64)]
+
+
+class tsds_server_config(ctypes.Structure):
+    _fields_ = [("streams", ctypes.c_int32), ("max_batch", ctypes.c_int32), ("memory_budget", ctypes.c_int64)]
+
+
+class tsds_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("batches", ctypes.c_int64),
+                ("points", ctypes.c_int64), ("bytes", ctypes.c_int64), ("span_s", ctypes.c_double),
+                ("p50_us", ctypes.c_double), ("p99_us", ctypes.c_double), ("mean_us", ctypes.c_double),
+                ("max_us", ctypes.c_double)]
+
+
+SERVER_ALGOS = {"minmax": 0, "m4": 1, "minmaxlttb": 2}
+
+
+def _declare_server(lib):
+    p, i64, c_int = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+    lib.tsds_server_create.argtypes = [ctypes.POINTER(p), ctypes.POINTER(tsds_server_config), c_int, c_int]
+    lib.tsds_server_create.restype = c_int
+    lib.tsds_server_add_series.argtypes = [p, p, p, i64, ctypes.POINTER(i64)]
+    lib.tsds_server_add_series.restype = c_int
+    lib.tsds_server_submit.argtypes = [p, ctypes.POINTER(tsds_query), ctypes.POINTER(i64)]
+    lib.tsds_server_submit.restype = c_int
+    lib.tsds_server_result.argtypes = [p, i64, i64, p, i64, ctypes.POINTER(i64), ctypes.POINTER(c_int),
+                                       ctypes.POINTER(ctypes.c_double)]
+    lib.tsds_server_result.restype = c_int
+    lib.tsds_server_stats_get.argtypes = [p, ctypes.POINTER(tsds_server_stats)]
+    lib.tsds_server_stats_get.restype = c_int
+    lib.tsds_server_reset_stats.argtypes = [p]
+    lib.tsds_server_reset_stats.restype = c_int
+    lib.tsds_server_destroy.argtypes = [p]
+    lib.tsds_server_destroy.restype = c_int
+
+
+class Server:
+    """Continuous-batching server over resident series (tsds_server_*)."""
+
+    def __init__(self, y_dtype, x_dtype=None, streams=2, max_batch=256, memory_budget=1 << 30):
+        lib = load()
+        if not hasattr(lib, "_server_declared"):
+            _declare_server(lib)
+            lib._server_declared = True
+        self.lib = lib
+        cfg = tsds_server_config(streams, max_batch, memory_budget)
+        self.handle = ctypes.c_void_p()
+        r = lib.tsds_server_create(ctypes.byref(self.handle), ctypes.byref(cfg),
+                                   DTYPES[x_dtype] if x_dtype else 0, DTYPES[y_dtype])
+        if r != 0:
+            raise TsdsError(r, last_error())
+        self._keep = []
+        self.n_out = {}
+
+    def add_series(self, y, x=None):
+        sid = ctypes.c_int64()
+        r = self.lib.tsds_server_add_series(self.handle, x.data_ptr() if x is not None else None, y.data_ptr(),
+                                            y.shape[0], ctypes.byref(sid))
+        if r != 0:
+            raise TsdsError(r, last_error())
+        self._keep.append((y, x))
+        return sid.value
+
+    def submit(self, series, algo, n_out, x_range=None, index_range=None, nan="propagate", minmax_ratio=4):
+        q = tsds_query()
+        q.series = series
+        q.algo = SERVER_ALGOS[algo]
+        q.nan = NAN_MODES[nan]
+        if x_range is not None:
+            q.by_x = 1
+            q.x_lo, q.x_hi = float(x_range[0]), float(x_range[1])
+        else:
+            q.by_x = 0
+            q.lo, q.hi = (0, 2 ** 62) if index_range is None else (int(index_range[0]), int(index_range[1]))
+        q.n_out = n_out
+        q.minmax_ratio = minmax_ratio
+        t = ctypes.c_int64()
+        r = self.lib.tsds_server_submit(self.handle, ctypes.byref(q), ctypes.byref(t))
+        if r != 0:
+            raise TsdsError(r, last_error())
+        self.n_out[t.value] = n_out
+        return t.value
+
+    def result(self, ticket, timeout_us=-1):
+        """(indices as numpy int64, latency in µs), or None if not done within the timeout."""
+        import numpy as np
+        cap = self.n_out.get(ticket, 1)
+        out = np.empty(max(cap, 1), dtype=np.int64)
+        cnt, done, lat = ctypes.c_int64(), ctypes.c_int(), ctypes.c_double()
+        r = self.lib.tsds_server_result(self.handle, ticket, timeout_us, out.ctypes.data_as(ctypes.c_void_p), cap,
+                                        ctypes.byref(cnt), ctypes.byref(done), ctypes.byref(lat))
+        if r != 0:
+            raise TsdsError(r, last_error())
+        if not done.value:
+            return None
+        self.n_out.pop(ticket, None)
+        return out[:cnt.value].copy(), lat.value
+
+    def stats(self):
+        s = tsds_server_stats()
+        r = self.lib.tsds_server_stats_get(self.handle, ctypes.byref(s))
+        if r != 0:
+            raise TsdsError(r, last_error())
+        return {f: getattr(s, f) for f, _ in tsds_server_stats._fields_}
+
+    def reset_stats(self):
+        self.lib.tsds_server_reset_stats(self.handle)
+
+    def close(self):
+        if self.handle:
+            self.lib.tsds_server_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def tsds_shutdown():
     load().tsds_shutdown()
 

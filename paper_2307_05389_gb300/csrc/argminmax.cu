@@ -399,9 +399,10 @@ template <class P, int NM, bool MULTI>
 __global__ void __launch_bounds__(kStreamThreads)
 k_argminmax(const SeriesDev* __restrict__ sd, SeriesDev single, const int32_t* __restrict__ win_series,
             int64_t total_windows, Piece* __restrict__ first_piece, Piece* __restrict__ last_piece,
-            WorkCounters* __restrict__ work, int64_t welems) {
+            WorkCounters* __restrict__ work, int64_t welems, const int64_t* __restrict__ total_dev) {
   using T = typename P::T;
   const int lane = threadIdx.x & 31;
+  if (total_dev) total_windows = *total_dev;
   for (;;) {
     unsigned long long wu = 0;
     if (lane == 0) wu = atomicAdd(&work->next_window, 1ull);
@@ -473,11 +474,12 @@ static cudaError_t launch_pol(const SeriesDev* s_dev, int count, const SeriesDev
   const int64_t warps_per_block = kStreamThreads / 32;
   int64_t blocks = (total_windows + warps_per_block - 1) / warps_per_block;
   const int64_t cap = (int64_t)device_sm_count() * per;
-  if (blocks > cap) blocks = cap;
+  if (blocks > cap || cfg.total_windows_dev) blocks = cap;
   if (blocks < 1) blocks = 1;
   note_launch();
   kern<<<(unsigned)blocks, kStreamThreads, 0, st>>>(s_dev, single, win_series, total_windows, fp, lp, work,
-                                                     cfg.window_bytes / (int64_t)sizeof(typename P::T));
+                                                     cfg.window_bytes / (int64_t)sizeof(typename P::T),
+                                                     cfg.total_windows_dev);
   return cudaGetLastError();
 }
 
@@ -526,7 +528,7 @@ static cudaError_t launch_pol_sm(const SeriesDev& single, int64_t total_windows,
   if (blocks < 1) blocks = 1;
   note_launch();
   kern<<<(unsigned)blocks, kStreamThreads, 0, st>>>(nullptr, single, nullptr, total_windows, fp, lp, work,
-                                                     kWindowBytes / (int64_t)sizeof(typename P::T));
+                                                     kWindowBytes / (int64_t)sizeof(typename P::T), nullptr);
   return cudaGetLastError();
 }
 

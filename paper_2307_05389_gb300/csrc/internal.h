@@ -59,6 +59,10 @@ inline int64_t window_elems(tsds_dtype y_dtype) { return kWindowBytes / dtype_si
 struct StreamConfig {
   int64_t window_bytes = kWindowBytes;  // bytes of y per warp claim: a multiple of 16, >= 4096
   int ctas_per_sm = 0;                  // 0: as many as fit
+  // When set, the number of windows is read from device memory here (the
+  // server resolves query ranges on the device) and the full persistent grid
+  // is launched.
+  const int64_t* total_windows_dev = nullptr;
 };
 
 // ---- launchers (each returns the launch's cudaError_t)

@@ -38,27 +38,8 @@ namespace tsds {
 typedef unsigned __int128 u128;
 
 constexpr int kChainThreads = 256;
-constexpr int kTableMaxK = 32;      // table mode when every bucket has <= 32 points
+constexpr int kTableMaxK = kLttbTableMaxK;  // table mode when every bucket has <= 32 points
 constexpr int kPrefetchMaxK = 4096; // chain prefetches buckets up to this size (48 B/point, two buffers)
-
-// One LTTB problem over m binary64 points.
-struct LttbJob {
-  const double* px;      // m x values
-  const double* py;      // m y values
-  const int64_t* m_dev;  // number of points on the device, or null (m_host)
-  int64_t m_host;
-  int64_t B;             // n_out - 2
-  int64_t K;             // bound on any bucket's size: ceil((m_max - 2) / B)
-  int nan;
-  int mode;              // 0: table, 1: filtered chain
-  const int64_t* R;      // point -> output index (null: index + bias)
-  int64_t bias;
-  double2* means;        // B+1 entries
-  int32_t* table;        // table mode: B*K picks, relative to the bucket start
-  float2* p32;           // chain mode: m points relative to their bucket's first point
-  int64_t* out;
-  int64_t* out_count;
-};
 
 __device__ __forceinline__ int64_t job_m(const LttbJob& J) { return J.m_dev ? *J.m_dev : J.m_host; }
 
@@ -143,18 +124,6 @@ __device__ __forceinline__ void amax_warp(uint64_t& k, int64_t& i) {
 }
 
 // ---------------------------------------------------------------- points and means
-
-struct PointsJob {
-  const void* x;
-  int x_dtype;
-  const void* y;
-  int y_dtype;
-  const int64_t* R;      // gather through R (MinMaxLTTB) or null
-  const int64_t* m_dev;
-  int64_t m_host;
-  double* px;
-  double* py;
-};
 
 // px[k] = x[i] or i, py[k] = y[i], with i = R[k] or k.
 __global__ void k_points(const PointsJob* __restrict__ jobs) {
@@ -488,22 +457,22 @@ static unsigned grid_for(int64_t n, int per_sm = 8) {
   return (unsigned)blocks;
 }
 
-// Scratch bytes one LTTB job needs besides its points.
-static size_t job_scratch(int64_t m_max, int64_t B, int64_t K, int mode) {
+size_t lttb_job_scratch(int64_t m_max, int64_t B, int64_t K, int mode) {
   size_t s = align_up((size_t)(B + 1) * sizeof(double2), 256);
   if (mode == 0) s += align_up((size_t)B * (size_t)K * 4, 256);
   else s += align_up((size_t)m_max * sizeof(float2), 256);
   return s;
 }
 
-// Runs the LTTB kernels for `count` jobs whose points are already in place;
-// scratch for means / table / p32 is carved from `scratch`.
-static tsds_status run_jobs(LttbJob* jobs_host, int count, int64_t max_B, int64_t max_m, int64_t max_K_chain,
-                            cudaStream_t st) {
-  Scratch dj;
-  TSDS_CK(scratch_alloc(dj, (size_t)count * sizeof(LttbJob), st));
-  LttbJob* jobs_dev = static_cast<LttbJob*>(dj.p);
-  TSDS_CK(cudaMemcpyAsync(jobs_dev, jobs_host, (size_t)count * sizeof(LttbJob), cudaMemcpyHostToDevice, st));
+tsds_status launch_points_jobs(const PointsJob* jobs_dev, int count, int64_t max_m, cudaStream_t st) {
+  note_launch();
+  k_points<<<dim3(grid_for(max_m), (unsigned)count), 256, 0, st>>>(jobs_dev);
+  TSDS_CK(cudaGetLastError());
+  return TSDS_OK;
+}
+
+tsds_status run_lttb_jobs(const LttbJob* jobs_host, const LttbJob* jobs_dev, int count, int64_t max_B,
+                          int64_t max_m, int64_t max_K_chain, cudaStream_t st) {
   bool any_table = false, any_chain = false;
   for (int i = 0; i < count; ++i) (jobs_host[i].mode == 0 ? any_table : any_chain) = true;
   dim3 gm(grid_for(max_B, 4), (unsigned)count);
@@ -555,13 +524,16 @@ static tsds_status lttb_points_core(const double* px, const double* py, const in
   J.out = out;
   J.out_count = out_count;
   Scratch s;
-  TSDS_CK(scratch_alloc(s, job_scratch(m_max, J.B, J.K, J.mode), st));
+  const size_t js = lttb_job_scratch(m_max, J.B, J.K, J.mode);
+  TSDS_CK(scratch_alloc(s, js + align_up(sizeof(LttbJob), 256), st));
   char* p = static_cast<char*>(s.p);
   J.means = reinterpret_cast<double2*>(p);
   p += align_up((size_t)(J.B + 1) * sizeof(double2), 256);
   if (J.mode == 0) J.table = reinterpret_cast<int32_t*>(p);
   else J.p32 = reinterpret_cast<float2*>(p);
-  return run_jobs(&J, 1, J.B, m_max, J.mode == 1 ? J.K : 0, st);
+  LttbJob* jd = reinterpret_cast<LttbJob*>(static_cast<char*>(s.p) + js);
+  TSDS_CK(cudaMemcpyAsync(jd, &J, sizeof J, cudaMemcpyHostToDevice, st));
+  return run_lttb_jobs(&J, jd, 1, J.B, m_max, J.mode == 1 ? J.K : 0, st);
 }
 
 static tsds_status points(const void* x, tsds_dtype x_dtype, const void* y, tsds_dtype y_dtype, const int64_t* R,

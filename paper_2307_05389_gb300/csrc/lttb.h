@@ -1,4 +1,5 @@
-// lttb.h -- host entry points of the LTTB and MinMaxLTTB pipelines.
+// lttb.h -- host entry points of the LTTB and MinMaxLTTB pipelines, and the
+// job descriptors the batched server reuses.
 #pragma once
 #include "internal.h"
 
@@ -16,5 +17,50 @@ tsds_status run_lttb(const void* x, tsds_dtype x_dtype, const void* y, tsds_dtyp
 tsds_status run_minmaxlttb(const void* x, tsds_dtype x_dtype, const void* y, tsds_dtype y_dtype,
                            int64_t n, int64_t n_out, int64_t minmax_ratio, tsds_nan_mode nan,
                            int64_t* out, int64_t* out_count, cudaStream_t st);
+
+// One LTTB problem over m binary64 points (see lttb.cu).
+struct LttbJob {
+  const double* px;      // m x values
+  const double* py;      // m y values
+  const int64_t* m_dev;  // number of points on the device, or null (m_host)
+  int64_t m_host;
+  int64_t B;             // n_out - 2
+  int64_t K;             // bound on any bucket's size: ceil((m_max - 2) / B)
+  int nan;
+  int mode;              // 0: transition table (K <= kLttbTableMaxK), 1: filtered chain
+  const int64_t* R;      // point -> output index (null: index + bias)
+  int64_t bias;
+  double2* means;        // B+1 entries
+  int32_t* table;        // table mode: B*K picks, relative to the bucket start
+  float2* p32;           // chain mode: m points relative to their bucket's first point
+  int64_t* out;
+  int64_t* out_count;
+};
+
+// Gathers points as binary64: px[k] = x[i] or i, py[k] = y[i], i = R[k] or k.
+struct PointsJob {
+  const void* x;
+  int x_dtype;
+  const void* y;
+  int y_dtype;
+  const int64_t* R;
+  const int64_t* m_dev;
+  int64_t m_host;
+  double* px;
+  double* py;
+};
+
+constexpr int kLttbTableMaxK = 32;
+
+// Scratch bytes a job needs for means and table / p32 (besides its points).
+size_t lttb_job_scratch(int64_t m_max, int64_t B, int64_t K, int mode);
+
+// Runs the LTTB kernels for jobs already filled in (device memory for their
+// points and scratch in place); jobs_dev must hold a copy of jobs_host.
+tsds_status run_lttb_jobs(const LttbJob* jobs_host, const LttbJob* jobs_dev, int count, int64_t max_B,
+                          int64_t max_m, int64_t max_K_chain, cudaStream_t st);
+
+// k_points over `count` jobs in device memory.
+tsds_status launch_points_jobs(const PointsJob* jobs_dev, int count, int64_t max_m, cudaStream_t st);
 
 }  // namespace tsds

@@ -1,0 +1,762 @@
+// server.cu -- the served form: viewport queries over resident series with
+// continuous batching.
+//
+// The paper's setting is interactive exploration, where every zoom or pan
+// re-downsamples the visible range (Section 1) and the downsampling itself
+// becomes the bottleneck at scale.  Here a host thread owns a queue of
+// queries (series, x range or index range, n_out = pixel width, algorithm)
+// and keeps up to `streams` batches in flight on the GPU.  Whenever a batch
+// finishes, queued queries are admitted into the next batch while its slot
+// count and the device-memory budget allow, so requests that arrive while
+// others run join the next launch instead of waiting for a drain.
+//
+// One batch is one launch sequence on its stream: the ranges are resolved on
+// the device (a warp search of x per query), each query becomes a binned
+// sub-series with an index offset, the window numbering is scanned on the
+// device, the shared binned kernels run with the window count read from
+// device memory, MinMaxLTTB queries continue through the LTTB job kernels,
+// and one device-to-host copy returns every result.  A host callback on the
+// stream marks the batch done.
+#include <cuda_runtime.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "device.cuh"
+#include "internal.h"
+#include "lttb.h"
+
+namespace tsds {
+
+// One admitted query as the batch kernels see it.
+struct QueryDev {
+  const void* y;
+  const void* x;
+  int64_t n;          // series length
+  int32_t algo;
+  int32_t nan;
+  int32_t by_x;
+  int32_t pad;
+  double x_lo, x_hi;
+  int64_t lo, hi;     // index range (by_x == 0)
+  int64_t n_out;
+  int64_t n_sel;      // MinMaxLTTB preselection size
+  int64_t* out;       // n_out entries
+  int64_t* info;      // [count, L, lo, k, m] (count = selected indices)
+  int64_t* R;         // MinMaxLTTB points (global indices)
+};
+
+constexpr int kInfoSlots = 8;
+
+template <class X>
+__device__ __forceinline__ double xval(const void* x, int64_t j) {
+  return (double)static_cast<const X*>(x)[j];
+}
+__device__ __forceinline__ double x_as_double(const void* x, int dt, int64_t j) {
+  switch (dt) {
+    case TSDS_I8: return xval<int8_t>(x, j);
+    case TSDS_I16: return xval<int16_t>(x, j);
+    case TSDS_I32: return xval<int32_t>(x, j);
+    case TSDS_I64: return (double)static_cast<const long long*>(x)[j];
+    case TSDS_U8: return xval<uint8_t>(x, j);
+    case TSDS_U16: return xval<uint16_t>(x, j);
+    case TSDS_U32: return xval<uint32_t>(x, j);
+    case TSDS_U64: return (double)static_cast<const unsigned long long*>(x)[j];
+    case TSDS_F16: return (double)__half2float(static_cast<const __half*>(x)[j]);
+    case TSDS_F32: return xval<float>(x, j);
+    default: return xval<double>(x, j);
+  }
+}
+
+// One warp per query: resolve [lo, hi) and fill the binned descriptor.
+__global__ void k_resolve(const QueryDev* __restrict__ qd, SeriesDev* __restrict__ sd, int64_t* __restrict__ windows,
+                          int count, int x_dtype, int y_size, int x_size, int64_t welems) {
+  const int lane = threadIdx.x & 31;
+  const int q = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (q >= count) return;
+  const QueryDev Q = qd[q];
+  int64_t lo, hi;
+  if (Q.by_x) {
+    lo = warp_lower_bound(0, Q.n, [&](int64_t j) { return x_as_double(Q.x, x_dtype, j) >= Q.x_lo; });
+    hi = warp_lower_bound(0, Q.n, [&](int64_t j) { return x_as_double(Q.x, x_dtype, j) > Q.x_hi; });
+    if (hi < lo) hi = lo;
+  } else {
+    lo = min(max(Q.lo, (int64_t)0), Q.n);
+    hi = min(max(Q.hi, lo), Q.n);
+  }
+  if (lane != 0) return;
+  const int64_t L = hi - lo;
+  SeriesDev S;
+  memset(&S, 0, sizeof S);
+  int64_t off, per = Q.algo == TSDS_ALGO_M4 ? 4 : 2;
+  if (Q.algo == 2) {   // MinMaxLTTB: MinMax over the interior, results into R[1..]
+    const int64_t n_in = L > 2 ? L - 2 : 0;
+    off = lo + 1;
+    S.n = n_in;
+    S.nb = (L > Q.n_out && Q.n_sel < n_in) ? Q.n_sel / 2 : 0;
+    S.idx_bias = lo + 1;
+    S.out = Q.R + 1;
+    S.out_count = Q.info + 3;
+  } else {
+    off = lo;
+    S.n = L;
+    S.nb = L > Q.n_out ? Q.n_out / per : 0;
+    S.idx_bias = lo;
+    S.out = Q.out;
+    S.out_count = Q.info;
+  }
+  if (S.n > 0) {
+    S.y = static_cast<const char*>(Q.y) + off * y_size;
+    S.x = Q.x ? static_cast<const char*>(Q.x) + off * x_size : nullptr;
+  }
+  // scratch pointers were placed by the host into sd[q] already: keep them
+  SeriesDev& D = sd[q];
+  D.y = S.y;
+  D.x = S.x;
+  D.n = S.n;
+  D.nb = S.nb;
+  D.idx_bias = S.idx_bias;
+  D.out = S.out;
+  D.out_count = S.out_count;
+  windows[q] = S.nb > 0 ? (S.n + welems - 1) / welems : 0;
+  Q.info[1] = L;
+  Q.info[2] = lo;
+}
+
+// Exclusive scan of the per-query window counts into the descriptors' window
+// bases; the total goes to *total.  One CTA.
+__global__ void k_scan_windows(SeriesDev* __restrict__ sd, const int64_t* __restrict__ windows, int count,
+                               int64_t* __restrict__ total) {
+  __shared__ int64_t part[1024];
+  const int t = threadIdx.x;
+  const int per = (count + blockDim.x - 1) / blockDim.x;
+  const int a = min(t * per, count), b = min(a + per, count);
+  int64_t s = 0;
+  for (int i = a; i < b; ++i) s += windows[i];
+  part[t] = s;
+  __syncthreads();
+  if (t == 0) {
+    int64_t run = 0;
+    for (int i = 0; i < (int)blockDim.x; ++i) { const int64_t v = part[i]; part[i] = run; run += v; }
+    *total = run;
+  }
+  __syncthreads();
+  int64_t run = part[t];
+  for (int i = a; i < b; ++i) { sd[i].win_base = run; run += windows[i]; }
+}
+
+// MinMaxLTTB: complete the point set R = [lo, preselection..., hi-1] and its
+// size m; small ranges keep every point.
+__global__ void k_close_queries(const QueryDev* __restrict__ qd, int count) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= count) return;
+  const QueryDev Q = qd[q];
+  if (Q.algo != 2) return;
+  const int64_t L = Q.info[1], lo = Q.info[2];
+  int64_t m;
+  if (L <= 2) {
+    for (int64_t i = 0; i < L; ++i) Q.R[i] = lo + i;
+    m = L;
+  } else {
+    const int64_t k = Q.info[3];
+    Q.R[0] = lo;
+    Q.R[k + 1] = lo + L - 1;
+    m = k + 2;
+  }
+  Q.info[4] = m;
+}
+
+// Copies the LTTB count into the query's result count (MinMaxLTTB writes its
+// count through the job's out_count, which points at info[0]).
+}  // namespace tsds
+
+using namespace tsds;
+
+namespace {
+
+double now_us() {
+  return std::chrono::duration<double, std::micro>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+size_t up256(size_t v) { return (v + 255) / 256 * 256; }
+
+struct SeriesHost {
+  const void* x;
+  const void* y;
+  int64_t n;
+};
+
+struct Ticket {
+  tsds_query q;
+  double t_submit = 0, t_done = 0;
+  bool done = false;
+  tsds_status status = TSDS_OK;
+  int64_t L = 0;
+  std::vector<int64_t> result;
+};
+
+struct Slot;
+
+struct Server {
+  tsds_server_config cfg;
+  tsds_dtype x_dtype, y_dtype;
+  int device = 0;
+  std::vector<SeriesHost> series;
+  std::mutex mu;
+  std::condition_variable cv, cv_done;
+  std::deque<int64_t> queue;
+  std::unordered_map<int64_t, Ticket> tickets;
+  std::vector<Slot*> slots;
+  std::thread th;
+  bool stop = false;
+  int64_t next_id = 1;
+  int64_t inflight_bytes = 0;
+  // statistics
+  std::vector<double> latencies;
+  int64_t submitted = 0, completed = 0, batches = 0, points = 0;
+  double t_first = -1, t_last = 0;
+  tsds_status sticky = TSDS_OK;
+  char sticky_msg[256] = "";
+};
+
+struct Slot {
+  Server* srv = nullptr;
+  cudaStream_t st = nullptr;
+  bool busy = false;
+  volatile bool finished = false;
+  std::vector<int64_t> ids;
+  std::vector<size_t> out_off;   // per query: offset (in int64) of its results in the output slab
+  std::vector<int64_t> n_outs;
+  size_t bytes = 0;              // scratch admitted
+  size_t out_words = 0;
+  void* pin_in = nullptr;
+  size_t pin_in_cap = 0;
+  int64_t* pin_out = nullptr;
+  size_t pin_out_cap = 0;
+};
+
+void CUDART_CB on_batch_done(void* p) {
+  Slot* s = static_cast<Slot*>(p);
+  {
+    std::lock_guard<std::mutex> lk(s->srv->mu);
+    s->finished = true;
+  }
+  s->srv->cv.notify_all();
+}
+
+int64_t nb_of(const tsds_query& q);
+int64_t lttb_m_max(const tsds_query& q);
+
+// Device scratch one query may need (upper bound: its range may be the whole series).
+size_t query_bytes(const Server& S, const tsds_query& q, int64_t window_bytes) {
+  const int64_t n = S.series[(size_t)q.series].n;
+  const int64_t ys = dtype_size(S.y_dtype);
+  const int64_t nb = nb_of(q);
+  const int64_t windows = (n * ys + window_bytes - 1) / window_bytes + 1;
+  size_t b = sizeof(QueryDev) + sizeof(SeriesDev) + 8 + up256((size_t)(nb + 1) * 8) + up256((size_t)nb * 16) +
+             (size_t)nb * 4 + (size_t)windows * (4 + 2 * sizeof(Piece)) + 1024;
+  b += (size_t)(q.n_out + kInfoSlots) * 8;
+  if (q.algo == 2) {
+    const int64_t m_max = lttb_m_max(q);
+    const int64_t B = q.n_out - 2;
+    const int64_t K = (m_max - 2 + B - 1) / B;
+    b += up256((size_t)m_max * 8 * 3) + lttb_job_scratch(m_max, B, K, K <= kLttbTableMaxK ? 0 : 1) +
+         sizeof(LttbJob) + sizeof(PointsJob) + 512;
+  }
+  return b;
+}
+
+#define SV_CK(call)                                                                   \
+  do {                                                                                \
+    cudaError_t e_ = (call);                                                          \
+    if (e_ != cudaSuccess) {                                                          \
+      snprintf(err, errlen, "%s: %s", #call, cudaGetErrorString(e_));                 \
+      return e_ == cudaErrorMemoryAllocation ? TSDS_ENOMEM : TSDS_ECUDA;              \
+    }                                                                                 \
+  } while (0)
+
+int64_t nb_of(const tsds_query& q) {
+  if (q.algo == 2) return (2 * ((q.n_out * q.minmax_ratio) / 2)) / 2;
+  return q.n_out / (q.algo == TSDS_ALGO_M4 ? 4 : 2);
+}
+
+int64_t lttb_m_max(const tsds_query& q) { return std::max(2 * ((q.n_out * q.minmax_ratio) / 2) + 2, q.n_out) + 2; }
+
+// Enqueues one batch on the slot's stream.  Called without the server lock:
+// everything it needs from the server is in `qs` and `ser` (the series of
+// each query) and the server's fixed dtypes.
+tsds_status launch_batch(const Server& S, Slot& sl, const std::vector<tsds_query>& qs,
+                         const std::vector<SeriesHost>& ser, bool has_x, char* err, size_t errlen) {
+  const int count = (int)qs.size();
+  const int64_t window_bytes = kWindowBytes;
+  const int64_t ys = dtype_size(S.y_dtype);
+  const int64_t welems = window_bytes / ys;
+  std::vector<int> lt;
+  for (int i = 0; i < count; ++i)
+    if (qs[i].algo == 2) lt.push_back(i);
+  const int nlt = (int)lt.size();
+  // ---- device layout: the descriptor block first, in the same order as the
+  // pinned staging block, so one copy places all descriptors
+  const size_t sz_q = (size_t)count * sizeof(QueryDev), sz_s = (size_t)count * sizeof(SeriesDev);
+  const size_t sz_l = (size_t)nlt * sizeof(LttbJob), sz_p = (size_t)nlt * sizeof(PointsJob);
+  const size_t off_q = 0, off_sd = off_q + sz_q, off_ljobs = off_sd + sz_s, off_pjobs = off_ljobs + sz_l;
+  const size_t in_bytes = off_pjobs + sz_p;
+  size_t o = up256(in_bytes);
+  const size_t off_win = o; o = up256(o + (size_t)count * 8 + 8);
+  std::vector<size_t> off_edges(count), off_res(count), off_cnt(count), off_R(count), off_lt(count);
+  int64_t max_nb = 0, win_ub = 0;
+  for (int i = 0; i < count; ++i) {
+    const int64_t nb = nb_of(qs[i]);
+    max_nb = std::max(max_nb, nb);
+    off_edges[i] = o; o = up256(o + (size_t)(nb + 1) * 8);
+    off_res[i] = o;   o = up256(o + (size_t)nb * 16);
+    win_ub += (ser[i].n * ys + window_bytes - 1) / window_bytes + 1;
+  }
+  const size_t zero_begin = o;    // piece counters and the work counter start at zero
+  for (int i = 0; i < count; ++i) { off_cnt[i] = o; o += (size_t)nb_of(qs[i]) * 4; }
+  o = up256(o);
+  const size_t off_work = o; o = up256(o + sizeof(WorkCounters));
+  const size_t zero_end = o;
+  const size_t off_map = o;   o = up256(o + (size_t)win_ub * 4);
+  const size_t off_first = o; o = up256(o + (size_t)win_ub * sizeof(Piece));
+  const size_t off_last = o;  o = up256(o + (size_t)win_ub * sizeof(Piece));
+  // results: per query n_out indices then kInfoSlots info words, contiguous for one copy back
+  const size_t off_out = o;
+  sl.out_off.assign(count, 0);
+  sl.n_outs.assign(count, 0);
+  size_t words = 0;
+  for (int i = 0; i < count; ++i) {
+    sl.out_off[i] = words;
+    sl.n_outs[i] = qs[i].n_out;
+    words += (size_t)qs[i].n_out + kInfoSlots;
+  }
+  o = up256(o + words * 8);
+  int64_t lt_max_B = 0, lt_max_m = 0, lt_max_K_chain = 0;
+  for (int i : lt) {
+    const int64_t m_max = lttb_m_max(qs[i]);
+    const int64_t B = qs[i].n_out - 2;
+    const int64_t K = (m_max - 2 + B - 1) / B;
+    off_R[i] = o;  o = up256(o + (size_t)m_max * 8 * 3);   // R, py, px
+    off_lt[i] = o; o = up256(o + lttb_job_scratch(m_max, B, K, K <= kLttbTableMaxK ? 0 : 1));
+    lt_max_B = std::max(lt_max_B, B);
+    lt_max_m = std::max(lt_max_m, m_max);
+    if (K > kLttbTableMaxK) lt_max_K_chain = std::max(lt_max_K_chain, K);
+  }
+  const size_t total = o;
+
+  // ---- pinned staging (the slot is idle, so its buffers are free)
+  if (sl.pin_in_cap < in_bytes) {
+    if (sl.pin_in) cudaFreeHost(sl.pin_in);
+    sl.pin_in = nullptr;
+    sl.pin_in_cap = 0;
+    SV_CK(cudaMallocHost(&sl.pin_in, in_bytes * 2));
+    sl.pin_in_cap = in_bytes * 2;
+  }
+  if (sl.pin_out_cap < words) {
+    if (sl.pin_out) cudaFreeHost(sl.pin_out);
+    sl.pin_out = nullptr;
+    sl.pin_out_cap = 0;
+    SV_CK(cudaMallocHost((void**)&sl.pin_out, words * 2 * 8));
+    sl.pin_out_cap = words * 2;
+  }
+  sl.out_words = words;
+
+  Scratch scr;   // returned to the library pool in stream order when this function returns
+  SV_CK(scratch_alloc(scr, total, sl.st));
+  char* base = static_cast<char*>(scr.p);
+  char* stage = static_cast<char*>(sl.pin_in);
+  QueryDev* hq = reinterpret_cast<QueryDev*>(stage + off_q);
+  SeriesDev* hs = reinterpret_cast<SeriesDev*>(stage + off_sd);
+  LttbJob* hl = reinterpret_cast<LttbJob*>(stage + off_ljobs);
+  PointsJob* hp = reinterpret_cast<PointsJob*>(stage + off_pjobs);
+  int64_t* outbase = reinterpret_cast<int64_t*>(base + off_out);
+  for (int i = 0; i < count; ++i) {
+    const tsds_query& q = qs[i];
+    QueryDev& d = hq[i];
+    memset(&d, 0, sizeof d);
+    d.y = ser[i].y;
+    d.x = ser[i].x;
+    d.n = ser[i].n;
+    d.algo = q.algo;
+    d.nan = q.nan;
+    d.by_x = q.by_x;
+    d.x_lo = q.x_lo;
+    d.x_hi = q.x_hi;
+    d.lo = q.lo;
+    d.hi = q.hi;
+    d.n_out = q.n_out;
+    d.n_sel = q.algo == 2 ? 2 * ((q.n_out * q.minmax_ratio) / 2) : 0;
+    d.out = outbase + sl.out_off[i];
+    d.info = outbase + sl.out_off[i] + q.n_out;
+    d.R = q.algo == 2 ? reinterpret_cast<int64_t*>(base + off_R[i]) : nullptr;
+    SeriesDev& s = hs[i];
+    memset(&s, 0, sizeof s);   // k_resolve fills the range-dependent fields
+    s.edges = reinterpret_cast<int64_t*>(base + off_edges[i]);
+    s.res = reinterpret_cast<int64_t*>(base + off_res[i]);
+    s.cnt = reinterpret_cast<uint32_t*>(base + off_cnt[i]);
+  }
+  for (int t = 0; t < nlt; ++t) {
+    const int i = lt[t];
+    const tsds_query& q = qs[i];
+    const int64_t m_max = lttb_m_max(q);
+    int64_t* R = hq[i].R;
+    double* py = reinterpret_cast<double*>(R + m_max);
+    double* px = py + m_max;
+    LttbJob& J = hl[t];
+    memset(&J, 0, sizeof J);
+    J.px = px;
+    J.py = py;
+    J.m_dev = hq[i].info + 4;
+    J.B = q.n_out - 2;
+    J.K = (m_max - 2 + J.B - 1) / J.B;
+    J.nan = q.nan;
+    J.mode = J.K <= kLttbTableMaxK ? 0 : 1;
+    J.R = R;
+    J.out = hq[i].out;
+    J.out_count = hq[i].info;
+    char* ls = base + off_lt[i];
+    J.means = reinterpret_cast<double2*>(ls);
+    ls += up256((size_t)(J.B + 1) * sizeof(double2));
+    if (J.mode == 0) J.table = reinterpret_cast<int32_t*>(ls);
+    else J.p32 = reinterpret_cast<float2*>(ls);
+    PointsJob& P = hp[t];
+    memset(&P, 0, sizeof P);
+    P.x = ser[i].x;
+    P.x_dtype = S.x_dtype;
+    P.y = ser[i].y;
+    P.y_dtype = S.y_dtype;
+    P.R = R;
+    P.m_dev = hq[i].info + 4;
+    P.px = px;
+    P.py = py;
+  }
+  // ---- launches
+  cudaStream_t st = sl.st;
+  SV_CK(cudaMemcpyAsync(base, stage, in_bytes, cudaMemcpyHostToDevice, st));
+  const QueryDev* dq = reinterpret_cast<const QueryDev*>(base + off_q);
+  SeriesDev* dsd = reinterpret_cast<SeriesDev*>(base + off_sd);
+  SV_CK(cudaMemsetAsync(base + zero_begin, 0, zero_end - zero_begin, st));
+  SV_CK(cudaMemsetAsync(outbase, 0, words * 8, st));
+  int64_t* windows = reinterpret_cast<int64_t*>(base + off_win);
+  int64_t* total_dev = windows + count;
+  note_launch();
+  k_resolve<<<(count + 7) / 8, 256, 0, st>>>(dq, dsd, windows, count, (int)S.x_dtype, (int)ys,
+                                             has_x ? (int)dtype_size(S.x_dtype) : 0, welems);
+  SV_CK(cudaGetLastError());
+  note_launch();
+  k_scan_windows<<<1, 1024, 0, st>>>(dsd, windows, count, total_dev);
+  SV_CK(cudaGetLastError());
+  SV_CK(launch_window_map(dsd, count, reinterpret_cast<int32_t*>(base + off_map), S.y_dtype, st, window_bytes));
+  SV_CK(launch_edges(dsd, count, nullptr, has_x, S.x_dtype, max_nb, st));
+  SeriesDev none;
+  memset(&none, 0, sizeof none);
+  StreamConfig cfg;
+  cfg.total_windows_dev = total_dev;
+  // a batch holds one NaN mode and either M4 or the MinMax-like algorithms (the admission groups them)
+  const tsds_nan_mode nan = (tsds_nan_mode)qs[0].nan;
+  const bool m4 = qs[0].algo == TSDS_ALGO_M4;
+  SV_CK(launch_argminmax(dsd, count, none, reinterpret_cast<const int32_t*>(base + off_map), std::max<int64_t>(win_ub, 1),
+                         reinterpret_cast<Piece*>(base + off_first), reinterpret_cast<Piece*>(base + off_last),
+                         reinterpret_cast<WorkCounters*>(base + off_work), S.y_dtype, nan, st, cfg));
+  SV_CK(launch_emit(dsd, count, none, m4 ? ALGO_M4 : ALGO_MINMAX, st));
+  SV_CK(launch_iota_batched(dsd, count, st));
+  if (nlt > 0) {
+    note_launch();
+    k_close_queries<<<(count + 255) / 256, 256, 0, st>>>(dq, count);
+    SV_CK(cudaGetLastError());
+    tsds_status r = launch_points_jobs(reinterpret_cast<const PointsJob*>(base + off_pjobs), nlt, lt_max_m, st);
+    if (r != TSDS_OK) { snprintf(err, errlen, "points: %s", tsds_last_error()); return r; }
+    r = run_lttb_jobs(hl, reinterpret_cast<const LttbJob*>(base + off_ljobs), nlt, lt_max_B, lt_max_m,
+                      lt_max_K_chain, st);
+    if (r != TSDS_OK) { snprintf(err, errlen, "lttb: %s", tsds_last_error()); return r; }
+  }
+  SV_CK(cudaMemcpyAsync(sl.pin_out, outbase, words * 8, cudaMemcpyDeviceToHost, st));
+  SV_CK(cudaLaunchHostFunc(st, on_batch_done, &sl));
+  return TSDS_OK;
+}
+
+// Moves a finished slot's results into its tickets.  Server lock held.
+void reap(Server& S, Slot& sl) {
+  const double t = now_us();
+  for (size_t i = 0; i < sl.ids.size(); ++i) {
+    auto it = S.tickets.find(sl.ids[i]);
+    if (it == S.tickets.end()) continue;
+    Ticket& tk = it->second;
+    const int64_t* res = sl.pin_out + sl.out_off[i];
+    const int64_t* info = res + sl.n_outs[i];
+    int64_t c = info[0];
+    if (c < 0 || c > sl.n_outs[i]) {
+      tk.status = TSDS_EINTERNAL;
+      c = 0;
+    }
+    tk.result.assign(res, res + c);
+    tk.L = info[1];
+    tk.done = true;
+    tk.t_done = t;
+    S.latencies.push_back(t - tk.t_submit);
+    S.points += tk.L;
+    ++S.completed;
+  }
+  S.t_last = t;
+  S.inflight_bytes -= (int64_t)sl.bytes;
+  sl.bytes = 0;
+  sl.ids.clear();
+  sl.busy = false;
+  sl.finished = false;
+}
+
+void server_loop(Server* sp) {
+  Server& S = *sp;
+  cudaSetDevice(S.device);
+  char err[256];
+  std::unique_lock<std::mutex> lk(S.mu);
+  for (;;) {
+    for (Slot* sl : S.slots) {
+      if (sl->busy && sl->finished) {
+        reap(S, *sl);
+        S.cv_done.notify_all();
+      }
+    }
+    // admit queued queries into free slots (continuous batching)
+    bool blocked = false;
+    for (Slot* sl : S.slots) {
+      if (sl->busy || S.queue.empty()) continue;
+      std::vector<tsds_query> qs;
+      std::vector<int64_t> ids;
+      std::vector<SeriesHost> ser;
+      size_t bytes = 0;
+      const tsds_query& head = S.tickets[S.queue.front()].q;
+      const int nan = head.nan;
+      const bool m4 = head.algo == TSDS_ALGO_M4;
+      for (auto it = S.queue.begin(); it != S.queue.end() && (int)qs.size() < S.cfg.max_batch;) {
+        const tsds_query& q = S.tickets[*it].q;
+        if (q.nan != nan || (q.algo == TSDS_ALGO_M4) != m4) { ++it; continue; }
+        const size_t b = query_bytes(S, q, kWindowBytes);
+        const bool fits = S.inflight_bytes + (int64_t)(bytes + b) <= S.cfg.memory_budget;
+        if (!fits && !(qs.empty() && S.inflight_bytes == 0)) break;   // an oversized query runs alone when idle
+        bytes += b;
+        qs.push_back(q);
+        ser.push_back(S.series[(size_t)q.series]);
+        ids.push_back(*it);
+        it = S.queue.erase(it);
+      }
+      if (qs.empty()) { blocked = true; break; }
+      sl->ids = ids;
+      sl->bytes = bytes;
+      sl->busy = true;
+      sl->finished = false;
+      S.inflight_bytes += (int64_t)bytes;
+      ++S.batches;
+      const bool has_x = !S.series.empty() && S.series[0].x != nullptr;
+      lk.unlock();
+      const tsds_status r = launch_batch(S, *sl, qs, ser, has_x, err, sizeof err);
+      if (r != TSDS_OK) cudaStreamSynchronize(sl->st);   // no host callback was enqueued for this batch
+      lk.lock();
+      if (r != TSDS_OK) {
+        for (int64_t id : ids) {
+          Ticket& tk = S.tickets[id];
+          tk.done = true;
+          tk.status = r;
+          tk.t_done = now_us();
+        }
+        S.sticky = r;
+        snprintf(S.sticky_msg, sizeof S.sticky_msg, "%s", err);
+        S.inflight_bytes -= (int64_t)bytes;
+        sl->busy = false;
+        sl->ids.clear();
+        S.cv_done.notify_all();
+      }
+    }
+    bool any_busy = false;
+    for (Slot* sl : S.slots) any_busy |= sl->busy;
+    if (S.stop && S.queue.empty() && !any_busy) break;
+    S.cv.wait(lk, [&] {
+      if (S.stop && S.queue.empty()) return true;
+      for (Slot* sl : S.slots) {
+        if (sl->busy && sl->finished) return true;
+        if (!blocked && !sl->busy && !S.queue.empty()) return true;
+      }
+      return false;
+    });
+  }
+}
+
+}  // namespace
+
+struct tsds_server_s {
+  Server s;
+};
+
+extern "C" {
+
+tsds_status tsds_server_create(tsds_server* out, const tsds_server_config* cfg, tsds_dtype x_dtype,
+                               tsds_dtype y_dtype) {
+  if (!out) return fail(TSDS_EINVAL, "tsds_server_create: out is NULL");
+  *out = nullptr;
+  if (!dtype_valid(y_dtype)) return fail(TSDS_EINVAL, "tsds_server_create: unknown y dtype");
+  tsds_server_config c = {2, 256, (int64_t)1 << 30};
+  if (cfg) c = *cfg;
+  if (c.streams < 1 || c.streams > 16 || c.max_batch < 1 || c.max_batch > 4096 || c.memory_budget < 1)
+    return fail(TSDS_EINVAL, "tsds_server_create: streams in [1,16], max_batch in [1,4096], memory_budget > 0");
+  tsds_server_s* h = new tsds_server_s();
+  Server& S = h->s;
+  S.cfg = c;
+  S.x_dtype = x_dtype;
+  S.y_dtype = y_dtype;
+  cudaGetDevice(&S.device);
+  for (int i = 0; i < c.streams; ++i) {
+    Slot* sl = new Slot();
+    sl->srv = &S;
+    if (cudaStreamCreateWithFlags(&sl->st, cudaStreamNonBlocking) != cudaSuccess) {
+      delete sl;
+      tsds_server_destroy(h);
+      return fail(TSDS_ECUDA, "tsds_server_create: stream creation failed");
+    }
+    S.slots.push_back(sl);
+  }
+  S.th = std::thread(server_loop, &S);
+  *out = h;
+  return TSDS_OK;
+}
+
+tsds_status tsds_server_add_series(tsds_server h, const void* x, const void* y, int64_t n, int64_t* id) {
+  if (!h || !id) return fail(TSDS_EINVAL, "tsds_server_add_series: NULL argument");
+  Server& S = h->s;
+  if (n < 0 || (n > 0 && !y)) return fail(TSDS_EINVAL, "tsds_server_add_series: bad series");
+  std::lock_guard<std::mutex> lk(S.mu);
+  if (!S.series.empty() && (S.series[0].x != nullptr) != (x != nullptr))
+    return fail(TSDS_EINVAL, "tsds_server_add_series: either every series has x or none");
+  if (x && !dtype_valid(S.x_dtype)) return fail(TSDS_EINVAL, "tsds_server_add_series: the server's x dtype is invalid");
+  S.series.push_back(SeriesHost{x, y, n});
+  *id = (int64_t)S.series.size() - 1;
+  return TSDS_OK;
+}
+
+tsds_status tsds_server_submit(tsds_server h, const tsds_query* q, int64_t* ticket) {
+  if (!h || !q || !ticket) return fail(TSDS_EINVAL, "tsds_server_submit: NULL argument");
+  Server& S = h->s;
+  std::lock_guard<std::mutex> lk(S.mu);
+  if (q->series < 0 || q->series >= (int64_t)S.series.size()) return fail(TSDS_EINVAL, "tsds_server_submit: unknown series");
+  if (q->algo == TSDS_ALGO_MINMAX) {
+    if (q->n_out < 2 || q->n_out % 2) return fail(TSDS_EINVAL, "tsds_server_submit: MinMax needs an even n_out >= 2");
+  } else if (q->algo == TSDS_ALGO_M4) {
+    if (q->n_out < 4 || q->n_out % 4) return fail(TSDS_EINVAL, "tsds_server_submit: M4 needs n_out a multiple of 4");
+  } else if (q->algo == 2) {
+    if (q->n_out < 3 || q->minmax_ratio < 1 || q->minmax_ratio > (INT64_MAX / 4) / q->n_out)
+      return fail(TSDS_EINVAL, "tsds_server_submit: MinMaxLTTB needs n_out >= 3 and minmax_ratio >= 1");
+  } else {
+    return fail(TSDS_EINVAL, "tsds_server_submit: unknown algorithm %d", q->algo);
+  }
+  if (q->nan != TSDS_NAN_PROPAGATE && q->nan != TSDS_NAN_IGNORE) return fail(TSDS_EINVAL, "tsds_server_submit: NaN mode");
+  if (q->by_x && !S.series[(size_t)q->series].x) return fail(TSDS_EINVAL, "tsds_server_submit: x range on a series without x");
+  const int64_t id = S.next_id++;
+  Ticket& t = S.tickets[id];
+  t.q = *q;
+  t.t_submit = now_us();
+  if (S.t_first < 0) S.t_first = t.t_submit;
+  S.queue.push_back(id);
+  ++S.submitted;
+  *ticket = id;
+  S.cv.notify_all();
+  return TSDS_OK;
+}
+
+tsds_status tsds_server_result(tsds_server h, int64_t ticket, int64_t timeout_us, int64_t* out, int64_t cap,
+                               int64_t* count, int* done, double* latency_us) {
+  if (!h) return fail(TSDS_EINVAL, "tsds_server_result: NULL server");
+  Server& S = h->s;
+  std::unique_lock<std::mutex> lk(S.mu);
+  auto it = S.tickets.find(ticket);
+  if (it == S.tickets.end()) return fail(TSDS_EINVAL, "tsds_server_result: unknown ticket %lld", (long long)ticket);
+  if (!it->second.done && timeout_us != 0) {
+    auto pred = [&] { return S.tickets[ticket].done; };
+    if (timeout_us < 0) S.cv_done.wait(lk, pred);
+    else S.cv_done.wait_for(lk, std::chrono::microseconds(timeout_us), pred);
+    it = S.tickets.find(ticket);
+  }
+  Ticket& t = it->second;
+  if (done) *done = t.done ? 1 : 0;
+  if (!t.done) return TSDS_OK;
+  if (t.status != TSDS_OK) {
+    const tsds_status s = t.status;
+    S.tickets.erase(it);
+    return fail(s, "tsds_server_result: the batch failed: %s", S.sticky_msg);
+  }
+  const int64_t c = (int64_t)t.result.size();
+  if (count) *count = c;
+  if (latency_us) *latency_us = t.t_done - t.t_submit;
+  if (out) {
+    if (cap < c) return fail(TSDS_EINVAL, "tsds_server_result: out holds %lld, result has %lld", (long long)cap, (long long)c);
+    memcpy(out, t.result.data(), (size_t)c * 8);
+  }
+  S.tickets.erase(it);
+  return TSDS_OK;
+}
+
+tsds_status tsds_server_stats_get(tsds_server h, tsds_server_stats* st) {
+  if (!h || !st) return fail(TSDS_EINVAL, "tsds_server_stats_get: NULL argument");
+  Server& S = h->s;
+  std::lock_guard<std::mutex> lk(S.mu);
+  memset(st, 0, sizeof *st);
+  st->submitted = S.submitted;
+  st->completed = S.completed;
+  st->batches = S.batches;
+  st->points = S.points;
+  st->bytes = S.points * dtype_size(S.y_dtype);
+  st->span_s = S.t_first < 0 ? 0.0 : (S.t_last - S.t_first) / 1e6;
+  if (!S.latencies.empty()) {
+    std::vector<double> v = S.latencies;
+    std::sort(v.begin(), v.end());
+    auto pct = [&](double p) { return v[(size_t)std::min<double>(v.size() - 1, p * (v.size() - 1) + 0.5)]; };
+    st->p50_us = pct(0.50);
+    st->p99_us = pct(0.99);
+    double s = 0;
+    for (double x : v) s += x;
+    st->mean_us = s / v.size();
+    st->max_us = v.back();
+  }
+  return TSDS_OK;
+}
+
+tsds_status tsds_server_reset_stats(tsds_server h) {
+  if (!h) return fail(TSDS_EINVAL, "tsds_server_reset_stats: NULL server");
+  Server& S = h->s;
+  std::lock_guard<std::mutex> lk(S.mu);
+  S.latencies.clear();
+  S.submitted = S.completed = S.batches = S.points = 0;
+  S.t_first = -1;
+  S.t_last = 0;
+  return TSDS_OK;
+}
+
+tsds_status tsds_server_destroy(tsds_server h) {
+  if (!h) return TSDS_OK;
+  Server& S = h->s;
+  {
+    std::lock_guard<std::mutex> lk(S.mu);
+    S.stop = true;
+  }
+  S.cv.notify_all();
+  if (S.th.joinable()) S.th.join();
+  for (Slot* sl : S.slots) {
+    if (sl->st) {
+      cudaStreamSynchronize(sl->st);
+      cudaStreamDestroy(sl->st);
+    }
+    if (sl->pin_in) cudaFreeHost(sl->pin_in);
+    if (sl->pin_out) cudaFreeHost(sl->pin_out);
+    delete sl;
+  }
+  delete h;
+  return TSDS_OK;
+}
+
+}  // extern "C"

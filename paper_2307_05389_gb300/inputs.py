@@ -149,6 +149,19 @@ def geometric_x_cuda(n: int, seed: int = 0, p: float = 0.5, device="cuda"):
     return out
 
 
+def exponential_x_cuda(n: int, seed: int = 0, device="cuda"):
+    import torch
+    out = torch.empty(n, dtype=torch.float64, device=device)
+    carry = torch.zeros((), dtype=torch.float64, device=device)
+    for c, lo in enumerate(range(0, n, _CHUNK)):
+        hi = min(n, lo + _CHUNK)
+        gaps = torch.empty(hi - lo, dtype=torch.float64, device=device).exponential_(1.0, generator=_gen(device, seed, c))
+        w = torch.cumsum(gaps, 0) + carry
+        carry = w[-1].clone()
+        out[lo:hi] = w
+    return out
+
+
 def quarter_range_cuda(n: int, dtype: str, seed: int = 0, device="cuda"):
     import torch
     dt = np.dtype(dtype)
