@@ -159,9 +159,12 @@ tsds_status tsds_plan_create(tsds_plan* plan, tsds_algo algo, const tsds_series*
  * share its scratch: do not let two of them overlap on the GPU. */
 tsds_status tsds_plan_execute(tsds_plan plan, void* stream);
 
-/* The launch shape the plan uses and its sizes (any pointer may be NULL). */
+/* The launch shape the plan uses and its sizes (any pointer may be NULL):
+ * window bytes, CTAs per SM (0: as many as fit), windows, scratch bytes, and
+ * the kernel variant of the streaming pass it runs (1, 2 or 3 as in
+ * tsds_stream_variant). */
 tsds_status tsds_plan_info(tsds_plan plan, int64_t* window_bytes, int* ctas_per_sm, int64_t* windows,
-                           int64_t* scratch_bytes);
+                           int64_t* scratch_bytes, int* variant);
 
 /* Waits for the device to finish queued work, then frees the plan. */
 tsds_status tsds_plan_destroy(tsds_plan plan);
@@ -276,6 +279,31 @@ int64_t tsds_kernel_launches(void);
  * MinMaxLTTB preselection) is bracketed by two CUDA events recorded on the
  * call's stream.  Recording adds no synchronisation. */
 void tsds_timing_enable(int on);
+
+/* Failure-detection check: runs one kernel whose shared-memory barrier wait
+ * is never satisfied and gives up after `rounds` bounded wait rounds, the same
+ * way the streaming pass gives up on a copy that never lands; returns the
+ * status the kernel recorded (TSDS_ETIMEOUT when the bound works).  Nothing is
+ * copied and the context stays usable.  Synchronises `stream`.  When the
+ * streaming pass itself records a timeout, the affected call reports
+ * *out_count = -TSDS_ETIMEOUT. */
+tsds_status tsds_check_wait_timeout(unsigned rounds, void* stream);
+
+/* Kernel variant of the streaming argmin/argmax pass for every later call in
+ * the process (no counterpart in the paper, whose CPU kernel has one form):
+ *   0  automatic (the default): per launch, by the bytes-weighted mean bin
+ *      size: variant 3 below 1.5 KB (4-byte y), 1 KB (2-byte) or 512 bytes
+ *      (1-byte), variant 2 otherwise;
+ *   1  shared-memory ring (bulk async copies into shared memory, one warp
+ *      per bin);
+ *   2  register streaming, one warp per bin;
+ *   3  register streaming with bins split across lanes (y dtypes of up to
+ *      32 bits; 64-bit dtypes run variant 2).
+ * The environment variable TSDS_STREAM_VARIANT=ring|ldg|seg sets 1, 2 or 3
+ * when the library loads.  Results are identical; only speed differs.
+ * Batched plans that were tuned keep the variant they chose.  Returns the
+ * previous setting, or -1 (and sets nothing) when `variant` is not 0..3. */
+int tsds_stream_variant(int variant);
 
 /* Waits for the launches recorded since the previous read, writes the sum of
  * their device durations in milliseconds to *total_ms (may be NULL) and their

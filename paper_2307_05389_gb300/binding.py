@@ -62,18 +62,22 @@ def load(path: str = LIB_PATH):
     lib.tsds_plan_execute.argtypes = [p, p]
     lib.tsds_plan_execute.restype = c_int
     lib.tsds_plan_info.argtypes = [p, ctypes.POINTER(i64), ctypes.POINTER(c_int), ctypes.POINTER(i64),
-                                   ctypes.POINTER(i64)]
+                                   ctypes.POINTER(i64), ctypes.POINTER(c_int)]
     lib.tsds_plan_info.restype = c_int
     lib.tsds_plan_destroy.argtypes = [p]
     lib.tsds_plan_destroy.restype = c_int
     lib.tsds_minmax_noalloc.argtypes = [p, c_int, p, c_int, i64, i64, c_int, p, p, p]
     lib.tsds_minmax_noalloc.restype = c_int
+    lib.tsds_check_wait_timeout.argtypes = [ctypes.c_uint, p]
+    lib.tsds_check_wait_timeout.restype = c_int
     lib.tsds_kernel_launches.argtypes = []
     lib.tsds_kernel_launches.restype = i64
     lib.tsds_timing_enable.argtypes = [c_int]
     lib.tsds_timing_enable.restype = None
     lib.tsds_timing_read.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)]
     lib.tsds_timing_read.restype = c_int
+    lib.tsds_stream_variant.argtypes = [c_int]
+    lib.tsds_stream_variant.restype = c_int
     _lib = lib
     return lib
 
@@ -84,6 +88,19 @@ def tsds_kernel_launches() -> int:
 
 def tsds_timing_enable(on: bool) -> None:
     load().tsds_timing_enable(1 if on else 0)
+
+
+STREAM_VARIANTS = {"auto": 0, "ring": 1, "ldg": 2, "seg": 3}
+
+
+def tsds_stream_variant(variant) -> str:
+    """Sets the streaming-pass kernel variant ("auto", "ring", "ldg", "seg" or 0..3)
+    for later calls; returns the previous one by name."""
+    v = STREAM_VARIANTS[variant] if isinstance(variant, str) else int(variant)
+    prev = load().tsds_stream_variant(v)
+    if prev < 0:
+        raise ValueError(f"unknown stream variant {variant!r}")
+    return {b: a for a, b in STREAM_VARIANTS.items()}[prev]
 
 
 def tsds_timing_read():
@@ -148,8 +165,8 @@ def tsds_plan_execute(plan, stream):
     return load().tsds_plan_execute(plan, stream)
 
 
-def tsds_plan_info(plan, window_bytes, ctas_per_sm, windows, scratch_bytes):
-    return load().tsds_plan_info(plan, window_bytes, ctas_per_sm, windows, scratch_bytes)
+def tsds_plan_info(plan, window_bytes, ctas_per_sm, windows, scratch_bytes, variant):
+    return load().tsds_plan_info(plan, window_bytes, ctas_per_sm, windows, scratch_bytes, variant)
 
 
 def tsds_plan_destroy(plan):
@@ -226,11 +243,14 @@ class Plan:
         return self.outs, self.counts
 
     def info(self):
-        wb, cp, w, sb = ctypes.c_int64(), ctypes.c_int(), ctypes.c_int64(), ctypes.c_int64()
-        r = tsds_plan_info(self.handle, ctypes.byref(wb), ctypes.byref(cp), ctypes.byref(w), ctypes.byref(sb))
+        wb, cp, w, sb, var = ctypes.c_int64(), ctypes.c_int(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int()
+        r = tsds_plan_info(self.handle, ctypes.byref(wb), ctypes.byref(cp), ctypes.byref(w), ctypes.byref(sb),
+                           ctypes.byref(var))
         if r != 0:
             raise TsdsError(r, last_error())
-        return {"window_bytes": wb.value, "ctas_per_sm": cp.value, "windows": w.value, "scratch_bytes": sb.value}
+        names = {b: a for a, b in STREAM_VARIANTS.items()}
+        return {"window_bytes": wb.value, "ctas_per_sm": cp.value, "windows": w.value, "scratch_bytes": sb.value,
+                "variant": names.get(var.value, var.value)}
 
     def close(self):
         if self.handle:

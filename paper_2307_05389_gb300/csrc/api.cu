@@ -172,7 +172,18 @@ static BinnedLayout binned_layout(int64_t nb, int64_t windows) {
 tsds_status run_binned_series(const void* x, tsds_dtype x_dtype, const void* y, tsds_dtype y_dtype,
                               int64_t n, int64_t nb, tsds_nan_mode nan, Algo algo, int64_t* out,
                               int64_t* out_count, int64_t idx_bias, cudaStream_t st) {
-  const int64_t welems = window_elems(y_dtype);
+  // Window size: 64 KB for large inputs; smaller (down to 8 KB, a multiple of
+  // the 4 KB ring chunk) when fewer windows than about twice the resident
+  // warps would leave SMs idle.
+  StreamConfig cfg;
+  cfg.mean_bin_bytes = nb > 0 ? n / nb * dtype_size(y_dtype) : 0;
+  {
+    const int64_t bytes = n * dtype_size(y_dtype);
+    const int64_t warps = (int64_t)device_sm_count() * 3 * 4;
+    int64_t wb = (bytes / (2 * warps) + 4095) / 4096 * 4096;
+    cfg.window_bytes = wb < 8192 ? 8192 : (wb > kWindowBytes ? kWindowBytes : wb);
+  }
+  const int64_t welems = cfg.window_bytes / dtype_size(y_dtype);
   const int64_t windows = (n + welems - 1) / welems;
   const BinnedLayout L = binned_layout(nb, windows);
   Scratch s;
@@ -180,6 +191,8 @@ tsds_status run_binned_series(const void* x, tsds_dtype x_dtype, const void* y, 
   char* base = static_cast<char*>(s.p);
   TSDS_CK(cudaMemsetAsync(base + L.zero_begin, 0, L.zero_bytes, st));
   SeriesDev S;
+  memset(&S, 0, sizeof S);
+  S.status = &reinterpret_cast<WorkCounters*>(base + L.work)->status;
   S.y = y;
   S.x = x;
   S.n = n;
@@ -196,7 +209,7 @@ tsds_status run_binned_series(const void* x, tsds_dtype x_dtype, const void* y, 
   timing_begin(st, &tok);
   TSDS_CK(launch_argminmax(nullptr, 1, S, nullptr, windows, reinterpret_cast<Piece*>(base + L.first),
                            reinterpret_cast<Piece*>(base + L.last), reinterpret_cast<WorkCounters*>(base + L.work),
-                           y_dtype, nan, st));
+                           y_dtype, nan, st, cfg));
   timing_end(st, tok);
   TSDS_CK(launch_emit(nullptr, 1, S, algo, st));
   return TSDS_OK;
@@ -284,6 +297,18 @@ void tsds_shutdown(void) {
 const char* tsds_version(void) { return "0.1.0"; }
 
 int64_t tsds_kernel_launches(void) { return g_launches.load(); }
+
+tsds_status tsds_check_wait_timeout(unsigned rounds, void* stream) {
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Scratch s;
+  TSDS_CK(scratch_alloc(s, 256, st));
+  unsigned long long* word = static_cast<unsigned long long*>(s.p);
+  TSDS_CK(launch_wait_probe(word, rounds, st));
+  unsigned long long v = 0;
+  TSDS_CK(cudaMemcpyAsync(&v, word, sizeof v, cudaMemcpyDeviceToHost, st));
+  TSDS_CK(cudaStreamSynchronize(st));
+  return (tsds_status)v;
+}
 
 void tsds_timing_enable(int on) { g_timing.store(on ? 1 : 0); }
 

@@ -9,23 +9,37 @@
 //
 // GB300 design.  The pass is HBM-bound (a few integer or FP32 operations per
 // byte), so the kernel is built around keeping enough bytes in flight:
-//  * y is cut into fixed windows of kWindowBytes; a persistent grid of warps
+//  * y is cut into windows (a multiple of 4 KB); a persistent grid of warps
 //    claims windows from an atomic counter (load balance across the 152 SMs
 //    whatever the bin sizes), and each warp walks the bins overlapping its
 //    window.  A bin is cut where windows cut it.
-//  * Within a bin piece every lane streams 16-byte vectors with coalesced
-//    loads, U vectors (64 bytes) per lane per step.  Per step the lane reduces
-//    its U vectors to one group minimum and maximum with packed 16x2 integer
-//    or FP32/FP16x2 min/max instructions (no per-element index bookkeeping)
-//    and remembers the step where the running extremum last strictly
-//    improved.  After every CH steps it resolves that step's element index by
-//    re-reading the 64 bytes (an L2 hit) and keeping the first element equal
-//    to the extremum.  The first step whose group extremum equals the final
-//    extremum holds its first occurrence, so the earliest index survives.
+//  * Each warp streams its window through a private ring of 4 shared-memory
+//    stages of 4 KB filled by bulk asynchronous copies (cp.async.bulk with an
+//    mbarrier per stage), so every warp keeps 16 KB in flight without holding
+//    any of it in registers; small bins cost shared-memory latency, not DRAM
+//    latency.
+//  * A bin's part of a chunk is reduced by all lanes, 4 vectors of 16 bytes
+//    per lane per step: packed 16x2 integer or FP32/FP16x2 min/max
+//    instructions reduce a step to one group minimum and maximum (no
+//    per-element index bookkeeping) and each lane remembers the step where its
+//    extremum last strictly improved.  Before the chunk is released the lane
+//    finds the first element equal to its extremum in that step, from shared
+//    memory; the first step whose group extremum equals the final one holds
+//    its first occurrence, so the earliest index survives.
+//  * A second variant (stream_ldg.cuh) loads the same steps straight into
+//    registers and resolves indices every 8 steps from a cached re-read; with
+//    less bookkeeping per byte it is the faster one for large bins, the ring
+//    for small ones.  Each launch picks one by its bytes-weighted mean bin
+//    size (the batched plans can also time both).
 //  * Lanes then combine (ordered 64-bit key, index) pairs with warp shuffles.
 //    A bin held by one window is written directly; pieces of a bin that
 //    spans windows go to per-window slots, and the warp whose atomic
-//    increment completes the bin's piece count combines them.  Nothing waits.
+//    increment completes the bin's piece count combines them.  The only waits
+//    are on the ring's barriers, and they are bounded.
+#include <stdlib.h>
+#include <string.h>
+
+#include <atomic>
 #include <type_traits>
 
 #include "device.cuh"
@@ -34,7 +48,6 @@
 namespace tsds {
 
 constexpr int kU = 4;    // 16-byte vectors per lane per step
-constexpr int kCH = 8;   // steps between index resolutions
 
 // ---------------------------------------------------------------------------
 // Packed 16x2 helpers (sm_90+ PTX).
@@ -94,6 +107,12 @@ struct PolF32 {
     gmin = mn(mn(a[0], a[1]), mn(a[2], a[3]));
     gmax = mx(mx(b[0], b[1]), mx(b[2], b[3]));
   }
+  __device__ static void group1(const uint4& v, Acc& gmin, Acc& gmax) {
+    const float f0 = __uint_as_float(v.x), f1 = __uint_as_float(v.y);
+    const float f2 = __uint_as_float(v.z), f3 = __uint_as_float(v.w);
+    gmin = mn(mn(f0, f1), mn(f2, f3));
+    gmax = mx(mx(f0, f1), mx(f2, f3));
+  }
   __device__ static bool better_min(Acc g, Acc r) {
     return NM == TSDS_NAN_PROPAGATE ? (g < r || (isnan(g) && !isnan(r))) : (g < r || (isnan(r) && !isnan(g)));
   }
@@ -131,6 +150,13 @@ struct PolF16 {
     }
     __half2 lo = mn2(mn2(a[0], a[1]), mn2(a[2], a[3]));
     __half2 hi = mx2(mx2(b[0], b[1]), mx2(b[2], b[3]));
+    gmin = mnf(__low2float(lo), __high2float(lo));
+    gmax = mxf(__low2float(hi), __high2float(hi));
+  }
+  __device__ static void group1(const uint4& v, Acc& gmin, Acc& gmax) {
+    const __half2 w0 = h2(v.x), w1 = h2(v.y), w2 = h2(v.z), w3 = h2(v.w);
+    const __half2 lo = mn2(mn2(w0, w1), mn2(w2, w3));
+    const __half2 hi = mx2(mx2(w0, w1), mx2(w2, w3));
     gmin = mnf(__low2float(lo), __high2float(lo));
     gmax = mxf(__low2float(hi), __high2float(hi));
   }
@@ -183,6 +209,24 @@ struct PolSmallInt {
     gmin = min(lane_lo(lo), lane_hi(lo));
     gmax = max(lane_lo(hi), lane_hi(hi));
   }
+  __device__ static void group1(const uint4& v, Acc& gmin, Acc& gmax) {
+    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+    uint32_t lo, hi;
+    if (sizeof(T_) == 2) {
+      lo = mn(mn(w[0], w[1]), mn(w[2], w[3]));
+      hi = mx(mx(w[0], w[1]), mx(w[2], w[3]));
+    } else {
+      const uint32_t sel_even = kSigned ? 0xA280u : 0x4240u;
+      const uint32_t sel_odd = kSigned ? 0xB391u : 0x4341u;
+      uint32_t e[4], o[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) { e[i] = prmt(w[i], 0u, sel_even); o[i] = prmt(w[i], 0u, sel_odd); }
+      lo = mn(mn(mn(e[0], o[0]), mn(e[1], o[1])), mn(mn(e[2], o[2]), mn(e[3], o[3])));
+      hi = mx(mx(mx(e[0], o[0]), mx(e[1], o[1])), mx(mx(e[2], o[2]), mx(e[3], o[3])));
+    }
+    gmin = min(lane_lo(lo), lane_hi(lo));
+    gmax = max(lane_lo(hi), lane_hi(hi));
+  }
   __device__ static bool better_min(Acc g, Acc r) { return g < r; }
   __device__ static bool better_max(Acc g, Acc r) { return g > r; }
   __device__ static bool match_min(T e, Acc t) { return (int32_t)e == t; }
@@ -211,6 +255,11 @@ struct PolInt32 {
     }
     gmin = min(min(a[0], a[1]), min(a[2], a[3]));
     gmax = max(max(b[0], b[1]), max(b[2], b[3]));
+  }
+  __device__ static void group1(const uint4& v, Acc& gmin, Acc& gmax) {
+    const T e0 = (T)v.x, e1 = (T)v.y, e2 = (T)v.z, e3 = (T)v.w;
+    gmin = min(min(e0, e1), min(e2, e3));
+    gmax = max(max(e0, e1), max(e2, e3));
   }
   __device__ static bool better_min(Acc g, Acc r) { return g < r; }
   __device__ static bool better_max(Acc g, Acc r) { return g > r; }
@@ -273,20 +322,152 @@ struct Pol64 {
   __device__ static uint64_t elem_key_max(T e) { return kmax_of(raw(bits(e))); }
 };
 
+
 // ---------------------------------------------------------------------------
-// One bin piece [a, b) of a series, reduced by one warp.
+// Per-warp shared-memory ring fed by bulk asynchronous copies (TMA).
+//
+// Each warp streams the 16-byte-aligned body of its window in kChunkBytes
+// chunks through kRingStages stages; lane 0 arms the stage's mbarrier with
+// the chunk's byte count and issues cp.async.bulk, all lanes wait on the
+// barrier's phase parity.  Every wait is bounded: when it runs out the warp
+// records TSDS_ETIMEOUT in the launch's status word, waits (again bounded)
+// for its own copies still in flight and stops.
 // ---------------------------------------------------------------------------
+constexpr int kRingStages = 4;
+constexpr int kChunkBytes = 4096;
+constexpr int kWarpsPerCta = 4;
+constexpr int kRingThreads = kWarpsPerCta * 32;
+constexpr int kRingSmemBytes = kWarpsPerCta * kRingStages * kChunkBytes;
+constexpr unsigned kWaitRounds = 1u << 22;   // try_wait rounds (each suspends briefly): seconds in total
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+// Bounded wait for the phase with the given parity; uniform across the warp.
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity) {
+  for (unsigned i = 0; i < kWaitRounds; ++i)
+    if (mbar_try(b, parity)) return true;
+  return false;
+}
+
+struct Ring {
+  unsigned char* buf;   // kRingStages * kChunkBytes of this warp
+  uint64_t* bar;        // kRingStages barriers of this warp
+  uintptr_t bl, bh;     // window body [bl, bh): global, 16-byte aligned
+  int64_t nchunks;      // chunks of the body
+  int64_t issued;       // chunks issued so far (window-local)
+  int64_t waited;       // chunks whose copy has completed and been observed
+  int64_t head;         // first chunk not yet released
+  uint64_t gbase;       // warp-wide count of chunks before this window (stage / parity)
+  bool ok;
+};
+
+__device__ __forceinline__ int ring_stage(const Ring& R, int64_t c) { return (int)((R.gbase + (uint64_t)c) % kRingStages); }
+__device__ __forceinline__ uint32_t ring_parity(const Ring& R, int64_t c) {
+  return (uint32_t)(((R.gbase + (uint64_t)c) / kRingStages) & 1u);
+}
+
+__device__ __forceinline__ void ring_issue(Ring& R, int64_t c, int lane) {
+  if (lane == 0) {
+    const uintptr_t src = R.bl + (uintptr_t)c * kChunkBytes;
+    const uint32_t bytes = (uint32_t)min((uintptr_t)kChunkBytes, R.bh - src);
+    const int s = ring_stage(R, c);
+    mbar_expect_tx(&R.bar[s], bytes);
+    bulk_g2s(R.buf + (size_t)s * kChunkBytes, reinterpret_cast<const void*>(src), bytes, &R.bar[s]);
+  }
+}
+
+__device__ __forceinline__ void ring_begin(Ring& R, uintptr_t bl, uintptr_t bh, int lane) {
+  R.bl = bl;
+  R.bh = bh;
+  R.nchunks = bh > bl ? (int64_t)((bh - bl + kChunkBytes - 1) / kChunkBytes) : 0;
+  R.issued = min((int64_t)kRingStages, R.nchunks);
+  R.waited = 0;
+  R.head = 0;
+  for (int64_t c = 0; c < R.issued; ++c) ring_issue(R, c, lane);
+}
+
+// Makes chunk c resident.  The chunks before it are released first (each is
+// observed complete before its stage is refilled with the chunk kRingStages
+// ahead), then chunk c is waited for.  Invariant: head <= waited <= issued,
+// and only issued chunks are ever waited for.
+__device__ __forceinline__ void ring_ensure(Ring& R, int64_t c, int lane) {
+  while (R.head < c && R.ok) {
+    while (R.waited <= R.head && R.ok) {
+      R.ok = mbar_wait(&R.bar[ring_stage(R, R.waited)], ring_parity(R, R.waited));
+      if (R.ok) ++R.waited;
+    }
+    if (!R.ok) break;
+    __syncwarp();   // every lane is done reading chunk `head`
+    if (R.issued < R.nchunks) {
+      if (lane == 0) fence_proxy_async();
+      ring_issue(R, R.issued, lane);
+      ++R.issued;
+    }
+    ++R.head;
+  }
+  while (R.waited <= c && R.ok) {
+    R.ok = mbar_wait(&R.bar[ring_stage(R, R.waited)], ring_parity(R, R.waited));
+    if (R.ok) ++R.waited;
+  }
+}
+
+// Observes every issued chunk so the barriers' phases stay in step for the
+// next window (bounded like every wait).
+__device__ __forceinline__ void ring_end(Ring& R) {
+  while (R.waited < R.issued && R.ok) {
+    R.ok = mbar_wait(&R.bar[ring_stage(R, R.waited)], ring_parity(R, R.waited));
+    if (R.ok) ++R.waited;
+  }
+  // issue the remaining chunks only if the pieces never reached them (cannot happen when
+  // the pieces cover the body); keep the phase count consistent either way
+  R.gbase += (uint64_t)R.issued;
+}
+
+// ---------------------------------------------------------------------------
+// Reduction of one sub-range [s0, s1) (global addresses) of a resident chunk.
+// ---------------------------------------------------------------------------
+template <class P>
+__device__ __forceinline__ typename P::T smem_elem(const unsigned char* p) {
+  using T = typename P::T;
+  if constexpr (sizeof(T) == 2 && std::is_same<T, __half>::value) {
+    return __ushort_as_half(*reinterpret_cast<const unsigned short*>(p));
+  } else {
+    return *reinterpret_cast<const T*>(p);
+  }
+}
+
 template <class P, bool MIN>
-__device__ __noinline__ int find_first(const uint4* __restrict__ vp, int nvec, int t, int lane,
-                                       typename P::Acc target) {
-  // element offset (from the first body element) of the first match in step t
+__device__ __noinline__ int find_first_smem(const uint4* __restrict__ sp, int nvec, int t, int lane,
+                                            typename P::Acc target) {
   using T = typename P::T;
   const int vb = t * (32 * kU) + lane;
 #pragma unroll 1
   for (int u = 0; u < kU; ++u) {
     const int vi = vb + u * 32;
     if (vi >= nvec) break;
-    const uint4 v = ldg_vec(vp + vi);
+    const uint4 v = sp[vi];
 #pragma unroll
     for (int e = 0; e < P::E; ++e) {
       const T val = vec_elem<T, P::E>(v, e);
@@ -296,80 +477,121 @@ __device__ __noinline__ int find_first(const uint4* __restrict__ vp, int nvec, i
   return -1;
 }
 
+// A lane's running extremum over the whole vectors of a piece, in the
+// policy's value space; its index is found (in the resident chunk) only when
+// a chunk strictly improves it.
 template <class P>
-__device__ __forceinline__ Cand piece_argminmax(const typename P::T* __restrict__ y, int64_t a, int64_t b) {
+struct LaneRun {
+  bool valid;
+  typename P::Acc mn, mx;
+  int64_t imn, imx;
+};
+
+template <class P>
+__device__ __forceinline__ void sub_reduce(LaneRun<P>& r, Cand& c, const unsigned char* chunk, uintptr_t cs,
+                                           uintptr_t s0, uintptr_t s1, uintptr_t ya, int lane) {
   using T = typename P::T;
   using Acc = typename P::Acc;
-  constexpr int E = P::E;
-  const int lane = threadIdx.x & 31;
+  constexpr int S = sizeof(T);
+  const uintptr_t v0 = (s0 + 15) & ~(uintptr_t)15, v1 = s1 & ~(uintptr_t)15;
+  // elements outside whole vectors, one per lane
+  if (v0 >= v1) {
+    for (uintptr_t a = s0 + (uintptr_t)lane * S; a < s1; a += 32 * S) {
+      const T e = smem_elem<P>(chunk + (a - cs));
+      const int64_t i = (int64_t)((a - ya) / S);
+      cand_merge_min(c, P::elem_key_min(e), i);
+      cand_merge_max(c, P::elem_key_max(e), i);
+    }
+    return;
+  }
+  for (uintptr_t a = s0 + (uintptr_t)lane * S; a < v0; a += 32 * S) {
+    const T e = smem_elem<P>(chunk + (a - cs));
+    const int64_t i = (int64_t)((a - ya) / S);
+    cand_merge_min(c, P::elem_key_min(e), i);
+    cand_merge_max(c, P::elem_key_max(e), i);
+  }
+  for (uintptr_t a = v1 + (uintptr_t)lane * S; a < s1; a += 32 * S) {
+    const T e = smem_elem<P>(chunk + (a - cs));
+    const int64_t i = (int64_t)((a - ya) / S);
+    cand_merge_min(c, P::elem_key_min(e), i);
+    cand_merge_max(c, P::elem_key_max(e), i);
+  }
+  const uint4* __restrict__ sp = reinterpret_cast<const uint4*>(chunk + (v0 - cs));
+  const int nv = (int)((v1 - v0) / 16);
+  const int iters = (nv + 32 * kU - 1) / (32 * kU);
+  bool cvalid = false;
+  Acc cmin{}, cmax{};
+  int tmin = 0, tmax = 0;
+  for (int t = 0; t < iters; ++t) {
+    const int vb = t * (32 * kU) + lane;
+    if (vb >= nv) continue;
+    uint4 v[kU];
+    v[0] = sp[vb];
+#pragma unroll
+    for (int u = 1; u < kU; ++u) v[u] = (vb + u * 32 < nv) ? sp[vb + u * 32] : v[0];
+    Acc gmin, gmax;
+    P::group(v, gmin, gmax);
+    if (!cvalid || P::better_min(gmin, cmin)) { cmin = gmin; tmin = t; }
+    if (!cvalid || P::better_max(gmax, cmax)) { cmax = gmax; tmax = t; }
+    cvalid = true;
+  }
+  if (cvalid) {
+    const int64_t i0 = (int64_t)((v0 - ya) / S);
+    // chunks are visited in index order, so a strict improvement is needed to move
+    if (!r.valid || P::better_min(cmin, r.mn)) {
+      r.mn = cmin;
+      r.imn = i0 + find_first_smem<P, true>(sp, nv, tmin, lane, cmin);
+    }
+    if (!r.valid || P::better_max(cmax, r.mx)) {
+      r.mx = cmax;
+      r.imx = i0 + find_first_smem<P, false>(sp, nv, tmax, lane, cmax);
+    }
+    r.valid = true;
+  }
+}
+
+// One bin piece [pa, pb) of the warp's window: elements outside the ring's body
+// come from global memory, the body from the resident chunks.
+template <class P>
+__device__ __forceinline__ Cand piece_ring(Ring& R, const typename P::T* __restrict__ y, int64_t pa, int64_t pb,
+                                           int lane) {
+  using T = typename P::T;
+  constexpr int S = sizeof(T);
   Cand c;
   cand_init(c);
-
-  // body: the 16-byte aligned vectors inside [a, b); head and tail elements
-  // outside it go through the scalar path
-  const uintptr_t addr = reinterpret_cast<uintptr_t>(y + a);
-  int64_t ia = a + (int64_t)(((16u - (unsigned)(addr & 15u)) & 15u) / sizeof(T));
-  if (ia > b) ia = b;
-  const int64_t nvec = (b - ia) / E;
-  const int64_t ib = ia + nvec * E;
-  for (int64_t i = a + lane; i < ia; i += 32) {
+  const uintptr_t ya = reinterpret_cast<uintptr_t>(y);
+  const uintptr_t a0 = ya + (uintptr_t)pa * S, a1 = ya + (uintptr_t)pb * S;
+  // before / after the body (array ends that are not 16-byte aligned)
+  for (uintptr_t a = a0 + (uintptr_t)lane * S; a < min(a1, R.bl); a += 32 * S) {
+    const int64_t i = (int64_t)((a - ya) / S);
     const T e = ldg_elem<T>(y + i);
     cand_merge_min(c, P::elem_key_min(e), i);
     cand_merge_max(c, P::elem_key_max(e), i);
   }
-  for (int64_t i = ib + lane; i < b; i += 32) {
+  for (uintptr_t a = max(a0, R.bh) + (uintptr_t)lane * S; a < a1; a += 32 * S) {
+    const int64_t i = (int64_t)((a - ya) / S);
     const T e = ldg_elem<T>(y + i);
     cand_merge_min(c, P::elem_key_min(e), i);
     cand_merge_max(c, P::elem_key_max(e), i);
   }
-
-  if (nvec > 0) {
-    // a piece never exceeds one window, so step and vector numbers fit in 32 bits
-    const uint4* __restrict__ vp = reinterpret_cast<const uint4*>(y + ia);
-    const int nv = (int)nvec;
-    const int iters = (nv + 32 * kU - 1) / (32 * kU);
-    bool rvalid = false;
-    Acc rmin{}, rmax{};
-    int rimin = -1, rimax = -1;
-    for (int t0 = 0; t0 < iters; t0 += kCH) {
-      const int t1 = min(t0 + kCH, iters);
-      bool cvalid = false;
-      Acc cmin{}, cmax{};
-      int tmin = 0, tmax = 0;
-      for (int t = t0; t < t1; ++t) {
-        const int vb = t * (32 * kU) + lane;
-        uint4 v[kU];
-        if (vb + (kU - 1) * 32 < nv) {
-#pragma unroll
-          for (int u = 0; u < kU; ++u) v[u] = ldg_vec(vp + vb + u * 32);
-        } else {
-          if (vb >= nv) continue;
-          v[0] = ldg_vec(vp + vb);
-#pragma unroll
-          for (int u = 1; u < kU; ++u) v[u] = (vb + u * 32 < nv) ? ldg_vec(vp + vb + u * 32) : v[0];
-        }
-        Acc gmin, gmax;
-        P::group(v, gmin, gmax);
-        if (!cvalid || P::better_min(gmin, cmin)) { cmin = gmin; tmin = t; }
-        if (!cvalid || P::better_max(gmax, cmax)) { cmax = gmax; tmax = t; }
-        cvalid = true;
-      }
-      if (cvalid) {
-        if (!rvalid || P::better_min(cmin, rmin)) {
-          rmin = cmin;
-          rimin = find_first<P, true>(vp, nv, tmin, lane, cmin);
-        }
-        if (!rvalid || P::better_max(cmax, rmax)) {
-          rmax = cmax;
-          rimax = find_first<P, false>(vp, nv, tmax, lane, cmax);
-        }
-        rvalid = true;
-      }
-    }
-    if (rvalid) {
-      cand_merge_min(c, P::key_min(rmin), ia + rimin);
-      cand_merge_max(c, P::key_max(rmax), ia + rimax);
-    }
+  uintptr_t b0 = max(a0, R.bl);
+  const uintptr_t b1 = min(a1, R.bh);
+  LaneRun<P> r;
+  r.valid = false;
+  r.imn = r.imx = kIdxNone;
+  while (b0 < b1 && R.ok) {
+    const int64_t ci = (int64_t)((b0 - R.bl) / kChunkBytes);
+    ring_ensure(R, ci, lane);
+    if (!R.ok) break;
+    const uintptr_t cs = R.bl + (uintptr_t)ci * kChunkBytes;
+    const uintptr_t ce = min(cs + (uintptr_t)kChunkBytes, R.bh);
+    const uintptr_t e = min(b1, ce);
+    sub_reduce<P>(r, c, R.buf + (size_t)ring_stage(R, ci) * kChunkBytes, cs, b0, e, ya, lane);
+    b0 = e;
+  }
+  if (r.valid) {
+    cand_merge_min(c, P::key_min(r.mn), r.imn);
+    cand_merge_max(c, P::key_max(r.mx), r.imx);
   }
   cand_warp_reduce(c);
   return c;
@@ -395,92 +617,220 @@ __device__ __forceinline__ Piece load_piece_cg(const Piece* p) {
   return r;
 }
 
+// The warp's reduction c of bin b = [lo, hi) over its part in window k: a bin
+// inside one window is written at once; otherwise the part goes to the
+// window's piece slot (the bin's first window uses last_piece, every later one
+// first_piece) and the warp whose increment completes the bin's piece count
+// combines all of them.  Warp-collective: every lane calls it with the same
+// arguments.
+template <class P, int NM>
+__device__ __forceinline__ void bin_result(const SeriesDev& S, int64_t b, int64_t lo, int64_t hi, int64_t k,
+                                           int64_t welems, Cand c, Piece* __restrict__ first_piece,
+                                           Piece* __restrict__ last_piece, int lane) {
+  const int64_t k0 = lo / welems, k1 = (hi - 1) / welems;
+  if (k0 == k1) {
+    finish_bin<P, NM>(c, lo);
+    if (lane == 0) { S.res[2 * b] = c.imin; S.res[2 * b + 1] = c.imax; }
+    return;
+  }
+  Piece* slot = (k == k0) ? &last_piece[S.win_base + k] : &first_piece[S.win_base + k];
+  unsigned done = 0;
+  if (lane == 0) {
+    *slot = Piece{c.kmin, c.imin, c.kmax, c.imax};
+    __threadfence();
+    done = atomicAdd(&S.cnt[b], 1u);
+  }
+  done = __shfl_sync(0xffffffffu, done, 0);
+  if ((int64_t)done == k1 - k0) {
+    // every other piece of this bin is published: combine them all
+    __threadfence();
+    Cand t;
+    cand_init(t);
+    for (int64_t p = lane; p <= k1 - k0; p += 32) {
+      const Piece q = load_piece_cg(p == 0 ? &last_piece[S.win_base + k0] : &first_piece[S.win_base + k0 + p]);
+      cand_merge_min(t, q.kmin, q.imin);
+      cand_merge_max(t, q.kmax, q.imax);
+    }
+    cand_warp_reduce(t);
+    finish_bin<P, NM>(t, lo);
+    if (lane == 0) { S.res[2 * b] = t.imin; S.res[2 * b + 1] = t.imax; S.cnt[b] = 0u; }
+  }
+}
+
 template <class P, int NM, bool MULTI>
-__global__ void __launch_bounds__(kStreamThreads)
+__global__ void __launch_bounds__(kRingThreads)
 k_argminmax(const SeriesDev* __restrict__ sd, SeriesDev single, const int32_t* __restrict__ win_series,
             int64_t total_windows, Piece* __restrict__ first_piece, Piece* __restrict__ last_piece,
             WorkCounters* __restrict__ work, int64_t welems, const int64_t* __restrict__ total_dev) {
   using T = typename P::T;
-  const int lane = threadIdx.x & 31;
+  extern __shared__ __align__(128) unsigned char ring_smem[];
+  __shared__ __align__(8) uint64_t bars[kWarpsPerCta][kRingStages];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (total_dev) total_windows = *total_dev;
+  Ring R;
+  R.buf = ring_smem + (size_t)warp * kRingStages * kChunkBytes;
+  R.bar = bars[warp];
+  R.gbase = 0;
+  R.ok = true;
+  if (lane == 0) {
+    for (int s = 0; s < kRingStages; ++s) mbar_init(&R.bar[s], 1);
+    fence_mbar_init();
+  }
+  __syncwarp();
   for (;;) {
     unsigned long long wu = 0;
     if (lane == 0) wu = atomicAdd(&work->next_window, 1ull);
     const int64_t w = (int64_t)__shfl_sync(0xffffffffu, wu, 0);
     if (w >= total_windows) break;
-    SeriesDev S = MULTI ? sd[win_series[w]] : single;
+    const SeriesDev S = MULTI ? sd[win_series[w]] : single;
     const T* __restrict__ y = static_cast<const T*>(S.y);
     const int64_t* __restrict__ edges = S.edges;
     const int64_t nb = S.nb;
     const int64_t k = w - S.win_base;
     const int64_t ws = k * welems;
     const int64_t we = min(ws + welems, S.n);
+    // the window's body: 16-byte aligned and inside the array
+    const uintptr_t ya = reinterpret_cast<uintptr_t>(y);
+    uintptr_t bl = max((ya + (uintptr_t)ws * sizeof(T)) & ~(uintptr_t)15, (ya + 15) & ~(uintptr_t)15);
+    uintptr_t bh = min((ya + (uintptr_t)we * sizeof(T) + 15) & ~(uintptr_t)15,
+                       (ya + (uintptr_t)S.n * sizeof(T)) & ~(uintptr_t)15);
+    if (bh < bl) bh = bl;
+    ring_begin(R, bl, bh, lane);
     // the bin holding ws: the last b with edges[b] <= ws
     int64_t b = warp_lower_bound(1, nb + 1, [&](int64_t j) { return __ldg(edges + j) > ws; }) - 1;
     int64_t lo = __ldg(edges + b);
-    while (b < nb && lo < we) {
-      const int64_t hi = __ldg(edges + b + 1);
-      if (hi > lo) {
-        const int64_t pa = max(lo, ws), pb = min(hi, we);
-        Cand c = piece_argminmax<P>(y, pa, pb);
-        const int64_t k0 = lo / welems, k1 = (hi - 1) / welems;
-        if (k0 == k1) {
-          finish_bin<P, NM>(c, lo);
-          if (lane == 0) { S.res[2 * b] = c.imin; S.res[2 * b + 1] = c.imax; }
-        } else {
-          Piece* slot = (k == k0) ? &last_piece[S.win_base + k] : &first_piece[S.win_base + k];
-          unsigned done = 0;
-          if (lane == 0) {
-            *slot = Piece{c.kmin, c.imin, c.kmax, c.imax};
-            __threadfence();
-            done = atomicAdd(&S.cnt[b], 1u);
-          }
-          done = __shfl_sync(0xffffffffu, done, 0);
-          if ((int64_t)done == k1 - k0) {
-            // every other piece of this bin is published: combine them all
-            __threadfence();
-            Cand t;
-            cand_init(t);
-            for (int64_t p = lane; p <= k1 - k0; p += 32) {
-              const Piece q = load_piece_cg(p == 0 ? &last_piece[S.win_base + k0] : &first_piece[S.win_base + k0 + p]);
-              cand_merge_min(t, q.kmin, q.imin);
-              cand_merge_max(t, q.kmax, q.imax);
-            }
-            cand_warp_reduce(t);
-            finish_bin<P, NM>(t, lo);
-            if (lane == 0) { S.res[2 * b] = t.imin; S.res[2 * b + 1] = t.imax; S.cnt[b] = 0u; }
-          }
+    while (b < nb && lo < we && R.ok) {
+      // the ends of the next 32 bins, one per lane
+      const int64_t my_hi = (b + lane < nb) ? __ldg(edges + b + 1 + lane) : INT64_MAX;
+      for (int q = 0; q < 32 && b < nb && lo < we && R.ok; ++q, ++b) {
+        const int64_t hi = __shfl_sync(0xffffffffu, my_hi, q);
+        if (hi > lo) {
+          const int64_t pa = max(lo, ws), pb = min(hi, we);
+          Cand c = piece_ring<P>(R, y, pa, pb, lane);
+          bin_result<P, NM>(S, b, lo, hi, k, welems, c, first_piece, last_piece, lane);
         }
+        lo = hi;
       }
-      lo = hi;
-      ++b;
     }
+    ring_end(R);
+    if (!R.ok) break;
   }
+  if (!R.ok && lane == 0) atomicExch(&work->status, (unsigned long long)TSDS_ETIMEOUT);
+}
+
+// A wait nothing will satisfy, bounded by `rounds`: exercises the timeout
+// path of the barrier waits without touching memory copies.
+__global__ void k_wait_probe(unsigned long long* status, unsigned rounds) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  bool ok = false;
+  for (unsigned i = 0; i < rounds && !ok; ++i) ok = mbar_try(&bar, 0);
+  __syncthreads();
+  if (threadIdx.x == 0) *status = ok ? 0ull : (unsigned long long)TSDS_ETIMEOUT;
+}
+
+cudaError_t launch_wait_probe(unsigned long long* status, unsigned rounds, cudaStream_t st) {
+  note_launch();
+  k_wait_probe<<<1, 32, 0, st>>>(status, rounds);
+  return cudaGetLastError();
+}
+
+#include "stream_ldg.cuh"
+#include "stream_seg.cuh"
+
+template <class P, int NM, bool MULTI, int VAR>
+static int stream_occupancy() {
+  static int occ = 0;
+  if (occ == 0) {
+    cudaError_t e;
+    if constexpr (VAR == STREAM_LDG) {
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_argminmax_ldg<P, NM, MULTI>, kStreamThreadsLdg, 0);
+    } else if constexpr (VAR == STREAM_SEG) {
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_argminmax_seg<P, NM, MULTI>, kSegThreads, 0);
+    } else {
+      auto kern = k_argminmax<P, NM, MULTI>;
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kRingSmemBytes);
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kRingThreads, kRingSmemBytes);
+    }
+    if (e != cudaSuccess || occ < 1) occ = 1;
+  }
+  return occ;
+}
+
+// Process-wide override of the per-launch choice (tsds_stream_variant; at
+// load, TSDS_STREAM_VARIANT=ring|ldg|seg).
+static std::atomic<int> g_variant{-1};
+
+static int variant_override() {
+  int v = g_variant.load(std::memory_order_relaxed);
+  if (v < 0) {
+    const char* e = getenv("TSDS_STREAM_VARIANT");
+    const int env = (e && !strcmp(e, "ring")) ? STREAM_RING
+                    : (e && !strcmp(e, "ldg")) ? STREAM_LDG
+                    : (e && !strcmp(e, "seg")) ? STREAM_SEG
+                                               : STREAM_AUTO;
+    int expect = -1;
+    g_variant.compare_exchange_strong(expect, env);
+    v = g_variant.load(std::memory_order_relaxed);
+  }
+  return v;
+}
+
+int stream_variant_for(const StreamConfig& cfg, int64_t elem_bytes) {
+  int v = cfg.variant != STREAM_AUTO ? cfg.variant : variant_override();
+  if (v == STREAM_AUTO) v = cfg.mean_bin_bytes < seg_max_bin_bytes(elem_bytes) ? STREAM_SEG : STREAM_LDG;
+  if (v == STREAM_SEG && elem_bytes > 4) v = STREAM_LDG;   // 64-bit keys do not pack
+  return v;
+}
+
+template <class P, int NM, int VAR, bool MULTI>
+static cudaError_t launch_var(const SeriesDev* s_dev, const SeriesDev& single, const int32_t* win_series,
+                              int64_t total_windows, Piece* fp, Piece* lp, WorkCounters* work,
+                              const StreamConfig& cfg, int sm_count, cudaStream_t st) {
+  const int occ = stream_occupancy<P, NM, MULTI, VAR>();
+  const int per = (cfg.ctas_per_sm > 0 && cfg.ctas_per_sm < occ) ? cfg.ctas_per_sm : occ;
+  const int threads = VAR == STREAM_LDG ? kStreamThreadsLdg : VAR == STREAM_SEG ? kSegThreads : kRingThreads;
+  const int warps_per_cta = threads / 32;
+  int64_t blocks = (total_windows + warps_per_cta - 1) / warps_per_cta;
+  const int64_t cap = (int64_t)(sm_count > 0 ? sm_count : device_sm_count()) * per;
+  if (blocks > cap || cfg.total_windows_dev) blocks = cap;
+  if (blocks < 1) blocks = 1;
+  const int64_t welems = cfg.window_bytes / (int64_t)sizeof(typename P::T);
+  note_launch();
+  if constexpr (VAR == STREAM_LDG) {
+    k_argminmax_ldg<P, NM, MULTI><<<(unsigned)blocks, threads, 0, st>>>(s_dev, single, win_series, total_windows, fp,
+                                                                        lp, work, welems, cfg.total_windows_dev);
+  } else if constexpr (VAR == STREAM_SEG) {
+    k_argminmax_seg<P, NM, MULTI><<<(unsigned)blocks, threads, 0, st>>>(s_dev, single, win_series, total_windows, fp,
+                                                                        lp, work, welems, cfg.total_windows_dev);
+  } else {
+    k_argminmax<P, NM, MULTI><<<(unsigned)blocks, threads, kRingSmemBytes, st>>>(
+        s_dev, single, win_series, total_windows, fp, lp, work, welems, cfg.total_windows_dev);
+  }
+  return cudaGetLastError();
 }
 
 template <class P, int NM>
 static cudaError_t launch_pol(const SeriesDev* s_dev, int count, const SeriesDev& single,
                               const int32_t* win_series, int64_t total_windows, Piece* fp, Piece* lp,
-                              WorkCounters* work, const StreamConfig& cfg, cudaStream_t st) {
+                              WorkCounters* work, const StreamConfig& cfg, int sm_count, cudaStream_t st) {
   const bool multi = count > 1 || s_dev != nullptr;
-  auto kern = multi ? k_argminmax<P, NM, true> : k_argminmax<P, NM, false>;
-  static int per_sm[2] = {0, 0};
-  int& occ = per_sm[multi ? 1 : 0];
-  if (occ == 0) {
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kStreamThreads, 0);
-    if (e != cudaSuccess || occ < 1) occ = 1;
+  const int var = stream_variant_for(cfg, (int64_t)sizeof(typename P::T));
+#define TSDS_VAR(V)                                                                                         \
+  return multi ? launch_var<P, NM, V, true>(s_dev, single, win_series, total_windows, fp, lp, work, cfg,    \
+                                            sm_count, st)                                                   \
+               : launch_var<P, NM, V, false>(s_dev, single, win_series, total_windows, fp, lp, work, cfg,   \
+                                             sm_count, st)
+  if (var == STREAM_LDG) TSDS_VAR(STREAM_LDG);
+  if constexpr (sizeof(typename P::T) <= 4) {
+    if (var == STREAM_SEG) TSDS_VAR(STREAM_SEG);
   }
-  const int per = (cfg.ctas_per_sm > 0 && cfg.ctas_per_sm < occ) ? cfg.ctas_per_sm : occ;
-  const int64_t warps_per_block = kStreamThreads / 32;
-  int64_t blocks = (total_windows + warps_per_block - 1) / warps_per_block;
-  const int64_t cap = (int64_t)device_sm_count() * per;
-  if (blocks > cap || cfg.total_windows_dev) blocks = cap;
-  if (blocks < 1) blocks = 1;
-  note_launch();
-  kern<<<(unsigned)blocks, kStreamThreads, 0, st>>>(s_dev, single, win_series, total_windows, fp, lp, work,
-                                                     cfg.window_bytes / (int64_t)sizeof(typename P::T),
-                                                     cfg.total_windows_dev);
-  return cudaGetLastError();
+  TSDS_VAR(STREAM_RING);
+#undef TSDS_VAR
 }
 
 using PolI64 = Pol64<0, 0>;
@@ -488,71 +838,53 @@ using PolU64 = Pol64<1, 0>;
 using PolF64Prop = Pol64<2, TSDS_NAN_PROPAGATE>;
 using PolF64Ign = Pol64<2, TSDS_NAN_IGNORE>;
 
+static cudaError_t launch_any(const SeriesDev* s_dev, int count, const SeriesDev& single,
+                              const int32_t* win_series, int64_t total_windows, Piece* first_piece,
+                              Piece* last_piece, WorkCounters* work, tsds_dtype y_dtype, tsds_nan_mode nan,
+                              const StreamConfig& cfg, int sm_count, cudaStream_t st) {
+  if (total_windows <= 0) return cudaSuccess;
+  // the ring consumes windows in whole 4 KB chunks; both variants need 16-byte windows
+  if (cfg.window_bytes <= 0 || cfg.window_bytes % kChunkBytes != 0) return cudaErrorInvalidValue;
+  const bool ign = nan == TSDS_NAN_IGNORE;
+#define TSDS_LAUNCH(POL, NM) \
+  launch_pol<POL, NM>(s_dev, count, single, win_series, total_windows, first_piece, last_piece, work, cfg, sm_count, st)
+  switch (y_dtype) {
+    case TSDS_I8: return TSDS_LAUNCH(PolSmallInt<int8_t>, 0);
+    case TSDS_U8: return TSDS_LAUNCH(PolSmallInt<uint8_t>, 0);
+    case TSDS_I16: return TSDS_LAUNCH(PolSmallInt<int16_t>, 0);
+    case TSDS_U16: return TSDS_LAUNCH(PolSmallInt<uint16_t>, 0);
+    case TSDS_I32: return TSDS_LAUNCH(PolInt32<int32_t>, 0);
+    case TSDS_U32: return TSDS_LAUNCH(PolInt32<uint32_t>, 0);
+    case TSDS_I64: return TSDS_LAUNCH(PolI64, 0);
+    case TSDS_U64: return TSDS_LAUNCH(PolU64, 0);
+    case TSDS_F16: return ign ? TSDS_LAUNCH(PolF16<1>, 1) : TSDS_LAUNCH(PolF16<0>, 0);
+    case TSDS_F32: return ign ? TSDS_LAUNCH(PolF32<1>, 1) : TSDS_LAUNCH(PolF32<0>, 0);
+    case TSDS_F64: return ign ? TSDS_LAUNCH(PolF64Ign, 1) : TSDS_LAUNCH(PolF64Prop, 0);
+    default: return cudaErrorInvalidValue;
+  }
+#undef TSDS_LAUNCH
+}
+
 cudaError_t launch_argminmax(const SeriesDev* s_dev, int count, const SeriesDev& single,
                              const int32_t* win_series, int64_t total_windows,
                              Piece* first_piece, Piece* last_piece, WorkCounters* work,
                              tsds_dtype y_dtype, tsds_nan_mode nan, cudaStream_t st, const StreamConfig& cfg) {
-  if (total_windows <= 0) return cudaSuccess;
-  const bool ign = nan == TSDS_NAN_IGNORE;
-#define TSDS_LAUNCH(POL, NM) launch_pol<POL, NM>(s_dev, count, single, win_series, total_windows, first_piece, last_piece, work, cfg, st)
-  switch (y_dtype) {
-    case TSDS_I8: return TSDS_LAUNCH(PolSmallInt<int8_t>, 0);
-    case TSDS_U8: return TSDS_LAUNCH(PolSmallInt<uint8_t>, 0);
-    case TSDS_I16: return TSDS_LAUNCH(PolSmallInt<int16_t>, 0);
-    case TSDS_U16: return TSDS_LAUNCH(PolSmallInt<uint16_t>, 0);
-    case TSDS_I32: return TSDS_LAUNCH(PolInt32<int32_t>, 0);
-    case TSDS_U32: return TSDS_LAUNCH(PolInt32<uint32_t>, 0);
-    case TSDS_I64: return TSDS_LAUNCH(PolI64, 0);
-    case TSDS_U64: return TSDS_LAUNCH(PolU64, 0);
-    case TSDS_F16: return ign ? TSDS_LAUNCH(PolF16<1>, 1) : TSDS_LAUNCH(PolF16<0>, 0);
-    case TSDS_F32: return ign ? TSDS_LAUNCH(PolF32<1>, 1) : TSDS_LAUNCH(PolF32<0>, 0);
-    case TSDS_F64: return ign ? TSDS_LAUNCH(PolF64Ign, 1) : TSDS_LAUNCH(PolF64Prop, 0);
-    default: return cudaErrorInvalidValue;
-  }
-#undef TSDS_LAUNCH
-}
-
-// Single-series launch with the SM count given by the caller instead of the
-// library's per-device state, for the entry point that must not create the
-// library's memory pool (tsds_minmax_noalloc).
-template <class P, int NM>
-static cudaError_t launch_pol_sm(const SeriesDev& single, int64_t total_windows, Piece* fp, Piece* lp,
-                                 WorkCounters* work, int sm_count, cudaStream_t st) {
-  auto kern = k_argminmax<P, NM, false>;
-  int occ = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kStreamThreads, 0) != cudaSuccess || occ < 1)
-    occ = 1;
-  int64_t blocks = (total_windows + kStreamThreads / 32 - 1) / (kStreamThreads / 32);
-  const int64_t cap = (int64_t)sm_count * occ;
-  if (blocks > cap) blocks = cap;
-  if (blocks < 1) blocks = 1;
-  note_launch();
-  kern<<<(unsigned)blocks, kStreamThreads, 0, st>>>(nullptr, single, nullptr, total_windows, fp, lp, work,
-                                                     kWindowBytes / (int64_t)sizeof(typename P::T), nullptr);
-  return cudaGetLastError();
+  return launch_any(s_dev, count, single, win_series, total_windows, first_piece, last_piece, work, y_dtype, nan,
+                    cfg, 0, st);
 }
 
 cudaError_t launch_argminmax_sm(const SeriesDev& single, int64_t total_windows, Piece* first_piece,
                                 Piece* last_piece, WorkCounters* work, tsds_dtype y_dtype, tsds_nan_mode nan,
-                                int sm_count, cudaStream_t st) {
-  if (total_windows <= 0) return cudaSuccess;
-  const bool ign = nan == TSDS_NAN_IGNORE;
-#define TSDS_LAUNCH(POL, NM) launch_pol_sm<POL, NM>(single, total_windows, first_piece, last_piece, work, sm_count, st)
-  switch (y_dtype) {
-    case TSDS_I8: return TSDS_LAUNCH(PolSmallInt<int8_t>, 0);
-    case TSDS_U8: return TSDS_LAUNCH(PolSmallInt<uint8_t>, 0);
-    case TSDS_I16: return TSDS_LAUNCH(PolSmallInt<int16_t>, 0);
-    case TSDS_U16: return TSDS_LAUNCH(PolSmallInt<uint16_t>, 0);
-    case TSDS_I32: return TSDS_LAUNCH(PolInt32<int32_t>, 0);
-    case TSDS_U32: return TSDS_LAUNCH(PolInt32<uint32_t>, 0);
-    case TSDS_I64: return TSDS_LAUNCH(PolI64, 0);
-    case TSDS_U64: return TSDS_LAUNCH(PolU64, 0);
-    case TSDS_F16: return ign ? TSDS_LAUNCH(PolF16<1>, 1) : TSDS_LAUNCH(PolF16<0>, 0);
-    case TSDS_F32: return ign ? TSDS_LAUNCH(PolF32<1>, 1) : TSDS_LAUNCH(PolF32<0>, 0);
-    case TSDS_F64: return ign ? TSDS_LAUNCH(PolF64Ign, 1) : TSDS_LAUNCH(PolF64Prop, 0);
-    default: return cudaErrorInvalidValue;
-  }
-#undef TSDS_LAUNCH
+                                const StreamConfig& cfg, int sm_count, cudaStream_t st) {
+  return launch_any(nullptr, 1, single, nullptr, total_windows, first_piece, last_piece, work, y_dtype, nan, cfg,
+                    sm_count, st);
 }
 
 }  // namespace tsds
+
+extern "C" int tsds_stream_variant(int variant) {
+  if (variant < tsds::STREAM_AUTO || variant > tsds::STREAM_SEG) return -1;
+  const int prev = tsds::variant_override();
+  tsds::g_variant.store(variant, std::memory_order_relaxed);
+  return prev;
+}

@@ -41,6 +41,7 @@ static size_t up256(size_t v) { return (v + 255) / 256 * 256; }
 struct BatchLayout {
   int64_t count = 0;
   int64_t total_nb = 0, max_nb = 0, total_windows = 0, y_bytes = 0;
+  int64_t mean_bin_bytes = 0;  // bytes-weighted mean bin size of the binned series
   bool any_full = false;       // some series returns every index
   size_t off_desc = 0, off_edges = 0, off_res = 0, off_cnt = 0, off_work = 0, off_map = 0, off_first = 0,
          off_last = 0, total = 0;
@@ -91,6 +92,7 @@ static BatchLayout make_layout(tsds_algo algo, const tsds_series* s, int64_t cou
   L.host.resize((size_t)count);
   L.nb_before.resize((size_t)count);
   int64_t nb_sum = 0, win_sum = 0;
+  double wsum = 0.0, wbin = 0.0;
   for (int64_t i = 0; i < count; ++i) {
     const tsds_series& q = s[i];
     SeriesDev& d = L.host[(size_t)i];
@@ -107,9 +109,15 @@ static BatchLayout make_layout(tsds_algo algo, const tsds_series* s, int64_t cou
     d.idx_bias = 0;
     nb_sum += d.nb;
     L.max_nb = std::max(L.max_nb, d.nb);
-    if (d.nb > 0) win_sum += (q.n + welems - 1) / welems;
+    if (d.nb > 0) {
+      win_sum += (q.n + welems - 1) / welems;
+      const double bytes = (double)q.n * (double)dtype_size(y_dtype);
+      wsum += bytes;
+      wbin += bytes * (bytes / (double)d.nb);
+    }
     L.y_bytes += q.n * dtype_size(y_dtype);
   }
+  L.mean_bin_bytes = wsum > 0.0 ? (int64_t)(wbin / wsum) : 0;
   L.total_nb = nb_sum;
   L.total_windows = win_sum;
   size_t o = 0;
@@ -138,6 +146,7 @@ static void bind_layout(BatchLayout& L, char* base, tsds_dtype y_dtype, int64_t 
     d.res = reinterpret_cast<int64_t*>(base + L.off_res) + 2 * before;
     d.cnt = reinterpret_cast<uint32_t*>(base + L.off_cnt) + before;
     d.win_base = win;
+    d.status = &reinterpret_cast<WorkCounters*>(base + L.off_work)->status;
     if (d.nb > 0) win += (d.n + welems - 1) / welems;
   }
   L.total_windows = win;
@@ -155,7 +164,9 @@ static void rebase_windows(BatchLayout& L, tsds_dtype y_dtype, int64_t window_by
 
 // The kernel sequence of one execution (descriptors and window map in place).
 static tsds_status enqueue(const BatchLayout& L, char* base, tsds_algo algo, bool has_x, tsds_dtype x_dtype,
-                           tsds_dtype y_dtype, tsds_nan_mode nan, const StreamConfig& cfg, cudaStream_t st) {
+                           tsds_dtype y_dtype, tsds_nan_mode nan, const StreamConfig& shape, cudaStream_t st) {
+  StreamConfig cfg = shape;
+  cfg.mean_bin_bytes = L.mean_bin_bytes;
   const SeriesDev* sd = reinterpret_cast<const SeriesDev*>(base + L.off_desc);
   SeriesDev none;
   memset(&none, 0, sizeof none);
@@ -189,10 +200,15 @@ static tsds_status upload(BatchLayout& L, char* base, tsds_dtype y_dtype, const 
 
 // ---------------------------------------------------------------- autotuner
 
-// Candidate launch shapes.  The smallest window must come first: the scratch is
-// laid out for it (the most windows).
+// Candidate launch shapes: window bytes, CTAs per SM, -, kernel variant.  The
+// smallest window must come first: the scratch is laid out for it (the most
+// windows).  Without a tuned choice a plan runs the default shape (64 KB
+// windows, variant by mean bin size).
 static const StreamConfig kCandidates[] = {
-    {16 * 1024, 0}, {32 * 1024, 0}, {64 * 1024, 0}, {128 * 1024, 0}, {64 * 1024, 2}, {256 * 1024, 0}};
+    {16 * 1024, 0, nullptr, STREAM_RING},  {32 * 1024, 0, nullptr, STREAM_RING}, {64 * 1024, 0, nullptr, STREAM_RING},
+    {128 * 1024, 0, nullptr, STREAM_RING}, {64 * 1024, 2, nullptr, STREAM_RING}, {256 * 1024, 0, nullptr, STREAM_RING},
+    {32 * 1024, 0, nullptr, STREAM_LDG},   {64 * 1024, 0, nullptr, STREAM_LDG},  {256 * 1024, 0, nullptr, STREAM_LDG},
+    {32 * 1024, 0, nullptr, STREAM_SEG},   {64 * 1024, 0, nullptr, STREAM_SEG},  {256 * 1024, 0, nullptr, STREAM_SEG}};
 constexpr int kNumCandidates = sizeof(kCandidates) / sizeof(kCandidates[0]);
 
 static std::mutex g_tune_mu;
@@ -204,7 +220,10 @@ static std::string tune_key(tsds_algo algo, tsds_dtype y_dtype, bool has_x, cons
   for (int64_t b = std::max<int64_t>(L.y_bytes, 1); b > 1; b >>= 1) ++bytes_class;
   for (int64_t c = L.count; c > 1; c >>= 1) ++count_class;
   char k[128];
-  snprintf(k, sizeof k, "a%d_y%d_x%d_b%d_c%d", (int)algo, (int)y_dtype, has_x ? 1 : 0, bytes_class, count_class);
+  int bin_class = 0;
+  for (int64_t b = std::max<int64_t>(L.mean_bin_bytes, 1); b > 1; b >>= 1) ++bin_class;
+  snprintf(k, sizeof k, "s2_a%d_y%d_x%d_b%d_c%d_m%d", (int)algo, (int)y_dtype, has_x ? 1 : 0, bytes_class,
+           count_class, bin_class);
   return k;
 }
 
@@ -327,7 +346,7 @@ tsds_status tsds_plan_create(tsds_plan* plan, tsds_algo algo, const tsds_series*
   }
   bind_layout(P->L, P->base, y_dtype, kCandidates[0].window_bytes);
 
-  int choice = 2;   // 64 KB windows, as many CTAs as fit
+  int choice = -1;   // the default shape
   const std::string key = tune_key(algo, y_dtype, P->has_x, P->L);
   bool have = false;
   {
@@ -350,7 +369,7 @@ tsds_status tsds_plan_create(tsds_plan* plan, tsds_algo algo, const tsds_series*
     tune_store_locked();
   }
   P->tuned_index = choice;
-  P->cfg = kCandidates[choice];
+  P->cfg = choice >= 0 ? kCandidates[choice] : StreamConfig();
   s = upload(P->L, P->base, y_dtype, P->cfg, st);
   if (s != TSDS_OK) { tsds_plan_destroy(p); return s; }
 
@@ -386,13 +405,18 @@ tsds_status tsds_plan_execute(tsds_plan plan, void* stream) {
 }
 
 tsds_status tsds_plan_info(tsds_plan plan, int64_t* window_bytes, int* ctas_per_sm, int64_t* windows,
-                           int64_t* scratch_bytes) {
+                           int64_t* scratch_bytes, int* variant) {
   if (!plan) return fail(TSDS_EINVAL, "tsds_plan_info: plan is NULL");
   PlanImpl* P = &plan->impl;
   if (window_bytes) *window_bytes = P->cfg.window_bytes;
   if (ctas_per_sm) *ctas_per_sm = P->cfg.ctas_per_sm;
   if (windows) *windows = P->L.total_windows;
   if (scratch_bytes) *scratch_bytes = (int64_t)P->L.total;
+  if (variant) {
+    StreamConfig c = P->cfg;
+    c.mean_bin_bytes = P->L.mean_bin_bytes;
+    *variant = stream_variant_for(c, dtype_size(P->y_dtype));
+  }
   return TSDS_OK;
 }
 

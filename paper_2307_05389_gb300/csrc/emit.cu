@@ -40,6 +40,11 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit(const SeriesDev* __restri
   const SeriesDev S = sd ? sd[blockIdx.x] : single;
   const int64_t nb = S.nb;
   if (nb <= 0) return;
+  if (S.status && *S.status) {
+    // the streaming pass failed on the device (a bounded wait ran out): report it as -status
+    if (threadIdx.x == 0 && S.out_count) *S.out_count = -(int64_t)*S.status;
+    return;
+  }
   __shared__ int64_t warp_tot[kEmitThreads / 32];
   __shared__ int64_t total_sh;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;

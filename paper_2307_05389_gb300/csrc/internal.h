@@ -27,6 +27,8 @@ struct SeriesDev {
   int64_t* out;       // output indices
   int64_t* out_count; // device count
   int64_t idx_bias;   // added to every index written (1 for the MinMaxLTTB interior)
+  const unsigned long long* status;  // device status word of the streaming pass (null: none);
+                                     // non-zero makes emit report -status as the count
 };
 
 // Partial argmin/argmax of one bin piece: ordered 64-bit keys plus indices.
@@ -39,7 +41,8 @@ struct Piece {
 
 struct WorkCounters {
   unsigned long long next_window;
-  unsigned long long pad[7];
+  unsigned long long status;   // tsds_status of a device-side failure (TSDS_ETIMEOUT), 0 when fine
+  unsigned long long pad[6];
 };
 
 inline int64_t dtype_size(tsds_dtype d) {
@@ -55,15 +58,32 @@ inline bool dtype_is_float(tsds_dtype d) { return d == TSDS_F16 || d == TSDS_F32
 
 inline int64_t window_elems(tsds_dtype y_dtype) { return kWindowBytes / dtype_size(y_dtype); }
 
+// Variants of the streaming pass: RING stages y through a shared-memory ring
+// filled by bulk async copies, LDG streams it through registers with one warp
+// per bin (cheapest per byte: large bins), SEG streams it through registers
+// and splits bins across lanes (cheapest per bin: small bins; dtypes of up to
+// 32 bits).  AUTO picks SEG when the bytes-weighted mean bin size is below
+// seg_max_bin_bytes(element size), LDG otherwise (crossovers measured on
+// GB300 over 1 GB and 40 MB inputs).
+enum StreamVariant : int { STREAM_AUTO = 0, STREAM_RING = 1, STREAM_LDG = 2, STREAM_SEG = 3 };
+inline int64_t seg_max_bin_bytes(int64_t elem_bytes) {
+  return elem_bytes >= 4 ? 1536 : elem_bytes == 2 ? 1024 : 512;
+}
+
 // Launch shape of the streaming pass (the batched plans autotune it).
 struct StreamConfig {
-  int64_t window_bytes = kWindowBytes;  // bytes of y per warp claim: a multiple of 16, >= 4096
+  int64_t window_bytes = kWindowBytes;  // bytes of y per warp claim: a multiple of 4096
   int ctas_per_sm = 0;                  // 0: as many as fit
   // When set, the number of windows is read from device memory here (the
   // server resolves query ranges on the device) and the full persistent grid
   // is launched.
   const int64_t* total_windows_dev = nullptr;
+  int variant = STREAM_AUTO;
+  int64_t mean_bin_bytes = 0;           // bytes-weighted mean bin size (0: unknown, ring)
 };
+
+// The variant a launch with this shape runs for elements of elem_bytes.
+int stream_variant_for(const StreamConfig& cfg, int64_t elem_bytes);
 
 // ---- launchers (each returns the launch's cudaError_t)
 
@@ -82,6 +102,17 @@ cudaError_t launch_argminmax(const SeriesDev* s_dev, int count, const SeriesDev&
                              Piece* first_piece, Piece* last_piece, WorkCounters* work,
                              tsds_dtype y_dtype, tsds_nan_mode nan, cudaStream_t st,
                              const StreamConfig& cfg = StreamConfig());
+
+// The same pass for one series with the SM count given by the caller instead
+// of the library's per-device state (for the entry point that must not create
+// the library's memory pool).
+cudaError_t launch_argminmax_sm(const SeriesDev& single, int64_t total_windows, Piece* first_piece,
+                                Piece* last_piece, WorkCounters* work, tsds_dtype y_dtype, tsds_nan_mode nan,
+                                const StreamConfig& cfg, int sm_count, cudaStream_t st);
+
+// A kernel whose barrier wait nothing satisfies, bounded by `rounds`; writes
+// the status it ends with (TSDS_ETIMEOUT) to *status.
+cudaError_t launch_wait_probe(unsigned long long* status, unsigned rounds, cudaStream_t st);
 
 // Every series with nb == 0 gets 0..n-1 (its n_out >= n) and *out_count = n.
 cudaError_t launch_iota_batched(const SeriesDev* s_dev, int count, cudaStream_t st);

@@ -32,9 +32,6 @@ namespace tsds {
 constexpr size_t kNoallocScratchBytes = 8u << 20;
 static __device__ __align__(256) unsigned char g_scratch[kNoallocScratchBytes];
 
-cudaError_t launch_argminmax_sm(const SeriesDev& single, int64_t total_windows, Piece* first_piece,
-                                Piece* last_piece, WorkCounters* work, tsds_dtype y_dtype, tsds_nan_mode nan,
-                                int sm_count, cudaStream_t st);
 tsds_status fail(tsds_status s, const char* fmt, ...);
 
 namespace {
@@ -161,10 +158,13 @@ extern "C" tsds_status tsds_minmax_noalloc(const void* x, tsds_dtype x_dtype, co
   S.out = out;
   S.out_count = out_count;
   S.idx_bias = 0;
+  S.status = &reinterpret_cast<WorkCounters*>(base + off_work)->status;
   NA_CK(launch_edges(nullptr, 1, &S, x != nullptr, x_dtype, nb, st));
+  StreamConfig cfg;
+  cfg.mean_bin_bytes = n / nb * dtype_size(y_dtype);
   NA_CK(launch_argminmax_sm(S, windows, reinterpret_cast<Piece*>(base + off_first),
                             reinterpret_cast<Piece*>(base + off_last), reinterpret_cast<WorkCounters*>(base + off_work),
-                            y_dtype, nan, dev->sm_count, st));
+                            y_dtype, nan, cfg, dev->sm_count, st));
   NA_CK(launch_emit(nullptr, 1, S, ALGO_MINMAX, st));
   return TSDS_OK;
 }

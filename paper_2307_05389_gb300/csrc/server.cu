@@ -313,12 +313,20 @@ tsds_status launch_batch(const Server& S, Slot& sl, const std::vector<tsds_query
   const size_t off_win = o; o = up256(o + (size_t)count * 8 + 8);
   std::vector<size_t> off_edges(count), off_res(count), off_cnt(count), off_R(count), off_lt(count);
   int64_t max_nb = 0, win_ub = 0;
+  double wsum = 0.0, wbin = 0.0;   // bytes-weighted mean bin size (x ranges: the whole series as the estimate)
   for (int i = 0; i < count; ++i) {
     const int64_t nb = nb_of(qs[i]);
     max_nb = std::max(max_nb, nb);
     off_edges[i] = o; o = up256(o + (size_t)(nb + 1) * 8);
     off_res[i] = o;   o = up256(o + (size_t)nb * 16);
     win_ub += (ser[i].n * ys + window_bytes - 1) / window_bytes + 1;
+    const int64_t pts = qs[i].by_x ? ser[i].n
+                                   : std::max<int64_t>(0, std::min(qs[i].hi, ser[i].n) - std::max<int64_t>(qs[i].lo, 0));
+    if (nb > 0 && pts > 0) {
+      const double bytes = (double)pts * (double)ys;
+      wsum += bytes;
+      wbin += bytes * (bytes / (double)nb);
+    }
   }
   const size_t zero_begin = o;    // piece counters and the work counter start at zero
   for (int i = 0; i < count; ++i) { off_cnt[i] = o; o += (size_t)nb_of(qs[i]) * 4; }
@@ -402,6 +410,7 @@ tsds_status launch_batch(const Server& S, Slot& sl, const std::vector<tsds_query
     s.edges = reinterpret_cast<int64_t*>(base + off_edges[i]);
     s.res = reinterpret_cast<int64_t*>(base + off_res[i]);
     s.cnt = reinterpret_cast<uint32_t*>(base + off_cnt[i]);
+    s.status = &reinterpret_cast<WorkCounters*>(base + off_work)->status;
   }
   for (int t = 0; t < nlt; ++t) {
     const int i = lt[t];
@@ -460,6 +469,7 @@ tsds_status launch_batch(const Server& S, Slot& sl, const std::vector<tsds_query
   memset(&none, 0, sizeof none);
   StreamConfig cfg;
   cfg.total_windows_dev = total_dev;
+  cfg.mean_bin_bytes = wsum > 0.0 ? (int64_t)(wbin / wsum) : 0;
   // a batch holds one NaN mode and either M4 or the MinMax-like algorithms (the admission groups them)
   const tsds_nan_mode nan = (tsds_nan_mode)qs[0].nan;
   const bool m4 = qs[0].algo == TSDS_ALGO_M4;

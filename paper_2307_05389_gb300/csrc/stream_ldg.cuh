@@ -1,0 +1,154 @@
+// stream_ldg.cuh -- the register-streaming variant of the per-bin
+// argmin/argmax pass (included by argminmax.cu after the policies).
+//
+// Each lane loads 4 vectors of 16 bytes per step straight into registers
+// (coalesced across the warp, 2 KB per warp-step) and resolves indices every
+// 8 steps from a cached re-read.  Its per-byte overhead is the smallest, so it
+// is the faster variant when bins are large (tens of KB and more); the ring
+// variant in argminmax.cu wins when bins are small, since there every bin
+// costs one shared-memory round trip instead of one DRAM round trip.
+#pragma once
+
+constexpr int kStreamThreadsLdg = 256;   // 8 warps per CTA
+constexpr int kCH = 8;                   // steps between index resolutions
+
+// ---------------------------------------------------------------------------
+// One bin piece [a, b) of a series, reduced by one warp.
+// ---------------------------------------------------------------------------
+template <class P, bool MIN>
+__device__ __noinline__ int find_first_g(const uint4* __restrict__ vp, int nvec, int t, int lane,
+                                       typename P::Acc target) {
+  // element offset (from the first body element) of the first match in step t
+  using T = typename P::T;
+  const int vb = t * (32 * kU) + lane;
+#pragma unroll 1
+  for (int u = 0; u < kU; ++u) {
+    const int vi = vb + u * 32;
+    if (vi >= nvec) break;
+    const uint4 v = ldg_vec(vp + vi);
+#pragma unroll
+    for (int e = 0; e < P::E; ++e) {
+      const T val = vec_elem<T, P::E>(v, e);
+      if (MIN ? P::match_min(val, target) : P::match_max(val, target)) return vi * P::E + e;
+    }
+  }
+  return -1;
+}
+
+template <class P>
+__device__ __forceinline__ Cand piece_ldg(const typename P::T* __restrict__ y, int64_t a, int64_t b) {
+  using T = typename P::T;
+  using Acc = typename P::Acc;
+  constexpr int E = P::E;
+  const int lane = threadIdx.x & 31;
+  Cand c;
+  cand_init(c);
+
+  // body: the 16-byte aligned vectors inside [a, b); head and tail elements
+  // outside it go through the scalar path
+  const uintptr_t addr = reinterpret_cast<uintptr_t>(y + a);
+  int64_t ia = a + (int64_t)(((16u - (unsigned)(addr & 15u)) & 15u) / sizeof(T));
+  if (ia > b) ia = b;
+  const int64_t nvec = (b - ia) / E;
+  const int64_t ib = ia + nvec * E;
+  for (int64_t i = a + lane; i < ia; i += 32) {
+    const T e = ldg_elem<T>(y + i);
+    cand_merge_min(c, P::elem_key_min(e), i);
+    cand_merge_max(c, P::elem_key_max(e), i);
+  }
+  for (int64_t i = ib + lane; i < b; i += 32) {
+    const T e = ldg_elem<T>(y + i);
+    cand_merge_min(c, P::elem_key_min(e), i);
+    cand_merge_max(c, P::elem_key_max(e), i);
+  }
+
+  if (nvec > 0) {
+    // a piece never exceeds one window, so step and vector numbers fit in 32 bits
+    const uint4* __restrict__ vp = reinterpret_cast<const uint4*>(y + ia);
+    const int nv = (int)nvec;
+    const int iters = (nv + 32 * kU - 1) / (32 * kU);
+    bool rvalid = false;
+    Acc rmin{}, rmax{};
+    int rimin = -1, rimax = -1;
+    for (int t0 = 0; t0 < iters; t0 += kCH) {
+      const int t1 = min(t0 + kCH, iters);
+      bool cvalid = false;
+      Acc cmin{}, cmax{};
+      int tmin = 0, tmax = 0;
+      for (int t = t0; t < t1; ++t) {
+        const int vb = t * (32 * kU) + lane;
+        uint4 v[kU];
+        if (vb + (kU - 1) * 32 < nv) {
+#pragma unroll
+          for (int u = 0; u < kU; ++u) v[u] = ldg_vec(vp + vb + u * 32);
+        } else {
+          if (vb >= nv) continue;
+          v[0] = ldg_vec(vp + vb);
+#pragma unroll
+          for (int u = 1; u < kU; ++u) v[u] = (vb + u * 32 < nv) ? ldg_vec(vp + vb + u * 32) : v[0];
+        }
+        Acc gmin, gmax;
+        P::group(v, gmin, gmax);
+        if (!cvalid || P::better_min(gmin, cmin)) { cmin = gmin; tmin = t; }
+        if (!cvalid || P::better_max(gmax, cmax)) { cmax = gmax; tmax = t; }
+        cvalid = true;
+      }
+      if (cvalid) {
+        if (!rvalid || P::better_min(cmin, rmin)) {
+          rmin = cmin;
+          rimin = find_first_g<P, true>(vp, nv, tmin, lane, cmin);
+        }
+        if (!rvalid || P::better_max(cmax, rmax)) {
+          rmax = cmax;
+          rimax = find_first_g<P, false>(vp, nv, tmax, lane, cmax);
+        }
+        rvalid = true;
+      }
+    }
+    if (rvalid) {
+      cand_merge_min(c, P::key_min(rmin), ia + rimin);
+      cand_merge_max(c, P::key_max(rmax), ia + rimax);
+    }
+  }
+  cand_warp_reduce(c);
+  return c;
+}
+
+template <class P, int NM, bool MULTI>
+__global__ void __launch_bounds__(kStreamThreadsLdg)
+k_argminmax_ldg(const SeriesDev* __restrict__ sd, SeriesDev single, const int32_t* __restrict__ win_series,
+            int64_t total_windows, Piece* __restrict__ first_piece, Piece* __restrict__ last_piece,
+            WorkCounters* __restrict__ work, int64_t welems, const int64_t* __restrict__ total_dev) {
+  using T = typename P::T;
+  const int lane = threadIdx.x & 31;
+  if (total_dev) total_windows = *total_dev;
+  for (;;) {
+    unsigned long long wu = 0;
+    if (lane == 0) wu = atomicAdd(&work->next_window, 1ull);
+    const int64_t w = (int64_t)__shfl_sync(0xffffffffu, wu, 0);
+    if (w >= total_windows) break;
+    SeriesDev S = MULTI ? sd[win_series[w]] : single;
+    const T* __restrict__ y = static_cast<const T*>(S.y);
+    const int64_t* __restrict__ edges = S.edges;
+    const int64_t nb = S.nb;
+    const int64_t k = w - S.win_base;
+    const int64_t ws = k * welems;
+    const int64_t we = min(ws + welems, S.n);
+    // the bin holding ws: the last b with edges[b] <= ws
+    int64_t b = warp_lower_bound(1, nb + 1, [&](int64_t j) { return __ldg(edges + j) > ws; }) - 1;
+    int64_t lo = __ldg(edges + b);
+    while (b < nb && lo < we) {
+      // the ends of the next 32 bins, one per lane
+      const int64_t my_hi = (b + lane < nb) ? __ldg(edges + b + 1 + lane) : INT64_MAX;
+      for (int q = 0; q < 32 && b < nb && lo < we; ++q, ++b) {
+        const int64_t hi = __shfl_sync(0xffffffffu, my_hi, q);
+        if (hi > lo) {
+          const int64_t pa = max(lo, ws), pb = min(hi, we);
+          Cand c = piece_ldg<P>(y, pa, pb);
+          bin_result<P, NM>(S, b, lo, hi, k, welems, c, first_piece, last_piece, lane);
+        }
+        lo = hi;
+      }
+    }
+  }
+}

@@ -1,0 +1,426 @@
+// stream_seg.cuh -- the segmented variant of the per-bin argmin/argmax pass
+// (included by argminmax.cu after the policies and bin_result), for dtypes of
+// up to 32 bits and bins of a few hundred bytes to some KB.
+//
+// The other variants give every bin to the whole warp: a bin costs a warp
+// reduction and a few dependent memory round trips, which dominate once bins
+// are small.  Here the warp streams its window in sub-steps of 512 bytes, one
+// 16-byte vector per lane, and the bins are handled by the lanes that hold
+// them:
+//  * every element becomes a 64-bit packed pair (32-bit ordered key, 32-bit
+//    offset in the window) for the minimum and (key, complemented offset) for
+//    the maximum, so one unsigned min/max keeps the smallest/largest value and
+//    the earliest index on ties;
+//  * a sub-step without a bin boundary costs one packed group min/max per
+//    lane (value space, as in the other variants); a lane looks up the
+//    element index only when its extremum strictly improves, and the lanes
+//    are joined when the next boundary comes;
+//  * in a sub-step with boundaries, the bin starts that fall in it (from 64
+//    prefetched bin starts in registers) become per-lane bit masks in shared
+//    memory; each lane walks its elements, writing the bins that open and
+//    close inside it directly, and a segmented warp scan joins the bins that
+//    cross lanes, so no bin costs a memory round trip of its own.
+// NaN rules live in the keys: NaN-propagate gives a NaN the smallest minimum
+// key and the largest maximum key (the first NaN wins both), NaN-ignore the
+// opposite, so an all-NaN bin selects its first index.
+#pragma once
+
+constexpr int kSegThreads = 256;   // 8 warps per CTA
+constexpr int kSegWarps = kSegThreads / 32;
+constexpr int kSegDepth = 8;       // sub-steps in flight per warp (4 KB)
+
+// Per-lane asynchronous 16-byte copies global -> shared (each lane reads back
+// only what it copied itself, so the lane's own group wait is the only
+// synchronisation).
+__device__ __forceinline__ void seg_cp16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void seg_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void seg_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// 32-bit ordered keys of one element (minimum side, maximum side).
+template <class T, int NM>
+__device__ __forceinline__ void seg_keys(T v, uint32_t& kmn, uint32_t& kmx) {
+  if constexpr (std::is_same<T, float>::value || std::is_same<T, __half>::value) {
+    float f;
+    if constexpr (std::is_same<T, __half>::value) f = __half2float(v);
+    else f = v;
+    uint32_t b = __float_as_uint(f);
+    if (b == 0x80000000u) b = 0u;   // -0 orders as +0
+    const uint32_t k = (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+    const bool nan = (b & 0x7fffffffu) > 0x7f800000u;
+    kmn = nan ? (NM == TSDS_NAN_PROPAGATE ? 0u : 0xffffffffu) : k;
+    kmx = nan ? (NM == TSDS_NAN_PROPAGATE ? 0xffffffffu : 0u) : k;
+  } else if constexpr (std::is_signed<T>::value) {
+    kmn = kmx = (uint32_t)(int32_t)v ^ 0x80000000u;
+  } else {
+    kmn = kmx = (uint32_t)v;
+  }
+}
+
+// A running selection: mn = (key << 32 | offset), mx = (key << 32 | ~offset).
+struct SegRun {
+  uint64_t mn, mx;
+};
+__device__ __forceinline__ void seg_empty(SegRun& r) {
+  r.mn = ~0ull;
+  r.mx = 0ull;
+}
+__device__ __forceinline__ void seg_add(SegRun& r, uint32_t kmn, uint32_t kmx, uint32_t rel) {
+  const uint64_t a = ((uint64_t)kmn << 32) | rel;
+  const uint64_t b = ((uint64_t)kmx << 32) | (0xffffffffu - rel);
+  r.mn = a < r.mn ? a : r.mn;
+  r.mx = b > r.mx ? b : r.mx;
+}
+__device__ __forceinline__ void seg_join(SegRun& r, const SegRun& o) {
+  r.mn = o.mn < r.mn ? o.mn : r.mn;
+  r.mx = o.mx > r.mx ? o.mx : r.mx;
+}
+__device__ __forceinline__ void seg_warp_join(SegRun& r) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    SegRun t;
+    t.mn = __shfl_xor_sync(0xffffffffu, r.mn, o);
+    t.mx = __shfl_xor_sync(0xffffffffu, r.mx, o);
+    seg_join(r, t);
+  }
+}
+// As an ordered-key candidate with series indices (offsets from ws).
+__device__ __forceinline__ Cand seg_cand(const SegRun& r, int64_t ws) {
+  Cand c;
+  c.kmin = r.mn >> 32;
+  c.imin = ws + (int64_t)(uint32_t)r.mn;
+  c.kmax = r.mx >> 32;
+  c.imax = ws + (int64_t)(0xffffffffu - (uint32_t)r.mx);
+  return c;
+}
+__device__ __forceinline__ void seg_write(const SeriesDev& S, int64_t b, const SegRun& r, int64_t ws) {
+  S.res[2 * b] = ws + (int64_t)(uint32_t)r.mn;
+  S.res[2 * b + 1] = ws + (int64_t)(0xffffffffu - (uint32_t)r.mx);
+}
+
+// The keys of a policy's running value (the value of one element).
+template <class P, int NM>
+__device__ __forceinline__ void seg_acc_keys(typename P::Acc a, uint32_t& kmn, uint32_t& kmx) {
+  if constexpr (P::kFloat) seg_keys<float, NM>((float)a, kmn, kmx);
+  else seg_keys<typename P::T, NM>((typename P::T)a, kmn, kmx);
+}
+
+// Per-lane running extremum of the full sub-steps without a bin start, kept
+// in value space: one packed group reduction per vector, and the element
+// index only when the lane's extremum strictly improves (the earliest
+// occurrence survives).
+template <class P>
+struct SegLane {
+  typename P::Acc vmin, vmax;
+  uint32_t rmin, rmax;   // window offsets
+  bool valid;
+};
+
+template <class P>
+__device__ __forceinline__ void seg_lane_group(SegLane<P>& L, const uint4& v, uint32_t rel) {
+  using T = typename P::T;
+  constexpr int E = 16 / sizeof(T);
+  typename P::Acc gmin, gmax;
+  P::group1(v, gmin, gmax);
+  const bool bmin = !L.valid || P::better_min(gmin, L.vmin);
+  const bool bmax = !L.valid || P::better_max(gmax, L.vmax);
+  if (bmin || bmax) {
+    T el[E];
+    memcpy(el, &v, 16);
+    if (bmin) {
+      int f = E - 1;
+#pragma unroll
+      for (int e = E - 2; e >= 0; --e)
+        if (P::match_min(el[e], gmin)) f = e;
+      L.vmin = gmin;
+      L.rmin = rel + (uint32_t)f;
+    }
+    if (bmax) {
+      int f = E - 1;
+#pragma unroll
+      for (int e = E - 2; e >= 0; --e)
+        if (P::match_max(el[e], gmax)) f = e;
+      L.vmax = gmax;
+      L.rmax = rel + (uint32_t)f;
+    }
+  }
+  L.valid = true;
+}
+
+template <class P, int NM>
+__device__ __forceinline__ void seg_lane_flush(SegLane<P>& L, SegRun& acc) {
+  if (L.valid) {
+    uint32_t kmn, kmx, t;
+    seg_acc_keys<P, NM>(L.vmin, kmn, t);
+    seg_acc_keys<P, NM>(L.vmax, t, kmx);
+    SegRun r;
+    r.mn = ((uint64_t)kmn << 32) | L.rmin;
+    r.mx = ((uint64_t)kmx << 32) | (0xffffffffu - L.rmax);
+    seg_join(acc, r);
+    L.valid = false;
+  }
+}
+
+// Starts the copy of sub-step m of the window's grid into the lane's slot:
+// lane `lane` takes the 16-byte vector (m*32 + lane) of the grid that starts
+// at the aligned address gbase (element position q0).  A vector that reaches
+// outside [ws, we) is assembled from the elements inside it with plain loads.
+// Commits one copy group per call, also past the last sub-step.
+template <class T>
+__device__ __forceinline__ void seg_issue(uint4* slot, const T* __restrict__ y, uintptr_t gbase, int64_t q0,
+                                          int64_t m, int64_t nsub, int64_t ws, int64_t we, int lane) {
+  constexpr int E = 16 / sizeof(T);
+  if (m < nsub) {
+    const int64_t vi = m * 32 + lane;
+    const int64_t p = q0 + vi * E;
+    if (p >= ws && p + E <= we) {
+      seg_cp16(slot, reinterpret_cast<const uint4*>(gbase) + vi);
+    } else {
+      T a[E];
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const int64_t i = p + e;
+        a[e] = (i >= ws && i < we) ? ldg_elem<T>(y + i) : T();
+      }
+      uint4 v;
+      memcpy(&v, a, 16);
+      *slot = v;
+    }
+  }
+  seg_commit();
+}
+
+// A partial sub-step (the window's first or last) with no bin start: each
+// lane adds its elements in [o_lo, o_hi).
+template <class T, int NM>
+__device__ __forceinline__ void seg_lane_add(SegRun& acc, const uint4& v, int lane, int o_lo, int o_hi,
+                                             uint32_t rel0) {
+  constexpr int E = 16 / sizeof(T);
+  T el[E];
+  memcpy(el, &v, 16);
+  const int ob = lane * E;
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    if (ob + e >= o_lo && ob + e < o_hi) {
+      uint32_t kmn, kmx;
+      seg_keys<T, NM>(el[e], kmn, kmx);
+      seg_add(acc, kmn, kmx, rel0 + (uint32_t)(ob + e));
+    }
+  }
+}
+
+template <class P, int NM, bool MULTI>
+__global__ void __launch_bounds__(kSegThreads)
+k_argminmax_seg(const SeriesDev* __restrict__ sd, SeriesDev single, const int32_t* __restrict__ win_series,
+                int64_t total_windows, Piece* __restrict__ first_piece, Piece* __restrict__ last_piece,
+                WorkCounters* __restrict__ work, int64_t welems, const int64_t* __restrict__ total_dev) {
+  using T = typename P::T;
+  static_assert(sizeof(T) <= 4, "the segmented pass packs 32-bit keys");
+  constexpr int E = 16 / sizeof(T);   // elements per lane per sub-step
+  constexpr int SUB = 32 * E;         // elements per sub-step
+  constexpr unsigned FULL = 0xffffffffu;
+  __shared__ __align__(16) uint4 s_stage[kSegWarps][kSegDepth][32];
+  __shared__ uint32_t s_mask[kSegWarps][32];
+  __shared__ uint8_t s_tab[kSegWarps][SUB];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t* mask = s_mask[warp];
+  uint8_t* tab = s_tab[warp];
+  uint4* stage = &s_stage[warp][0][lane];   // slot d of this lane: stage[d * 32]
+  if (total_dev) total_windows = *total_dev;
+  for (;;) {
+    unsigned long long wu = 0;
+    if (lane == 0) wu = atomicAdd(&work->next_window, 1ull);
+    const int64_t w = (int64_t)__shfl_sync(FULL, wu, 0);
+    if (w >= total_windows) break;
+    const SeriesDev S = MULTI ? sd[win_series[w]] : single;
+    const T* __restrict__ y = static_cast<const T*>(S.y);
+    const int64_t* __restrict__ edges = S.edges;
+    const int64_t nb = S.nb;
+    const int64_t k = w - S.win_base;
+    const int64_t ws = k * welems;
+    const int64_t we = min(ws + welems, S.n);
+    // the sub-step grid: 16-byte aligned, starting at or before ws
+    const uintptr_t a_ws = reinterpret_cast<uintptr_t>(y + ws);
+    const uintptr_t gbase = a_ws & ~(uintptr_t)15;
+    const int64_t q0 = ws - (int64_t)((a_ws - gbase) / sizeof(T));
+    const int64_t nsub = (we - q0 + SUB - 1) / SUB;
+    // kSegDepth - 1 sub-steps in flight ahead of the one being reduced
+#pragma unroll
+    for (int d = 0; d < kSegDepth - 1; ++d) seg_issue<T>(stage + d * 32, y, gbase, q0, d, nsub, ws, we, lane);
+
+    // the bin holding ws, and the next 64 bin starts (cur: eb..eb+31, nxt: eb+32..eb+63)
+    const int64_t b0 = warp_lower_bound(1, nb + 1, [&](int64_t j) { return __ldg(edges + j) > ws; }) - 1;
+    const int64_t lo0 = __ldg(edges + b0);
+    int64_t eb = b0 + 1;
+    int64_t cur = (eb + lane <= nb) ? __ldg(edges + eb + lane) : INT64_MAX;
+    int64_t nxt = (eb + 32 + lane <= nb) ? __ldg(edges + eb + 32 + lane) : INT64_MAX;
+    int ep = 0;                          // cur[ep..31] not yet passed
+    int64_t cb = b0;                     // the open bin
+    SegRun carry, acc, fpart;            // open bin before the sub-step (uniform); lanes' open-bin
+    seg_empty(carry);                    // pairs since the last boundary; b0's part when it began
+    seg_empty(acc);                      // before ws and closes in this window (uniform)
+    seg_empty(fpart);
+    SegLane<P> lane_run;
+    lane_run.valid = false;
+    bool adirty = false, fset = false;
+    const bool b0_piece = lo0 < ws;
+
+#pragma unroll 1
+    for (int64_t m = 0; m < nsub; ++m) {
+      {
+        seg_issue<T>(stage + (int)((m + kSegDepth - 1) % kSegDepth) * 32, y, gbase, q0, m + kSegDepth - 1, nsub, ws,
+                     we, lane);
+        seg_wait<kSegDepth - 1>();
+        const uint4 cv = stage[(int)(m % kSegDepth) * 32];
+        const int64_t qs = q0 + m * SUB;
+        const int64_t s_hi = min(qs + SUB, we);
+        const int o_lo = (int)(max(qs, ws) - qs), o_hi = (int)(s_hi - qs);
+        const uint32_t rel0 = (uint32_t)(qs - ws);   // offsets wrap back into range for valid elements
+        const int64_t ne = __shfl_sync(FULL, cur, ep);
+        if (ne >= s_hi) {
+          if (o_lo == 0 && o_hi == SUB) seg_lane_group<P>(lane_run, cv, rel0 + (uint32_t)(lane * E));
+          else seg_lane_add<T, NM>(acc, cv, lane, o_lo, o_hi, rel0);
+          adirty = true;
+          continue;
+        }
+        if (adirty) {
+          seg_lane_flush<P, NM>(lane_run, acc);
+          seg_warp_join(acc);
+          seg_join(carry, acc);
+          seg_empty(acc);
+          adirty = false;
+        }
+        T el[E];
+        memcpy(el, &cv, 16);
+        int r_lo = o_lo;
+        for (;;) {
+          // this round: positions [r_lo, r_hi) and the bin starts cur[j] < qs + r_hi
+          const int64_t n0 = __shfl_sync(FULL, nxt, 0);
+          const int r_hi = n0 < s_hi ? (int)(n0 - qs) : o_hi;
+          const bool in = lane >= ep && cur < qs + r_hi;
+          const int64_t cdn = __shfl_down_sync(FULL, cur, 1);
+          // of equal starts (empty bins) only the last opens a bin
+          const bool last = in && (lane == 31 || cdn != cur);
+          const unsigned inb = __ballot_sync(FULL, in);
+          __syncwarp();
+          mask[lane] = 0u;
+          __syncwarp();
+          // (the range check only matters for bin starts that are out of
+          // order, which an unsorted x can produce)
+          if (last && cur >= qs + r_lo) {
+            const int pos = (int)(cur - qs);
+            tab[pos] = (uint8_t)lane;
+            atomicOr(&mask[pos / E], 1u << (pos % E));
+          }
+          __syncwarp();
+          const uint32_t my = mask[lane];
+
+          SegRun run, head;
+          seg_empty(run);
+          seg_empty(head);
+          bool hv = false, ropen = false;
+          int64_t rb = cb;
+#pragma unroll
+          for (int e = 0; e < E; ++e) {
+            const int o = lane * E + e;
+            if ((my >> e) & 1u) {
+              if (ropen) seg_write(S, rb, run, ws);   // opened and closed in this lane
+              else { head = run; hv = true; }         // closes the bin open at the lane's start
+              rb = eb + tab[o];
+              ropen = true;
+              seg_empty(run);
+            }
+            if (o >= r_lo && o < r_hi) {
+              uint32_t kmn, kmx;
+              seg_keys<T, NM>(el[e], kmn, kmx);
+              seg_add(run, kmn, kmx, rel0 + (uint32_t)o);
+            }
+          }
+
+          // segmented inclusive scan of the lanes' open runs (a lane that
+          // opened a bin starts a segment; lane 0 continues the carry)
+          SegRun sc = run;
+          int64_t sb = ropen ? rb : cb;
+          bool f = ropen;
+          if (lane == 0 && !f) {
+            seg_join(sc, carry);
+            f = true;
+          }
+#pragma unroll
+          for (int d = 1; d < 32; d <<= 1) {
+            SegRun o;
+            o.mn = __shfl_up_sync(FULL, sc.mn, d);
+            o.mx = __shfl_up_sync(FULL, sc.mx, d);
+            const int64_t ob = __shfl_up_sync(FULL, sb, d);
+            const int of = __shfl_up_sync(FULL, (int)f, d);
+            if (lane >= d) {
+              if (!f) {
+                seg_join(sc, o);
+                sb = ob;
+              }
+              f = f || of;
+            }
+          }
+          // a lane's head joins everything before it in its bin
+          SegRun pv;
+          pv.mn = __shfl_up_sync(FULL, sc.mn, 1);
+          pv.mx = __shfl_up_sync(FULL, sc.mx, 1);
+          int64_t pb = __shfl_up_sync(FULL, sb, 1);
+          if (lane == 0) {
+            pv = carry;
+            pb = cb;
+          }
+          bool is_first = false;
+          if (hv) {
+            seg_join(head, pv);
+            if (pb == b0 && b0_piece) is_first = true;
+            else seg_write(S, pb, head, ws);
+          }
+          const unsigned fb = __ballot_sync(FULL, is_first);
+          if (fb) {
+            const int src = __ffs(fb) - 1;
+            fpart.mn = __shfl_sync(FULL, head.mn, src);
+            fpart.mx = __shfl_sync(FULL, head.mx, src);
+            fset = true;
+          }
+          carry.mn = __shfl_sync(FULL, sc.mn, 31);
+          carry.mx = __shfl_sync(FULL, sc.mx, 31);
+          cb = __shfl_sync(FULL, sb, 31);
+
+          if (r_hi < o_hi) {
+            // every start in cur is passed (those equal to nxt[0] open empty bins)
+            cur = nxt;
+            eb += 32;
+            nxt = (eb + 32 + lane <= nb) ? __ldg(edges + eb + 32 + lane) : INT64_MAX;
+            ep = 0;
+            r_lo = r_hi;
+            continue;
+          }
+          ep += __popc(inb);
+          if (ep >= 32) {
+            cur = nxt;
+            eb += 32;
+            nxt = (eb + 32 + lane <= nb) ? __ldg(edges + eb + 32 + lane) : INT64_MAX;
+            ep = 0;
+          }
+          break;
+        }
+      }
+    }
+    if (adirty) {
+      seg_lane_flush<P, NM>(lane_run, acc);
+      seg_warp_join(acc);
+      seg_join(carry, acc);
+    }
+    // the bin open at the window's end, then b0 if it began before ws and closed here
+    bin_result<P, NM>(S, cb, __ldg(edges + cb), __ldg(edges + cb + 1), k, welems, seg_cand(carry, ws), first_piece,
+                      last_piece, lane);
+    if (fset)
+      bin_result<P, NM>(S, b0, lo0, __ldg(edges + b0 + 1), k, welems, seg_cand(fpart, ws), first_piece, last_piece,
+                        lane);
+  }
+}

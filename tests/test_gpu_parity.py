@@ -214,3 +214,92 @@ def test_invalid_arguments_on_gpu():
     assert call("m4", None, y, 6)[0] == 1
     assert call("lttb", None, y, 2)[0] == 1
     assert call("minmaxlttb", None, y, 10, ratio=0)[0] == 1
+
+
+def test_bounded_wait_reports_timeout_and_context_survives():
+    """Failure detection without a fault: a barrier wait nothing satisfies
+    gives up after its bound and reports TSDS_ETIMEOUT; later calls work."""
+    import torch
+    from paper_2307_05389_gb300 import binding
+    lib = binding.load()
+    assert lib.tsds_check_wait_timeout(2000, None) == 4          # TSDS_ETIMEOUT
+    y = inputs.random_walk(100_000, "float32", seed=90)
+    check("minmax", None, y, 100)
+    torch.cuda.synchronize()
+
+
+@pytest.mark.parametrize("n", [8191, 65_537, 400_003, 2_000_001])
+@pytest.mark.parametrize("offset", [0, 3])
+def test_ring_window_and_chunk_boundaries(n, offset):
+    """Sizes around the window / 4 KB chunk structure of the streaming ring,
+    bins far smaller and far larger than a chunk, unaligned starts."""
+    for dtype in ("float32", "int8", "float64"):
+        y = series(dtype, n, seed=n % 97)
+        for n_out in (2, 8, 1000, n // 3 - (n // 3) % 4):
+            if n_out >= 2:
+                check("minmax", None, y, n_out, offset=offset)
+                if n_out % 4 == 0:
+                    check("m4", None, y, n_out, offset=offset)
+
+
+@pytest.fixture
+def stream_variant():
+    """Forces one kernel variant of the streaming pass for a test, then restores."""
+    from paper_2307_05389_gb300 import binding
+    prev = []
+
+    def force(v):
+        prev.append(binding.tsds_stream_variant(v))
+    yield force
+    if prev:
+        binding.tsds_stream_variant(prev[0])
+
+
+@pytest.mark.parametrize("variant", ["ring", "ldg", "seg"])
+@pytest.mark.parametrize("dtype", ALL_DTYPES)
+def test_each_stream_variant(variant, dtype, stream_variant):
+    """Each variant on its own over bins far below and far above the automatic
+    threshold, with ties, unaligned starts and both NaN modes (64-bit dtypes
+    run the register-streaming variant when the segmented one is asked for)."""
+    stream_variant(variant)
+    n = 700_001 if np.dtype(dtype).itemsize <= 2 else 260_003
+    for kind in ("walk", "ties"):
+        y = series(dtype, n, seed=31, kind=kind)
+        for n_out in (4, 40, 4000, 60_000):
+            for nan in (("propagate", "ignore") if np.dtype(dtype).kind == "f" else ("propagate",)):
+                check("minmax", None, y, n_out, nan, offset=1 if kind == "ties" else 0)
+                check("m4", None, y, n_out, nan)
+
+
+@pytest.mark.parametrize("variant", ["ring", "ldg", "seg"])
+def test_each_variant_with_x_and_lttb_preselection(variant, stream_variant):
+    stream_variant(variant)
+    y = inputs.quantised_nan(300_000, seed=33)
+    x = inputs.geometric_x(len(y), seed=34)
+    for n_out in (8, 1000):
+        check("minmax", x, y, n_out, "ignore")
+        check("minmaxlttb", x, y, n_out, "propagate", 4)
+
+
+@pytest.mark.parametrize("dtype", ["float32", "int8", "uint16", "float16", "int32"])
+@pytest.mark.parametrize("nan", ["propagate", "ignore"])
+def test_segmented_tiny_and_mixed_bins(dtype, nan, stream_variant):
+    """The segmented variant where bins are one to a few elements (many bin
+    starts per 512-byte sub-step, several refills of the prefetched starts),
+    around the sub-step size, and with x making empty bins and long runs of
+    equal bin starts."""
+    stream_variant("seg")
+    rng = np.random.default_rng(61)
+    n = 300_001
+    y = series(dtype, n, seed=62, kind="ties")
+    if np.dtype(dtype).kind == "f":
+        y[rng.choice(n, 400, replace=False)] = np.nan
+        y[1000:1700] = np.nan
+    for n_out in (n // 2 - (n // 2) % 4, n // 5 - (n // 5) % 4, 4 * (n // 130), 4 * (n // 1100)):
+        check("minmax", None, y, n_out, nan, offset=3)
+        check("m4", None, y, n_out, nan)
+    # x with clusters and gaps: runs of empty bins (equal bin starts)
+    x = np.sort(np.concatenate([rng.integers(0, 1000, n // 2), rng.integers(10 ** 6, 10 ** 6 + 50, n - n // 2)]))
+    for n_out in (400, 4000, 40_000):
+        check("minmax", x.astype(np.int64), y, n_out, nan)
+        check("m4", x.astype(np.int64), y, n_out, nan)
