@@ -661,7 +661,8 @@ template <class P, int NM, bool MULTI>
 __global__ void __launch_bounds__(kRingThreads)
 k_argminmax(const SeriesDev* __restrict__ sd, SeriesDev single, const int32_t* __restrict__ win_series,
             int64_t total_windows, Piece* __restrict__ first_piece, Piece* __restrict__ last_piece,
-            WorkCounters* __restrict__ work, int64_t welems, const int64_t* __restrict__ total_dev) {
+            WorkCounters* __restrict__ work, int64_t welems, const int64_t* __restrict__ total_dev,
+            int64_t w_first) {
   using T = typename P::T;
   extern __shared__ __align__(128) unsigned char ring_smem[];
   __shared__ __align__(8) uint64_t bars[kWarpsPerCta][kRingStages];
@@ -680,7 +681,7 @@ k_argminmax(const SeriesDev* __restrict__ sd, SeriesDev single, const int32_t* _
   for (;;) {
     unsigned long long wu = 0;
     if (lane == 0) wu = atomicAdd(&work->next_window, 1ull);
-    const int64_t w = (int64_t)__shfl_sync(0xffffffffu, wu, 0);
+    const int64_t w = w_first + (int64_t)__shfl_sync(0xffffffffu, wu, 0);
     if (w >= total_windows) break;
     const SeriesDev S = MULTI ? sd[win_series[w]] : single;
     const T* __restrict__ y = static_cast<const T*>(S.y);
@@ -795,7 +796,7 @@ static cudaError_t launch_var(const SeriesDev* s_dev, const SeriesDev& single, c
   const int per = (cfg.ctas_per_sm > 0 && cfg.ctas_per_sm < occ) ? cfg.ctas_per_sm : occ;
   const int threads = VAR == STREAM_LDG ? kStreamThreadsLdg : VAR == STREAM_SEG ? kSegThreads : kRingThreads;
   const int warps_per_cta = threads / 32;
-  int64_t blocks = (total_windows + warps_per_cta - 1) / warps_per_cta;
+  int64_t blocks = (total_windows - cfg.window_first + warps_per_cta - 1) / warps_per_cta;
   const int64_t cap = (int64_t)(sm_count > 0 ? sm_count : device_sm_count()) * per;
   if (blocks > cap || cfg.total_windows_dev) blocks = cap;
   if (blocks < 1) blocks = 1;
@@ -803,13 +804,15 @@ static cudaError_t launch_var(const SeriesDev* s_dev, const SeriesDev& single, c
   note_launch();
   if constexpr (VAR == STREAM_LDG) {
     k_argminmax_ldg<P, NM, MULTI><<<(unsigned)blocks, threads, 0, st>>>(s_dev, single, win_series, total_windows, fp,
-                                                                        lp, work, welems, cfg.total_windows_dev);
+                                                                        lp, work, welems, cfg.total_windows_dev,
+                                                                        cfg.window_first);
   } else if constexpr (VAR == STREAM_SEG) {
     k_argminmax_seg<P, NM, MULTI><<<(unsigned)blocks, threads, 0, st>>>(s_dev, single, win_series, total_windows, fp,
-                                                                        lp, work, welems, cfg.total_windows_dev);
+                                                                        lp, work, welems, cfg.total_windows_dev,
+                                                                        cfg.window_first);
   } else {
     k_argminmax<P, NM, MULTI><<<(unsigned)blocks, threads, kRingSmemBytes, st>>>(
-        s_dev, single, win_series, total_windows, fp, lp, work, welems, cfg.total_windows_dev);
+        s_dev, single, win_series, total_windows, fp, lp, work, welems, cfg.total_windows_dev, cfg.window_first);
   }
   return cudaGetLastError();
 }
@@ -842,8 +845,8 @@ static cudaError_t launch_any(const SeriesDev* s_dev, int count, const SeriesDev
                               const int32_t* win_series, int64_t total_windows, Piece* first_piece,
                               Piece* last_piece, WorkCounters* work, tsds_dtype y_dtype, tsds_nan_mode nan,
                               const StreamConfig& cfg, int sm_count, cudaStream_t st) {
-  if (total_windows <= 0) return cudaSuccess;
-  // the ring consumes windows in whole 4 KB chunks; both variants need 16-byte windows
+  if (total_windows <= cfg.window_first) return cudaSuccess;
+  // the ring consumes windows in whole 4 KB chunks; every variant needs 16-byte windows
   if (cfg.window_bytes <= 0 || cfg.window_bytes % kChunkBytes != 0) return cudaErrorInvalidValue;
   const bool ign = nan == TSDS_NAN_IGNORE;
 #define TSDS_LAUNCH(POL, NM) \

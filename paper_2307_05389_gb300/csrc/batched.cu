@@ -42,6 +42,11 @@ struct BatchLayout {
   int64_t count = 0;
   int64_t total_nb = 0, max_nb = 0, total_windows = 0, y_bytes = 0;
   int64_t mean_bin_bytes = 0;  // bytes-weighted mean bin size of the binned series
+  // Series whose bins are small (below seg_max_bin_bytes) form the second
+  // group: their windows are numbered after all others, from split_windows on,
+  // so that one launch of each variant can take its own range.
+  std::vector<uint8_t> small_bins;
+  int64_t split_windows = 0;
   bool any_full = false;       // some series returns every index
   size_t off_desc = 0, off_edges = 0, off_res = 0, off_cnt = 0, off_work = 0, off_map = 0, off_first = 0,
          off_last = 0, total = 0;
@@ -82,6 +87,22 @@ static tsds_status check_series(tsds_algo algo, const tsds_series* s, int64_t co
   return TSDS_OK;
 }
 
+// Window bases for windows of welems elements: the series with large bins
+// first, then those with small bins (from split_windows on).
+static void number_windows(BatchLayout& L, int64_t welems) {
+  int64_t win = 0;
+  for (int pass = 0; pass < 2; ++pass) {
+    if (pass == 1) L.split_windows = win;
+    for (size_t i = 0; i < L.host.size(); ++i) {
+      SeriesDev& d = L.host[i];
+      if (L.small_bins[i] != pass) continue;
+      d.win_base = win;
+      if (d.nb > 0) win += (d.n + welems - 1) / welems;
+    }
+  }
+  L.total_windows = win;
+}
+
 // Layout for the smallest window size a plan may try (most windows).
 static BatchLayout make_layout(tsds_algo algo, const tsds_series* s, int64_t count, tsds_dtype y_dtype,
                                int64_t window_bytes) {
@@ -91,8 +112,9 @@ static BatchLayout make_layout(tsds_algo algo, const tsds_series* s, int64_t cou
   const int64_t welems = window_bytes / dtype_size(y_dtype);
   L.host.resize((size_t)count);
   L.nb_before.resize((size_t)count);
-  int64_t nb_sum = 0, win_sum = 0;
+  int64_t nb_sum = 0;
   double wsum = 0.0, wbin = 0.0;
+  L.small_bins.assign((size_t)count, 0);
   for (int64_t i = 0; i < count; ++i) {
     const tsds_series& q = s[i];
     SeriesDev& d = L.host[(size_t)i];
@@ -103,29 +125,29 @@ static BatchLayout make_layout(tsds_algo algo, const tsds_series* s, int64_t cou
     d.nb = (q.n > 0 && q.n_out < q.n) ? q.n_out / per : 0;
     if (d.nb == 0) L.any_full = true;
     L.nb_before[(size_t)i] = nb_sum;
-    d.win_base = win_sum;
     d.out = q.out;
     d.out_count = q.out_count;
     d.idx_bias = 0;
     nb_sum += d.nb;
     L.max_nb = std::max(L.max_nb, d.nb);
     if (d.nb > 0) {
-      win_sum += (q.n + welems - 1) / welems;
       const double bytes = (double)q.n * (double)dtype_size(y_dtype);
       wsum += bytes;
       wbin += bytes * (bytes / (double)d.nb);
+      L.small_bins[(size_t)i] = dtype_size(y_dtype) <= 4 && bytes / (double)d.nb < (double)seg_max_bin_bytes(dtype_size(y_dtype));
     }
     L.y_bytes += q.n * dtype_size(y_dtype);
   }
   L.mean_bin_bytes = wsum > 0.0 ? (int64_t)(wbin / wsum) : 0;
+  number_windows(L, welems);
+  const int64_t win_sum = L.total_windows;
   L.total_nb = nb_sum;
-  L.total_windows = win_sum;
   size_t o = 0;
   L.off_desc = o;  o = up256(o + (size_t)count * sizeof(SeriesDev));
   L.off_edges = o; o = up256(o + (size_t)(nb_sum + count) * 8);
   L.off_res = o;   o = up256(o + (size_t)nb_sum * 16);
   L.off_cnt = o;   o = up256(o + (size_t)nb_sum * 4);
-  L.off_work = o;  o = up256(o + sizeof(WorkCounters));
+  L.off_work = o;  o = up256(o + 2 * sizeof(WorkCounters));   // one counter per launch of a split pass
   L.off_map = o;   o = up256(o + (size_t)win_sum * 4);
   L.off_first = o; o = up256(o + (size_t)win_sum * sizeof(Piece));
   L.off_last = o;  o = up256(o + (size_t)win_sum * sizeof(Piece));
@@ -136,8 +158,6 @@ static BatchLayout make_layout(tsds_algo algo, const tsds_series* s, int64_t cou
 // Points the descriptors' scratch pointers into `base` and recomputes the
 // window bases for `window_bytes` (which must be >= the layout's).
 static void bind_layout(BatchLayout& L, char* base, tsds_dtype y_dtype, int64_t window_bytes) {
-  const int64_t welems = window_bytes / dtype_size(y_dtype);
-  int64_t win = 0;
   for (size_t i = 0; i < L.host.size(); ++i) {
     SeriesDev& d = L.host[i];
     const int64_t before = L.nb_before[i];
@@ -145,26 +165,29 @@ static void bind_layout(BatchLayout& L, char* base, tsds_dtype y_dtype, int64_t 
     d.edges = reinterpret_cast<int64_t*>(base + L.off_edges) + before + (int64_t)i;
     d.res = reinterpret_cast<int64_t*>(base + L.off_res) + 2 * before;
     d.cnt = reinterpret_cast<uint32_t*>(base + L.off_cnt) + before;
-    d.win_base = win;
     d.status = &reinterpret_cast<WorkCounters*>(base + L.off_work)->status;
-    if (d.nb > 0) win += (d.n + welems - 1) / welems;
   }
-  L.total_windows = win;
+  number_windows(L, window_bytes / dtype_size(y_dtype));
 }
 
 static void rebase_windows(BatchLayout& L, tsds_dtype y_dtype, int64_t window_bytes) {
-  const int64_t welems = window_bytes / dtype_size(y_dtype);
-  int64_t win = 0;
-  for (auto& d : L.host) {
-    d.win_base = win;
-    if (d.nb > 0) win += (d.n + welems - 1) / welems;
-  }
-  L.total_windows = win;
+  number_windows(L, window_bytes / dtype_size(y_dtype));
 }
 
+// Side stream and events a plan uses to run the two launches of a split pass
+// side by side (null: one after the other on the caller's stream).
+struct Fork {
+  cudaStream_t side = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+};
+
 // The kernel sequence of one execution (descriptors and window map in place).
+// With the automatic variant and series of both kinds, the streaming pass is
+// two launches: register streaming over the large-bin series' windows and the
+// segmented kernel over the small-bin ones (each with its own work counter).
 static tsds_status enqueue(const BatchLayout& L, char* base, tsds_algo algo, bool has_x, tsds_dtype x_dtype,
-                           tsds_dtype y_dtype, tsds_nan_mode nan, const StreamConfig& shape, cudaStream_t st) {
+                           tsds_dtype y_dtype, tsds_nan_mode nan, const StreamConfig& shape, cudaStream_t st,
+                           const Fork& fk = Fork()) {
   StreamConfig cfg = shape;
   cfg.mean_bin_bytes = L.mean_bin_bytes;
   const SeriesDev* sd = reinterpret_cast<const SeriesDev*>(base + L.off_desc);
@@ -173,12 +196,34 @@ static tsds_status enqueue(const BatchLayout& L, char* base, tsds_algo algo, boo
   BT_CK(cudaMemsetAsync(base + L.off_cnt, 0, L.off_map - L.off_cnt, st));
   if (L.max_nb > 0) {
     BT_CK(launch_edges(sd, (int)L.count, nullptr, has_x, x_dtype, L.max_nb, st));
+    const int32_t* map = reinterpret_cast<const int32_t*>(base + L.off_map);
+    Piece* fp = reinterpret_cast<Piece*>(base + L.off_first);
+    Piece* lp = reinterpret_cast<Piece*>(base + L.off_last);
+    WorkCounters* work = reinterpret_cast<WorkCounters*>(base + L.off_work);
     void* tok;
     timing_begin(st, &tok);
-    BT_CK(launch_argminmax(sd, (int)L.count, none, reinterpret_cast<const int32_t*>(base + L.off_map),
-                           L.total_windows, reinterpret_cast<Piece*>(base + L.off_first),
-                           reinterpret_cast<Piece*>(base + L.off_last), reinterpret_cast<WorkCounters*>(base + L.off_work),
-                           y_dtype, nan, st, cfg));
+    const bool split = cfg.variant == STREAM_AUTO && L.split_windows > 0 && L.split_windows < L.total_windows;
+    if (!split) {
+      BT_CK(launch_argminmax(sd, (int)L.count, none, map, L.total_windows, fp, lp, work, y_dtype, nan, st, cfg));
+    } else {
+      StreamConfig big = cfg, small = cfg;
+      big.variant = STREAM_LDG;
+      small.variant = STREAM_SEG;
+      small.window_first = L.split_windows;
+      cudaStream_t st2 = st;
+      if (fk.side) {
+        BT_CK(cudaEventRecord(fk.fork, st));
+        BT_CK(cudaStreamWaitEvent(fk.side, fk.fork, 0));
+        st2 = fk.side;
+      }
+      BT_CK(launch_argminmax(sd, (int)L.count, none, map, L.total_windows, fp, lp, work + 1, y_dtype, nan, st2,
+                             small));
+      BT_CK(launch_argminmax(sd, (int)L.count, none, map, L.split_windows, fp, lp, work, y_dtype, nan, st, big));
+      if (fk.side) {
+        BT_CK(cudaEventRecord(fk.join, fk.side));
+        BT_CK(cudaStreamWaitEvent(st, fk.join, 0));
+      }
+    }
     timing_end(st, tok);
     BT_CK(launch_emit(sd, (int)L.count, none, algo == TSDS_ALGO_MINMAX ? ALGO_MINMAX : ALGO_M4, st));
   }
@@ -200,15 +245,16 @@ static tsds_status upload(BatchLayout& L, char* base, tsds_dtype y_dtype, const 
 
 // ---------------------------------------------------------------- autotuner
 
-// Candidate launch shapes: window bytes, CTAs per SM, -, kernel variant.  The
-// smallest window must come first: the scratch is laid out for it (the most
-// windows).  Without a tuned choice a plan runs the default shape (64 KB
-// windows, variant by mean bin size).
+// Candidate launch shapes: window bytes, CTAs per SM, -, kernel variant
+// (automatic: split by series bin size).  The smallest window must come
+// first: the scratch is laid out for it (the most windows).  Without a tuned
+// choice a plan runs the default shape (64 KB windows, automatic variant).
 static const StreamConfig kCandidates[] = {
     {16 * 1024, 0, nullptr, STREAM_RING},  {32 * 1024, 0, nullptr, STREAM_RING}, {64 * 1024, 0, nullptr, STREAM_RING},
     {128 * 1024, 0, nullptr, STREAM_RING}, {64 * 1024, 2, nullptr, STREAM_RING}, {256 * 1024, 0, nullptr, STREAM_RING},
     {32 * 1024, 0, nullptr, STREAM_LDG},   {64 * 1024, 0, nullptr, STREAM_LDG},  {256 * 1024, 0, nullptr, STREAM_LDG},
-    {32 * 1024, 0, nullptr, STREAM_SEG},   {64 * 1024, 0, nullptr, STREAM_SEG},  {256 * 1024, 0, nullptr, STREAM_SEG}};
+    {32 * 1024, 0, nullptr, STREAM_SEG},   {64 * 1024, 0, nullptr, STREAM_SEG},  {256 * 1024, 0, nullptr, STREAM_SEG},
+    {64 * 1024, 0, nullptr, STREAM_AUTO},  {256 * 1024, 0, nullptr, STREAM_AUTO}};
 constexpr int kNumCandidates = sizeof(kCandidates) / sizeof(kCandidates[0]);
 
 static std::mutex g_tune_mu;
@@ -222,7 +268,7 @@ static std::string tune_key(tsds_algo algo, tsds_dtype y_dtype, bool has_x, cons
   char k[128];
   int bin_class = 0;
   for (int64_t b = std::max<int64_t>(L.mean_bin_bytes, 1); b > 1; b >>= 1) ++bin_class;
-  snprintf(k, sizeof k, "s2_a%d_y%d_x%d_b%d_c%d_m%d", (int)algo, (int)y_dtype, has_x ? 1 : 0, bytes_class,
+  snprintf(k, sizeof k, "s3_a%d_y%d_x%d_b%d_c%d_m%d", (int)algo, (int)y_dtype, has_x ? 1 : 0, bytes_class,
            count_class, bin_class);
   return k;
 }
@@ -265,6 +311,8 @@ struct PlanImpl {
   int tuned_index = -1;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
+  Fork fork;
+  int graph_kernels = 0;   // kernels one graph launch runs
   float tune_ms[kNumCandidates] = {0};
 };
 
@@ -277,7 +325,7 @@ static tsds_status time_candidate(PlanImpl* P, const StreamConfig& c, cudaStream
   float best = 1e30f;
   for (int rep = 0; rep < 4; ++rep) {
     cudaEventRecord(a, st);
-    s = enqueue(P->L, P->base, P->algo, P->has_x, P->x_dtype, P->y_dtype, P->nan, c, st);
+    s = enqueue(P->L, P->base, P->algo, P->has_x, P->x_dtype, P->y_dtype, P->nan, c, st, P->fork);
     cudaEventRecord(b, st);
     if (s != TSDS_OK) break;
     cudaEventSynchronize(b);
@@ -345,6 +393,12 @@ tsds_status tsds_plan_create(tsds_plan* plan, tsds_algo algo, const tsds_series*
     return fail(TSDS_ENOMEM, "tsds_plan_create: cudaMalloc(%zu): %s", P->L.total, cudaGetErrorString(e));
   }
   bind_layout(P->L, P->base, y_dtype, kCandidates[0].window_bytes);
+  if (cudaStreamCreateWithFlags(&P->fork.side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&P->fork.fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&P->fork.join, cudaEventDisableTiming) != cudaSuccess) {
+    tsds_plan_destroy(p);
+    return fail(TSDS_ECUDA, "tsds_plan_create: side stream or events could not be created");
+  }
 
   int choice = -1;   // the default shape
   const std::string key = tune_key(algo, y_dtype, P->has_x, P->L);
@@ -379,7 +433,11 @@ tsds_status tsds_plan_create(tsds_plan* plan, tsds_algo algo, const tsds_series*
     if (e != cudaSuccess) { tsds_plan_destroy(p); return fail(TSDS_ECUDA, "graph capture stream: %s", cudaGetErrorString(e)); }
     e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-      s = enqueue(P->L, P->base, algo, P->has_x, x_dtype, y_dtype, nan, P->cfg, cap);
+      // kernels recorded into the graph count when the graph is launched
+      const long long before = tsds_kernel_launches();
+      s = enqueue(P->L, P->base, algo, P->has_x, x_dtype, y_dtype, nan, P->cfg, cap, P->fork);
+      P->graph_kernels = (int)(tsds_kernel_launches() - before);
+      note_launch(-P->graph_kernels);
       cudaError_t e2 = cudaStreamEndCapture(cap, &P->graph);
       if (s == TSDS_OK && e2 == cudaSuccess) e = cudaGraphInstantiate(&P->exec, P->graph, 0);
       else if (e2 != cudaSuccess) e = e2;
@@ -397,11 +455,11 @@ tsds_status tsds_plan_execute(tsds_plan plan, void* stream) {
   PlanImpl* P = &plan->impl;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (P->exec) {
-    note_launch(P->L.max_nb > 0 ? 3 + (P->L.any_full ? 1 : 0) : (P->L.any_full ? 1 : 0));
+    note_launch(P->graph_kernels);
     BT_CK(cudaGraphLaunch(P->exec, st));
     return TSDS_OK;
   }
-  return enqueue(P->L, P->base, P->algo, P->has_x, P->x_dtype, P->y_dtype, P->nan, P->cfg, st);
+  return enqueue(P->L, P->base, P->algo, P->has_x, P->x_dtype, P->y_dtype, P->nan, P->cfg, st, P->fork);
 }
 
 tsds_status tsds_plan_info(tsds_plan plan, int64_t* window_bytes, int* ctas_per_sm, int64_t* windows,
@@ -415,7 +473,8 @@ tsds_status tsds_plan_info(tsds_plan plan, int64_t* window_bytes, int* ctas_per_
   if (variant) {
     StreamConfig c = P->cfg;
     c.mean_bin_bytes = P->L.mean_bin_bytes;
-    *variant = stream_variant_for(c, dtype_size(P->y_dtype));
+    const bool split = c.variant == STREAM_AUTO && P->L.split_windows > 0 && P->L.split_windows < P->L.total_windows;
+    *variant = split ? STREAM_AUTO : stream_variant_for(c, dtype_size(P->y_dtype));
   }
   return TSDS_OK;
 }
@@ -426,11 +485,14 @@ tsds_status tsds_plan_destroy(tsds_plan plan) {
   cudaError_t e = cudaSuccess;
   if (P->exec) cudaGraphExecDestroy(P->exec);
   if (P->graph) cudaGraphDestroy(P->graph);
+  if (P->fork.fork) cudaEventDestroy(P->fork.fork);
+  if (P->fork.join) cudaEventDestroy(P->fork.join);
   if (P->base) {
     // plans own plain device memory: make sure no queued work still uses it
     e = cudaDeviceSynchronize();
     cudaFree(P->base);
   }
+  if (P->fork.side) cudaStreamDestroy(P->fork.side);
   delete plan;
   if (e != cudaSuccess) return fail(TSDS_ECUDA, "tsds_plan_destroy: %s", cudaGetErrorString(e));
   return TSDS_OK;

@@ -79,7 +79,8 @@ struct StreamConfig {
   // is launched.
   const int64_t* total_windows_dev = nullptr;
   int variant = STREAM_AUTO;
-  int64_t mean_bin_bytes = 0;           // bytes-weighted mean bin size (0: unknown, ring)
+  int64_t mean_bin_bytes = 0;           // bytes-weighted mean bin size of the launch
+  int64_t window_first = 0;             // the launch takes windows [window_first, total_windows)
 };
 
 // The variant a launch with this shape runs for elements of elem_bytes.

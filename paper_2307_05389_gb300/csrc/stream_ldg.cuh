@@ -118,14 +118,15 @@ template <class P, int NM, bool MULTI>
 __global__ void __launch_bounds__(kStreamThreadsLdg)
 k_argminmax_ldg(const SeriesDev* __restrict__ sd, SeriesDev single, const int32_t* __restrict__ win_series,
             int64_t total_windows, Piece* __restrict__ first_piece, Piece* __restrict__ last_piece,
-            WorkCounters* __restrict__ work, int64_t welems, const int64_t* __restrict__ total_dev) {
+            WorkCounters* __restrict__ work, int64_t welems, const int64_t* __restrict__ total_dev,
+            int64_t w_first) {
   using T = typename P::T;
   const int lane = threadIdx.x & 31;
   if (total_dev) total_windows = *total_dev;
   for (;;) {
     unsigned long long wu = 0;
     if (lane == 0) wu = atomicAdd(&work->next_window, 1ull);
-    const int64_t w = (int64_t)__shfl_sync(0xffffffffu, wu, 0);
+    const int64_t w = w_first + (int64_t)__shfl_sync(0xffffffffu, wu, 0);
     if (w >= total_windows) break;
     SeriesDev S = MULTI ? sd[win_series[w]] : single;
     const T* __restrict__ y = static_cast<const T*>(S.y);

@@ -151,6 +151,41 @@ __device__ __forceinline__ void seg_lane_group(SegLane<P>& L, const uint4& v, ui
   L.valid = true;
 }
 
+// The same over four consecutive full sub-steps (v[u] is sub-step u; rel is
+// the window offset of the lane's first element in sub-step 0).
+template <class P>
+__device__ __forceinline__ void seg_lane_group4(SegLane<P>& L, const uint4 (&v)[4], uint32_t rel) {
+  using T = typename P::T;
+  constexpr int E = 16 / sizeof(T);
+  constexpr int SUB = 32 * E;
+  typename P::Acc gmin, gmax;
+  P::group(v, gmin, gmax);
+  const bool bmin = !L.valid || P::better_min(gmin, L.vmin);
+  const bool bmax = !L.valid || P::better_max(gmax, L.vmax);
+  if (bmin || bmax) {
+    int fmin = 0, fmax = 0;
+#pragma unroll
+    for (int u = 3; u >= 0; --u) {
+      T el[E];
+      memcpy(el, &v[u], 16);
+#pragma unroll
+      for (int e = E - 1; e >= 0; --e) {
+        if (P::match_min(el[e], gmin)) fmin = u * SUB + e;
+        if (P::match_max(el[e], gmax)) fmax = u * SUB + e;
+      }
+    }
+    if (bmin) {
+      L.vmin = gmin;
+      L.rmin = rel + (uint32_t)fmin;
+    }
+    if (bmax) {
+      L.vmax = gmax;
+      L.rmax = rel + (uint32_t)fmax;
+    }
+  }
+  L.valid = true;
+}
+
 template <class P, int NM>
 __device__ __forceinline__ void seg_lane_flush(SegLane<P>& L, SegRun& acc) {
   if (L.valid) {
@@ -165,26 +200,36 @@ __device__ __forceinline__ void seg_lane_flush(SegLane<P>& L, SegRun& acc) {
   }
 }
 
-// Starts the copy of sub-step m of the window's grid into the lane's slot:
-// lane `lane` takes the 16-byte vector (m*32 + lane) of the grid that starts
-// at the aligned address gbase (element position q0).  A vector that reaches
-// outside [ws, we) is assembled from the elements inside it with plain loads.
-// Commits one copy group per call, also past the last sub-step.
+// Where the window's sub-step grid lies: the 16-byte aligned start gbase
+// (element position q0), the number of sub-steps, and the range [mlo, mhi)
+// of sub-steps that lie wholly inside [ws, we).
+struct SegGrid {
+  uintptr_t gbase;
+  int64_t q0, nsub, mlo, mhi, ws, we;
+};
+
+// Starts the copy of sub-step m into the lane's slot: lane `lane` takes the
+// 16-byte vector (m*32 + lane) of the grid.  A vector that reaches outside
+// [ws, we) (only in the window's first and last sub-steps) is assembled from
+// the elements inside it with plain loads.  Commits one copy group per call,
+// also past the last sub-step.
 template <class T>
-__device__ __forceinline__ void seg_issue(uint4* slot, const T* __restrict__ y, uintptr_t gbase, int64_t q0,
-                                          int64_t m, int64_t nsub, int64_t ws, int64_t we, int lane) {
+__device__ __forceinline__ void seg_issue(uint4* slot, const T* __restrict__ y, const SegGrid& g, int64_t m,
+                                          int lane) {
   constexpr int E = 16 / sizeof(T);
-  if (m < nsub) {
-    const int64_t vi = m * 32 + lane;
-    const int64_t p = q0 + vi * E;
-    if (p >= ws && p + E <= we) {
-      seg_cp16(slot, reinterpret_cast<const uint4*>(gbase) + vi);
+  const uint4* src = reinterpret_cast<const uint4*>(g.gbase) + m * 32 + lane;
+  if (m >= g.mlo && m < g.mhi) {
+    seg_cp16(slot, src);
+  } else if (m < g.nsub) {
+    const int64_t p = g.q0 + (m * 32 + lane) * E;
+    if (p >= g.ws && p + E <= g.we) {
+      seg_cp16(slot, src);
     } else {
       T a[E];
 #pragma unroll
       for (int e = 0; e < E; ++e) {
         const int64_t i = p + e;
-        a[e] = (i >= ws && i < we) ? ldg_elem<T>(y + i) : T();
+        a[e] = (i >= g.ws && i < g.we) ? ldg_elem<T>(y + i) : T();
       }
       uint4 v;
       memcpy(&v, a, 16);
@@ -217,7 +262,8 @@ template <class P, int NM, bool MULTI>
 __global__ void __launch_bounds__(kSegThreads)
 k_argminmax_seg(const SeriesDev* __restrict__ sd, SeriesDev single, const int32_t* __restrict__ win_series,
                 int64_t total_windows, Piece* __restrict__ first_piece, Piece* __restrict__ last_piece,
-                WorkCounters* __restrict__ work, int64_t welems, const int64_t* __restrict__ total_dev) {
+                WorkCounters* __restrict__ work, int64_t welems, const int64_t* __restrict__ total_dev,
+            int64_t w_first) {
   using T = typename P::T;
   static_assert(sizeof(T) <= 4, "the segmented pass packs 32-bit keys");
   constexpr int E = 16 / sizeof(T);   // elements per lane per sub-step
@@ -234,7 +280,7 @@ k_argminmax_seg(const SeriesDev* __restrict__ sd, SeriesDev single, const int32_
   for (;;) {
     unsigned long long wu = 0;
     if (lane == 0) wu = atomicAdd(&work->next_window, 1ull);
-    const int64_t w = (int64_t)__shfl_sync(FULL, wu, 0);
+    const int64_t w = w_first + (int64_t)__shfl_sync(FULL, wu, 0);
     if (w >= total_windows) break;
     const SeriesDev S = MULTI ? sd[win_series[w]] : single;
     const T* __restrict__ y = static_cast<const T*>(S.y);
@@ -245,12 +291,19 @@ k_argminmax_seg(const SeriesDev* __restrict__ sd, SeriesDev single, const int32_
     const int64_t we = min(ws + welems, S.n);
     // the sub-step grid: 16-byte aligned, starting at or before ws
     const uintptr_t a_ws = reinterpret_cast<uintptr_t>(y + ws);
-    const uintptr_t gbase = a_ws & ~(uintptr_t)15;
-    const int64_t q0 = ws - (int64_t)((a_ws - gbase) / sizeof(T));
+    SegGrid g;
+    g.gbase = a_ws & ~(uintptr_t)15;
+    const int64_t q0 = ws - (int64_t)((a_ws - g.gbase) / sizeof(T));
     const int64_t nsub = (we - q0 + SUB - 1) / SUB;
+    g.q0 = q0;
+    g.nsub = nsub;
+    g.mlo = (ws - q0 + SUB - 1) / SUB;
+    g.mhi = (we - q0) / SUB;
+    g.ws = ws;
+    g.we = we;
     // kSegDepth - 1 sub-steps in flight ahead of the one being reduced
 #pragma unroll
-    for (int d = 0; d < kSegDepth - 1; ++d) seg_issue<T>(stage + d * 32, y, gbase, q0, d, nsub, ws, we, lane);
+    for (int d = 0; d < kSegDepth - 1; ++d) seg_issue<T>(stage + d * 32, y, g, d, lane);
 
     // the bin holding ws, and the next 64 bin starts (cur: eb..eb+31, nxt: eb+32..eb+63)
     const int64_t b0 = warp_lower_bound(1, nb + 1, [&](int64_t j) { return __ldg(edges + j) > ws; }) - 1;
@@ -269,18 +322,32 @@ k_argminmax_seg(const SeriesDev* __restrict__ sd, SeriesDev single, const int32_
     bool adirty = false, fset = false;
     const bool b0_piece = lo0 < ws;
 
+    // at the top of each iteration, sub-steps up to m + kSegDepth - 2 are issued
 #pragma unroll 1
     for (int64_t m = 0; m < nsub; ++m) {
       {
-        seg_issue<T>(stage + (int)((m + kSegDepth - 1) % kSegDepth) * 32, y, gbase, q0, m + kSegDepth - 1, nsub, ws,
-                     we, lane);
-        seg_wait<kSegDepth - 1>();
-        const uint4 cv = stage[(int)(m % kSegDepth) * 32];
         const int64_t qs = q0 + m * SUB;
+        const int64_t ne = __shfl_sync(FULL, cur, ep);
+        if (m >= g.mlo && m + 4 <= g.mhi && ne >= qs + 4 * SUB) {
+          // four full sub-steps inside the open bin: one packed group reduction
+          seg_wait<kSegDepth - 5>();
+          uint4 v4[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) v4[u] = stage[(int)((m + u) % kSegDepth) * 32];
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            seg_issue<T>(stage + (int)((m + kSegDepth - 1 + u) % kSegDepth) * 32, y, g, m + kSegDepth - 1 + u, lane);
+          seg_lane_group4<P>(lane_run, v4, (uint32_t)(qs - ws) + (uint32_t)(lane * E));
+          adirty = true;
+          m += 3;
+          continue;
+        }
+        seg_wait<kSegDepth - 2>();
+        const uint4 cv = stage[(int)(m % kSegDepth) * 32];
+        seg_issue<T>(stage + (int)((m + kSegDepth - 1) % kSegDepth) * 32, y, g, m + kSegDepth - 1, lane);
         const int64_t s_hi = min(qs + SUB, we);
         const int o_lo = (int)(max(qs, ws) - qs), o_hi = (int)(s_hi - qs);
         const uint32_t rel0 = (uint32_t)(qs - ws);   // offsets wrap back into range for valid elements
-        const int64_t ne = __shfl_sync(FULL, cur, ep);
         if (ne >= s_hi) {
           if (o_lo == 0 && o_hi == SUB) seg_lane_group<P>(lane_run, cv, rel0 + (uint32_t)(lane * E));
           else seg_lane_add<T, NM>(acc, cv, lane, o_lo, o_hi, rel0);

@@ -112,3 +112,36 @@ def test_batched_rejects_mixed_x_and_bad_n_out():
     arr = binding._series_array(ys, [8, 6], None, outs, counts)
     assert binding.tsds_batched(1, arr, 2, 0, binding.DTYPES["float32"], 0, None) == 1
     torch.cuda.synchronize()
+
+
+@pytest.mark.parametrize("graph", [False, True])
+@pytest.mark.parametrize("algo", ["minmax", "m4"])
+def test_split_pass_small_and_large_bins(graph, algo):
+    """A batch whose series fall on both sides of the small-bin threshold runs
+    the streaming pass as two launches (one per kernel variant, side by side in
+    a plan); every series must still match the oracle, bins cut by windows
+    included."""
+    rng = np.random.default_rng(21)
+    ys, n_outs = [], []
+    for i in range(24):
+        if i % 2:
+            n = int(rng.integers(20_000, 90_000)); n_out = 4000    # bins of tens of bytes
+        else:
+            n = int(rng.integers(300_000, 900_000)); n_out = 40    # bins of tens of KB
+        ys.append(inputs.ties_and_specials(n, "float32", seed=100 + i) if i % 3 == 0 else
+                  inputs.random_walk(n, "float32", seed=100 + i))
+        n_outs.append(n_out)
+    n_outs = np.array(n_outs)
+    dys = to_dev(ys)
+    plan = binding.Plan(algo, dys, n_outs, graph=graph, autotune=False)
+    assert plan.info()["variant"] == "auto"
+    for _ in range(2):
+        got = results(*plan.execute())
+        for i, y in enumerate(ys):
+            np.testing.assert_array_equal(got[i], oracle.downsample(algo, None, y, int(n_outs[i])),
+                                          err_msg=f"series {i}")
+    plan.close()
+    outs, counts = binding.downsample_batched(algo, dys, n_outs)
+    got = results(outs, counts)
+    for i, y in enumerate(ys):
+        np.testing.assert_array_equal(got[i], oracle.downsample(algo, None, y, int(n_outs[i])))
