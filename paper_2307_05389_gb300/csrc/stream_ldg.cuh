@@ -115,7 +115,7 @@ __device__ __forceinline__ Cand piece_ldg(const typename P::T* __restrict__ y, i
 }
 
 template <class P, int NM, bool MULTI>
-__global__ void __launch_bounds__(kStreamThreadsLdg)
+__global__ void __launch_bounds__(kStreamThreadsLdg, MULTI ? 3 : 4)
 k_argminmax_ldg(const SeriesDev* __restrict__ sd, SeriesDev single, const int32_t* __restrict__ win_series,
             int64_t total_windows, Piece* __restrict__ first_piece, Piece* __restrict__ last_piece,
             WorkCounters* __restrict__ work, int64_t welems, const int64_t* __restrict__ total_dev,
