@@ -55,6 +55,9 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--n-out", type=int, default=N_OUT, help="n_out of the default step (profiling other bin sizes)")
+    ap.add_argument("--stream-variant", default="auto", choices=["auto", "ring", "ldg", "seg"],
+                    help="kernel variant of the streaming pass (tsds_stream_variant)")
     ap.add_argument("--suite", default=None, choices=["dtypes", "config1", "lttb", "batched", "serve"],
                     help="instead of the headline step, measure one of the other workloads and print one JSON line")
     return ap.parse_args()
@@ -366,6 +369,16 @@ def step_bytes(n, n_out=N_OUT, x_itemsize=8):
     return per
 
 
+def stream_kernel_name(n, n_out, forced):
+    """The streaming kernel a float32 MinMax launch of this shape runs (the
+    library's automatic rule: segmented below 1.5 KB mean bins)."""
+    v = forced
+    if v == "auto":
+        v = "seg" if n * 4 / max(n_out // 2, 1) < 1536 else "ldg"
+    return {"ldg": "tsds::k_argminmax_ldg (register streaming)", "seg": "tsds::k_argminmax_seg (segmented)",
+            "ring": "tsds::k_argminmax (shared-memory ring)"}[v] + " — streaming per-bin argmin/argmax"
+
+
 def hbm_peak():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -460,19 +473,19 @@ def run_reference(args, rank):
     oracle.build()
     for _ in range(args.warmup):
         for algo in ALGOS:
-            oracle.downsample(algo, x, y, N_OUT)
+            oracle.downsample(algo, x, y, args.n_out)
     t0 = time.perf_counter()
     for _ in range(args.steps):
         for algo in ALGOS:
-            oracle.downsample(algo, x, y, N_OUT)
+            oracle.downsample(algo, x, y, args.n_out)
     dt = time.perf_counter() - t0
-    per = step_bytes(n)
+    per = step_bytes(n, args.n_out)
     gbs = sum(per.values()) * args.steps / dt / 1e9
     sample = f"first {n} points of the workload (numpy default_rng seed 2), MinMax + M4, single-threaded C oracle"
     line = {"impl": "reference", "metric": METRIC, "value": gbs, "unit": "GB/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "n_sample": n, "n_out": N_OUT},
+            "data": "synthetic", "config": {"workload": WORKLOAD, "n_sample": n, "n_out": args.n_out},
             "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": gbs, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -509,11 +522,13 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
     pkg.load()
+    if args.stream_variant != "auto":
+        binding.tsds_stream_variant(args.stream_variant)
 
     n = args.n
     y = inputs.random_walk_cuda(n, "float32", seed=2 + rank, device=dev)
     x = inputs.geometric_x_cuda(n, seed=2 + rank, device=dev)
-    outs = {a: torch.empty(N_OUT, dtype=torch.int64, device=dev) for a in ALGOS}
+    outs = {a: torch.empty(args.n_out, dtype=torch.int64, device=dev) for a in ALGOS}
     cnts = {a: torch.empty(1, dtype=torch.int64, device=dev) for a in ALGOS}
     torch.cuda.synchronize()
     torch.cuda.empty_cache()               # drop the generators' temporaries
@@ -522,7 +537,7 @@ def main():
     fns = {"minmax": binding.tsds_minmax, "m4": binding.tsds_m4}
 
     def call(algo):
-        r = fns[algo](x.data_ptr(), binding.DTYPES["int64"], y.data_ptr(), binding.DTYPES["float32"], n, N_OUT,
+        r = fns[algo](x.data_ptr(), binding.DTYPES["int64"], y.data_ptr(), binding.DTYPES["float32"], n, args.n_out,
                       0, outs[algo].data_ptr(), cnts[algo].data_ptr(), sp)
         if r != 0:
             raise RuntimeError(binding.last_error())
@@ -562,7 +577,7 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     ms_max = float(t.item())
 
-    per = step_bytes(n)
+    per = step_bytes(n, args.n_out)
     total_bytes = sum(per.values()) * args.steps * world
     value = total_bytes / (ms_max / 1e3) / 1e9
     peak, peak_src = hbm_peak()
@@ -594,14 +609,14 @@ def main():
         yh = y.cpu().pin_memory()
         xh = x.cpu().pin_memory()
         yd, xd = torch.empty_like(y), torch.empty_like(x)
-        pkg.downsample_host(ALGOS, yh, N_OUT, x=xh, y_dev=yd, x_dev=xd)   # warm-up
+        pkg.downsample_host(ALGOS, yh, args.n_out, x=xh, y_dev=yd, x_dev=xd)   # warm-up
         torch.cuda.synchronize()
         if dist:
             dist.barrier()
         t0 = time.perf_counter()
         d2h = 0
         for _ in range(args.e2e_steps):
-            res = pkg.downsample_host(ALGOS, yh, N_OUT, x=xh, y_dev=yd, x_dev=xd)
+            res = pkg.downsample_host(ALGOS, yh, args.n_out, x=xh, y_dev=yd, x_dev=xd)
             d2h = sum(r.numel() * 8 + 8 for r in res)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
@@ -624,9 +639,9 @@ def main():
         xs = x[:ns].cpu().numpy()
         t0 = time.perf_counter()
         for a in ALGOS:
-            oracle.downsample(a, xs, ys, N_OUT)
+            oracle.downsample(a, xs, ys, args.n_out)
         dt = time.perf_counter() - t0
-        cpu = {"value": sum(step_bytes(ns).values()) / dt / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
+        cpu = {"value": sum(step_bytes(ns, args.n_out).values()) / dt / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
                "sample": f"first {ns} points of the same series and x, MinMax + M4 once each ({dt:.1f} s)"}
 
     # ---- output check of the timed results against each other (counts)
@@ -638,14 +653,14 @@ def main():
             "warmup": max(3, args.warmup), "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "impl": "native",
-            "config": {"workload": WORKLOAD, "n": n, "n_out": N_OUT, "algorithms": list(ALGOS),
+            "config": {"workload": WORKLOAD, "n": n, "n_out": args.n_out, "algorithms": list(ALGOS),
                        "x": "int64", "y": "float32", "l2": "inputs larger than L2 (4 GB y, 8 GB x); no flush",
                        "parallelism": f"{world} independent series (one per GPU)" if world > 1 else "single GPU"},
             "pct_of_hbm_peak": 100.0 * value / world / peak,
             "per_algo": per_algo,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": kernel_traffic(),
-                         "kernel": "tsds::k_argminmax (streaming per-bin argmin/argmax)",
+                         "kernel": stream_kernel_name(n, args.n_out, args.stream_variant),
                          "bytes_per_launch": n * 4, "launches_timed": kern_launches,
                          "peak_source": f"{peak_src} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"},
             "clocks": clk,
