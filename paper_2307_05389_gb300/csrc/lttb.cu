@@ -22,13 +22,18 @@
 //    parallel (one warp per bucket, exact binary64 areas), and the chain
 //    becomes a walk through the table that one warp does from registers,
 //    with the next rows loaded ahead.
-//  * Large buckets: one CTA walks the buckets.  Each step first scores every
-//    point with an FP32 estimate of its area and a rigorous bound on the
-//    estimate's error, then evaluates the exact binary64 area only for the
-//    points whose bound reaches the best lower bound (usually one or two).
-//    Any non-finite or out-of-range value sends the step to the exact path.
-//    The next bucket's points are copied into shared memory with cp.async
-//    while the current step reduces.
+//  * Larger buckets: the pick of bucket j is the largest |linear form| of its
+//    points, which a vertex of the bucket's convex hull attains, so the
+//    picks that can feed bucket j+1 are few (a random walk's hull has about
+//    2 ln K vertices).  Each bucket's candidates (hull vertices in FP32,
+//    plus its first point and its first non-finite point) are found in
+//    parallel, a table best[j][c] over the candidates c of bucket j-1 is
+//    filled in parallel (one warp per entry: an FP32 estimate of every area
+//    with a rigorous error bound, then exact binary64 areas for the points
+//    the bound cannot rule out), and one warp chases the table.  A previous
+//    pick that is not among the candidates (ties along hull edges, rounding
+//    at near-ties, more than 32 hull vertices) is computed on the spot by
+//    the same exact warp search, so the table only decides speed.
 #include "device.cuh"
 #include "internal.h"
 #include "lttb.h"
@@ -37,9 +42,7 @@ namespace tsds {
 
 typedef unsigned __int128 u128;
 
-constexpr int kChainThreads = 256;
 constexpr int kTableMaxK = kLttbTableMaxK;  // table mode when every bucket has <= 32 points
-constexpr int kPrefetchMaxK = 4096; // chain prefetches buckets up to this size (48 B/point, two buffers)
 
 __device__ __forceinline__ int64_t job_m(const LttbJob& J) { return J.m_dev ? *J.m_dev : J.m_host; }
 
@@ -47,36 +50,7 @@ __device__ __forceinline__ int64_t bucket_start(int64_t j, int64_t m, int64_t B)
   return 1 + (int64_t)(((u128)j * (u128)(m - 2)) / (u128)B);
 }
 
-// The bucket that holds point k (1 <= k <= m-2).
-__device__ __forceinline__ int64_t bucket_of(int64_t k, int64_t m, int64_t B) {
-  const u128 q1 = (u128)k;   // (k-1) + 1
-  int64_t j = (int64_t)((q1 * (u128)B - 1) / (u128)(m - 2));
-  if (j > B - 1) j = B - 1;
-  if (j < 0) j = 0;
-  while (j > 0 && bucket_start(j, m, B) > k) --j;
-  while (j < B - 1 && bucket_start(j + 1, m, B) <= k) ++j;
-  return j;
-}
-
 __device__ __forceinline__ int64_t out_index(const LttbJob& J, int64_t k) { return J.R ? J.R[k] : k + J.bias; }
-
-// Bucket starts walked incrementally: start(j) = 1 + floor(j*(m-2)/B).
-struct BucketWalk {
-  int64_t q, r, dq, dr, B;
-  __device__ void init(int64_t m, int64_t B_) {
-    B = B_;
-    q = 0;
-    r = 0;
-    dq = (m - 2) / B_;
-    dr = (m - 2) % B_;
-  }
-  __device__ int64_t start() const { return 1 + q; }
-  __device__ void next() {
-    q += dq;
-    r += dr;
-    if (r >= B) { r -= B; ++q; }
-  }
-};
 
 __device__ __forceinline__ double load_as_f64(const void* p, int dt, int64_t i) {
   switch (dt) {
@@ -136,23 +110,146 @@ __global__ void k_points(const PointsJob* __restrict__ jobs) {
   }
 }
 
-// means[j] for buckets 1..B-1 (the third vertex of steps 0..B-2).
+// means[j] for buckets 1..B-1 (the third vertex of steps 0..B-2): binary64
+// sums in index order divided once by the count.  Small buckets (table mode):
+// a thread per bucket.
 __global__ void k_means(const LttbJob* __restrict__ jobs) {
-  const LttbJob& J = jobs[blockIdx.y];
+  const LttbJob J = jobs[blockIdx.y];
+  if (J.mode != 0) return;
   const int64_t m = job_m(J), B = J.B;
   if (m <= B + 2) return;
+  const bool ign = J.nan == TSDS_NAN_IGNORE;
   for (int64_t j = 1 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < B; j += (int64_t)gridDim.x * blockDim.x) {
     const int64_t lo = bucket_start(j, m, B), hi = bucket_start(j + 1, m, B);
     double sx = 0.0, sy = 0.0;
     int64_t c = 0;
     for (int64_t k = lo; k < hi; ++k) {
       const double yk = J.py[k];
-      if (J.nan == TSDS_NAN_IGNORE && isnan(yk)) continue;
+      if (ign && isnan(yk)) continue;
       sx = __dadd_rn(sx, J.px[k]);
       sy = __dadd_rn(sy, yk);
       ++c;
     }
     J.means[j] = make_double2(__ddiv_rn(sx, (double)c), __ddiv_rn(sy, (double)c));
+  }
+}
+
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((unsigned)__cvta_generic_to_shared(smem)), "l"(gmem)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((unsigned)__cvta_generic_to_shared(smem)), "l"(gmem)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(smem)),
+               "l"(gmem)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Hull-table mode, larger buckets: the same index-order sums, one thread per
+// bucket.  Each thread streams its own bucket through a private ring of three
+// 32-point chunks in shared memory (cp.async, two chunks in flight), so the
+// only serial work is the two chains of binary64 additions.
+constexpr int kSumChunk = 32;
+constexpr int kSumRing = 3;
+
+// The warp's rings, thread-minor (element i of thread t at [r][i][t]) so that
+// the 32 threads' accesses fall in distinct banks.
+struct SumRing {
+  double x[kSumRing][kSumChunk][32], y[kSumRing][kSumChunk][32];
+};
+
+__global__ void __launch_bounds__(32) k_sums_wide(const LttbJob* __restrict__ jobs) {
+  const LttbJob J = jobs[blockIdx.y];
+  if (J.mode != 2) return;
+  const int64_t m = job_m(J), B = J.B;
+  if (m <= B + 2) return;
+  extern __shared__ __align__(16) unsigned char sum_smem[];
+  SumRing& R = *reinterpret_cast<SumRing*>(sum_smem);
+  const int t = threadIdx.x;
+  const bool ign = J.nan == TSDS_NAN_IGNORE;
+  for (int64_t jb = (int64_t)blockIdx.x * 32; jb < B; jb += (int64_t)gridDim.x * 32) {
+    const int64_t j = jb + threadIdx.x;
+    const bool mine = j >= 1 && j < B;
+    const int64_t lo = mine ? bucket_start(j, m, B) : 0, hi = mine ? bucket_start(j + 1, m, B) : 0;
+    const int64_t chunks = (hi - lo + kSumChunk - 1) / kSumChunk;
+    auto issue = [&](int64_t c) {
+      if (c < chunks) {
+        const int r = (int)(c % kSumRing);
+        const int64_t k0 = lo + c * kSumChunk, k1 = min(k0 + kSumChunk, hi);
+        for (int64_t k = k0; k < k1; ++k) {
+          cp_async8(&R.x[r][k - k0][t], J.px + k);
+          cp_async8(&R.y[r][k - k0][t], J.py + k);
+        }
+      }
+      cp_async_commit();
+    };
+    issue(0);
+    issue(1);
+    double sx = 0.0, sy = 0.0;
+    int64_t cnt = 0;
+    for (int64_t c = 0; c < chunks; ++c) {
+      issue(c + 2);
+      cp_async_wait<2>();
+      const int r = (int)(c % kSumRing);
+      const int n = (int)min((int64_t)kSumChunk, hi - lo - c * kSumChunk);
+      // loads of a group of 8 first, then the two dependent chains of adds
+      for (int i0 = 0; i0 < n; i0 += 8) {
+        double xv[8], yv[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          xv[u] = R.x[r][min(i0 + u, kSumChunk - 1)][t];
+          yv[u] = R.y[r][min(i0 + u, kSumChunk - 1)][t];
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          if (i0 + u < n && !(ign && isnan(yv[u]))) {
+            sx = __dadd_rn(sx, xv[u]);
+            sy = __dadd_rn(sy, yv[u]);
+            ++cnt;
+          }
+        }
+      }
+    }
+    cp_async_wait<0>();
+    if (mine) J.means[j] = make_double2(__ddiv_rn(sx, (double)cnt), __ddiv_rn(sy, (double)cnt));
+  }
+}
+
+// p32[k] = point k relative to its bucket's first point, rounded to FP32: a
+// warp per bucket, coalesced.
+__global__ void k_p32(const LttbJob* __restrict__ jobs) {
+  const LttbJob J = jobs[blockIdx.y];
+  if (J.mode != 2) return;
+  const int64_t m = job_m(J), B = J.B;
+  if (m <= B + 2) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t j = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); j < B; j += warps) {
+    const int64_t lo = bucket_start(j, m, B), hi = bucket_start(j + 1, m, B);
+    const double X0 = J.px[lo], Y0 = J.py[lo];
+    for (int64_t k0 = lo + lane; k0 < hi; k0 += 128) {
+      double xv[4], yv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int64_t k = k0 + 32 * u;
+        xv[u] = k < hi ? J.px[k] : 0.0;
+        yv[u] = k < hi ? J.py[k] : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int64_t k = k0 + 32 * u;
+        if (k < hi)
+          J.p32[k] = make_float2(__double2float_rn(__dsub_rn(xv[u], X0)), __double2float_rn(__dsub_rn(yv[u], Y0)));
+      }
+    }
   }
 }
 
@@ -162,7 +259,7 @@ __global__ void k_means(const LttbJob* __restrict__ jobs) {
 // point start(j-1) + ai (for j = 0 the previous pick is point 0, slot 0).
 // One warp per bucket; lanes are the candidates b.
 __global__ void k_table(const LttbJob* __restrict__ jobs) {
-  const LttbJob& J = jobs[blockIdx.y];
+  const LttbJob J = jobs[blockIdx.y];
   if (J.mode != 0) return;
   const int64_t m = job_m(J), B = J.B;
   if (m <= B + 2) return;
@@ -191,12 +288,39 @@ __global__ void k_table(const LttbJob* __restrict__ jobs) {
   }
 }
 
-// One warp walks the table.  Rows are loaded kRing steps ahead into
-// registers (lane l holds entry l of a row); each step is one shuffle.
-constexpr int kRing = 8;
+// Starts of the buckets one lane writes out: lane l owns steps l, l+32,
+// l+64, ...; start(j) = 1 + floor(j(m-2)/B) advances by 32 steps with one
+// add and a carry (q32, r32: quotient and remainder of 32(m-2) by B).
+struct LaneStarts {
+  int64_t j, lo, rem, q32, r32, B;
+  __device__ void init(int64_t j0, int64_t m, int64_t B_) {
+    B = B_;
+    j = j0;
+    const u128 t = (u128)j0 * (u128)(m - 2);
+    lo = 1 + (int64_t)(t / (u128)B_);
+    rem = (int64_t)(t % (u128)B_);
+    const u128 t32 = (u128)32 * (u128)(m - 2);
+    q32 = (int64_t)(t32 / (u128)B_);
+    r32 = (int64_t)(t32 % (u128)B_);
+  }
+  __device__ void advance() {
+    j += 32;
+    lo += q32;
+    rem += r32;
+    if (rem >= B) { rem -= B; ++lo; }
+  }
+};
 
-__global__ void k_chase(const LttbJob* __restrict__ jobs) {
-  const LttbJob& J = jobs[blockIdx.x];
+// One warp walks the table.  The chain is one shared-memory read per bucket:
+// the slot of bucket j's pick is row j's entry at the slot of bucket j-1's
+// pick.  Rows come in blocks of 32 through a ring of four blocks in shared
+// memory (cp.async, three blocks in flight); lane s keeps the slot of step s
+// of a block, and the block's picks are written together afterwards.
+constexpr int kBlk = 32;
+constexpr int kChaseRing = 4;
+
+__global__ void __launch_bounds__(32) k_chase(const LttbJob* __restrict__ jobs) {
+  const LttbJob J = jobs[blockIdx.x];
   const int lane = threadIdx.x & 31;
   const int64_t m = job_m(J), B = J.B;
   if (m <= B + 2) {
@@ -205,31 +329,37 @@ __global__ void k_chase(const LttbJob* __restrict__ jobs) {
     return;
   }
   if (J.mode != 0) return;
+  __shared__ int32_t ring[kChaseRing][kBlk * kTableMaxK];
   const int64_t K = J.K;
-  int32_t ring[kRing];
-#pragma unroll
-  for (int s = 0; s < kRing; ++s) ring[s] = (s < B && lane < K) ? J.table[(int64_t)s * K + lane] : 0;
-  BucketWalk w;
-  w.init(m, B);
-  int64_t a = 0, prev_lo = 0;
-  if (lane == 0) J.out[0] = out_index(J, 0);
-  for (int64_t j0 = 0; j0 < B; j0 += kRing) {
-#pragma unroll
-    for (int s = 0; s < kRing; ++s) {
-      const int64_t j = j0 + s;
-      if (j < B) {
-        const int64_t lo = w.start();
-        const int ai = (int)(a - prev_lo);   // slot of the previous pick in bucket j-1 (0 for j = 0)
-        const int32_t rel = __shfl_sync(0xffffffffu, ring[s], ai);
-        const int64_t pick = lo + rel;
-        if (lane == 0) J.out[j + 1] = out_index(J, pick);
-        a = pick;
-        prev_lo = lo;
-        w.next();
-        const int64_t jn = j + kRing;
-        ring[s] = (jn < B && lane < K) ? J.table[jn * K + lane] : 0;
-      }
+  const int64_t nblk = (B + kBlk - 1) / kBlk;
+  auto issue = [&](int64_t b) {
+    if (b < nblk) {
+      const int64_t base = b * kBlk * K;
+      const int64_t n = min((int64_t)kBlk, B - b * kBlk) * K;
+      int32_t* dst = ring[b % kChaseRing];
+      for (int64_t i = lane; i < n; i += 32) cp_async4(dst + i, J.table + base + i);
     }
+    cp_async_commit();
+  };
+  for (int b = 0; b < kChaseRing - 1; ++b) issue(b);
+  LaneStarts ls;
+  ls.init(lane, m, B);
+  if (lane == 0) J.out[0] = out_index(J, 0);
+  int32_t rel = 0;   // slot of the previous pick (point 0 for bucket 0)
+  for (int64_t b = 0; b < nblk; ++b) {
+    issue(b + kChaseRing - 1);
+    cp_async_wait<kChaseRing - 1>();
+    __syncwarp();
+    const int32_t* row = ring[b % kChaseRing];
+    const int n = (int)min((int64_t)kBlk, B - b * kBlk);
+    int32_t mine = 0;
+    for (int t = 0; t < n; ++t) {
+      rel = row[t * K + rel];
+      if (lane == t) mine = rel;
+    }
+    if (ls.j < B) J.out[ls.j + 1] = out_index(J, ls.lo + mine);
+    ls.advance();
+    __syncwarp();
   }
   if (lane == 0) {
     J.out[B + 1] = out_index(J, m - 1);
@@ -237,20 +367,9 @@ __global__ void k_chase(const LttbJob* __restrict__ jobs) {
   }
 }
 
-// ---------------------------------------------------------------- chain mode
+// ---------------------------------------------------------------- hull-table mode
 
-// p32[k] = point k relative to its bucket's first point, rounded to FP32.
-__global__ void k_p32(const LttbJob* __restrict__ jobs) {
-  const LttbJob& J = jobs[blockIdx.y];
-  if (J.mode != 1) return;
-  const int64_t m = job_m(J), B = J.B;
-  if (m <= B + 2) return;
-  for (int64_t k = 1 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < m - 1; k += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t lo = bucket_start(bucket_of(k, m, B), m, B);
-    J.p32[k] = make_float2(__double2float_rn(__dsub_rn(J.px[k], J.px[lo])),
-                           __double2float_rn(__dsub_rn(J.py[k], J.py[lo])));
-  }
-}
+constexpr int kCandMax = kLttbCandMax;
 
 // A value the FP32 filter accepts: finite, 0 or within [2^-60, 2^60] in magnitude.
 __device__ __forceinline__ bool filt_ok(float v) {
@@ -258,176 +377,323 @@ __device__ __forceinline__ bool filt_ok(float v) {
   return a == 0.0f || (a >= 8.6736174e-19f && a <= 1.1529215e18f);
 }
 
-struct ChainShared {
-  uint64_t key[kChainThreads / 32];
-  int64_t idx[kChainThreads / 32];
-  float fmax[kChainThreads / 32];
-  int bad[kChainThreads / 32];
-  int64_t pick;
-};
-
-__device__ __forceinline__ float block_max_f(float v, ChainShared& sh, int lane, int warp) {
-#pragma unroll
-  for (int o = 16; o; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
-  if (lane == 0) sh.fmax[warp] = v;
-  __syncthreads();
-  float r = sh.fmax[0];
-  for (int w = 1; w < kChainThreads / 32; ++w) r = fmaxf(r, sh.fmax[w]);
-  __syncthreads();
-  return r;
-}
-
-__device__ __forceinline__ int block_or(int v, ChainShared& sh, int lane, int warp) {
-  v = __any_sync(0xffffffffu, v) ? 1 : 0;
-  if (lane == 0) sh.bad[warp] = v;
-  __syncthreads();
-  int r = 0;
-  for (int w = 0; w < kChainThreads / 32; ++w) r |= sh.bad[w];
-  __syncthreads();
-  return r;
-}
-
-__device__ __forceinline__ void block_amax(uint64_t& k, int64_t& i, ChainShared& sh, int lane, int warp) {
-  amax_warp(k, i);
-  if (lane == 0) { sh.key[warp] = k; sh.idx[warp] = i; }
-  __syncthreads();
-  k = sh.key[0];
-  i = sh.idx[0];
-  for (int w = 1; w < kChainThreads / 32; ++w) amax_merge(k, i, sh.key[w], sh.idx[w]);
-  __syncthreads();
-}
-
-__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" :: "r"(s), "l"(gmem));
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
-
-// Copies bucket [lo, hi) (p32, px, py) into shared buffer `buf` with cp.async.
-__device__ __forceinline__ void prefetch_bucket(const LttbJob& J, int64_t lo, int64_t hi, float2* s32, double* sx,
-                                                double* sy) {
-  for (int64_t b = lo + threadIdx.x; b < hi; b += blockDim.x) {
-    const int64_t o = b - lo;
-    cp_async8(&s32[o], &J.p32[b]);
-    cp_async8(&sx[o], &J.px[b]);
-    cp_async8(&sy[o], &J.py[b]);
-  }
-  cp_async_commit();
-}
-
-__global__ void __launch_bounds__(kChainThreads) k_chain(const LttbJob* __restrict__ jobs) {
-  const LttbJob& J = jobs[blockIdx.x];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int64_t m = job_m(J), B = J.B;
-  if (m <= B + 2 || J.mode != 1) return;   // table-mode jobs and short jobs are done by k_chase
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ ChainShared sh;
-  const bool pre = J.K <= kPrefetchMaxK;
-  const int64_t K = pre ? J.K : 0;
-  // two buffers of (p32, px, py) for K points each
-  float2* s32[2];
-  double* sx[2];
-  double* sy[2];
-  {
-    unsigned char* p = smem_raw;
-    for (int t = 0; t < 2; ++t) {
-      sx[t] = reinterpret_cast<double*>(p); p += K * 8;
-      sy[t] = reinterpret_cast<double*>(p); p += K * 8;
-      s32[t] = reinterpret_cast<float2*>(p); p += K * 8;
-    }
-  }
-  BucketWalk w;
-  w.init(m, B);
-  int64_t a = 0;
-  double xa = J.px[0], ya = J.py[0];
-  if (tid == 0) J.out[0] = out_index(J, 0);
-  int64_t lo = w.start();
-  w.next();
-  int64_t hi = w.start();
-  if (pre) prefetch_bucket(J, lo, hi, s32[0], sx[0], sy[0]);
+// The exact pick of bucket j = [lo, hi) after previous pick a, by one warp.
+// Every point first gets an FP32 estimate of its area and a rigorous bound
+// on the estimate's error (relative to the bucket's first point, where the
+// FP32 copies are exact enough); only points whose upper bound reaches the
+// best lower bound get the exact binary64 area.  Values outside the range
+// where the bound holds send the step to exact areas for every point.
+__device__ __noinline__ int64_t warp_pick(const LttbJob& J, int64_t j, int64_t lo, int64_t hi, int64_t a, int64_t m, int64_t B,
+                             int lane) {
+  double xm, ym;
+  if (j == B - 1) { xm = J.px[m - 1]; ym = J.py[m - 1]; }
+  else { const double2 c = J.means[j + 1]; xm = c.x; ym = c.y; }
+  const double xa = J.px[a], ya = J.py[a];
+  const double dxm = __dsub_rn(xa, xm), dym = __dsub_rn(ym, ya);
+  const double X0 = J.px[lo], Y0 = J.py[lo];
+  const float al = __double2float_rn(dxm), be = __double2float_rn(dym);
+  const float ax = __double2float_rn(__dsub_rn(xa, X0)), ay = __double2float_rn(__dsub_rn(ya, Y0));
+  const bool fast = filt_ok(al) && filt_ok(be) && filt_ok(ax) && filt_ok(ay) && !isnan(dxm) && !isnan(dym) &&
+                    !isinf(dxm) && !isinf(dym);
   const float u8 = 4.7683716e-07f;   // 8 * 2^-24
   const float u4 = 2.3841858e-07f;   // 4 * 2^-24
   const float tiny = 7.5231638e-37f; // 2^-120
-  for (int64_t j = 0; j < B; ++j) {
-    const int cur = (int)(j & 1);
-    // next bucket's bounds and its prefetch (overlaps this step)
-    w.next();
-    const int64_t nhi = w.start();
-    if (pre) {
-      cp_async_wait_all();
-      __syncthreads();
-      if (j + 1 < B) prefetch_bucket(J, hi, nhi, s32[cur ^ 1], sx[cur ^ 1], sy[cur ^ 1]);
+  uint64_t bk = 0ull;
+  int64_t bi = kIdxNone;
+  bool done = false;
+  if (fast) {
+    float lmax = -INFINITY;
+    bool bad = false;
+    for (int64_t b = lo + lane; b < hi; b += 32) {
+      const float2 p = J.p32[b];
+      if (!(filt_ok(p.x) && filt_ok(p.y))) { bad = true; continue; }
+      const float d1 = p.y - ay, d2 = ax - p.x;
+      const float est = fabsf(al * d1 - d2 * be);
+      const float err = u8 * (fabsf(al) * (fabsf(p.y) + fabsf(ay) + fabsf(d1)) +
+                              fabsf(be) * (fabsf(p.x) + fabsf(ax) + fabsf(d2))) + u4 * est + tiny;
+      lmax = fmaxf(lmax, est - err);
     }
-    double xm, ym;
-    if (j == B - 1) { xm = J.px[m - 1]; ym = J.py[m - 1]; }
-    else { const double2 c = J.means[j + 1]; xm = c.x; ym = c.y; }
-    const double dxm = __dsub_rn(xa, xm), dym = __dsub_rn(ym, ya);
-    const double X0 = pre ? sx[cur][0] : J.px[lo];
-    const double Y0 = pre ? sy[cur][0] : J.py[lo];
-    const float al = __double2float_rn(dxm), be = __double2float_rn(dym);
-    const float ax = __double2float_rn(__dsub_rn(xa, X0)), ay = __double2float_rn(__dsub_rn(ya, Y0));
-    const bool fast = filt_ok(al) && filt_ok(be) && filt_ok(ax) && filt_ok(ay) &&
-                      !isnan(dxm) && !isnan(dym) && !isinf(dxm) && !isinf(dym);
-    uint64_t bk = 0ull;
-    int64_t bi = kIdxNone;
-    bool done = false;
-    if (fast) {
-      // pass 1: best lower bound of the area over the bucket
-      float lmax = -INFINITY;
-      int bad = 0;
-      for (int64_t b = lo + tid; b < hi; b += blockDim.x) {
-        const float2 p = pre ? s32[cur][b - lo] : J.p32[b];
-        if (!(filt_ok(p.x) && filt_ok(p.y))) { bad = 1; continue; }
+    if (!__any_sync(0xffffffffu, bad)) {
+#pragma unroll
+      for (int o = 16; o; o >>= 1) lmax = fmaxf(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
+      for (int64_t b = lo + lane; b < hi; b += 32) {
+        const float2 p = J.p32[b];
         const float d1 = p.y - ay, d2 = ax - p.x;
-        const float t1 = al * d1, t2 = d2 * be;
-        const float est = fabsf(t1 - t2);
+        const float est = fabsf(al * d1 - d2 * be);
         const float err = u8 * (fabsf(al) * (fabsf(p.y) + fabsf(ay) + fabsf(d1)) +
                                 fabsf(be) * (fabsf(p.x) + fabsf(ax) + fabsf(d2))) + u4 * est + tiny;
-        lmax = fmaxf(lmax, est - err);
+        if (est + err >= lmax)
+          amax_merge(bk, bi, area_key(exact_area(xa, ya, dxm, dym, J.px[b], J.py[b]), J.nan), b);
       }
-      if (!block_or(bad, sh, lane, warp)) {
-        const float L = block_max_f(lmax, sh, lane, warp);
-        // pass 2: exact areas of the points whose upper bound reaches L
-        for (int64_t b = lo + tid; b < hi; b += blockDim.x) {
-          const float2 p = pre ? s32[cur][b - lo] : J.p32[b];
-          const float d1 = p.y - ay, d2 = ax - p.x;
-          const float t1 = al * d1, t2 = d2 * be;
-          const float est = fabsf(t1 - t2);
-          const float err = u8 * (fabsf(al) * (fabsf(p.y) + fabsf(ay) + fabsf(d1)) +
-                                  fabsf(be) * (fabsf(p.x) + fabsf(ax) + fabsf(d2))) + u4 * est + tiny;
-          if (est + err >= L) {
-            const double xb = pre ? sx[cur][b - lo] : J.px[b];
-            const double yb = pre ? sy[cur][b - lo] : J.py[b];
-            amax_merge(bk, bi, area_key(exact_area(xa, ya, dxm, dym, xb, yb), J.nan), b);
-          }
-        }
-        done = true;
-      }
+      done = true;
     }
-    if (!done) {
-      // exact path: every point of the bucket
-      for (int64_t b = lo + tid; b < hi; b += blockDim.x) {
-        const double xb = pre ? sx[cur][b - lo] : J.px[b];
-        const double yb = pre ? sy[cur][b - lo] : J.py[b];
-        amax_merge(bk, bi, area_key(exact_area(xa, ya, dxm, dym, xb, yb), J.nan), b);
-      }
-    }
-    block_amax(bk, bi, sh, lane, warp);
-    const int64_t pick = (bk == 0ull) ? lo : bi;   // no candidate (NaN-ignore): first index
-    if (tid == 0) J.out[j + 1] = out_index(J, pick);
-    a = pick;
-    xa = pre ? sx[cur][pick - lo] : J.px[pick];
-    ya = pre ? sy[cur][pick - lo] : J.py[pick];
-    lo = hi;
-    hi = nhi;
   }
-  if (pre) cp_async_wait_all();
-  if (tid == 0) {
+  if (!done)
+    for (int64_t b = lo + lane; b < hi; b += 32)
+      amax_merge(bk, bi, area_key(exact_area(xa, ya, dxm, dym, J.px[b], J.py[b]), J.nan), b);
+  amax_warp(bk, bi);
+  return bk == 0ull ? lo : bi;   // no candidate (NaN-ignore): first index
+}
+
+// Candidates of every bucket, one warp per bucket: each lane builds the upper
+// and lower hulls of its slice of the bucket (Andrew's monotone chain over the
+// FP32 points, x ascending), then pairs of neighbouring slice hulls are merged
+// in five rounds (lane 2i takes lane 2i+1's lists, lane 4i lane 4i+2's, ...),
+// all stacks in shared memory.  Lane 0 writes candidate row j+1 (the row the
+// step after bucket j reads): the first point, the first non-finite point,
+// then hull vertices, at most kCandMax, -1 after.  A stack that would
+// overflow replaces its top, so an unusually long hull only yields fewer
+// useful candidates (the chase then computes those steps directly).
+constexpr int kHullWarps = 4;
+constexpr int kSliceStack = 24;    // per lane and hull
+
+// Per warp: entry i of lane l's stacks at [i][l] (distinct banks across lanes).
+struct HullWarp {
+  float2 p[2][kSliceStack][32];
+  int32_t r[2][kSliceStack][32];
+  int n[2][32];
+};
+
+__device__ __forceinline__ float cross3(float2 o, float2 a, float2 b) {
+  return (a.x - o.x) * (b.y - o.y) - (a.y - o.y) * (b.x - o.x);
+}
+
+// Pushes (p, r) onto column `col` of stack h (upper: pops on left or straight
+// turns, lower: on right or straight turns).
+__device__ __forceinline__ void hull_push(HullWarp& H, int h, int col, int& n, float2 p, int32_t r) {
+  while (n >= 2) {
+    const float c = cross3(H.p[h][n - 2][col], H.p[h][n - 1][col], p);
+    if (h == 0 ? c >= 0.0f : c <= 0.0f) --n;
+    else break;
+  }
+  if (n == kSliceStack) --n;
+  H.p[h][n][col] = p;
+  H.r[h][n][col] = r;
+  ++n;
+}
+
+__global__ void __launch_bounds__(kHullWarps * 32) k_hull(const LttbJob* __restrict__ jobs) {
+  const LttbJob J = jobs[blockIdx.y];
+  if (J.mode != 2) return;
+  const int64_t m = job_m(J), B = J.B;
+  if (m <= B + 2) return;
+  extern __shared__ __align__(16) unsigned char hull_smem[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  HullWarp& H = reinterpret_cast<HullWarp*>(hull_smem)[wib];
+  for (int64_t j = (int64_t)blockIdx.x * kHullWarps + wib; j < B; j += (int64_t)gridDim.x * kHullWarps) {
+    const int64_t lo = bucket_start(j, m, B), hi = bucket_start(j + 1, m, B);
+    const int64_t c = (hi - lo + 31) / 32;
+    const int64_t s0 = lo + lane * c, s1 = min(s0 + c, hi);
+    int n0 = 0, n1 = 0;
+    int64_t bad = INT64_MAX;
+    for (int64_t b0 = s0; b0 < s1; b0 += 8) {
+      float2 pv[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) pv[u] = b0 + u < s1 ? J.p32[b0 + u] : make_float2(0.f, 0.f);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int64_t b = b0 + u;
+        if (b >= s1) break;
+        const float2 p = pv[u];
+        if (!(isfinite(p.x) && isfinite(p.y))) { bad = min(bad, b); continue; }
+        const int32_t r = (int32_t)(b - lo);
+        hull_push(H, 0, lane, n0, p, r);
+        hull_push(H, 1, lane, n1, p, r);
+      }
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) bad = min(bad, (int64_t)__shfl_xor_sync(0xffffffffu, bad, o));
+    H.n[0][lane] = n0;
+    H.n[1][lane] = n1;
+    for (int d = 1; d < 32; d <<= 1) {
+      __syncwarp();
+      if ((lane & (2 * d - 1)) == 0) {
+        const int src = lane + d;
+        for (int h = 0; h < 2; ++h) {
+          int n = H.n[h][lane];
+          const int ns = H.n[h][src];
+          for (int i = 0; i < ns; ++i) hull_push(H, h, lane, n, H.p[h][i][src], H.r[h][i][src]);
+          H.n[h][lane] = n;
+        }
+      }
+    }
+    __syncwarp();
+    if (lane == 0 && j + 1 <= B) {
+      int32_t* row = J.cand + (j + 1) * kCandMax;
+      int nc = 0;
+      auto add = [&](int32_t r) {
+        for (int i = 0; i < nc; ++i)
+          if (row[i] == r) return;
+        if (nc < kCandMax) row[nc++] = r;
+      };
+      add(0);
+      if (bad < hi) add((int32_t)(bad - lo));
+      for (int h = 0; h < 2; ++h)
+        for (int i = 0; i < H.n[h][0]; ++i) add(H.r[h][i][0]);
+      for (int i = nc; i < kCandMax; ++i) row[i] = -1;
+    }
+    __syncwarp();
+  }
+}
+
+// table[j*kCandMax + s] = (pick of bucket j) - start(j) when the previous pick
+// is candidate s of bucket j-1 (row j of cand; for j = 0: point 0, slot 0).
+// One CTA per bucket: the bucket's FP32 points are staged in shared memory
+// once, and each warp takes candidates in turn.  For a candidate, the exact
+// areas of bucket j's own hull candidates (row j+1) give a lower bound L of
+// the best area; one pass of FP32 estimates with rigorous error bounds then
+// keeps only the points whose upper bound reaches L, whose exact binary64
+// areas decide the pick.  Values outside the range where the bound holds,
+// and non-finite areas, take the exact path over every point.
+constexpr int kTableWarps = 4;
+constexpr int kStageMax = 6144;    // points of a bucket staged in shared memory (48 KB)
+
+__global__ void __launch_bounds__(kTableWarps * 32) k_htable(const LttbJob* __restrict__ jobs) {
+  const LttbJob J = jobs[blockIdx.y];
+  if (J.mode != 2) return;
+  const int64_t m = job_m(J), B = J.B;
+  if (m <= B + 2) return;
+  extern __shared__ __align__(16) float2 stage[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const float u8 = 4.7683716e-07f;   // 8 * 2^-24
+  const float u4 = 2.3841858e-07f;   // 4 * 2^-24
+  const float tiny = 7.5231638e-37f; // 2^-120
+  for (int64_t j = blockIdx.x; j < B; j += gridDim.x) {
+    const int64_t lo = bucket_start(j, m, B), hi = bucket_start(j + 1, m, B);
+    const int64_t K = hi - lo;
+    const bool staged = K <= kStageMax;
+    __syncthreads();   // the previous bucket's readers are done with the stage
+    if (staged)
+      for (int64_t i = threadIdx.x; i < K; i += blockDim.x) stage[i] = J.p32[lo + i];
+    __syncthreads();
+    bool any_bad = false;
+    for (int64_t i = lane; i < K; i += 32) {
+      const float2 p = staged ? stage[i] : J.p32[lo + i];
+      any_bad |= !(filt_ok(p.x) && filt_ok(p.y));
+    }
+    any_bad = __any_sync(0xffffffffu, any_bad);
+    double xm, ym;
+    if (j == B - 1) { xm = J.px[m - 1]; ym = J.py[m - 1]; }
+    else { const double2 cm = J.means[j + 1]; xm = cm.x; ym = cm.y; }
+    const double X0 = J.px[lo], Y0 = J.py[lo];
+    const int32_t own = J.cand[(j + 1) * kCandMax + lane];   // this bucket's hull candidates
+    const int64_t alo = j == 0 ? 0 : bucket_start(j - 1, m, B);
+    for (int s = wib; s < kCandMax; s += kTableWarps) {
+      int32_t r;
+      if (j == 0) r = s == 0 ? 0 : -1;
+      else r = J.cand[j * kCandMax + s];
+      if (r < 0) continue;   // uniform per warp
+      const int64_t a = alo + r;
+      const double xa = J.px[a], ya = J.py[a];
+      const double dxm = __dsub_rn(xa, xm), dym = __dsub_rn(ym, ya);
+      uint64_t bk = 0ull;
+      int64_t bi = kIdxNone;
+      const float al = __double2float_rn(dxm), be = __double2float_rn(dym);
+      const float ax = __double2float_rn(__dsub_rn(xa, X0)), ay = __double2float_rn(__dsub_rn(ya, Y0));
+      const bool fast = !any_bad && filt_ok(al) && filt_ok(be) && filt_ok(ax) && filt_ok(ay) && !isnan(dxm) &&
+                        !isnan(dym) && !isinf(dxm) && !isinf(dym);
+      bool done = false;
+      if (fast) {
+        // lower bound from the exact areas of the bucket's own candidates
+        double best = -1.0;
+        if (own >= 0) {
+          const double ar = exact_area(xa, ya, dxm, dym, J.px[lo + own], J.py[lo + own]);
+          if (isfinite(ar)) best = ar;
+          amax_merge(bk, bi, area_key(ar, J.nan), lo + own);
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) best = fmax(best, __shfl_xor_sync(0xffffffffu, best, o));
+        if (best >= 0.0) {
+          float L = __double2float_rd(best);
+          for (int64_t i = lane; i < K; i += 32) {
+            const float2 p = staged ? stage[i] : J.p32[lo + i];
+            const float d1 = p.y - ay, d2 = ax - p.x;
+            const float est = fabsf(al * d1 - d2 * be);
+            const float err = u8 * (fabsf(al) * (fabsf(p.y) + fabsf(ay) + fabsf(d1)) +
+                                    fabsf(be) * (fabsf(p.x) + fabsf(ax) + fabsf(d2))) + u4 * est + tiny;
+            if (est + err >= L)
+              amax_merge(bk, bi, area_key(exact_area(xa, ya, dxm, dym, J.px[lo + i], J.py[lo + i]), J.nan), lo + i);
+          }
+          done = true;
+        }
+      }
+      if (!done) {
+        bk = 0ull;
+        bi = kIdxNone;
+        for (int64_t b = lo + lane; b < hi; b += 32)
+          amax_merge(bk, bi, area_key(exact_area(xa, ya, dxm, dym, J.px[b], J.py[b]), J.nan), b);
+      }
+      amax_warp(bk, bi);
+      if (lane == 0) J.table[j * kCandMax + s] = (int32_t)((bk == 0ull ? lo : bi) - lo);
+    }
+  }
+}
+
+// One warp walks the candidate tables: per block of 32 buckets, candidate rows
+// and table rows come through rings of four blocks in shared memory (16-byte
+// cp.async, three blocks in flight).  A step is a ballot for the previous
+// pick's slot among the candidates and one shared-memory read of the table
+// entry; a previous pick that is not a candidate costs the exact warp search.
+__global__ void __launch_bounds__(32) k_hchase(const LttbJob* __restrict__ jobs) {
+  const LttbJob J = jobs[blockIdx.x];
+  if (J.mode != 2) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t m = job_m(J), B = J.B;
+  if (m <= B + 2) return;   // k_chase wrote every index
+  __shared__ __align__(16) int32_t cring[kChaseRing][kBlk * kCandMax];
+  __shared__ __align__(16) int32_t tring[kChaseRing][kBlk * kCandMax];
+  const int64_t nblk = (B + kBlk - 1) / kBlk;
+  auto issue = [&](int64_t b) {
+    if (b < nblk) {
+      const int64_t rows = min((int64_t)kBlk, B - b * kBlk);
+      const int64_t n16 = rows * kCandMax / 4;   // 16-byte pieces
+      const int r = (int)(b % kChaseRing);
+      for (int64_t i = lane; i < n16; i += 32) {
+        cp_async16(&cring[r][4 * i], J.cand + b * kBlk * kCandMax + 4 * i);
+        cp_async16(&tring[r][4 * i], J.table + b * kBlk * kCandMax + 4 * i);
+      }
+    }
+    cp_async_commit();
+  };
+  for (int b = 0; b < kChaseRing - 1; ++b) issue(b);
+  LaneStarts ls;
+  ls.init(lane, m, B);
+  if (lane == 0) J.out[0] = out_index(J, 0);
+  int32_t rel = 0;
+  for (int64_t b = 0; b < nblk; ++b) {
+    issue(b + kChaseRing - 1);
+    cp_async_wait<kChaseRing - 1>();
+    __syncwarp();
+    const int r = (int)(b % kChaseRing);
+    const int n = (int)min((int64_t)kBlk, B - b * kBlk);
+    int32_t mine = 0;
+    int32_t cnext = cring[r][lane];
+    for (int t = 0; t < n; ++t) {
+      const int64_t j = b * kBlk + t;
+      const int32_t cand_t = cnext;
+      if (t + 1 < n) cnext = cring[r][(t + 1) * kCandMax + lane];   // off the chain
+      int slot = 0;
+      if (j > 0) {
+        const unsigned hit = __ballot_sync(0xffffffffu, cand_t == rel);
+        slot = hit ? __ffs(hit) - 1 : -1;
+      }
+      if (slot >= 0) {
+        rel = tring[r][t * kCandMax + slot];
+      } else {
+        const int64_t lo = bucket_start(j, m, B);
+        const int64_t a = bucket_start(j - 1, m, B) + rel;
+        rel = (int32_t)(warp_pick(J, j, lo, bucket_start(j + 1, m, B), a, m, B, lane) - lo);
+      }
+      if (lane == t) mine = rel;
+    }
+    if (ls.j < B) J.out[ls.j + 1] = out_index(J, ls.lo + mine);
+    ls.advance();
+    __syncwarp();
+  }
+  if (lane == 0) {
     J.out[B + 1] = out_index(J, m - 1);
     *J.out_count = B + 2;
   }
-  (void)a;
 }
 
 // Completes the MinMaxLTTB point set: R[0] = 0, R[k+1] = n-1, m = k+2 where k
@@ -457,11 +723,31 @@ static unsigned grid_for(int64_t n, int per_sm = 8) {
   return (unsigned)blocks;
 }
 
-size_t lttb_job_scratch(int64_t m_max, int64_t B, int64_t K, int mode) {
+size_t lttb_job_scratch(int64_t m_max, int64_t B, int64_t K) {
   size_t s = align_up((size_t)(B + 1) * sizeof(double2), 256);
-  if (mode == 0) s += align_up((size_t)B * (size_t)K * 4, 256);
-  else s += align_up((size_t)m_max * sizeof(float2), 256);
+  if (lttb_mode(K) == 0) {
+    s += align_up((size_t)B * (size_t)K * 4, 256);
+  } else {
+    s += align_up((size_t)m_max * sizeof(float2), 256);           // p32
+    s += align_up((size_t)(B + 1) * kCandMax * 4, 256);           // candidate rows 0..B
+    s += align_up((size_t)B * kCandMax * 4, 256);                 // table
+  }
   return s;
+}
+
+void lttb_job_bind(LttbJob& J, char* p, int64_t m_max) {
+  J.mode = lttb_mode(J.K);
+  J.means = reinterpret_cast<double2*>(p);
+  p += align_up((size_t)(J.B + 1) * sizeof(double2), 256);
+  if (J.mode == 0) {
+    J.table = reinterpret_cast<int32_t*>(p);
+    return;
+  }
+  J.p32 = reinterpret_cast<float2*>(p);
+  p += align_up((size_t)m_max * sizeof(float2), 256);
+  J.cand = reinterpret_cast<int32_t*>(p);
+  p += align_up((size_t)(J.B + 1) * kCandMax * 4, 256);
+  J.table = reinterpret_cast<int32_t*>(p);
 }
 
 tsds_status launch_points_jobs(const PointsJob* jobs_dev, int count, int64_t max_m, cudaStream_t st) {
@@ -472,36 +758,54 @@ tsds_status launch_points_jobs(const PointsJob* jobs_dev, int count, int64_t max
 }
 
 tsds_status run_lttb_jobs(const LttbJob* jobs_host, const LttbJob* jobs_dev, int count, int64_t max_B,
-                          int64_t max_m, int64_t max_K_chain, cudaStream_t st) {
-  bool any_table = false, any_chain = false;
-  for (int i = 0; i < count; ++i) (jobs_host[i].mode == 0 ? any_table : any_chain) = true;
-  dim3 gm(grid_for(max_B, 4), (unsigned)count);
-  note_launch();
-  k_means<<<gm, 256, 0, st>>>(jobs_dev);
-  TSDS_CK(cudaGetLastError());
+                          int64_t max_m, cudaStream_t st) {
+  bool any_table = false, any_hull = false;
+  for (int i = 0; i < count; ++i) (jobs_host[i].mode == 0 ? any_table : any_hull) = true;
+  const int64_t cap = (int64_t)device_sm_count() * 16;
   if (any_table) {
+    note_launch();
+    k_means<<<dim3(grid_for(max_B, 4), (unsigned)count), 256, 0, st>>>(jobs_dev);
+    TSDS_CK(cudaGetLastError());
     int64_t blocks = (max_B + 7) / 8;
-    const int64_t cap = (int64_t)device_sm_count() * 16;
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
     note_launch();
     k_table<<<dim3((unsigned)blocks, (unsigned)count), 256, 0, st>>>(jobs_dev);
     TSDS_CK(cudaGetLastError());
   }
-  if (any_chain) {
-    note_launch();
-    k_p32<<<dim3(grid_for(max_m, 4), (unsigned)count), 256, 0, st>>>(jobs_dev);
-    TSDS_CK(cudaGetLastError());
-    const size_t smem = max_K_chain <= kPrefetchMaxK ? (size_t)max_K_chain * 48 : 0;
-    if (smem > 48 * 1024) TSDS_CK(cudaFuncSetAttribute(k_chain, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    note_launch();
-    k_chain<<<(unsigned)count, kChainThreads, smem, st>>>(jobs_dev);
-    TSDS_CK(cudaGetLastError());
-  }
   // table-mode jobs, and every job whose points are all kept, finish here
   note_launch();
   k_chase<<<(unsigned)count, 32, 0, st>>>(jobs_dev);
   TSDS_CK(cudaGetLastError());
+  if (any_hull) {
+    int64_t pb = (max_B + 7) / 8;
+    if (pb > cap) pb = cap;
+    note_launch();
+    k_p32<<<dim3((unsigned)pb, (unsigned)count), 256, 0, st>>>(jobs_dev);
+    TSDS_CK(cudaGetLastError());
+    const int ssmem = (int)sizeof(SumRing);
+    note_launch();
+    k_sums_wide<<<dim3((unsigned)((max_B + 31) / 32), (unsigned)count), 32, ssmem, st>>>(jobs_dev);
+    TSDS_CK(cudaGetLastError());
+    int64_t hb = (max_B + kHullWarps - 1) / kHullWarps;
+    if (hb > cap) hb = cap;
+    if (hb < 1) hb = 1;
+    const int hsmem = (int)(kHullWarps * sizeof(HullWarp));
+    TSDS_CK(cudaFuncSetAttribute(k_hull, cudaFuncAttributeMaxDynamicSharedMemorySize, hsmem));
+    note_launch();
+    k_hull<<<dim3((unsigned)hb, (unsigned)count), kHullWarps * 32, hsmem, st>>>(jobs_dev);
+    TSDS_CK(cudaGetLastError());
+    int64_t tb = max_B;
+    if (tb > cap) tb = cap;
+    if (tb < 1) tb = 1;
+    const int tsmem = (int)(kStageMax * sizeof(float2));
+    note_launch();
+    k_htable<<<dim3((unsigned)tb, (unsigned)count), kTableWarps * 32, tsmem, st>>>(jobs_dev);
+    TSDS_CK(cudaGetLastError());
+    note_launch();
+    k_hchase<<<(unsigned)count, 32, 0, st>>>(jobs_dev);
+    TSDS_CK(cudaGetLastError());
+  }
   return TSDS_OK;
 }
 
@@ -519,21 +823,16 @@ static tsds_status lttb_points_core(const double* px, const double* py, const in
   J.B = n_out - 2;
   J.K = m_max > 2 ? (m_max - 2 + J.B - 1) / J.B : 1;
   J.nan = nan;
-  J.mode = J.K <= kTableMaxK ? 0 : 1;
   J.R = R;
   J.out = out;
   J.out_count = out_count;
   Scratch s;
-  const size_t js = lttb_job_scratch(m_max, J.B, J.K, J.mode);
+  const size_t js = lttb_job_scratch(m_max, J.B, J.K);
   TSDS_CK(scratch_alloc(s, js + align_up(sizeof(LttbJob), 256), st));
-  char* p = static_cast<char*>(s.p);
-  J.means = reinterpret_cast<double2*>(p);
-  p += align_up((size_t)(J.B + 1) * sizeof(double2), 256);
-  if (J.mode == 0) J.table = reinterpret_cast<int32_t*>(p);
-  else J.p32 = reinterpret_cast<float2*>(p);
+  lttb_job_bind(J, static_cast<char*>(s.p), m_max);
   LttbJob* jd = reinterpret_cast<LttbJob*>(static_cast<char*>(s.p) + js);
   TSDS_CK(cudaMemcpyAsync(jd, &J, sizeof J, cudaMemcpyHostToDevice, st));
-  return run_lttb_jobs(&J, jd, 1, J.B, m_max, J.mode == 1 ? J.K : 0, st);
+  return run_lttb_jobs(&J, jd, 1, J.B, m_max, st);
 }
 
 static tsds_status points(const void* x, tsds_dtype x_dtype, const void* y, tsds_dtype y_dtype, const int64_t* R,

@@ -27,12 +27,14 @@ struct LttbJob {
   int64_t B;             // n_out - 2
   int64_t K;             // bound on any bucket's size: ceil((m_max - 2) / B)
   int nan;
-  int mode;              // 0: transition table (K <= kLttbTableMaxK), 1: filtered chain
+  int mode;              // 0: transition table over whole buckets (K <= kLttbTableMaxK),
+                         // 2: transition table over each bucket's hull candidates
   const int64_t* R;      // point -> output index (null: index + bias)
   int64_t bias;
   double2* means;        // B+1 entries
-  int32_t* table;        // table mode: B*K picks, relative to the bucket start
-  float2* p32;           // chain mode: m points relative to their bucket's first point
+  int32_t* table;        // mode 0: B*K picks; mode 2: B*kLttbCandMax picks (relative to the bucket start)
+  float2* p32;           // mode 2: m points relative to their bucket's first point, in FP32
+  int32_t* cand;         // mode 2: B*kLttbCandMax candidate picks per bucket (relative, -1: none)
   int64_t* out;
   int64_t* out_count;
 };
@@ -51,14 +53,19 @@ struct PointsJob {
 };
 
 constexpr int kLttbTableMaxK = 32;
+constexpr int kLttbCandMax = 32;
 
-// Scratch bytes a job needs for means and table / p32 (besides its points).
-size_t lttb_job_scratch(int64_t m_max, int64_t B, int64_t K, int mode);
+inline int lttb_mode(int64_t K) { return K <= kLttbTableMaxK ? 0 : 2; }
+
+// Scratch bytes a job needs besides its points (means, tables, candidates),
+// and the binding of those pointers into `p` (J.B, J.K set; sets J.mode).
+size_t lttb_job_scratch(int64_t m_max, int64_t B, int64_t K);
+void lttb_job_bind(LttbJob& J, char* p, int64_t m_max);
 
 // Runs the LTTB kernels for jobs already filled in (device memory for their
 // points and scratch in place); jobs_dev must hold a copy of jobs_host.
 tsds_status run_lttb_jobs(const LttbJob* jobs_host, const LttbJob* jobs_dev, int count, int64_t max_B,
-                          int64_t max_m, int64_t max_K_chain, cudaStream_t st);
+                          int64_t max_m, cudaStream_t st);
 
 // k_points over `count` jobs in device memory.
 tsds_status launch_points_jobs(const PointsJob* jobs_dev, int count, int64_t max_m, cudaStream_t st);

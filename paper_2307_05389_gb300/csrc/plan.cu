@@ -17,7 +17,7 @@ namespace tsds {
 typedef unsigned __int128 u128;
 
 __global__ void k_edges_index(const SeriesDev* sd, SeriesDev single, int count) {
-  const SeriesDev& S = count == 1 && sd == nullptr ? single : sd[blockIdx.y];
+  const SeriesDev S = count == 1 && sd == nullptr ? single : sd[blockIdx.y];
   const int64_t nb = S.nb;
   if (nb <= 0) return;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= nb; i += (int64_t)gridDim.x * blockDim.x) {
@@ -51,7 +51,7 @@ __device__ __forceinline__ double x_as_f64<__half>(const __half* x, int64_t j) {
 
 template <class X, bool FLOATX>
 __global__ void k_edges_x(const SeriesDev* sd, SeriesDev single, int count) {
-  const SeriesDev& S = count == 1 && sd == nullptr ? single : sd[blockIdx.y];
+  const SeriesDev S = count == 1 && sd == nullptr ? single : sd[blockIdx.y];
   const int64_t nb = S.nb;
   if (nb <= 0) return;
   const X* x = static_cast<const X*>(S.x);
@@ -115,7 +115,7 @@ cudaError_t launch_edges(const SeriesDev* s_dev, int count, const SeriesDev* s_h
 }
 
 __global__ void k_window_map(const SeriesDev* sd, int32_t* win_series, int64_t welems) {
-  const SeriesDev& S = sd[blockIdx.x];
+  const SeriesDev S = sd[blockIdx.x];
   if (S.nb <= 0) return;
   int64_t k = (S.n + welems - 1) / welems;
   for (int64_t w = threadIdx.x; w < k; w += blockDim.x) win_series[S.win_base + w] = (int32_t)blockIdx.x;
@@ -130,7 +130,7 @@ cudaError_t launch_window_map(const SeriesDev* s_dev, int count, int32_t* win_se
 
 // One CTA per series; only series whose n_out >= n (nb == 0) write.
 __global__ void k_iota_batched(const SeriesDev* sd) {
-  const SeriesDev& S = sd[blockIdx.x];
+  const SeriesDev S = sd[blockIdx.x];
   if (S.nb != 0) return;
   for (int64_t i = threadIdx.x; i < S.n; i += blockDim.x) S.out[i] = i + S.idx_bias;
   if (threadIdx.x == 0) *S.out_count = S.n;

@@ -268,7 +268,7 @@ size_t query_bytes(const Server& S, const tsds_query& q, int64_t window_bytes) {
     const int64_t m_max = lttb_m_max(q);
     const int64_t B = q.n_out - 2;
     const int64_t K = (m_max - 2 + B - 1) / B;
-    b += up256((size_t)m_max * 8 * 3) + lttb_job_scratch(m_max, B, K, K <= kLttbTableMaxK ? 0 : 1) +
+    b += up256((size_t)m_max * 8 * 3) + lttb_job_scratch(m_max, B, K) +
          sizeof(LttbJob) + sizeof(PointsJob) + 512;
   }
   return b;
@@ -347,16 +347,15 @@ tsds_status launch_batch(const Server& S, Slot& sl, const std::vector<tsds_query
     words += (size_t)qs[i].n_out + kInfoSlots;
   }
   o = up256(o + words * 8);
-  int64_t lt_max_B = 0, lt_max_m = 0, lt_max_K_chain = 0;
+  int64_t lt_max_B = 0, lt_max_m = 0;
   for (int i : lt) {
     const int64_t m_max = lttb_m_max(qs[i]);
     const int64_t B = qs[i].n_out - 2;
     const int64_t K = (m_max - 2 + B - 1) / B;
     off_R[i] = o;  o = up256(o + (size_t)m_max * 8 * 3);   // R, py, px
-    off_lt[i] = o; o = up256(o + lttb_job_scratch(m_max, B, K, K <= kLttbTableMaxK ? 0 : 1));
+    off_lt[i] = o; o = up256(o + lttb_job_scratch(m_max, B, K));
     lt_max_B = std::max(lt_max_B, B);
     lt_max_m = std::max(lt_max_m, m_max);
-    if (K > kLttbTableMaxK) lt_max_K_chain = std::max(lt_max_K_chain, K);
   }
   const size_t total = o;
 
@@ -427,15 +426,10 @@ tsds_status launch_batch(const Server& S, Slot& sl, const std::vector<tsds_query
     J.B = q.n_out - 2;
     J.K = (m_max - 2 + J.B - 1) / J.B;
     J.nan = q.nan;
-    J.mode = J.K <= kLttbTableMaxK ? 0 : 1;
     J.R = R;
     J.out = hq[i].out;
     J.out_count = hq[i].info;
-    char* ls = base + off_lt[i];
-    J.means = reinterpret_cast<double2*>(ls);
-    ls += up256((size_t)(J.B + 1) * sizeof(double2));
-    if (J.mode == 0) J.table = reinterpret_cast<int32_t*>(ls);
-    else J.p32 = reinterpret_cast<float2*>(ls);
+    lttb_job_bind(J, base + off_lt[i], m_max);
     PointsJob& P = hp[t];
     memset(&P, 0, sizeof P);
     P.x = ser[i].x;
@@ -484,8 +478,7 @@ tsds_status launch_batch(const Server& S, Slot& sl, const std::vector<tsds_query
     SV_CK(cudaGetLastError());
     tsds_status r = launch_points_jobs(reinterpret_cast<const PointsJob*>(base + off_pjobs), nlt, lt_max_m, st);
     if (r != TSDS_OK) { snprintf(err, errlen, "points: %s", tsds_last_error()); return r; }
-    r = run_lttb_jobs(hl, reinterpret_cast<const LttbJob*>(base + off_ljobs), nlt, lt_max_B, lt_max_m,
-                      lt_max_K_chain, st);
+    r = run_lttb_jobs(hl, reinterpret_cast<const LttbJob*>(base + off_ljobs), nlt, lt_max_B, lt_max_m, st);
     if (r != TSDS_OK) { snprintf(err, errlen, "lttb: %s", tsds_last_error()); return r; }
   }
   SV_CK(cudaMemcpyAsync(sl.pin_out, outbase, words * 8, cudaMemcpyDeviceToHost, st));
