@@ -662,12 +662,13 @@ __global__ void __launch_bounds__(kRingThreads)
 k_argminmax(const SeriesDev* __restrict__ sd, SeriesDev single, const int32_t* __restrict__ win_series,
             int64_t total_windows, Piece* __restrict__ first_piece, Piece* __restrict__ last_piece,
             WorkCounters* __restrict__ work, int64_t welems, const int64_t* __restrict__ total_dev,
-            int64_t w_first) {
+            int64_t w_first, const int64_t* __restrict__ first_dev) {
   using T = typename P::T;
   extern __shared__ __align__(128) unsigned char ring_smem[];
   __shared__ __align__(8) uint64_t bars[kWarpsPerCta][kRingStages];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (total_dev) total_windows = *total_dev;
+  if (first_dev) w_first = *first_dev;
   Ring R;
   R.buf = ring_smem + (size_t)warp * kRingStages * kChunkBytes;
   R.bar = bars[warp];
@@ -805,14 +806,15 @@ static cudaError_t launch_var(const SeriesDev* s_dev, const SeriesDev& single, c
   if constexpr (VAR == STREAM_LDG) {
     k_argminmax_ldg<P, NM, MULTI><<<(unsigned)blocks, threads, 0, st>>>(s_dev, single, win_series, total_windows, fp,
                                                                         lp, work, welems, cfg.total_windows_dev,
-                                                                        cfg.window_first);
+                                                                        cfg.window_first, cfg.window_first_dev);
   } else if constexpr (VAR == STREAM_SEG) {
     k_argminmax_seg<P, NM, MULTI><<<(unsigned)blocks, threads, 0, st>>>(s_dev, single, win_series, total_windows, fp,
                                                                         lp, work, welems, cfg.total_windows_dev,
-                                                                        cfg.window_first);
+                                                                        cfg.window_first, cfg.window_first_dev);
   } else {
     k_argminmax<P, NM, MULTI><<<(unsigned)blocks, threads, kRingSmemBytes, st>>>(
-        s_dev, single, win_series, total_windows, fp, lp, work, welems, cfg.total_windows_dev, cfg.window_first);
+        s_dev, single, win_series, total_windows, fp, lp, work, welems, cfg.total_windows_dev, cfg.window_first,
+        cfg.window_first_dev);
   }
   return cudaGetLastError();
 }

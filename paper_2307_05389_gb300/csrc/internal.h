@@ -81,6 +81,7 @@ struct StreamConfig {
   int variant = STREAM_AUTO;
   int64_t mean_bin_bytes = 0;           // bytes-weighted mean bin size of the launch
   int64_t window_first = 0;             // the launch takes windows [window_first, total_windows)
+  const int64_t* window_first_dev = nullptr;   // when set, window_first is read here on the device
 };
 
 // The variant a launch with this shape runs for elements of elem_bytes.

@@ -78,7 +78,8 @@ __device__ __forceinline__ double x_as_double(const void* x, int dt, int64_t j) 
 
 // One warp per query: resolve [lo, hi) and fill the binned descriptor.
 __global__ void k_resolve(const QueryDev* __restrict__ qd, SeriesDev* __restrict__ sd, int64_t* __restrict__ windows,
-                          int count, int x_dtype, int y_size, int x_size, int64_t welems) {
+                          int8_t* __restrict__ small, int count, int x_dtype, int y_size, int x_size, int64_t welems,
+                          int64_t small_bin_bytes) {
   const int lane = threadIdx.x & 31;
   const int q = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (q >= count) return;
@@ -127,30 +128,40 @@ __global__ void k_resolve(const QueryDev* __restrict__ qd, SeriesDev* __restrict
   D.out = S.out;
   D.out_count = S.out_count;
   windows[q] = S.nb > 0 ? (S.n + welems - 1) / welems : 0;
+  // bins under the small-bin size go to the segmented launch
+  small[q] = (S.nb > 0 && S.n * y_size < small_bin_bytes * S.nb) ? 1 : 0;
   Q.info[1] = L;
   Q.info[2] = lo;
 }
 
-// Exclusive scan of the per-query window counts into the descriptors' window
-// bases; the total goes to *total.  One CTA.
-__global__ void k_scan_windows(SeriesDev* __restrict__ sd, const int64_t* __restrict__ windows, int count,
-                               int64_t* __restrict__ total) {
-  __shared__ int64_t part[1024];
+// Window bases of the queries: those with large bins first, then those with
+// small bins; total[0] = all windows, total[1] = the large-bin windows (where
+// the small-bin range starts).  One CTA.
+__global__ void k_scan_windows(SeriesDev* __restrict__ sd, const int64_t* __restrict__ windows,
+                               const int8_t* __restrict__ small, int count, int64_t* __restrict__ total) {
+  __shared__ int64_t part[2][1024];
   const int t = threadIdx.x;
   const int per = (count + blockDim.x - 1) / blockDim.x;
   const int a = min(t * per, count), b = min(a + per, count);
-  int64_t s = 0;
-  for (int i = a; i < b; ++i) s += windows[i];
-  part[t] = s;
+  int64_t s0 = 0, s1 = 0;
+  for (int i = a; i < b; ++i) (small[i] ? s1 : s0) += windows[i];
+  part[0][t] = s0;
+  part[1][t] = s1;
   __syncthreads();
   if (t == 0) {
     int64_t run = 0;
-    for (int i = 0; i < (int)blockDim.x; ++i) { const int64_t v = part[i]; part[i] = run; run += v; }
-    *total = run;
+    for (int g = 0; g < 2; ++g) {
+      if (g == 1) total[1] = run;
+      for (int i = 0; i < (int)blockDim.x; ++i) { const int64_t v = part[g][i]; part[g][i] = run; run += v; }
+    }
+    total[0] = run;
   }
   __syncthreads();
-  int64_t run = part[t];
-  for (int i = a; i < b; ++i) { sd[i].win_base = run; run += windows[i]; }
+  int64_t r0 = part[0][t], r1 = part[1][t];
+  for (int i = a; i < b; ++i) {
+    if (small[i]) { sd[i].win_base = r1; r1 += windows[i]; }
+    else { sd[i].win_base = r0; r0 += windows[i]; }
+  }
 }
 
 // MinMaxLTTB: complete the point set R = [lo, preselection..., hi-1] and its
@@ -310,28 +321,21 @@ tsds_status launch_batch(const Server& S, Slot& sl, const std::vector<tsds_query
   const size_t off_q = 0, off_sd = off_q + sz_q, off_ljobs = off_sd + sz_s, off_pjobs = off_ljobs + sz_l;
   const size_t in_bytes = off_pjobs + sz_p;
   size_t o = up256(in_bytes);
-  const size_t off_win = o; o = up256(o + (size_t)count * 8 + 8);
+  const size_t off_win = o; o = up256(o + (size_t)count * 8 + 16);   // windows, total, large-bin windows
+  const size_t off_small = o; o = up256(o + (size_t)count);
   std::vector<size_t> off_edges(count), off_res(count), off_cnt(count), off_R(count), off_lt(count);
   int64_t max_nb = 0, win_ub = 0;
-  double wsum = 0.0, wbin = 0.0;   // bytes-weighted mean bin size (x ranges: the whole series as the estimate)
   for (int i = 0; i < count; ++i) {
     const int64_t nb = nb_of(qs[i]);
     max_nb = std::max(max_nb, nb);
     off_edges[i] = o; o = up256(o + (size_t)(nb + 1) * 8);
     off_res[i] = o;   o = up256(o + (size_t)nb * 16);
     win_ub += (ser[i].n * ys + window_bytes - 1) / window_bytes + 1;
-    const int64_t pts = qs[i].by_x ? ser[i].n
-                                   : std::max<int64_t>(0, std::min(qs[i].hi, ser[i].n) - std::max<int64_t>(qs[i].lo, 0));
-    if (nb > 0 && pts > 0) {
-      const double bytes = (double)pts * (double)ys;
-      wsum += bytes;
-      wbin += bytes * (bytes / (double)nb);
-    }
   }
   const size_t zero_begin = o;    // piece counters and the work counter start at zero
   for (int i = 0; i < count; ++i) { off_cnt[i] = o; o += (size_t)nb_of(qs[i]) * 4; }
   o = up256(o);
-  const size_t off_work = o; o = up256(o + sizeof(WorkCounters));
+  const size_t off_work = o; o = up256(o + 2 * sizeof(WorkCounters));   // one per launch of the split pass
   const size_t zero_end = o;
   const size_t off_map = o;   o = up256(o + (size_t)win_ub * 4);
   const size_t off_first = o; o = up256(o + (size_t)win_ub * sizeof(Piece));
@@ -449,27 +453,43 @@ tsds_status launch_batch(const Server& S, Slot& sl, const std::vector<tsds_query
   SV_CK(cudaMemsetAsync(base + zero_begin, 0, zero_end - zero_begin, st));
   SV_CK(cudaMemsetAsync(outbase, 0, words * 8, st));
   int64_t* windows = reinterpret_cast<int64_t*>(base + off_win);
-  int64_t* total_dev = windows + count;
+  int64_t* total_dev = windows + count;   // [all windows, large-bin windows]
+  int8_t* small = reinterpret_cast<int8_t*>(base + off_small);
+  const bool can_split = ys <= 4;         // the segmented kernel takes y of up to 32 bits
   note_launch();
-  k_resolve<<<(count + 7) / 8, 256, 0, st>>>(dq, dsd, windows, count, (int)S.x_dtype, (int)ys,
-                                             has_x ? (int)dtype_size(S.x_dtype) : 0, welems);
+  k_resolve<<<(count + 7) / 8, 256, 0, st>>>(dq, dsd, windows, small, count, (int)S.x_dtype, (int)ys,
+                                             has_x ? (int)dtype_size(S.x_dtype) : 0, welems,
+                                             can_split ? seg_max_bin_bytes(ys) : 0);
   SV_CK(cudaGetLastError());
   note_launch();
-  k_scan_windows<<<1, 1024, 0, st>>>(dsd, windows, count, total_dev);
+  k_scan_windows<<<1, 1024, 0, st>>>(dsd, windows, small, count, total_dev);
   SV_CK(cudaGetLastError());
   SV_CK(launch_window_map(dsd, count, reinterpret_cast<int32_t*>(base + off_map), S.y_dtype, st, window_bytes));
   SV_CK(launch_edges(dsd, count, nullptr, has_x, S.x_dtype, max_nb, st));
   SeriesDev none;
   memset(&none, 0, sizeof none);
-  StreamConfig cfg;
-  cfg.total_windows_dev = total_dev;
-  cfg.mean_bin_bytes = wsum > 0.0 ? (int64_t)(wbin / wsum) : 0;
   // a batch holds one NaN mode and either M4 or the MinMax-like algorithms (the admission groups them)
   const tsds_nan_mode nan = (tsds_nan_mode)qs[0].nan;
   const bool m4 = qs[0].algo == TSDS_ALGO_M4;
-  SV_CK(launch_argminmax(dsd, count, none, reinterpret_cast<const int32_t*>(base + off_map), std::max<int64_t>(win_ub, 1),
-                         reinterpret_cast<Piece*>(base + off_first), reinterpret_cast<Piece*>(base + off_last),
-                         reinterpret_cast<WorkCounters*>(base + off_work), S.y_dtype, nan, st, cfg));
+  // the streaming pass: register streaming over the large-bin queries' windows
+  // [0, total[1]), the segmented kernel over the small-bin ones [total[1], total[0])
+  // (ranges read on the device; an empty range is a launch with nothing to claim)
+  const int32_t* map = reinterpret_cast<const int32_t*>(base + off_map);
+  Piece* fp = reinterpret_cast<Piece*>(base + off_first);
+  Piece* lp = reinterpret_cast<Piece*>(base + off_last);
+  WorkCounters* work = reinterpret_cast<WorkCounters*>(base + off_work);
+  StreamConfig big;
+  big.variant = STREAM_LDG;
+  big.total_windows_dev = can_split ? total_dev + 1 : total_dev;
+  SV_CK(launch_argminmax(dsd, count, none, map, std::max<int64_t>(win_ub, 1), fp, lp, work, S.y_dtype, nan, st, big));
+  if (can_split) {
+    StreamConfig sm;
+    sm.variant = STREAM_SEG;
+    sm.total_windows_dev = total_dev;
+    sm.window_first_dev = total_dev + 1;
+    SV_CK(launch_argminmax(dsd, count, none, map, std::max<int64_t>(win_ub, 1), fp, lp, work + 1, S.y_dtype, nan, st,
+                           sm));
+  }
   SV_CK(launch_emit(dsd, count, none, m4 ? ALGO_M4 : ALGO_MINMAX, st));
   SV_CK(launch_iota_batched(dsd, count, st));
   if (nlt > 0) {
@@ -624,6 +644,25 @@ tsds_status tsds_server_create(tsds_server* out, const tsds_server_config* cfg, 
       return fail(TSDS_ECUDA, "tsds_server_create: stream creation failed");
     }
     S.slots.push_back(sl);
+    // pinned staging sized for a full batch of typical queries (it grows if a
+    // batch needs more), so the first batches do not pay for page-locking
+    const size_t in0 = (size_t)c.max_batch * 1024;
+    const size_t out0 = (size_t)c.max_batch * (4096 + kInfoSlots);
+    if (cudaMallocHost(&sl->pin_in, in0) == cudaSuccess) sl->pin_in_cap = in0;
+    else sl->pin_in = nullptr;
+    if (cudaMallocHost((void**)&sl->pin_out, out0 * 8) == cudaSuccess) sl->pin_out_cap = out0;
+    else sl->pin_out = nullptr;
+  }
+  {
+    // map the device-memory budget into the library's pool once (the pool
+    // keeps freed memory), so batches do not wait for the pool to grow
+    Scratch warm;
+    if (scratch_alloc(warm, (size_t)c.memory_budget, S.slots[0]->st) == cudaSuccess) {
+      cudaFreeAsync(warm.p, warm.st);
+      warm.p = nullptr;
+    }
+    cudaStreamSynchronize(S.slots[0]->st);
+    cudaGetLastError();
   }
   S.th = std::thread(server_loop, &S);
   *out = h;

@@ -119,10 +119,11 @@ __global__ void __launch_bounds__(kStreamThreadsLdg, MULTI ? 3 : 4)
 k_argminmax_ldg(const SeriesDev* __restrict__ sd, SeriesDev single, const int32_t* __restrict__ win_series,
             int64_t total_windows, Piece* __restrict__ first_piece, Piece* __restrict__ last_piece,
             WorkCounters* __restrict__ work, int64_t welems, const int64_t* __restrict__ total_dev,
-            int64_t w_first) {
+            int64_t w_first, const int64_t* __restrict__ first_dev) {
   using T = typename P::T;
   const int lane = threadIdx.x & 31;
   if (total_dev) total_windows = *total_dev;
+  if (first_dev) w_first = *first_dev;
   for (;;) {
     unsigned long long wu = 0;
     if (lane == 0) wu = atomicAdd(&work->next_window, 1ull);

@@ -263,7 +263,7 @@ __global__ void __launch_bounds__(kSegThreads)
 k_argminmax_seg(const SeriesDev* __restrict__ sd, SeriesDev single, const int32_t* __restrict__ win_series,
                 int64_t total_windows, Piece* __restrict__ first_piece, Piece* __restrict__ last_piece,
                 WorkCounters* __restrict__ work, int64_t welems, const int64_t* __restrict__ total_dev,
-            int64_t w_first) {
+            int64_t w_first, const int64_t* __restrict__ first_dev) {
   using T = typename P::T;
   static_assert(sizeof(T) <= 4, "the segmented pass packs 32-bit keys");
   constexpr int E = 16 / sizeof(T);   // elements per lane per sub-step
@@ -277,6 +277,7 @@ k_argminmax_seg(const SeriesDev* __restrict__ sd, SeriesDev single, const int32_
   uint8_t* tab = s_tab[warp];
   uint4* stage = &s_stage[warp][0][lane];   // slot d of this lane: stage[d * 32]
   if (total_dev) total_windows = *total_dev;
+  if (first_dev) w_first = *first_dev;
   for (;;) {
     unsigned long long wu = 0;
     if (lane == 0) wu = atomicAdd(&work->next_window, 1ull);
