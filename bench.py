@@ -369,6 +369,29 @@ def step_bytes(n, n_out=N_OUT, x_itemsize=8):
     return per
 
 
+def oracle_all_cores(oracle, x, y, n_out):
+    """The oracle's per-bin argmin/argmax (MinMax and M4 bins of the same sample) split over
+    the host's cores by contiguous bin ranges, one thread each (the C oracle releases the
+    GIL), as a second CPU line beside the single-threaded one."""
+    import concurrent.futures
+    cores = os.cpu_count() or 1
+    n = len(y)
+    t0 = time.perf_counter()
+    for algo in ALGOS:
+        nb = n_out // (2 if algo == "minmax" else 4)
+        edges = oracle.bin_edges(x, n, nb)
+
+        def work(b0, b1, edges=edges):
+            return [oracle.argminmax(y, int(edges[b]), int(edges[b + 1])) for b in range(b0, b1) if edges[b + 1] > edges[b]]
+        step = (nb + cores - 1) // cores
+        with concurrent.futures.ThreadPoolExecutor(cores) as ex:
+            list(ex.map(lambda b0: work(b0, min(b0 + step, nb)), range(0, nb, step)))
+    dt = time.perf_counter() - t0
+    return {"value": sum(step_bytes(n, n_out).values()) / dt / 1e9, "unit": "GB/s", "cores": cores,
+            "kind": "oracle per-bin argmin/argmax, bins split over threads",
+            "sample": f"the same {n} points, MinMax + M4 bins once each ({dt:.2f} s)"}
+
+
 def stream_kernel_name(n, n_out, forced):
     """The streaming kernel a float32 MinMax launch of this shape runs (the
     library's automatic rule: segmented below 1.5 KB mean bins)."""
@@ -643,6 +666,7 @@ def main():
         dt = time.perf_counter() - t0
         cpu = {"value": sum(step_bytes(ns, args.n_out).values()) / dt / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
                "sample": f"first {ns} points of the same series and x, MinMax + M4 once each ({dt:.1f} s)"}
+        cpu["all_cores"] = oracle_all_cores(oracle, xs, ys, args.n_out)
 
     # ---- output check of the timed results against each other (counts)
     counts = {a: int(cnts[a].item()) for a in ALGOS}
