@@ -292,13 +292,13 @@ tsds_status tsds_check_wait_timeout(unsigned rounds, void* stream);
 /* Kernel variant of the streaming argmin/argmax pass for every later call in
  * the process (no counterpart in the paper, whose CPU kernel has one form):
  *   0  automatic (the default): per launch, by the bytes-weighted mean bin
- *      size: variant 3 below 1.5 KB (4-byte y), 1 KB (2-byte) or 512 bytes
- *      (1-byte), variant 2 otherwise;
+ *      size: variant 3 below 768 bytes (8-byte y), 1.5 KB (4-byte), 1 KB
+ *      (2-byte) or 512 bytes (1-byte), variant 2 otherwise;
  *   1  shared-memory ring (bulk async copies into shared memory, one warp
  *      per bin);
  *   2  register streaming, one warp per bin;
- *   3  register streaming with bins split across lanes (y dtypes of up to
- *      32 bits; 64-bit dtypes run variant 2).
+ *   3  segmented: y staged through shared memory by per-lane async copies,
+ *      bins split across lanes.
  * The environment variable TSDS_STREAM_VARIANT=ring|ldg|seg sets 1, 2 or 3
  * when the library loads.  Results are identical; only speed differs.
  * Batched plans that were tuned keep the variant they chose.  Returns the

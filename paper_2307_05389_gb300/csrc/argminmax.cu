@@ -305,6 +305,16 @@ struct Pol64 {
     gmin = lo;
     gmax = hi;
   }
+  __device__ static void group1(const uint4& v, Acc& gmin, Acc& gmax) {
+    const uint64_t k0 = raw(((uint64_t)v.y << 32) | v.x), k1 = raw(((uint64_t)v.w << 32) | v.z);
+    if (KIND == 2 && (raw_key_is_nan(k0) || raw_key_is_nan(k1))) {
+      gmin = min(kmin_of(k0), kmin_of(k1));
+      gmax = max(kmax_of(k0), kmax_of(k1));
+    } else {
+      gmin = min(k0, k1);
+      gmax = max(k0, k1);
+    }
+  }
   __device__ static uint64_t bits(T e) {
     if constexpr (KIND == 2) {
       return f64_bits(e);   // opaque move: keeps the key arithmetic integer
@@ -785,7 +795,6 @@ static int variant_override() {
 int stream_variant_for(const StreamConfig& cfg, int64_t elem_bytes) {
   int v = cfg.variant != STREAM_AUTO ? cfg.variant : variant_override();
   if (v == STREAM_AUTO) v = cfg.mean_bin_bytes < seg_max_bin_bytes(elem_bytes) ? STREAM_SEG : STREAM_LDG;
-  if (v == STREAM_SEG && elem_bytes > 4) v = STREAM_LDG;   // 64-bit keys do not pack
   return v;
 }
 
@@ -831,9 +840,7 @@ static cudaError_t launch_pol(const SeriesDev* s_dev, int count, const SeriesDev
                : launch_var<P, NM, V, false>(s_dev, single, win_series, total_windows, fp, lp, work, cfg,   \
                                              sm_count, st)
   if (var == STREAM_LDG) TSDS_VAR(STREAM_LDG);
-  if constexpr (sizeof(typename P::T) <= 4) {
-    if (var == STREAM_SEG) TSDS_VAR(STREAM_SEG);
-  }
+  if (var == STREAM_SEG) TSDS_VAR(STREAM_SEG);
   TSDS_VAR(STREAM_RING);
 #undef TSDS_VAR
 }

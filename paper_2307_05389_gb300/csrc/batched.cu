@@ -134,7 +134,7 @@ static BatchLayout make_layout(tsds_algo algo, const tsds_series* s, int64_t cou
       const double bytes = (double)q.n * (double)dtype_size(y_dtype);
       wsum += bytes;
       wbin += bytes * (bytes / (double)d.nb);
-      L.small_bins[(size_t)i] = dtype_size(y_dtype) <= 4 && bytes / (double)d.nb < (double)seg_max_bin_bytes(dtype_size(y_dtype));
+      L.small_bins[(size_t)i] = bytes / (double)d.nb < (double)seg_max_bin_bytes(dtype_size(y_dtype));
     }
     L.y_bytes += q.n * dtype_size(y_dtype);
   }

@@ -60,14 +60,13 @@ inline int64_t window_elems(tsds_dtype y_dtype) { return kWindowBytes / dtype_si
 
 // Variants of the streaming pass: RING stages y through a shared-memory ring
 // filled by bulk async copies, LDG streams it through registers with one warp
-// per bin (cheapest per byte: large bins), SEG streams it through registers
-// and splits bins across lanes (cheapest per bin: small bins; dtypes of up to
-// 32 bits).  AUTO picks SEG when the bytes-weighted mean bin size is below
+// per bin (cheapest per byte: large bins), SEG stages it through per-lane
+// async copies and splits bins across lanes (cheapest per bin: small bins).  AUTO picks SEG when the bytes-weighted mean bin size is below
 // seg_max_bin_bytes(element size), LDG otherwise (crossovers measured on
 // GB300 over 1 GB and 40 MB inputs).
 enum StreamVariant : int { STREAM_AUTO = 0, STREAM_RING = 1, STREAM_LDG = 2, STREAM_SEG = 3 };
 inline int64_t seg_max_bin_bytes(int64_t elem_bytes) {
-  return elem_bytes >= 4 ? 1536 : elem_bytes == 2 ? 1024 : 512;
+  return elem_bytes == 8 ? 768 : elem_bytes == 4 ? 1536 : elem_bytes == 2 ? 1024 : 512;
 }
 
 // Launch shape of the streaming pass (the batched plans autotune it).

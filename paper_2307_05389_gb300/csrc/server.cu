@@ -455,7 +455,7 @@ tsds_status launch_batch(const Server& S, Slot& sl, const std::vector<tsds_query
   int64_t* windows = reinterpret_cast<int64_t*>(base + off_win);
   int64_t* total_dev = windows + count;   // [all windows, large-bin windows]
   int8_t* small = reinterpret_cast<int8_t*>(base + off_small);
-  const bool can_split = ys <= 4;         // the segmented kernel takes y of up to 32 bits
+  const bool can_split = true;
   note_launch();
   k_resolve<<<(count + 7) / 8, 256, 0, st>>>(dq, dsd, windows, small, count, (int)S.x_dtype, (int)ys,
                                              has_x ? (int)dtype_size(S.x_dtype) : 0, welems,

@@ -1,16 +1,16 @@
 // stream_seg.cuh -- the segmented variant of the per-bin argmin/argmax pass
-// (included by argminmax.cu after the policies and bin_result), for dtypes of
-// up to 32 bits and bins of a few hundred bytes to some KB.
+// (included by argminmax.cu after the policies and bin_result), for bins of a
+// few bytes to about a KB.
 //
 // The other variants give every bin to the whole warp: a bin costs a warp
 // reduction and a few dependent memory round trips, which dominate once bins
 // are small.  Here the warp streams its window in sub-steps of 512 bytes, one
 // 16-byte vector per lane, and the bins are handled by the lanes that hold
 // them:
-//  * every element becomes a 64-bit packed pair (32-bit ordered key, 32-bit
-//    offset in the window) for the minimum and (key, complemented offset) for
-//    the maximum, so one unsigned min/max keeps the smallest/largest value and
-//    the earliest index on ties;
+//  * every element becomes an (ordered key, offset in the window) pair for the
+//    minimum and (key, complemented offset) for the maximum, so the smallest /
+//    largest value with the earliest index wins; with 32-bit keys the pair is
+//    one packed 64-bit word and one unsigned min/max decides;
 //  * a sub-step without a bin boundary costs one packed group min/max per
 //    lane (value space, as in the other variants); a lane looks up the
 //    element index only when its extremum strictly improves, and the lanes
@@ -41,10 +41,18 @@ __device__ __forceinline__ void seg_wait() {
   asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-// 32-bit ordered keys of one element (minimum side, maximum side).
-template <class T, int NM>
-__device__ __forceinline__ void seg_keys(T v, uint32_t& kmn, uint32_t& kmx) {
-  if constexpr (std::is_same<T, float>::value || std::is_same<T, __half>::value) {
+// Ordered keys of one element (minimum side, maximum side): 32-bit for
+// dtypes of up to 32 bits, 64-bit for the 64-bit dtypes.
+template <class T, int NM, class K>
+__device__ __forceinline__ void seg_keys(T v, K& kmn, K& kmx) {
+  if constexpr (std::is_same<T, double>::value) {
+    const uint64_t k = f64_bits_key(f64_bits(v));
+    const bool nan = raw_key_is_nan(k);
+    kmn = nan ? nan_key_min<NM>() : k;
+    kmx = nan ? nan_key_max<NM>() : k;
+  } else if constexpr (sizeof(T) == 8) {
+    kmn = kmx = std::is_signed<T>::value ? ((uint64_t)v ^ kSign64) : (uint64_t)v;
+  } else if constexpr (std::is_same<T, float>::value || std::is_same<T, __half>::value) {
     float f;
     if constexpr (std::is_same<T, __half>::value) f = __half2float(v);
     else f = v;
@@ -61,35 +69,105 @@ __device__ __forceinline__ void seg_keys(T v, uint32_t& kmn, uint32_t& kmx) {
   }
 }
 
-// A running selection: mn = (key << 32 | offset), mx = (key << 32 | ~offset).
-struct SegRun {
+// A running selection (smallest key, earliest offset; largest key, earliest
+// offset).  With 32-bit keys it is two packed words, mn = (key << 32 |
+// offset) and mx = (key << 32 | ~offset), so one unsigned min/max decides;
+// with 64-bit keys the offsets ride beside the keys.
+template <int KB>
+struct SegRun;
+
+template <>
+struct SegRun<4> {
+  using Key = uint32_t;
   uint64_t mn, mx;
 };
-__device__ __forceinline__ void seg_empty(SegRun& r) {
+
+template <>
+struct SegRun<8> {
+  using Key = uint64_t;
+  uint64_t kmn, kmx;
+  uint32_t omn, omx;   // offset of the minimum; complemented offset of the maximum
+};
+
+__device__ __forceinline__ void seg_empty(SegRun<4>& r) {
   r.mn = ~0ull;
   r.mx = 0ull;
 }
-__device__ __forceinline__ void seg_add(SegRun& r, uint32_t kmn, uint32_t kmx, uint32_t rel) {
+__device__ __forceinline__ void seg_empty(SegRun<8>& r) {
+  r.kmn = ~0ull;
+  r.omn = 0xffffffffu;
+  r.kmx = 0ull;
+  r.omx = 0u;
+}
+__device__ __forceinline__ void seg_add(SegRun<4>& r, uint32_t kmn, uint32_t kmx, uint32_t rel) {
   const uint64_t a = ((uint64_t)kmn << 32) | rel;
   const uint64_t b = ((uint64_t)kmx << 32) | (0xffffffffu - rel);
   r.mn = a < r.mn ? a : r.mn;
   r.mx = b > r.mx ? b : r.mx;
 }
-__device__ __forceinline__ void seg_join(SegRun& r, const SegRun& o) {
+__device__ __forceinline__ void seg_add(SegRun<8>& r, uint64_t kmn, uint64_t kmx, uint32_t rel) {
+  if (kmn < r.kmn || (kmn == r.kmn && rel < r.omn)) { r.kmn = kmn; r.omn = rel; }
+  const uint32_t nrel = 0xffffffffu - rel;
+  if (kmx > r.kmx || (kmx == r.kmx && nrel > r.omx)) { r.kmx = kmx; r.omx = nrel; }
+}
+__device__ __forceinline__ void seg_join(SegRun<4>& r, const SegRun<4>& o) {
   r.mn = o.mn < r.mn ? o.mn : r.mn;
   r.mx = o.mx > r.mx ? o.mx : r.mx;
 }
-__device__ __forceinline__ void seg_warp_join(SegRun& r) {
+__device__ __forceinline__ void seg_join(SegRun<8>& r, const SegRun<8>& o) {
+  if (o.kmn < r.kmn || (o.kmn == r.kmn && o.omn < r.omn)) { r.kmn = o.kmn; r.omn = o.omn; }
+  if (o.kmx > r.kmx || (o.kmx == r.kmx && o.omx > r.omx)) { r.kmx = o.kmx; r.omx = o.omx; }
+}
+// Shuffles of a whole run.
+__device__ __forceinline__ SegRun<4> seg_shfl_xor(const SegRun<4>& r, int o) {
+  SegRun<4> t;
+  t.mn = __shfl_xor_sync(0xffffffffu, r.mn, o);
+  t.mx = __shfl_xor_sync(0xffffffffu, r.mx, o);
+  return t;
+}
+__device__ __forceinline__ SegRun<8> seg_shfl_xor(const SegRun<8>& r, int o) {
+  SegRun<8> t;
+  t.kmn = __shfl_xor_sync(0xffffffffu, r.kmn, o);
+  t.kmx = __shfl_xor_sync(0xffffffffu, r.kmx, o);
+  t.omn = __shfl_xor_sync(0xffffffffu, r.omn, o);
+  t.omx = __shfl_xor_sync(0xffffffffu, r.omx, o);
+  return t;
+}
+__device__ __forceinline__ SegRun<4> seg_shfl_up(const SegRun<4>& r, int d) {
+  SegRun<4> t;
+  t.mn = __shfl_up_sync(0xffffffffu, r.mn, d);
+  t.mx = __shfl_up_sync(0xffffffffu, r.mx, d);
+  return t;
+}
+__device__ __forceinline__ SegRun<8> seg_shfl_up(const SegRun<8>& r, int d) {
+  SegRun<8> t;
+  t.kmn = __shfl_up_sync(0xffffffffu, r.kmn, d);
+  t.kmx = __shfl_up_sync(0xffffffffu, r.kmx, d);
+  t.omn = __shfl_up_sync(0xffffffffu, r.omn, d);
+  t.omx = __shfl_up_sync(0xffffffffu, r.omx, d);
+  return t;
+}
+__device__ __forceinline__ SegRun<4> seg_shfl(const SegRun<4>& r, int src) {
+  SegRun<4> t;
+  t.mn = __shfl_sync(0xffffffffu, r.mn, src);
+  t.mx = __shfl_sync(0xffffffffu, r.mx, src);
+  return t;
+}
+__device__ __forceinline__ SegRun<8> seg_shfl(const SegRun<8>& r, int src) {
+  SegRun<8> t;
+  t.kmn = __shfl_sync(0xffffffffu, r.kmn, src);
+  t.kmx = __shfl_sync(0xffffffffu, r.kmx, src);
+  t.omn = __shfl_sync(0xffffffffu, r.omn, src);
+  t.omx = __shfl_sync(0xffffffffu, r.omx, src);
+  return t;
+}
+template <int KB>
+__device__ __forceinline__ void seg_warp_join(SegRun<KB>& r) {
 #pragma unroll
-  for (int o = 16; o; o >>= 1) {
-    SegRun t;
-    t.mn = __shfl_xor_sync(0xffffffffu, r.mn, o);
-    t.mx = __shfl_xor_sync(0xffffffffu, r.mx, o);
-    seg_join(r, t);
-  }
+  for (int o = 16; o; o >>= 1) seg_join(r, seg_shfl_xor(r, o));
 }
 // As an ordered-key candidate with series indices (offsets from ws).
-__device__ __forceinline__ Cand seg_cand(const SegRun& r, int64_t ws) {
+__device__ __forceinline__ Cand seg_cand(const SegRun<4>& r, int64_t ws) {
   Cand c;
   c.kmin = r.mn >> 32;
   c.imin = ws + (int64_t)(uint32_t)r.mn;
@@ -97,17 +175,31 @@ __device__ __forceinline__ Cand seg_cand(const SegRun& r, int64_t ws) {
   c.imax = ws + (int64_t)(0xffffffffu - (uint32_t)r.mx);
   return c;
 }
-__device__ __forceinline__ void seg_write(const SeriesDev& S, int64_t b, const SegRun& r, int64_t ws) {
-  S.res[2 * b] = ws + (int64_t)(uint32_t)r.mn;
-  S.res[2 * b + 1] = ws + (int64_t)(0xffffffffu - (uint32_t)r.mx);
+__device__ __forceinline__ Cand seg_cand(const SegRun<8>& r, int64_t ws) {
+  Cand c;
+  c.kmin = r.kmn;
+  c.imin = ws + (int64_t)r.omn;
+  c.kmax = r.kmx;
+  c.imax = ws + (int64_t)(0xffffffffu - r.omx);
+  return c;
+}
+template <int KB>
+__device__ __forceinline__ void seg_write(const SeriesDev& S, int64_t b, const SegRun<KB>& r, int64_t ws) {
+  const Cand c = seg_cand(r, ws);
+  S.res[2 * b] = c.imin;
+  S.res[2 * b + 1] = c.imax;
 }
 
 // The keys of a policy's running value (the value of one element).
-template <class P, int NM>
-__device__ __forceinline__ void seg_acc_keys(typename P::Acc a, uint32_t& kmn, uint32_t& kmx) {
-  if constexpr (P::kFloat) seg_keys<float, NM>((float)a, kmn, kmx);
+template <class P, int NM, class K>
+__device__ __forceinline__ void seg_acc_keys(typename P::Acc a, K& kmn, K& kmx) {
+  if constexpr (sizeof(typename P::T) == 8) kmn = kmx = a;   // the 64-bit policies keep ordered keys
+  else if constexpr (P::kFloat) seg_keys<float, NM>((float)a, kmn, kmx);
   else seg_keys<typename P::T, NM>((typename P::T)a, kmn, kmx);
 }
+
+template <class T>
+using SegRunFor = SegRun<sizeof(T) == 8 ? 8 : 4>;
 
 // Per-lane running extremum of the full sub-steps without a bin start, kept
 // in value space: one packed group reduction per vector, and the element
@@ -186,16 +278,28 @@ __device__ __forceinline__ void seg_lane_group4(SegLane<P>& L, const uint4 (&v)[
   L.valid = true;
 }
 
-template <class P, int NM>
-__device__ __forceinline__ void seg_lane_flush(SegLane<P>& L, SegRun& acc) {
+__device__ __forceinline__ SegRun<4> seg_pair(uint32_t kmn, uint32_t omn, uint32_t kmx, uint32_t omx) {
+  SegRun<4> r;
+  r.mn = ((uint64_t)kmn << 32) | omn;
+  r.mx = ((uint64_t)kmx << 32) | (0xffffffffu - omx);
+  return r;
+}
+__device__ __forceinline__ SegRun<8> seg_pair(uint64_t kmn, uint32_t omn, uint64_t kmx, uint32_t omx) {
+  SegRun<8> r;
+  r.kmn = kmn;
+  r.omn = omn;
+  r.kmx = kmx;
+  r.omx = 0xffffffffu - omx;
+  return r;
+}
+
+template <class P, int NM, int KB>
+__device__ __forceinline__ void seg_lane_flush(SegLane<P>& L, SegRun<KB>& acc) {
   if (L.valid) {
-    uint32_t kmn, kmx, t;
+    typename SegRun<KB>::Key kmn, kmx, t;
     seg_acc_keys<P, NM>(L.vmin, kmn, t);
     seg_acc_keys<P, NM>(L.vmax, t, kmx);
-    SegRun r;
-    r.mn = ((uint64_t)kmn << 32) | L.rmin;
-    r.mx = ((uint64_t)kmx << 32) | (0xffffffffu - L.rmax);
-    seg_join(acc, r);
+    seg_join(acc, seg_pair(kmn, L.rmin, kmx, L.rmax));
     L.valid = false;
   }
 }
@@ -241,8 +345,8 @@ __device__ __forceinline__ void seg_issue(uint4* slot, const T* __restrict__ y, 
 
 // A partial sub-step (the window's first or last) with no bin start: each
 // lane adds its elements in [o_lo, o_hi).
-template <class T, int NM>
-__device__ __forceinline__ void seg_lane_add(SegRun& acc, const uint4& v, int lane, int o_lo, int o_hi,
+template <class T, int NM, int KB>
+__device__ __forceinline__ void seg_lane_add(SegRun<KB>& acc, const uint4& v, int lane, int o_lo, int o_hi,
                                              uint32_t rel0) {
   constexpr int E = 16 / sizeof(T);
   T el[E];
@@ -251,7 +355,7 @@ __device__ __forceinline__ void seg_lane_add(SegRun& acc, const uint4& v, int la
 #pragma unroll
   for (int e = 0; e < E; ++e) {
     if (ob + e >= o_lo && ob + e < o_hi) {
-      uint32_t kmn, kmx;
+      typename SegRun<KB>::Key kmn, kmx;
       seg_keys<T, NM>(el[e], kmn, kmx);
       seg_add(acc, kmn, kmx, rel0 + (uint32_t)(ob + e));
     }
@@ -265,7 +369,8 @@ k_argminmax_seg(const SeriesDev* __restrict__ sd, SeriesDev single, const int32_
                 WorkCounters* __restrict__ work, int64_t welems, const int64_t* __restrict__ total_dev,
             int64_t w_first, const int64_t* __restrict__ first_dev) {
   using T = typename P::T;
-  static_assert(sizeof(T) <= 4, "the segmented pass packs 32-bit keys");
+  using Run = SegRunFor<T>;
+  using Key = typename Run::Key;
   constexpr int E = 16 / sizeof(T);   // elements per lane per sub-step
   constexpr int SUB = 32 * E;         // elements per sub-step
   constexpr unsigned FULL = 0xffffffffu;
@@ -314,7 +419,7 @@ k_argminmax_seg(const SeriesDev* __restrict__ sd, SeriesDev single, const int32_
     int64_t nxt = (eb + 32 + lane <= nb) ? __ldg(edges + eb + 32 + lane) : INT64_MAX;
     int ep = 0;                          // cur[ep..31] not yet passed
     int64_t cb = b0;                     // the open bin
-    SegRun carry, acc, fpart;            // open bin before the sub-step (uniform); lanes' open-bin
+    Run carry, acc, fpart;               // open bin before the sub-step (uniform); lanes' open-bin
     seg_empty(carry);                    // pairs since the last boundary; b0's part when it began
     seg_empty(acc);                      // before ws and closes in this window (uniform)
     seg_empty(fpart);
@@ -387,7 +492,7 @@ k_argminmax_seg(const SeriesDev* __restrict__ sd, SeriesDev single, const int32_
           __syncwarp();
           const uint32_t my = mask[lane];
 
-          SegRun run, head;
+          Run run, head;
           seg_empty(run);
           seg_empty(head);
           bool hv = false, ropen = false;
@@ -403,7 +508,7 @@ k_argminmax_seg(const SeriesDev* __restrict__ sd, SeriesDev single, const int32_
               seg_empty(run);
             }
             if (o >= r_lo && o < r_hi) {
-              uint32_t kmn, kmx;
+              Key kmn, kmx;
               seg_keys<T, NM>(el[e], kmn, kmx);
               seg_add(run, kmn, kmx, rel0 + (uint32_t)o);
             }
@@ -411,7 +516,7 @@ k_argminmax_seg(const SeriesDev* __restrict__ sd, SeriesDev single, const int32_
 
           // segmented inclusive scan of the lanes' open runs (a lane that
           // opened a bin starts a segment; lane 0 continues the carry)
-          SegRun sc = run;
+          Run sc = run;
           int64_t sb = ropen ? rb : cb;
           bool f = ropen;
           if (lane == 0 && !f) {
@@ -420,9 +525,7 @@ k_argminmax_seg(const SeriesDev* __restrict__ sd, SeriesDev single, const int32_
           }
 #pragma unroll
           for (int d = 1; d < 32; d <<= 1) {
-            SegRun o;
-            o.mn = __shfl_up_sync(FULL, sc.mn, d);
-            o.mx = __shfl_up_sync(FULL, sc.mx, d);
+            const Run o = seg_shfl_up(sc, d);
             const int64_t ob = __shfl_up_sync(FULL, sb, d);
             const int of = __shfl_up_sync(FULL, (int)f, d);
             if (lane >= d) {
@@ -434,9 +537,7 @@ k_argminmax_seg(const SeriesDev* __restrict__ sd, SeriesDev single, const int32_
             }
           }
           // a lane's head joins everything before it in its bin
-          SegRun pv;
-          pv.mn = __shfl_up_sync(FULL, sc.mn, 1);
-          pv.mx = __shfl_up_sync(FULL, sc.mx, 1);
+          Run pv = seg_shfl_up(sc, 1);
           int64_t pb = __shfl_up_sync(FULL, sb, 1);
           if (lane == 0) {
             pv = carry;
@@ -451,12 +552,10 @@ k_argminmax_seg(const SeriesDev* __restrict__ sd, SeriesDev single, const int32_
           const unsigned fb = __ballot_sync(FULL, is_first);
           if (fb) {
             const int src = __ffs(fb) - 1;
-            fpart.mn = __shfl_sync(FULL, head.mn, src);
-            fpart.mx = __shfl_sync(FULL, head.mx, src);
+            fpart = seg_shfl(head, src);
             fset = true;
           }
-          carry.mn = __shfl_sync(FULL, sc.mn, 31);
-          carry.mx = __shfl_sync(FULL, sc.mx, 31);
+          carry = seg_shfl(sc, 31);
           cb = __shfl_sync(FULL, sb, 31);
 
           if (r_hi < o_hi) {

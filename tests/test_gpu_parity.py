@@ -259,8 +259,7 @@ def stream_variant():
 @pytest.mark.parametrize("dtype", ALL_DTYPES)
 def test_each_stream_variant(variant, dtype, stream_variant):
     """Each variant on its own over bins far below and far above the automatic
-    threshold, with ties, unaligned starts and both NaN modes (64-bit dtypes
-    run the register-streaming variant when the segmented one is asked for)."""
+    threshold, with ties, unaligned starts and both NaN modes."""
     stream_variant(variant)
     n = 700_001 if np.dtype(dtype).itemsize <= 2 else 260_003
     for kind in ("walk", "ties"):
@@ -281,7 +280,7 @@ def test_each_variant_with_x_and_lttb_preselection(variant, stream_variant):
         check("minmaxlttb", x, y, n_out, "propagate", 4)
 
 
-@pytest.mark.parametrize("dtype", ["float32", "int8", "uint16", "float16", "int32"])
+@pytest.mark.parametrize("dtype", ["float32", "int8", "uint16", "float16", "int32", "float64", "int64", "uint64"])
 @pytest.mark.parametrize("nan", ["propagate", "ignore"])
 def test_segmented_tiny_and_mixed_bins(dtype, nan, stream_variant):
     """The segmented variant where bins are one to a few elements (many bin
