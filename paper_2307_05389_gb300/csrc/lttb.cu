@@ -19,9 +19,7 @@
 //  * Small buckets (at most 32 points, the MinMaxLTTB case): the pick of
 //    bucket j depends on the chain only through which point a of bucket j-1
 //    was picked.  A transition table best[j][a] is filled for every bucket in
-//    parallel (one warp per bucket, exact binary64 areas), and the chain
-//    becomes a walk through the table that one warp does from registers,
-//    with the next rows loaded ahead.
+//    parallel (one warp per bucket, exact binary64 areas).
 //  * Larger buckets: the pick of bucket j is the largest |linear form| of its
 //    points, which a vertex of the bucket's convex hull attains, so the
 //    picks that can feed bucket j+1 are few (a random walk's hull has about
@@ -288,37 +286,7 @@ __global__ void k_table(const LttbJob* __restrict__ jobs) {
   }
 }
 
-// Starts of the buckets one lane writes out: lane l owns steps l, l+32,
-// l+64, ...; start(j) = 1 + floor(j(m-2)/B) advances by 32 steps with one
-// add and a carry (q32, r32: quotient and remainder of 32(m-2) by B).
-struct LaneStarts {
-  int64_t j, lo, rem, q32, r32, B;
-  __device__ void init(int64_t j0, int64_t m, int64_t B_) {
-    B = B_;
-    j = j0;
-    const u128 t = (u128)j0 * (u128)(m - 2);
-    lo = 1 + (int64_t)(t / (u128)B_);
-    rem = (int64_t)(t % (u128)B_);
-    const u128 t32 = (u128)32 * (u128)(m - 2);
-    q32 = (int64_t)(t32 / (u128)B_);
-    r32 = (int64_t)(t32 % (u128)B_);
-  }
-  __device__ void advance() {
-    j += 32;
-    lo += q32;
-    rem += r32;
-    if (rem >= B) { rem -= B; ++lo; }
-  }
-};
-
-// One warp walks the table.  The chain is one shared-memory read per bucket:
-// the slot of bucket j's pick is row j's entry at the slot of bucket j-1's
-// pick.  Rows come in blocks of 32 through a ring of four blocks in shared
-// memory (cp.async, three blocks in flight); lane s keeps the slot of step s
-// of a block, and the block's picks are written together afterwards.
-constexpr int kBlk = 32;
-constexpr int kChaseRing = 4;
-
+// Jobs whose points are all kept return every index.
 __global__ void __launch_bounds__(32) k_chase(const LttbJob* __restrict__ jobs) {
   const LttbJob J = jobs[blockIdx.x];
   const int lane = threadIdx.x & 31;
@@ -326,44 +294,6 @@ __global__ void __launch_bounds__(32) k_chase(const LttbJob* __restrict__ jobs) 
   if (m <= B + 2) {
     for (int64_t i = lane; i < m; i += 32) J.out[i] = out_index(J, i);
     if (lane == 0) *J.out_count = m;
-    return;
-  }
-  if (J.mode != 0) return;
-  __shared__ int32_t ring[kChaseRing][kBlk * kTableMaxK];
-  const int64_t K = J.K;
-  const int64_t nblk = (B + kBlk - 1) / kBlk;
-  auto issue = [&](int64_t b) {
-    if (b < nblk) {
-      const int64_t base = b * kBlk * K;
-      const int64_t n = min((int64_t)kBlk, B - b * kBlk) * K;
-      int32_t* dst = ring[b % kChaseRing];
-      for (int64_t i = lane; i < n; i += 32) cp_async4(dst + i, J.table + base + i);
-    }
-    cp_async_commit();
-  };
-  for (int b = 0; b < kChaseRing - 1; ++b) issue(b);
-  LaneStarts ls;
-  ls.init(lane, m, B);
-  if (lane == 0) J.out[0] = out_index(J, 0);
-  int32_t rel = 0;   // slot of the previous pick (point 0 for bucket 0)
-  for (int64_t b = 0; b < nblk; ++b) {
-    issue(b + kChaseRing - 1);
-    cp_async_wait<kChaseRing - 1>();
-    __syncwarp();
-    const int32_t* row = ring[b % kChaseRing];
-    const int n = (int)min((int64_t)kBlk, B - b * kBlk);
-    int32_t mine = 0;
-    for (int t = 0; t < n; ++t) {
-      rel = row[t * K + rel];
-      if (lane == t) mine = rel;
-    }
-    if (ls.j < B) J.out[ls.j + 1] = out_index(J, ls.lo + mine);
-    ls.advance();
-    __syncwarp();
-  }
-  if (lane == 0) {
-    J.out[B + 1] = out_index(J, m - 1);
-    *J.out_count = B + 2;
   }
 }
 
@@ -582,7 +512,10 @@ __global__ void __launch_bounds__(kTableWarps * 32) k_htable(const LttbJob* __re
       int32_t r;
       if (j == 0) r = s == 0 ? 0 : -1;
       else r = J.cand[j * kCandMax + s];
-      if (r < 0) continue;   // uniform per warp
+      if (r < 0) {   // uniform per warp
+        if (lane == 0) J.fslot[j * kCandMax + s] = -1;
+        continue;
+      }
       const int64_t a = alo + r;
       const double xa = J.px[a], ya = J.py[a];
       const double dxm = __dsub_rn(xa, xm), dym = __dsub_rn(ym, ya);
@@ -624,75 +557,152 @@ __global__ void __launch_bounds__(kTableWarps * 32) k_htable(const LttbJob* __re
           amax_merge(bk, bi, area_key(exact_area(xa, ya, dxm, dym, J.px[b], J.py[b]), J.nan), b);
       }
       amax_warp(bk, bi);
-      if (lane == 0) J.table[j * kCandMax + s] = (int32_t)((bk == 0ull ? lo : bi) - lo);
+      const int32_t rel = (int32_t)((bk == 0ull ? lo : bi) - lo);
+      // its slot among the next step's inputs (this bucket's candidates, row j+1)
+      const unsigned hit = __ballot_sync(0xffffffffu, own == rel);
+      if (lane == 0) {
+        J.table[j * kCandMax + s] = rel;
+        J.fslot[j * kCandMax + s] = hit ? __ffs(hit) - 1 : -1;
+      }
     }
   }
 }
 
-// One warp walks the candidate tables: per block of 32 buckets, candidate rows
-// and table rows come through rings of four blocks in shared memory (16-byte
-// cp.async, three blocks in flight).  A step is a ballot for the previous
-// pick's slot among the candidates and one shared-memory read of the table
-// entry; a previous pick that is not a candidate costs the exact warp search.
-__global__ void __launch_bounds__(32) k_hchase(const LttbJob* __restrict__ jobs) {
+// ---------------------------------------------------------------- the chain
+//
+// With the tables in place the chain is a composition of small functions:
+// step j maps the slot of the previous pick (its place among step j's
+// inputs: the points of bucket j-1 in table mode, its candidates in
+// hull-table mode) to the slot of its own pick among step j+1's inputs
+// (fslot), and emits the pick (table).  Functions compose associatively, so
+// the B steps are cut into segments of 32: one warp per segment follows all
+// 32 possible input slots through its segment at once (k_compose), one warp
+// then chains the segments, 32 steps per lookup (k_chain_seg), and one warp
+// per segment replays its segment from the known input to write the picks
+// (k_replay).  A path that leaves the tables (a previous pick that is not a
+// candidate) marks its segment, and k_chain_seg walks such a segment step by
+// step with the exact warp search.
+constexpr int kSeg = 32;
+constexpr int kSegWarpsC = 8;
+constexpr int kBlk = 32;          // segments per block of the chain's shared-memory ring
+constexpr int kChaseRing = 4;     // blocks in the ring (three in flight)
+
+__device__ __forceinline__ int job_width(const LttbJob& J) { return J.mode == 0 ? (int)J.K : kCandMax; }
+
+__global__ void __launch_bounds__(kSegWarpsC * 32) k_compose(const LttbJob* __restrict__ jobs) {
+  const LttbJob J = jobs[blockIdx.y];
+  const int64_t m = job_m(J), B = J.B;
+  if (m <= B + 2) return;
+  __shared__ int32_t rows[kSegWarpsC][kSeg][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int W = job_width(J);
+  const int64_t nseg = (B + kSeg - 1) / kSeg;
+  for (int64_t seg = (int64_t)blockIdx.x * kSegWarpsC + w; seg < nseg; seg += (int64_t)gridDim.x * kSegWarpsC) {
+    const int64_t j0 = seg * kSeg;
+    const int len = (int)min((int64_t)kSeg, B - j0);
+    for (int t = 0; t < len; ++t) rows[w][t][lane] = lane < W ? J.fslot[(j0 + t) * W + lane] : -1;
+    __syncwarp();
+    int32_t cur = lane;
+    for (int t = 0; t < len; ++t) {
+      if (j0 + t == B - 1) break;   // the last step's slot feeds nothing
+      cur = (cur >= 0 && cur < W) ? rows[w][t][cur] : -1;
+    }
+    J.comp[seg * kSeg + lane] = cur;
+    __syncwarp();
+  }
+}
+
+// The slot of point `rel` of bucket j among step j+1's inputs (-1: none).
+__device__ __forceinline__ int32_t next_slot(const LttbJob& J, int64_t j, int32_t rel, int lane) {
+  if (J.mode == 0) return rel;
+  const unsigned hit = __ballot_sync(0xffffffffu, J.cand[(j + 1) * kCandMax + lane] == rel);
+  return hit ? __ffs(hit) - 1 : -1;
+}
+
+__global__ void __launch_bounds__(32) k_chain_seg(const LttbJob* __restrict__ jobs) {
   const LttbJob J = jobs[blockIdx.x];
-  if (J.mode != 2) return;
   const int lane = threadIdx.x & 31;
   const int64_t m = job_m(J), B = J.B;
-  if (m <= B + 2) return;   // k_chase wrote every index
-  __shared__ __align__(16) int32_t cring[kChaseRing][kBlk * kCandMax];
-  __shared__ __align__(16) int32_t tring[kChaseRing][kBlk * kCandMax];
-  const int64_t nblk = (B + kBlk - 1) / kBlk;
+  if (m <= B + 2) return;
+  __shared__ __align__(16) int32_t ring[kChaseRing][kBlk * kSeg];
+  const int W = job_width(J);
+  const int64_t nseg = (B + kSeg - 1) / kSeg;
+  const int64_t nblk = (nseg + kBlk - 1) / kBlk;
   auto issue = [&](int64_t b) {
     if (b < nblk) {
-      const int64_t rows = min((int64_t)kBlk, B - b * kBlk);
-      const int64_t n16 = rows * kCandMax / 4;   // 16-byte pieces
-      const int r = (int)(b % kChaseRing);
-      for (int64_t i = lane; i < n16; i += 32) {
-        cp_async16(&cring[r][4 * i], J.cand + b * kBlk * kCandMax + 4 * i);
-        cp_async16(&tring[r][4 * i], J.table + b * kBlk * kCandMax + 4 * i);
-      }
+      const int64_t n16 = min((int64_t)kBlk, nseg - b * kBlk) * kSeg / 4;
+      for (int64_t i = lane; i < n16; i += 32)
+        cp_async16(&ring[b % kChaseRing][4 * i], J.comp + b * kBlk * kSeg + 4 * i);
     }
     cp_async_commit();
   };
   for (int b = 0; b < kChaseRing - 1; ++b) issue(b);
-  LaneStarts ls;
-  ls.init(lane, m, B);
   if (lane == 0) J.out[0] = out_index(J, 0);
-  int32_t rel = 0;
+  int32_t s = 0;        // input slot of the current segment (-1: the previous pick is not a table input)
+  int64_t a = 0;        // the previous pick, when s < 0
   for (int64_t b = 0; b < nblk; ++b) {
     issue(b + kChaseRing - 1);
     cp_async_wait<kChaseRing - 1>();
     __syncwarp();
-    const int r = (int)(b % kChaseRing);
-    const int n = (int)min((int64_t)kBlk, B - b * kBlk);
-    int32_t mine = 0;
-    int32_t cnext = cring[r][lane];
+    const int n = (int)min((int64_t)kBlk, nseg - b * kBlk);
     for (int t = 0; t < n; ++t) {
-      const int64_t j = b * kBlk + t;
-      const int32_t cand_t = cnext;
-      if (t + 1 < n) cnext = cring[r][(t + 1) * kCandMax + lane];   // off the chain
-      int slot = 0;
-      if (j > 0) {
-        const unsigned hit = __ballot_sync(0xffffffffu, cand_t == rel);
-        slot = hit ? __ffs(hit) - 1 : -1;
+      const int64_t seg = b * kBlk + t;
+      const int32_t nxt = s >= 0 ? ring[b % kChaseRing][t * kSeg + s] : -1;
+      if (nxt >= 0) {
+        if (lane == 0) J.seg_start[seg] = s;
+        s = nxt;
+        continue;
       }
-      if (slot >= 0) {
-        rel = tring[r][t * kCandMax + slot];
-      } else {
-        const int64_t lo = bucket_start(j, m, B);
-        const int64_t a = bucket_start(j - 1, m, B) + rel;
-        rel = (int32_t)(warp_pick(J, j, lo, bucket_start(j + 1, m, B), a, m, B, lane) - lo);
+      // the path leaves the tables inside this segment: walk it here
+      if (lane == 0) J.seg_start[seg] = -1;
+      const int64_t j0 = seg * kSeg, j1 = min(j0 + kSeg, B);
+      int64_t lo = bucket_start(j0, m, B);
+      for (int64_t j = j0; j < j1; ++j) {
+        const int64_t hi = bucket_start(j + 1, m, B);
+        int32_t rel;
+        if (s >= 0) rel = J.table[j * W + s];
+        else rel = (int32_t)(warp_pick(J, j, lo, hi, a, m, B, lane) - lo);
+        if (lane == 0) J.out[j + 1] = out_index(J, lo + rel);
+        a = lo + rel;
+        s = j + 1 < B ? next_slot(J, j, rel, lane) : 0;
+        lo = hi;
       }
-      if (lane == t) mine = rel;
     }
-    if (ls.j < B) J.out[ls.j + 1] = out_index(J, ls.lo + mine);
-    ls.advance();
     __syncwarp();
   }
   if (lane == 0) {
     J.out[B + 1] = out_index(J, m - 1);
     *J.out_count = B + 2;
+  }
+}
+
+__global__ void __launch_bounds__(kSegWarpsC * 32) k_replay(const LttbJob* __restrict__ jobs) {
+  const LttbJob J = jobs[blockIdx.y];
+  const int64_t m = job_m(J), B = J.B;
+  if (m <= B + 2) return;
+  __shared__ int32_t pr[kSegWarpsC][kSeg][32], fr[kSegWarpsC][kSeg][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int W = job_width(J);
+  const int64_t nseg = (B + kSeg - 1) / kSeg;
+  for (int64_t seg = (int64_t)blockIdx.x * kSegWarpsC + w; seg < nseg; seg += (int64_t)gridDim.x * kSegWarpsC) {
+    int32_t s = J.seg_start[seg];
+    if (s < 0) continue;   // written by k_chain_seg
+    const int64_t j0 = seg * kSeg;
+    const int len = (int)min((int64_t)kSeg, B - j0);
+    for (int t = 0; t < len; ++t) {
+      pr[w][t][lane] = lane < W ? J.table[(j0 + t) * W + lane] : 0;
+      fr[w][t][lane] = lane < W ? J.fslot[(j0 + t) * W + lane] : 0;
+    }
+    __syncwarp();
+    int32_t mine = 0;
+    for (int t = 0; t < len; ++t) {
+      const int32_t rel = pr[w][t][s];
+      if (lane == t) mine = rel;
+      s = fr[w][t][s];
+      s = (s >= 0 && s < W) ? s : 0;   // only the last step's slot can be outside the table
+    }
+    if (lane < len) J.out[j0 + lane + 1] = out_index(J, bucket_start(j0 + lane, m, B) + mine);
+    __syncwarp();
   }
 }
 
@@ -724,23 +734,31 @@ static unsigned grid_for(int64_t n, int per_sm = 8) {
 }
 
 size_t lttb_job_scratch(int64_t m_max, int64_t B, int64_t K) {
+  const int64_t nseg = (B + kSeg - 1) / kSeg;
   size_t s = align_up((size_t)(B + 1) * sizeof(double2), 256);
+  s += align_up((size_t)nseg * kSeg * 4, 256) + align_up((size_t)nseg * 4, 256);   // comp, seg_start
   if (lttb_mode(K) == 0) {
     s += align_up((size_t)B * (size_t)K * 4, 256);
   } else {
     s += align_up((size_t)m_max * sizeof(float2), 256);           // p32
     s += align_up((size_t)(B + 1) * kCandMax * 4, 256);           // candidate rows 0..B
-    s += align_up((size_t)B * kCandMax * 4, 256);                 // table
+    s += 2 * align_up((size_t)B * kCandMax * 4, 256);             // table, fslot
   }
   return s;
 }
 
 void lttb_job_bind(LttbJob& J, char* p, int64_t m_max) {
   J.mode = lttb_mode(J.K);
+  const int64_t nseg = (J.B + kSeg - 1) / kSeg;
   J.means = reinterpret_cast<double2*>(p);
   p += align_up((size_t)(J.B + 1) * sizeof(double2), 256);
+  J.comp = reinterpret_cast<int32_t*>(p);
+  p += align_up((size_t)nseg * kSeg * 4, 256);
+  J.seg_start = reinterpret_cast<int32_t*>(p);
+  p += align_up((size_t)nseg * 4, 256);
   if (J.mode == 0) {
     J.table = reinterpret_cast<int32_t*>(p);
+    J.fslot = J.table;
     return;
   }
   J.p32 = reinterpret_cast<float2*>(p);
@@ -748,6 +766,8 @@ void lttb_job_bind(LttbJob& J, char* p, int64_t m_max) {
   J.cand = reinterpret_cast<int32_t*>(p);
   p += align_up((size_t)(J.B + 1) * kCandMax * 4, 256);
   J.table = reinterpret_cast<int32_t*>(p);
+  p += align_up((size_t)J.B * kCandMax * 4, 256);
+  J.fslot = reinterpret_cast<int32_t*>(p);
 }
 
 tsds_status launch_points_jobs(const PointsJob* jobs_dev, int count, int64_t max_m, cudaStream_t st) {
@@ -802,8 +822,20 @@ tsds_status run_lttb_jobs(const LttbJob* jobs_host, const LttbJob* jobs_dev, int
     note_launch();
     k_htable<<<dim3((unsigned)tb, (unsigned)count), kTableWarps * 32, tsmem, st>>>(jobs_dev);
     TSDS_CK(cudaGetLastError());
+  }
+  {
+    const int64_t nseg = (max_B + kSeg - 1) / kSeg;
+    int64_t cb = (nseg + kSegWarpsC - 1) / kSegWarpsC;
+    if (cb > cap) cb = cap;
+    if (cb < 1) cb = 1;
     note_launch();
-    k_hchase<<<(unsigned)count, 32, 0, st>>>(jobs_dev);
+    k_compose<<<dim3((unsigned)cb, (unsigned)count), kSegWarpsC * 32, 0, st>>>(jobs_dev);
+    TSDS_CK(cudaGetLastError());
+    note_launch();
+    k_chain_seg<<<(unsigned)count, 32, 0, st>>>(jobs_dev);
+    TSDS_CK(cudaGetLastError());
+    note_launch();
+    k_replay<<<dim3((unsigned)cb, (unsigned)count), kSegWarpsC * 32, 0, st>>>(jobs_dev);
     TSDS_CK(cudaGetLastError());
   }
   return TSDS_OK;

@@ -35,6 +35,9 @@ struct LttbJob {
   int32_t* table;        // mode 0: B*K picks; mode 2: B*kLttbCandMax picks (relative to the bucket start)
   float2* p32;           // mode 2: m points relative to their bucket's first point, in FP32
   int32_t* cand;         // mode 2: B*kLttbCandMax candidate picks per bucket (relative, -1: none)
+  int32_t* fslot;        // slot of the pick among the next step's inputs (mode 0: the table itself)
+  int32_t* comp;         // per segment of 32 steps and input slot: the slot after the segment (-1: leaves the table)
+  int32_t* seg_start;    // per segment: its input slot, or -1 when the chain was replayed there directly
   int64_t* out;
   int64_t* out_count;
 };
