@@ -149,12 +149,13 @@ static tsds_status check_common(const void* x, int x_dtype, const void* y, int y
 
 // Scratch layout of one binned call.
 struct BinnedLayout {
-  size_t edges, res, cnt, work, first, last, total, zero_begin, zero_bytes;
+  size_t edges, res, cnt, work, first, last, tiles, total, zero_begin, zero_bytes;
 };
 
 static BinnedLayout binned_layout(int64_t nb, int64_t windows) {
   BinnedLayout L;
   size_t o = 0;
+  L.tiles = o; o = align_up(o + (size_t)(nb >= kEmitTiledMinBins ? emit_tiles(nb) : 0) * 8, 256);
   L.edges = o; o = align_up(o + (size_t)(nb + 1) * 8, 256);
   L.res = o;   o = align_up(o + (size_t)nb * 16, 256);
   L.cnt = o;   o = align_up(o + (size_t)nb * 4, 256);
@@ -211,7 +212,8 @@ tsds_status run_binned_series(const void* x, tsds_dtype x_dtype, const void* y, 
                            reinterpret_cast<Piece*>(base + L.last), reinterpret_cast<WorkCounters*>(base + L.work),
                            y_dtype, nan, st, cfg));
   timing_end(st, tok);
-  TSDS_CK(launch_emit(nullptr, 1, S, algo, st));
+  if (nb >= kEmitTiledMinBins) TSDS_CK(launch_emit_tiled(S, algo, reinterpret_cast<int64_t*>(base + L.tiles), st));
+  else TSDS_CK(launch_emit(nullptr, 1, S, algo, st));
   return TSDS_OK;
 }
 

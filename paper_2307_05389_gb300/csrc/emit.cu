@@ -6,7 +6,8 @@
 // strictly increasing.  Empty bins (possible with gaps in x) emit nothing,
 // which is why fewer than n_out indices can come back (Section 2.3 footnote).
 // One CTA per series: per-thread runs of bins, a block-wide exclusive scan of
-// their counts, then a second pass that writes.
+// their counts, then a second pass that writes.  A single series with many
+// bins takes the tiled form below (many CTAs).
 #include "device.cuh"
 #include "internal.h"
 
@@ -82,6 +83,104 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit(const SeriesDev* __restri
     off += k;
   }
   if (tid == 0 && S.out_count) *S.out_count = total_sh;
+}
+
+// Many bins in one series: tiles of kTileBins bins, one CTA each.  Pass 1
+// counts every tile's selections; pass 2 adds the counts of the tiles before
+// its own (at most a few thousand) to place the tile, scans within it and
+// writes.  The last tile also writes the total.
+constexpr int kTileThreads = 256;
+constexpr int kTileItems = 4;
+constexpr int64_t kTileBins = kTileThreads * kTileItems;
+
+template <int ALGO>
+__device__ __forceinline__ int64_t tile_thread_count(const SeriesDev& S, int64_t b0, int64_t b1) {
+  int64_t v[4], c = 0;
+  for (int64_t b = b0; b < b1; ++b) c += bin_select<ALGO>(S, b, v);
+  return c;
+}
+
+// Block-wide exclusive scan of one value per thread (kTileThreads); returns
+// the thread's prefix and sets *total.
+__device__ __forceinline__ int64_t tile_scan(int64_t x, int64_t* warp_tot, int64_t* total) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  int64_t incl = x;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int64_t t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  if (lane == 31) warp_tot[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    const int nw = kTileThreads / 32;
+    const int64_t wv = lane < nw ? warp_tot[lane] : 0;
+    int64_t wi = wv;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int64_t t = __shfl_up_sync(0xffffffffu, wi, o);
+      if (lane >= o) wi += t;
+    }
+    if (lane < nw) warp_tot[lane] = wi - wv;
+    if (lane == nw - 1) *total = wi;
+  }
+  __syncthreads();
+  return warp_tot[warp] + incl - x;
+}
+
+template <int ALGO>
+__global__ void __launch_bounds__(kTileThreads) k_emit_count(SeriesDev S, int64_t* __restrict__ tile_count) {
+  __shared__ int64_t warp_tot[kTileThreads / 32];
+  __shared__ int64_t total;
+  const int64_t b0 = (int64_t)blockIdx.x * kTileBins + (int64_t)threadIdx.x * kTileItems;
+  const int64_t c = tile_thread_count<ALGO>(S, min(b0, S.nb), min(b0 + kTileItems, S.nb));
+  tile_scan(c, warp_tot, &total);
+  if (threadIdx.x == 0) tile_count[blockIdx.x] = total;
+}
+
+template <int ALGO>
+__global__ void __launch_bounds__(kTileThreads) k_emit_write(SeriesDev S, const int64_t* __restrict__ tile_count) {
+  __shared__ int64_t warp_tot[kTileThreads / 32];
+  __shared__ int64_t total, before_sh;
+  if (S.status && *S.status) {
+    if (blockIdx.x == 0 && threadIdx.x == 0 && S.out_count) *S.out_count = -(int64_t)*S.status;
+    return;
+  }
+  // selections of the tiles before this one
+  int64_t before = 0;
+  for (int64_t t = threadIdx.x; t < blockIdx.x; t += kTileThreads) before += tile_count[t];
+  const int64_t b_off = tile_scan(before, warp_tot, &total);
+  (void)b_off;
+  if (threadIdx.x == 0) before_sh = total;
+  __syncthreads();
+  const int64_t base = before_sh;
+  const int64_t b0 = min((int64_t)blockIdx.x * kTileBins + (int64_t)threadIdx.x * kTileItems, S.nb);
+  const int64_t b1 = min(b0 + kTileItems, S.nb);
+  const int64_t c = tile_thread_count<ALGO>(S, b0, b1);
+  int64_t off = base + tile_scan(c, warp_tot, &total);
+  int64_t v[4];
+  for (int64_t b = b0; b < b1; ++b) {
+    const int k = bin_select<ALGO>(S, b, v);
+    for (int i = 0; i < k; ++i) S.out[off + i] = v[i] + S.idx_bias;
+    off += k;
+  }
+  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0 && S.out_count) *S.out_count = base + total;
+}
+
+int64_t emit_tiles(int64_t nb) { return (nb + kTileBins - 1) / kTileBins; }
+
+cudaError_t launch_emit_tiled(const SeriesDev& single, Algo algo, int64_t* tile_count, cudaStream_t st) {
+  const int64_t tiles = emit_tiles(single.nb);
+  if (tiles <= 0) return cudaSuccess;
+  note_launch(2);
+  if (algo == ALGO_MINMAX) {
+    k_emit_count<ALGO_MINMAX><<<(unsigned)tiles, kTileThreads, 0, st>>>(single, tile_count);
+    k_emit_write<ALGO_MINMAX><<<(unsigned)tiles, kTileThreads, 0, st>>>(single, tile_count);
+  } else {
+    k_emit_count<ALGO_M4><<<(unsigned)tiles, kTileThreads, 0, st>>>(single, tile_count);
+    k_emit_write<ALGO_M4><<<(unsigned)tiles, kTileThreads, 0, st>>>(single, tile_count);
+  }
+  return cudaGetLastError();
 }
 
 cudaError_t launch_emit(const SeriesDev* s_dev, int count, const SeriesDev& single, Algo algo,

@@ -122,6 +122,12 @@ cudaError_t launch_iota_batched(const SeriesDev* s_dev, int count, cudaStream_t 
 cudaError_t launch_emit(const SeriesDev* s_dev, int count, const SeriesDev& single, Algo algo,
                         cudaStream_t st);
 
+// The same for one series with many bins, over tiles of bins on many CTAs
+// (tile_count: emit_tiles(nb) int64 of scratch).
+constexpr int64_t kEmitTiledMinBins = 16384;
+int64_t emit_tiles(int64_t nb);
+cudaError_t launch_emit_tiled(const SeriesDev& single, Algo algo, int64_t* tile_count, cudaStream_t st);
+
 // out[i] = i + offset for i < n, *count = n.
 cudaError_t launch_iota(int64_t* out, int64_t n, int64_t* count, cudaStream_t st);
 
