@@ -392,6 +392,20 @@ def oracle_all_cores(oracle, x, y, n_out):
             "sample": f"the same {n} points, MinMax + M4 bins once each ({dt:.2f} s)"}
 
 
+def aggregate_ranks(ms_local, bytes_local, dist=None, device=None):
+    """Whole-job numbers of a timed region: (the slowest rank's milliseconds,
+    the bytes all ranks processed, GB/s of the whole job).  Every rank must
+    call it (collectives); with dist None it is the single-rank case."""
+    import torch
+    ms = torch.tensor([float(ms_local)], dtype=torch.float64, device=device)
+    by = torch.tensor([float(bytes_local)], dtype=torch.float64, device=device)
+    if dist:
+        dist.all_reduce(ms, op=dist.ReduceOp.MAX)
+        dist.all_reduce(by, op=dist.ReduceOp.SUM)
+    ms_max, total = float(ms.item()), float(by.item())
+    return ms_max, total, total / (ms_max / 1e3) / 1e9
+
+
 def stream_kernel_name(n, n_out, forced):
     """The streaming kernel a float32 MinMax launch of this shape runs (the
     library's automatic rule: segmented below 1.5 KB mean bins)."""
@@ -595,14 +609,8 @@ def main():
         dist.barrier()
     clk = clocks.stop()
     kern_ms, kern_launches = pkg.tsds_timing_read()
-    t = torch.tensor([ms], device=dev)
-    if dist:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-
     per = step_bytes(n, args.n_out)
-    total_bytes = sum(per.values()) * args.steps * world
-    value = total_bytes / (ms_max / 1e3) / 1e9
+    ms_max, total_bytes, value = aggregate_ranks(ms, sum(per.values()) * args.steps, dist, dev)
     peak, peak_src = hbm_peak()
     kern_avg_ms = kern_ms / max(kern_launches, 1)
     achieved = n * 4 / (kern_avg_ms / 1e3) / 1e9
