@@ -173,6 +173,32 @@ static BinnedLayout binned_layout(int64_t nb, int64_t windows) {
 tsds_status run_binned_series(const void* x, tsds_dtype x_dtype, const void* y, tsds_dtype y_dtype,
                               int64_t n, int64_t nb, tsds_nan_mode nan, Algo algo, int64_t* out,
                               int64_t* out_count, int64_t idx_bias, cudaStream_t st) {
+  if (small_call(n, nb, y_dtype)) {
+    // a small call: one launch (after the edge search when x is given)
+    const size_t o_res = align_up((size_t)(nb + 1) * 8, 256);
+    const size_t o_done = o_res + align_up((size_t)nb * 16, 256);
+    Scratch s;
+    TSDS_CK(scratch_alloc(s, o_done + 256, st));
+    char* base = static_cast<char*>(s.p);
+    TSDS_CK(cudaMemsetAsync(base + o_done, 0, sizeof(unsigned), st));
+    SeriesDev S;
+    memset(&S, 0, sizeof S);
+    S.y = y;
+    S.x = x;
+    S.n = n;
+    S.nb = nb;
+    S.edges = reinterpret_cast<int64_t*>(base);
+    S.res = reinterpret_cast<int64_t*>(base + o_res);
+    S.out = out;
+    S.out_count = out_count;
+    S.idx_bias = idx_bias;
+    if (x) TSDS_CK(launch_edges(nullptr, 1, &S, true, x_dtype, nb, st));
+    void* tok;
+    timing_begin(st, &tok);
+    TSDS_CK(launch_small(S, y_dtype, nan, algo, x != nullptr, reinterpret_cast<unsigned*>(base + o_done), st));
+    timing_end(st, tok);
+    return TSDS_OK;
+  }
   // Window size: 64 KB for large inputs; smaller (down to 8 KB, a multiple of
   // the 4 KB ring chunk) when fewer windows than about twice the resident
   // warps would leave SMs idle.

@@ -754,6 +754,9 @@ cudaError_t launch_wait_probe(unsigned long long* status, unsigned rounds, cudaS
 #include "stream_ldg.cuh"
 #include "stream_seg.cuh"
 
+typedef unsigned __int128 u128;
+#include "stream_small.cuh"
+
 template <class P, int NM, bool MULTI, int VAR>
 static int stream_occupancy() {
   static int occ = 0;
@@ -890,6 +893,31 @@ cudaError_t launch_argminmax_sm(const SeriesDev& single, int64_t total_windows, 
                                 const StreamConfig& cfg, int sm_count, cudaStream_t st) {
   return launch_any(nullptr, 1, single, nullptr, total_windows, first_piece, last_piece, work, y_dtype, nan, cfg,
                     sm_count, st);
+}
+
+bool small_call(int64_t n, int64_t nb, tsds_dtype y_dtype) {
+  return nb >= 1 && nb <= kSmallMaxBins && n * dtype_size(y_dtype) <= kSmallMaxBinBytes * nb;
+}
+
+cudaError_t launch_small(const SeriesDev& S, tsds_dtype y_dtype, tsds_nan_mode nan, Algo algo, bool has_x,
+                         unsigned* done, cudaStream_t st) {
+  const bool ign = nan == TSDS_NAN_IGNORE;
+#define TSDS_SMALL(POL, NM) launch_small_pol<POL, NM>(S, algo, has_x, done, st)
+  switch (y_dtype) {
+    case TSDS_I8: return TSDS_SMALL(PolSmallInt<int8_t>, 0);
+    case TSDS_U8: return TSDS_SMALL(PolSmallInt<uint8_t>, 0);
+    case TSDS_I16: return TSDS_SMALL(PolSmallInt<int16_t>, 0);
+    case TSDS_U16: return TSDS_SMALL(PolSmallInt<uint16_t>, 0);
+    case TSDS_I32: return TSDS_SMALL(PolInt32<int32_t>, 0);
+    case TSDS_U32: return TSDS_SMALL(PolInt32<uint32_t>, 0);
+    case TSDS_I64: return TSDS_SMALL(PolI64, 0);
+    case TSDS_U64: return TSDS_SMALL(PolU64, 0);
+    case TSDS_F16: return ign ? TSDS_SMALL(PolF16<1>, 1) : TSDS_SMALL(PolF16<0>, 0);
+    case TSDS_F32: return ign ? TSDS_SMALL(PolF32<1>, 1) : TSDS_SMALL(PolF32<0>, 0);
+    case TSDS_F64: return ign ? TSDS_SMALL(PolF64Ign, 1) : TSDS_SMALL(PolF64Prop, 0);
+    default: return cudaErrorInvalidValue;
+  }
+#undef TSDS_SMALL
 }
 
 }  // namespace tsds

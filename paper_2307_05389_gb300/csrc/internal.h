@@ -111,6 +111,13 @@ cudaError_t launch_argminmax_sm(const SeriesDev& single, int64_t total_windows, 
                                 Piece* last_piece, WorkCounters* work, tsds_dtype y_dtype, tsds_nan_mode nan,
                                 const StreamConfig& cfg, int sm_count, cudaStream_t st);
 
+// Small single-series calls (n*sizeof(y) <= 64 KB per bin, at most 4096
+// bins): the whole MinMax/M4 pipeline in one launch (index-bin starts in the
+// kernel, x-space starts from launch_edges first); `done` is a zeroed counter.
+bool small_call(int64_t n, int64_t nb, tsds_dtype y_dtype);
+cudaError_t launch_small(const SeriesDev& S, tsds_dtype y_dtype, tsds_nan_mode nan, Algo algo, bool has_x,
+                         unsigned* done, cudaStream_t st);
+
 // A kernel whose barrier wait nothing satisfies, bounded by `rounds`; writes
 // the status it ends with (TSDS_ETIMEOUT) to *status.
 cudaError_t launch_wait_probe(unsigned long long* status, unsigned rounds, cudaStream_t st);

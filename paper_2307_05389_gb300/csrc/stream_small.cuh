@@ -1,0 +1,125 @@
+// stream_small.cuh -- the whole MinMax/M4 pipeline of a small single-series
+// call in one launch (included by argminmax.cu after the other variants).
+//
+// For an input of a few MB the window machinery is all latency: claiming
+// windows, searching bin starts, publishing pieces, and separate launches for
+// the bin starts and the emit step.  Here one warp takes one bin (at most
+// kSmallMaxBinBytes of it, a few register-streaming steps): index-bin starts
+// are computed in place (x-space starts come from the edge kernel), the warp
+// reduces its bin and writes its selections, and the CTA whose arrival on a
+// device counter is the last one emits the sorted output of every bin (a
+// block-wide scan, as the emit kernel does).
+#pragma once
+
+constexpr int kSmallThreads = 256;          // 8 warps, 8 bins per CTA
+constexpr int64_t kSmallMaxBins = 4096;
+constexpr int64_t kSmallMaxBinBytes = 64 * 1024;
+
+// A bin's selections for the emit, read with loads that bypass L1 (the
+// selections were written by other CTAs of the same launch).
+template <int ALGO>
+__device__ __forceinline__ int small_select(const SeriesDev& S, int64_t b, int64_t (&v)[4]) {
+  const int64_t lo = __ldcg(S.edges + b), hi = __ldcg(S.edges + b + 1);
+  if (hi <= lo) return 0;
+  const int64_t mn = __ldcg(S.res + 2 * b), mx = __ldcg(S.res + 2 * b + 1);
+  const int64_t a = min(mn, mx), c = max(mn, mx);
+  if (ALGO == ALGO_MINMAX) {
+    v[0] = a;
+    v[1] = c;
+    return a == c ? 1 : 2;
+  }
+  const int64_t t[4] = {lo, a, c, hi - 1};
+  int k = 0;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+    if (k == 0 || t[i] != v[k - 1]) v[k++] = t[i];
+  return k;
+}
+
+template <class P, int NM, int ALGO, bool HASX>
+__global__ void __launch_bounds__(kSmallThreads) k_small(SeriesDev S, unsigned* __restrict__ done) {
+  using T = typename P::T;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t nb = S.nb;
+  const int64_t b = (int64_t)blockIdx.x * (kSmallThreads / 32) + warp;
+  if (b < nb) {
+    int64_t lo, hi;
+    if (HASX) {
+      lo = __ldg(S.edges + b);
+      hi = __ldg(S.edges + b + 1);
+    } else {
+      const u128 nm1 = (u128)(S.n - 1);
+      lo = (int64_t)(((u128)b * nm1 + (u128)nb - 1) / (u128)nb);
+      hi = b + 1 == nb ? S.n : (int64_t)(((u128)(b + 1) * nm1 + (u128)nb - 1) / (u128)nb);
+      if (lane == 0) {
+        S.edges[b] = lo;
+        if (b + 1 == nb) S.edges[nb] = S.n;
+      }
+    }
+    if (hi > lo) {
+      Cand c = piece_ldg<P>(static_cast<const T*>(S.y), lo, hi);
+      finish_bin<P, NM>(c, lo);
+      if (lane == 0) {
+        S.res[2 * b] = c.imin;
+        S.res[2 * b + 1] = c.imax;
+      }
+    }
+  }
+  // the last CTA to arrive emits every bin
+  __shared__ unsigned last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(done, 1u) == gridDim.x - 1 ? 1u : 0u;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  __shared__ int64_t warp_tot[kSmallThreads / 32];
+  __shared__ int64_t total;
+  const int64_t per = (nb + kSmallThreads - 1) / kSmallThreads;
+  const int64_t b0 = min((int64_t)threadIdx.x * per, nb), b1 = min(b0 + per, nb);
+  int64_t v[4];
+  int64_t local = 0;
+  for (int64_t q = b0; q < b1; ++q) local += small_select<ALGO>(S, q, v);
+  int64_t incl = local;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int64_t t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  if (lane == 31) warp_tot[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    constexpr int nw = kSmallThreads / 32;
+    const int64_t wv = lane < nw ? warp_tot[lane] : 0;
+    int64_t wi = wv;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int64_t t = __shfl_up_sync(0xffffffffu, wi, o);
+      if (lane >= o) wi += t;
+    }
+    if (lane < nw) warp_tot[lane] = wi - wv;
+    if (lane == nw - 1) total = wi;
+  }
+  __syncthreads();
+  int64_t off = warp_tot[warp] + incl - local;
+  for (int64_t q = b0; q < b1; ++q) {
+    const int k = small_select<ALGO>(S, q, v);
+    for (int i = 0; i < k; ++i) S.out[off + i] = v[i] + S.idx_bias;
+    off += k;
+  }
+  if (threadIdx.x == 0 && S.out_count) *S.out_count = total;
+}
+
+template <class P, int NM>
+static cudaError_t launch_small_pol(const SeriesDev& S, Algo algo, bool has_x, unsigned* done, cudaStream_t st) {
+  const unsigned blocks = (unsigned)((S.nb + kSmallThreads / 32 - 1) / (kSmallThreads / 32));
+  note_launch();
+  if (algo == ALGO_MINMAX) {
+    if (has_x) k_small<P, NM, ALGO_MINMAX, true><<<blocks, kSmallThreads, 0, st>>>(S, done);
+    else k_small<P, NM, ALGO_MINMAX, false><<<blocks, kSmallThreads, 0, st>>>(S, done);
+  } else {
+    if (has_x) k_small<P, NM, ALGO_M4, true><<<blocks, kSmallThreads, 0, st>>>(S, done);
+    else k_small<P, NM, ALGO_M4, false><<<blocks, kSmallThreads, 0, st>>>(S, done);
+  }
+  return cudaGetLastError();
+}
