@@ -174,15 +174,24 @@ def tsds_plan_destroy(plan):
 
 
 def _series_array(ys, n_outs, xs, outs, counts):
-    arr = (tsds_series * len(ys))()
-    for i, y in enumerate(ys):
-        arr[i].x = xs[i].data_ptr() if xs is not None else None
-        arr[i].y = y.data_ptr()
-        arr[i].n = y.shape[0]
-        arr[i].n_out = int(n_outs[i])
-        arr[i].out = outs[i].data_ptr()
-        arr[i].out_count = counts[i:i + 1].data_ptr()
-    return arr
+    """The tsds_series array of a batch, built column-wise with numpy (48-byte
+    records: x, y, n, n_out, out, out_count); returns the array, which owns
+    the memory the pointer refers to."""
+    import numpy as np
+    k = len(ys)
+    a = np.zeros((k, 6), dtype=np.uint64)
+    if xs is not None:
+        a[:, 0] = [x.data_ptr() for x in xs]
+    a[:, 1] = [y.data_ptr() for y in ys]
+    a[:, 2] = [y.shape[0] for y in ys]
+    a[:, 3] = np.asarray(n_outs, dtype=np.int64).astype(np.uint64)
+    a[:, 4] = [o.data_ptr() for o in outs]
+    a[:, 5] = counts.data_ptr() + 8 * np.arange(k, dtype=np.uint64)
+    return a
+
+
+def _array_ptr(a):
+    return ctypes.c_void_p(a.ctypes.data)
 
 
 def batch_buffers(ys, n_outs, device):
@@ -207,7 +216,8 @@ def downsample_batched(algo, ys, n_outs, xs=None, nan="propagate", stream=None, 
     yd = DTYPES[y_dtype or _torch_dtype_name(ys[0])]
     xd = DTYPES[x_dtype or _torch_dtype_name(xs[0])] if xs is not None else 0
     with torch.cuda.device(dev):
-        r = tsds_batched(ALGO_CODES[algo], arr, len(ys), xd, yd, NAN_MODES[nan], ctypes.c_void_p(st.cuda_stream))
+        r = tsds_batched(ALGO_CODES[algo], _array_ptr(arr), len(ys), xd, yd, NAN_MODES[nan],
+                         ctypes.c_void_p(st.cuda_stream))
     if r != 0:
         raise TsdsError(r, last_error())
     return outs, counts
@@ -229,7 +239,7 @@ class Plan:
         self.handle = ctypes.c_void_p()
         flags = (PLAN_GRAPH if graph else 0) | (PLAN_AUTOTUNE if autotune else 0)
         with torch.cuda.device(self.device):
-            r = tsds_plan_create(ctypes.byref(self.handle), ALGO_CODES[algo], arr, len(ys), xd, yd,
+            r = tsds_plan_create(ctypes.byref(self.handle), ALGO_CODES[algo], _array_ptr(arr), len(ys), xd, yd,
                                  NAN_MODES[nan], flags, ctypes.c_void_p(st.cuda_stream))
         if r != 0:
             raise TsdsError(r, last_error())

@@ -81,3 +81,28 @@ def test_missing_library_fails_loudly(tmp_path):
             binding.load(binding_path)
         finally:
             binding._lib = saved
+
+
+def test_series_array_matches_the_struct_layout():
+    """The batch descriptor array built column-wise has the tsds_series layout
+    (six 8-byte fields in header order), without touching device memory."""
+    import numpy as np
+
+    class FakeTensor:
+        def __init__(self, ptr, n):
+            self.ptr, self.shape = ptr, (n,)
+
+        def data_ptr(self):
+            return self.ptr
+
+    ys = [FakeTensor(0x1000 * (i + 1), 100 + i) for i in range(3)]
+    xs = [FakeTensor(0x9000 + 0x100 * i, 100 + i) for i in range(3)]
+    outs = [FakeTensor(0x20000 + 0x40 * i, 8) for i in range(3)]
+    counts = FakeTensor(0x30000, 3)
+    a = binding._series_array(ys, [8, 12, 16], xs, outs, counts)
+    assert a.dtype == np.uint64 and a.shape == (3, 6)
+    assert ctypes.sizeof(binding.tsds_series) == a.itemsize * a.shape[1]
+    s = binding.tsds_series.from_buffer_copy(a.tobytes(), ctypes.sizeof(binding.tsds_series))
+    assert (s.x, s.y, s.n, s.n_out, s.out, s.out_count) == (0x9100, 0x2000, 101, 12, 0x20040, 0x30008)
+    a = binding._series_array(ys, [8, 12, 16], None, outs, counts)
+    assert (a[:, 0] == 0).all()

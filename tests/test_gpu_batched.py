@@ -106,11 +106,12 @@ def test_batched_rejects_mixed_x_and_bad_n_out():
     xs = to_dev([inputs.geometric_x(100, 1), inputs.geometric_x(100, 2)])
     outs, counts = binding.batch_buffers(ys, [8, 8], ys[0].device)
     arr = binding._series_array(ys, [8, 8], xs, outs, counts)
-    arr[1].x = None
-    assert binding.tsds_batched(0, arr, 2, binding.DTYPES["int64"], binding.DTYPES["float32"], 0, None) == 1
+    arr[1, 0] = 0                                      # series 1 without x
+    assert binding.tsds_batched(0, binding._array_ptr(arr), 2, binding.DTYPES["int64"],
+                                binding.DTYPES["float32"], 0, None) == 1
     assert "x" in binding.last_error()
     arr = binding._series_array(ys, [8, 6], None, outs, counts)
-    assert binding.tsds_batched(1, arr, 2, 0, binding.DTYPES["float32"], 0, None) == 1
+    assert binding.tsds_batched(1, binding._array_ptr(arr), 2, 0, binding.DTYPES["float32"], 0, None) == 1
     torch.cuda.synchronize()
 
 
