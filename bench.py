@@ -344,8 +344,13 @@ def suite_lttb(args):
         f = lambda: _raw_call(binding, "lttb", None, None, y, dt, n, n_out, out, cnt, stream)
         f()
         med, _ = _timed_calls(torch, stream, f, 3)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        f()
+        issue = (time.perf_counter() - t0) * 1e3
+        torch.cuda.synchronize()
         res[f"lttb_{dt}_{n}"] = {"ms": med, "GBps": n * y.element_size() / (med / 1e3) / 1e9,
-                                 "us_per_bucket": med * 1e3 / (n_out - 2)}
+                                 "us_per_bucket": med * 1e3 / (n_out - 2), "host_issue_ms": issue}
     series = [torch.from_numpy(inputs.quantised_nan(1_562_500, seed=4 + i)).to(dev) for i in range(64)]
     for nan, nm in ((0, "propagate"), (1, "ignore")):
         for r in (2, 4, 30):
@@ -355,7 +360,15 @@ def suite_lttb(args):
                               nan=nan, ratio=r)
             f()
             med, _ = _timed_calls(torch, stream, f, 3)
-            res[f"minmaxlttb_r{r}_{nm}"] = {"ms_64_series": med, "GBps": 1e8 * 8 / (med / 1e3) / 1e9}
+            # host time to issue the 64 calls (no synchronisation inside): close to the
+            # device time means the loop is bound by issuing launches, not by the GPU
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            f()
+            issue = (time.perf_counter() - t0) * 1e3
+            torch.cuda.synchronize()
+            res[f"minmaxlttb_r{r}_{nm}"] = {"ms_64_series": med, "GBps": 1e8 * 8 / (med / 1e3) / 1e9,
+                                            "host_issue_ms": issue}
     return {"suite": "lttb", "unit": "ms", "config": {"workload": "LTTB: float64/float32 random walks, n_out=4000; "
             "MinMaxLTTB: 64 x 1.5625e6 float64 quantised to 256 levels with 1% NaN, one call per series"},
             "results": res}
@@ -543,7 +556,10 @@ def main():
         pkg.load()
         fn = {"dtypes": suite_dtypes, "config1": suite_config1, "lttb": suite_lttb, "batched": suite_batched,
               "serve": suite_serve}[args.suite]
-        print(json.dumps(fn(args)), flush=True)
+        clocks = ClockSampler(0)
+        out = fn(args)
+        out["clocks"] = clocks.stop()
+        print(json.dumps(out), flush=True)
         return
 
     import numpy as np
