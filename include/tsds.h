@@ -311,6 +311,18 @@ int tsds_stream_variant(int variant);
  * event query fails. */
 tsds_status tsds_timing_read(double* total_ms, int64_t* launches);
 
+/* Diagnostic: the bucket averages an LTTB call with the same arguments uses
+ * (Section 1: the third point of each step's triangle is the average of the
+ * next bucket).  Bucket j of B = n_out - 2 covers points
+ * [1 + floor(j(n-2)/B), 1 + floor((j+1)(n-2)/B)); its average is the binary64
+ * sum of its x (or index) and y values in index order, each divided by the
+ * count (NaN-ignore leaves out points whose y is NaN).  Writes the averages of
+ * buckets 1 .. B-1 to `means` (device memory, 2*(n_out-3) doubles: x then y of
+ * each bucket), enqueued on `stream`.  Needs 3 <= n_out < n; TSDS_EINVAL
+ * otherwise (nothing written). */
+tsds_status tsds_lttb_means(const void* x, tsds_dtype x_dtype, const void* y, tsds_dtype y_dtype,
+                            int64_t n, int64_t n_out, tsds_nan_mode nan, double* means, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -67,6 +67,8 @@ def _load():
     lib.orc_minmaxlttb.restype = i64
     lib.orc_lttb_points.argtypes = [p, p, i64, i64, c_int, p]
     lib.orc_lttb_points.restype = i64
+    lib.orc_lttb_means.argtypes = [p, c_int, p, c_int, i64, i64, c_int, p]
+    lib.orc_lttb_means.restype = i64
     _lib = lib
     return lib
 
@@ -171,6 +173,19 @@ def lttb_points(px, py, n_out, nan="propagate"):
     if r < 0:
         raise OracleError("lttb_points: invalid arguments")
     return out[:r].copy()
+
+
+def lttb_means(x, y, n_out, nan="propagate"):
+    """(n_out-3, 2) array: the (x, y) average of LTTB buckets 1 .. n_out-3."""
+    lib = _load()
+    x, y = _prep(x, y)
+    n = y.shape[0]
+    out = np.empty((max(n_out - 3, 0), 2), dtype=np.float64)
+    xc = DTYPE_CODES[x.dtype.name] if x is not None else 0
+    r = lib.orc_lttb_means(_ptr(x), xc, _ptr(y), DTYPE_CODES[y.dtype.name], n, n_out, NAN_MODES[nan], _ptr(out))
+    if r < 0:
+        raise OracleError(f"lttb_means: invalid arguments (n={n}, n_out={n_out})")
+    return out
 
 
 def f16_to_f64(bits: int) -> float:

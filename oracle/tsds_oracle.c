@@ -354,6 +354,29 @@ int64_t orc_lttb(const void* x, int x_dtype, const void* y, int y_dtype, int64_t
   return r;
 }
 
+/* The averages step j = 0 .. B-2 of orc_lttb_points uses: buckets 1 .. B-1,
+ * (x, y) pairs, from the same binary64 conversion as orc_lttb. */
+int64_t orc_lttb_means(const void* x, int x_dtype, const void* y, int y_dtype, int64_t n,
+                       int64_t n_out, int nan_mode, double* out) {
+  if (!args_ok(x, x_dtype, y, y_dtype, n) || n_out < 3 || n_out >= n) return ORC_EINVAL;
+  double* px = NULL;
+  double* py = (double*)malloc((size_t)n * sizeof(double));
+  if (!py) return ORC_EINVAL;
+  if (x) {
+    px = (double*)malloc((size_t)n * sizeof(double));
+    if (!px) { free(py); return ORC_EINVAL; }
+    for (int64_t i = 0; i < n; ++i) px[i] = get_as_double(x, x_dtype, i);
+  }
+  for (int64_t i = 0; i < n; ++i) py[i] = get_as_double(y, y_dtype, i);
+  int64_t B = n_out - 2;
+  for (int64_t j = 1; j < B; ++j)
+    bucket_mean(px, py, bucket_start(j, n, B), bucket_start(j + 1, n, B), nan_mode, &out[2 * (j - 1)],
+                &out[2 * (j - 1) + 1]);
+  free(px);
+  free(py);
+  return B - 1;
+}
+
 /* ---------------------------------------------------------------- MinMaxLTTB */
 
 int64_t orc_minmaxlttb(const void* x, int x_dtype, const void* y, int y_dtype, int64_t n,

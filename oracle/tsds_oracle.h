@@ -59,6 +59,12 @@ int64_t orc_minmaxlttb(const void* x, int x_dtype, const void* y, int y_dtype, i
 int64_t orc_lttb_points(const double* px, const double* py, int64_t m, int64_t n_out,
                         int nan_mode, int64_t* out);
 
+/* The bucket averages of orc_lttb (buckets 1 .. n_out-3, (x, y) pairs into
+ * out[2*(n_out-3)]): binary64 sums in index order divided by the count.
+ * Needs 3 <= n_out < n.  Returns n_out - 3. */
+int64_t orc_lttb_means(const void* x, int x_dtype, const void* y, int y_dtype, int64_t n,
+                       int64_t n_out, int nan_mode, double* out);
+
 #ifdef __cplusplus
 }
 #endif

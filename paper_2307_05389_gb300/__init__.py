@@ -27,6 +27,7 @@ from .binding import (  # noqa: F401
     last_error,
     load,
     tsds_lttb,
+    tsds_lttb_means,
     tsds_m4,
     tsds_minmax,
     tsds_minmaxlttb,

@@ -78,6 +78,8 @@ def load(path: str = LIB_PATH):
     lib.tsds_timing_read.restype = c_int
     lib.tsds_stream_variant.argtypes = [c_int]
     lib.tsds_stream_variant.restype = c_int
+    lib.tsds_lttb_means.argtypes = [p, c_int, p, c_int, i64, i64, c_int, p, p]
+    lib.tsds_lttb_means.restype = c_int
     _lib = lib
     return lib
 
@@ -129,6 +131,10 @@ def tsds_m4(x, x_dtype, y, y_dtype, n, n_out, nan, out, out_count, stream):
 
 def tsds_lttb(x, x_dtype, y, y_dtype, n, n_out, nan, out, out_count, stream):
     return load().tsds_lttb(x, x_dtype, y, y_dtype, n, n_out, nan, out, out_count, stream)
+
+
+def tsds_lttb_means(x, x_dtype, y, y_dtype, n, n_out, nan, means, stream):
+    return load().tsds_lttb_means(x, x_dtype, y, y_dtype, n, n_out, nan, means, stream)
 
 
 def tsds_minmaxlttb(x, x_dtype, y, y_dtype, n, n_out, minmax_ratio, nan, out, out_count, stream):
@@ -417,6 +423,23 @@ def _torch_dtype_name(t) -> str:
 
 def out_capacity(algo: str, n: int, n_out: int) -> int:
     return max(1, n if n_out >= n else n_out)
+
+
+def lttb_means(y, n_out, x=None, nan="propagate"):
+    """The (x, y) averages of LTTB buckets 1 .. n_out-3 on a CUDA tensor y (and x), as a
+    (n_out-3, 2) float64 device tensor (tsds_lttb_means)."""
+    import torch
+    n = y.shape[0]
+    means = torch.empty((max(n_out - 3, 0), 2), dtype=torch.float64, device=y.device)
+    st = torch.cuda.current_stream(y.device)
+    xp = x.data_ptr() if x is not None else None
+    xd = DTYPES[_torch_dtype_name(x)] if x is not None else 0
+    with torch.cuda.device(y.device):
+        r = tsds_lttb_means(xp, xd, y.data_ptr(), DTYPES[_torch_dtype_name(y)], n, n_out, NAN_MODES[nan],
+                            means.data_ptr(), ctypes.c_void_p(st.cuda_stream))
+    if r != 0:
+        raise TsdsError(r, last_error())
+    return means
 
 
 def downsample(algo, y, n_out, x=None, nan="propagate", minmax_ratio=4, out=None, out_count=None,

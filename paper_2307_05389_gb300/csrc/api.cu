@@ -306,6 +306,22 @@ tsds_status tsds_minmaxlttb(const void* x, tsds_dtype x_dtype, const void* y, ts
                         static_cast<cudaStream_t>(stream));
 }
 
+tsds_status tsds_lttb_means(const void* x, tsds_dtype x_dtype, const void* y, tsds_dtype y_dtype,
+                            int64_t n, int64_t n_out, tsds_nan_mode nan, double* means, void* stream) {
+  g_err[0] = 0;
+  if (!means) return fail(TSDS_EINVAL, "tsds_lttb_means: means is NULL");
+  if (n_out < 3 || n_out >= n)
+    return fail(TSDS_EINVAL, "tsds_lttb_means needs 3 <= n_out < n (got n_out %lld, n %lld)", (long long)n_out,
+                (long long)n);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Scratch sc;
+  TSDS_CK(scratch_alloc(sc, align_up((size_t)(n_out + 1) * sizeof(int64_t), 256), st));
+  int64_t* out = static_cast<int64_t*>(sc.p);
+  tsds_status s = check_common(x, x_dtype, y, y_dtype, n, nan, out, out + n_out);
+  if (s != TSDS_OK) return s;
+  return run_lttb(x, x_dtype, y, y_dtype, n, n_out, nan, out, out + n_out, st, means);
+}
+
 const char* tsds_last_error(void) { return g_err; }
 
 void tsds_shutdown(void) {

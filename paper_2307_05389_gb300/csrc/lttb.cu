@@ -151,17 +151,20 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-// Hull-table mode, larger buckets: the same index-order sums, one thread per
-// bucket.  Each thread streams its own bucket through a private ring of three
-// 32-point chunks in shared memory (cp.async, two chunks in flight), so the
-// only serial work is the two chains of binary64 additions.
+// Hull-table mode, larger buckets.  Most buckets get their mean from k_p32
+// (exact sums, below); a bucket it flags takes the sequential sum here, one
+// thread per bucket.  The warp's 32 buckets stream through a ring of three
+// 32-point chunks in shared memory: lane i copies point i of every flagged
+// bucket's chunk (coalesced cp.async, two chunks in flight) and thread t then
+// adds up column t, so the only serial work is the two chains of binary64
+// additions.
 constexpr int kSumChunk = 32;
 constexpr int kSumRing = 3;
 
-// The warp's rings, thread-minor (element i of thread t at [r][i][t]) so that
-// the 32 threads' accesses fall in distinct banks.
+// [ring slot][point of the chunk][bucket], rows padded by one so that both
+// the copies (fixed bucket) and the adds (fixed point) spread over the banks.
 struct SumRing {
-  double x[kSumRing][kSumChunk][32], y[kSumRing][kSumChunk][32];
+  double x[kSumRing][kSumChunk][33], y[kSumRing][kSumChunk][33];
 };
 
 __global__ void __launch_bounds__(32) k_sums_wide(const LttbJob* __restrict__ jobs) {
@@ -171,20 +174,30 @@ __global__ void __launch_bounds__(32) k_sums_wide(const LttbJob* __restrict__ jo
   if (m <= B + 2) return;
   extern __shared__ __align__(16) unsigned char sum_smem[];
   SumRing& R = *reinterpret_cast<SumRing*>(sum_smem);
+  __shared__ int64_t lo_s[32], n_s[32];
   const int t = threadIdx.x;
   const bool ign = J.nan == TSDS_NAN_IGNORE;
   for (int64_t jb = (int64_t)blockIdx.x * 32; jb < B; jb += (int64_t)gridDim.x * 32) {
-    const int64_t j = jb + threadIdx.x;
-    const bool mine = j >= 1 && j < B;
+    const int64_t j = jb + t;
+    const bool mine = j >= 1 && j < B && J.chain[j];
+    if (!__any_sync(0xffffffffu, mine)) continue;
     const int64_t lo = mine ? bucket_start(j, m, B) : 0, hi = mine ? bucket_start(j + 1, m, B) : 0;
-    const int64_t chunks = (hi - lo + kSumChunk - 1) / kSumChunk;
+    __syncwarp();
+    lo_s[t] = lo;
+    n_s[t] = hi - lo;
+    int64_t chunks = (hi - lo + kSumChunk - 1) / kSumChunk;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) chunks = max(chunks, __shfl_xor_sync(0xffffffffu, chunks, o));
+    __syncwarp();
     auto issue = [&](int64_t c) {
       if (c < chunks) {
         const int r = (int)(c % kSumRing);
-        const int64_t k0 = lo + c * kSumChunk, k1 = min(k0 + kSumChunk, hi);
-        for (int64_t k = k0; k < k1; ++k) {
-          cp_async8(&R.x[r][k - k0][t], J.px + k);
-          cp_async8(&R.y[r][k - k0][t], J.py + k);
+        const int64_t k = c * kSumChunk + t;
+        for (int b = 0; b < 32; ++b) {
+          if (k < n_s[b]) {
+            cp_async8(&R.x[r][t][b], J.px + lo_s[b] + k);
+            cp_async8(&R.y[r][t][b], J.py + lo_s[b] + k);
+          }
         }
       }
       cp_async_commit();
@@ -194,11 +207,12 @@ __global__ void __launch_bounds__(32) k_sums_wide(const LttbJob* __restrict__ jo
     double sx = 0.0, sy = 0.0;
     int64_t cnt = 0;
     for (int64_t c = 0; c < chunks; ++c) {
+      __syncwarp();                 // slot (c+2)%3 was read by the whole warp at c-1
       issue(c + 2);
       cp_async_wait<2>();
+      __syncwarp();                 // every lane's copies of chunk c have landed
       const int r = (int)(c % kSumRing);
-      const int n = (int)min((int64_t)kSumChunk, hi - lo - c * kSumChunk);
-      // loads of a group of 8 first, then the two dependent chains of adds
+      const int n = (int)max((int64_t)0, min((int64_t)kSumChunk, hi - lo - c * kSumChunk));
       for (int i0 = 0; i0 < n; i0 += 8) {
         double xv[8], yv[8];
 #pragma unroll
@@ -221,18 +235,93 @@ __global__ void __launch_bounds__(32) k_sums_wide(const LttbJob* __restrict__ jo
   }
 }
 
+// Exact bucket sums.  Each binary64 value is +-M * 2^q with M odd; a lane
+// keeps its running sum as an integer multiple of 2^s, s its smallest q so
+// far, and the largest binary exponent `top` it has seen.  With L the
+// smallest q and T the largest exponent over a bucket's c added values, every
+// partial sum of the index-order sum is a multiple of 2^L of magnitude below
+// c * 2^(T+1); when that bound is at most 2^(53+L) every partial sum is a
+// binary64 number, so no addition of the sequential sum rounds and it equals
+// the exact sum, which the lanes' integers give in any order.  Otherwise (or
+// for a NaN or an infinity) the integers may have wrapped and the bucket
+// takes the sequential sum instead.
+struct ExactSum {
+  unsigned long long acc;   // two's complement, units of 2^s
+  int s, top;
+};
+
+__device__ __forceinline__ void exact_init(ExactSum& e) {
+  e.acc = 0ull;
+  e.s = 4096;
+  e.top = -4096;
+}
+
+__device__ __forceinline__ void exact_add(ExactSum& e, double v, bool& bad) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  const int eb = (int)((b >> 52) & 0x7ff);
+  unsigned long long M = b & 0xfffffffffffffull;
+  if (eb == 0x7ff) {
+    bad = true;
+    return;
+  }
+  if (eb == 0 && M == 0ull) return;                      // a zero adds nothing
+  int q = eb == 0 ? -1074 : eb - 1075;
+  if (eb != 0) M |= 1ull << 52;
+  const int tz = __ffsll((long long)M) - 1;
+  M >>= tz;
+  q += tz;
+  e.top = max(e.top, q + 63 - __clzll((long long)M));
+  if (q < e.s) {
+    e.acc <<= min(e.s - q, 63);
+    e.s = q;
+  }
+  const unsigned long long w = M << min(q - e.s, 63);
+  e.acc += (b >> 63) ? (0ull - w) : w;
+}
+
+// The warp's exact sum of one coordinate, or false when the bound fails.
+__device__ __forceinline__ bool exact_finish(const ExactSum& e, int cnt, double& out) {
+  const int L = __reduce_min_sync(0xffffffffu, e.s + 8192) - 8192;
+  const int T = __reduce_max_sync(0xffffffffu, e.top + 8192) - 8192;
+  unsigned long long a = e.acc << min(e.s - L, 63);
+  if (e.s == 4096) a = 0ull;                             // lane saw no nonzero value
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+  if (T == -4096) {                                      // every value was zero
+    out = 0.0;
+    return true;
+  }
+  const int lg = cnt <= 1 ? 0 : 32 - __clz(cnt - 1);     // ceil(log2 cnt)
+  if (T + 1 + lg > 53 + L) return false;
+  double r = __ll2double_rn((long long)a);               // exact: |a| < 2^53
+  int e2 = L;
+  if (e2 < -1022) {                                      // scale in two exact steps
+    r = __dmul_rn(r, __longlong_as_double((long long)(-600 + 1023) << 52));
+    e2 += 600;
+  }
+  out = __dmul_rn(r, __longlong_as_double((long long)(e2 + 1023) << 52));
+  return true;
+}
+
 // p32[k] = point k relative to its bucket's first point, rounded to FP32: a
-// warp per bucket, coalesced.
+// warp per bucket, coalesced.  The same pass adds the bucket up exactly
+// (ExactSum) and writes its mean, or flags the bucket for k_sums_wide.
 __global__ void k_p32(const LttbJob* __restrict__ jobs) {
   const LttbJob J = jobs[blockIdx.y];
   if (J.mode != 2) return;
   const int64_t m = job_m(J), B = J.B;
   if (m <= B + 2) return;
   const int lane = threadIdx.x & 31;
+  const bool ign = J.nan == TSDS_NAN_IGNORE;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t j = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); j < B; j += warps) {
     const int64_t lo = bucket_start(j, m, B), hi = bucket_start(j + 1, m, B);
     const double X0 = J.px[lo], Y0 = J.py[lo];
+    ExactSum ex, ey;
+    exact_init(ex);
+    exact_init(ey);
+    bool bad = hi - lo > (int64_t)1 << 30;
+    int cnt = 0;
     for (int64_t k0 = lo + lane; k0 < hi; k0 += 128) {
       double xv[4], yv[4];
 #pragma unroll
@@ -244,9 +333,26 @@ __global__ void k_p32(const LttbJob* __restrict__ jobs) {
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const int64_t k = k0 + 32 * u;
-        if (k < hi)
+        if (k < hi) {
           J.p32[k] = make_float2(__double2float_rn(__dsub_rn(xv[u], X0)), __double2float_rn(__dsub_rn(yv[u], Y0)));
+          if (!(ign && isnan(yv[u]))) {
+            ++cnt;
+            exact_add(ex, xv[u], bad);
+            exact_add(ey, yv[u], bad);
+          }
+        }
       }
+    }
+    if (j == 0) continue;
+    cnt = (int)__reduce_add_sync(0xffffffffu, (unsigned)cnt);
+    bad = __any_sync(0xffffffffu, bad) || cnt == 0;
+    double sx = 0.0, sy = 0.0;
+    const bool okx = exact_finish(ex, cnt, sx);
+    const bool oky = exact_finish(ey, cnt, sy);
+    const bool exact = !bad && okx && oky;
+    if (lane == 0) {
+      J.chain[j] = exact ? 0 : 1;
+      if (exact) J.means[j] = make_double2(__ddiv_rn(sx, (double)cnt), __ddiv_rn(sy, (double)cnt));
     }
   }
 }
@@ -743,6 +849,7 @@ size_t lttb_job_scratch(int64_t m_max, int64_t B, int64_t K) {
     s += align_up((size_t)m_max * sizeof(float2), 256);           // p32
     s += align_up((size_t)(B + 1) * kCandMax * 4, 256);           // candidate rows 0..B
     s += 2 * align_up((size_t)B * kCandMax * 4, 256);             // table, fslot
+    s += align_up((size_t)B, 256);                                // chain flags
   }
   return s;
 }
@@ -768,6 +875,8 @@ void lttb_job_bind(LttbJob& J, char* p, int64_t m_max) {
   J.table = reinterpret_cast<int32_t*>(p);
   p += align_up((size_t)J.B * kCandMax * 4, 256);
   J.fslot = reinterpret_cast<int32_t*>(p);
+  p += align_up((size_t)J.B * kCandMax * 4, 256);
+  J.chain = reinterpret_cast<uint8_t*>(p);
 }
 
 tsds_status launch_points_jobs(const PointsJob* jobs_dev, int count, int64_t max_m, cudaStream_t st) {
@@ -804,6 +913,7 @@ tsds_status run_lttb_jobs(const LttbJob* jobs_host, const LttbJob* jobs_dev, int
     k_p32<<<dim3((unsigned)pb, (unsigned)count), 256, 0, st>>>(jobs_dev);
     TSDS_CK(cudaGetLastError());
     const int ssmem = (int)sizeof(SumRing);
+    TSDS_CK(cudaFuncSetAttribute(k_sums_wide, cudaFuncAttributeMaxDynamicSharedMemorySize, ssmem));
     note_launch();
     k_sums_wide<<<dim3((unsigned)((max_B + 31) / 32), (unsigned)count), 32, ssmem, st>>>(jobs_dev);
     TSDS_CK(cudaGetLastError());
@@ -845,7 +955,8 @@ tsds_status run_lttb_jobs(const LttbJob* jobs_host, const LttbJob* jobs_dev, int
 // set, otherwise m_host; m_max bounds it), writing R[pick] (or pick) to out.
 static tsds_status lttb_points_core(const double* px, const double* py, const int64_t* m_dev, int64_t m_host,
                                     int64_t m_max, int64_t n_out, tsds_nan_mode nan, const int64_t* R,
-                                    int64_t* out, int64_t* out_count, cudaStream_t st) {
+                                    int64_t* out, int64_t* out_count, cudaStream_t st,
+                                    double* means_out = nullptr) {
   LttbJob J;
   memset(&J, 0, sizeof J);
   J.px = px;
@@ -864,7 +975,11 @@ static tsds_status lttb_points_core(const double* px, const double* py, const in
   lttb_job_bind(J, static_cast<char*>(s.p), m_max);
   LttbJob* jd = reinterpret_cast<LttbJob*>(static_cast<char*>(s.p) + js);
   TSDS_CK(cudaMemcpyAsync(jd, &J, sizeof J, cudaMemcpyHostToDevice, st));
-  return run_lttb_jobs(&J, jd, 1, J.B, m_max, st);
+  const tsds_status r = run_lttb_jobs(&J, jd, 1, J.B, m_max, st);
+  if (r == TSDS_OK && means_out && J.B > 1)
+    TSDS_CK(cudaMemcpyAsync(means_out, J.means + 1, (size_t)(J.B - 1) * sizeof(double2), cudaMemcpyDeviceToDevice,
+                            st));
+  return r;
 }
 
 static tsds_status points(const void* x, tsds_dtype x_dtype, const void* y, tsds_dtype y_dtype, const int64_t* R,
@@ -889,7 +1004,8 @@ static tsds_status points(const void* x, tsds_dtype x_dtype, const void* y, tsds
 }
 
 tsds_status run_lttb(const void* x, tsds_dtype x_dtype, const void* y, tsds_dtype y_dtype, int64_t n,
-                     int64_t n_out, tsds_nan_mode nan, int64_t* out, int64_t* out_count, cudaStream_t st) {
+                     int64_t n_out, tsds_nan_mode nan, int64_t* out, int64_t* out_count, cudaStream_t st,
+                     double* means_out) {
   if (n == 0) {
     TSDS_CK(cudaMemsetAsync(out_count, 0, sizeof(int64_t), st));
     return TSDS_OK;
@@ -905,7 +1021,7 @@ tsds_status run_lttb(const void* x, tsds_dtype x_dtype, const void* y, tsds_dtyp
   double* px = reinterpret_cast<double*>(static_cast<char*>(s.p) + pb);
   tsds_status r = points(x, x_dtype, y, y_dtype, nullptr, nullptr, n, n, px, py, st);
   if (r != TSDS_OK) return r;
-  return lttb_points_core(px, py, nullptr, n, n, n_out, nan, nullptr, out, out_count, st);
+  return lttb_points_core(px, py, nullptr, n, n, n_out, nan, nullptr, out, out_count, st, means_out);
 }
 
 tsds_status run_minmaxlttb(const void* x, tsds_dtype x_dtype, const void* y, tsds_dtype y_dtype,

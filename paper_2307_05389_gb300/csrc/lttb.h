@@ -11,8 +11,10 @@ tsds_status run_binned_series(const void* x, tsds_dtype x_dtype, const void* y, 
                               int64_t n, int64_t nb, tsds_nan_mode nan, Algo algo, int64_t* out,
                               int64_t* out_count, int64_t idx_bias, cudaStream_t st);
 
+// means_out (optional, device): the averages of buckets 1..B-1 as (x, y) pairs
 tsds_status run_lttb(const void* x, tsds_dtype x_dtype, const void* y, tsds_dtype y_dtype, int64_t n,
-                     int64_t n_out, tsds_nan_mode nan, int64_t* out, int64_t* out_count, cudaStream_t st);
+                     int64_t n_out, tsds_nan_mode nan, int64_t* out, int64_t* out_count, cudaStream_t st,
+                     double* means_out = nullptr);
 
 tsds_status run_minmaxlttb(const void* x, tsds_dtype x_dtype, const void* y, tsds_dtype y_dtype,
                            int64_t n, int64_t n_out, int64_t minmax_ratio, tsds_nan_mode nan,
@@ -36,6 +38,7 @@ struct LttbJob {
   float2* p32;           // mode 2: m points relative to their bucket's first point, in FP32
   int32_t* cand;         // mode 2: B*kLttbCandMax candidate picks per bucket (relative, -1: none)
   int32_t* fslot;        // slot of the pick among the next step's inputs (mode 0: the table itself)
+  uint8_t* chain;        // mode 2: per bucket, 1 when its mean needs the sequential sum (k_sums_wide)
   int32_t* comp;         // per segment of 32 steps and input slot: the slot after the segment (-1: leaves the table)
   int32_t* seg_start;    // per segment: its input slot, or -1 when the chain was replayed there directly
   int64_t* out;

@@ -454,3 +454,63 @@ def test_minmaxlttb_brute_force():
         np.testing.assert_array_equal(oracle.minmaxlttb(None, y, n_out, ratio), [R[p] for p in picks])
         checked += 1
     assert checked > 100
+
+
+# ----------------------------------------------------------------------------- LTTB bucket averages
+
+def lttb_bucket(j, n, n_out):
+    """[lo, hi) of LTTB bucket j over points 1..n-2 (B = n_out - 2 equal-count buckets)."""
+    B = n_out - 2
+    return 1 + (j * (n - 2)) // B, 1 + ((j + 1) * (n - 2)) // B
+
+
+@pytest.mark.parametrize("n,n_out", [(11, 5), (1000, 7), (4001, 50), (100_003, 1000)])
+def test_lttb_means_closed_form_on_index_values(n, n_out):
+    """y = index and no x: every average of bucket [lo, hi) is (lo + hi - 1) / 2
+    in both coordinates, exactly (sums of integers below 2^53, one division)."""
+    y = np.arange(n, dtype=np.int64)
+    got = oracle.lttb_means(None, y, n_out)
+    assert got.shape == (n_out - 3, 2)
+    for j in range(1, n_out - 2):
+        lo, hi = lttb_bucket(j, n, n_out)
+        exp = float(Fraction(lo + hi - 1, 2))
+        assert got[j - 1, 0] == exp and got[j - 1, 1] == exp, j
+
+
+def test_lttb_means_sum_in_index_order_not_exactly():
+    """The average is the binary64 sum taken in index order: 1e16 + 1 rounds
+    back to 1e16 (a tie, to even), so [1e16, 1, -1e16] averages to 0, not 1/3."""
+    n, n_out = 11, 5
+    lo, hi = lttb_bucket(1, n, n_out)
+    assert (lo, hi) == (4, 7)
+    y = np.zeros(n)
+    y[4:7] = [1e16, 1.0, -1e16]
+    got = oracle.lttb_means(None, y, n_out)
+    assert got[0, 1] == 0.0
+    assert abs(float(Fraction(1, 3)) - got[0, 1]) > 0.3
+    y[4:7] = [1.0, 1e16, -1e16]            # 1 + 1e16 rounds the same way
+    assert oracle.lttb_means(None, y, n_out)[0, 1] == 0.0
+    y[4:7] = [1e16, -1e16, 1.0]            # cancellation first: the 1 survives
+    assert oracle.lttb_means(None, y, n_out)[0, 1] == float(Fraction(1, 3))
+
+
+def test_lttb_means_nan_modes():
+    """NaN-propagate: a NaN y makes the bucket's y average NaN (its x average
+    stays finite); NaN-ignore leaves that point out of both sums and the count."""
+    n, n_out = 11, 5
+    y = np.arange(n, dtype=np.float64)
+    y[5] = np.nan
+    x = np.arange(n, dtype=np.float64) * 3.0
+    prop = oracle.lttb_means(x, y, n_out, nan="propagate")
+    assert np.isnan(prop[0, 1]) and prop[0, 0] == 15.0           # x = 12, 15, 18
+    ign = oracle.lttb_means(x, y, n_out, nan="ignore")
+    assert ign[0, 0] == 15.0 and ign[0, 1] == 5.0                # points 4 and 6
+    y[4:7] = np.nan
+    assert np.isnan(oracle.lttb_means(x, y, n_out, nan="ignore")[0]).all()   # 0 / 0
+
+
+def test_lttb_means_rejects_undefined_shapes():
+    y = np.arange(10, dtype=np.float64)
+    for n_out in (2, 10, 11):
+        with pytest.raises(oracle.OracleError):
+            oracle.lttb_means(None, y, n_out)
