@@ -40,7 +40,6 @@ namespace tsds {
 
 typedef unsigned __int128 u128;
 
-constexpr int kTableMaxK = kLttbTableMaxK;  // table mode when every bucket has <= 32 points
 
 __device__ __forceinline__ int64_t job_m(const LttbJob& J) { return J.m_dev ? *J.m_dev : J.m_host; }
 
@@ -153,21 +152,62 @@ __device__ __forceinline__ void cp_async_wait() {
 
 // Hull-table mode, larger buckets.  Most buckets get their mean from k_p32
 // (exact sums, below); a bucket it flags takes the sequential sum here, one
-// thread per bucket.  The warp's 32 buckets stream through a ring of three
-// 32-point chunks in shared memory: lane i copies point i of every flagged
-// bucket's chunk (coalesced cp.async, two chunks in flight) and thread t then
-// adds up column t, so the only serial work is the two chains of binary64
-// additions.
+// chain per bucket and coordinate.  A CTA covers 32 buckets with four warps,
+// one per SM sub-partition: two producer warps stream the flagged buckets'
+// x and y values through a ring of three 32-point chunks in shared memory
+// (lane i copies point i of each bucket's chunk: coalesced cp.async), and two
+// consumer warps add them up, thread t of the first the x values of bucket t
+// and of the second its y values.  Named barriers hand each ring slot back
+// and forth (one pair per slot, so no warp arrives twice on a barrier before
+// the others have passed it).  The consumers then do nothing but
+// shared-memory loads and one chain of binary64 additions each, and the two
+// chains of a bucket run on different sub-partitions.
 constexpr int kSumChunk = 32;
 constexpr int kSumRing = 3;
+constexpr int kSumThreads = 128;
+constexpr int kBarReady = 1;               // named barriers 1..3: slot holds a chunk
+constexpr int kBarFree = 1 + kSumRing;     // named barriers 4..6: slot may be refilled
 
 // [ring slot][point of the chunk][bucket], rows padded by one so that both
 // the copies (fixed bucket) and the adds (fixed point) spread over the banks.
+typedef double SumSlots[kSumRing][kSumChunk][33];
 struct SumRing {
-  double x[kSumRing][kSumChunk][33], y[kSumRing][kSumChunk][33];
+  SumSlots x, y;
 };
 
-__global__ void __launch_bounds__(32) k_sums_wide(const LttbJob* __restrict__ jobs) {
+__device__ __forceinline__ void named_bar_sync(int id) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "n"(kSumThreads) : "memory");
+}
+__device__ __forceinline__ void named_bar_arrive(int id) {
+  asm volatile("bar.arrive %0, %1;" ::"r"(id), "n"(kSumThreads) : "memory");
+}
+
+// One chunk of one coordinate's chain: v are the values added, y decides
+// (NaN-ignore) which points count.
+template <bool IGN>
+__device__ __forceinline__ void sums_consume(const SumSlots& v, const SumSlots& y, int slot, int t, int nn,
+                                             double& s, int64_t& cnt) {
+#pragma unroll
+  for (int i0 = 0; i0 < kSumChunk; i0 += 8) {
+    double a[8];
+    bool keep[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      a[u] = v[slot][i0 + u][t];
+      keep[u] = i0 + u < nn;
+      if (IGN) keep[u] = keep[u] && !isnan(y[slot][i0 + u][t]);
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      if (keep[u]) {
+        s = __dadd_rn(s, a[u]);
+        if (IGN) ++cnt;
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kSumThreads) k_sums_wide(const LttbJob* __restrict__ jobs) {
   const LttbJob J = jobs[blockIdx.y];
   if (J.mode != 2) return;
   const int64_t m = job_m(J), B = J.B;
@@ -175,63 +215,62 @@ __global__ void __launch_bounds__(32) k_sums_wide(const LttbJob* __restrict__ jo
   extern __shared__ __align__(16) unsigned char sum_smem[];
   SumRing& R = *reinterpret_cast<SumRing*>(sum_smem);
   __shared__ int64_t lo_s[32], n_s[32];
-  const int t = threadIdx.x;
+  __shared__ int64_t chunks_s;
+  const int warp = threadIdx.x >> 5, t = threadIdx.x & 31;
   const bool ign = J.nan == TSDS_NAN_IGNORE;
   for (int64_t jb = (int64_t)blockIdx.x * 32; jb < B; jb += (int64_t)gridDim.x * 32) {
     const int64_t j = jb + t;
-    const bool mine = j >= 1 && j < B && J.chain[j];
-    if (!__any_sync(0xffffffffu, mine)) continue;
-    const int64_t lo = mine ? bucket_start(j, m, B) : 0, hi = mine ? bucket_start(j + 1, m, B) : 0;
-    __syncwarp();
-    lo_s[t] = lo;
-    n_s[t] = hi - lo;
-    int64_t chunks = (hi - lo + kSumChunk - 1) / kSumChunk;
+    __syncthreads();                        // the previous group's readers of lo_s/n_s are done
+    if (warp == 0) {
+      const bool mine = j >= 1 && j < B && J.chain[j];
+      const int64_t lo = mine ? bucket_start(j, m, B) : 0, hi = mine ? bucket_start(j + 1, m, B) : 0;
+      lo_s[t] = lo;
+      n_s[t] = hi - lo;
+      int64_t chunks = (hi - lo + kSumChunk - 1) / kSumChunk;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) chunks = max(chunks, __shfl_xor_sync(0xffffffffu, chunks, o));
-    __syncwarp();
-    auto issue = [&](int64_t c) {
-      if (c < chunks) {
-        const int r = (int)(c % kSumRing);
-        const int64_t k = c * kSumChunk + t;
-        for (int b = 0; b < 32; ++b) {
-          if (k < n_s[b]) {
-            cp_async8(&R.x[r][t][b], J.px + lo_s[b] + k);
-            cp_async8(&R.y[r][t][b], J.py + lo_s[b] + k);
-          }
-        }
-      }
-      cp_async_commit();
-    };
-    issue(0);
-    issue(1);
-    double sx = 0.0, sy = 0.0;
-    int64_t cnt = 0;
-    for (int64_t c = 0; c < chunks; ++c) {
-      __syncwarp();                 // slot (c+2)%3 was read by the whole warp at c-1
-      issue(c + 2);
-      cp_async_wait<2>();
-      __syncwarp();                 // every lane's copies of chunk c have landed
-      const int r = (int)(c % kSumRing);
-      const int n = (int)max((int64_t)0, min((int64_t)kSumChunk, hi - lo - c * kSumChunk));
-      for (int i0 = 0; i0 < n; i0 += 8) {
-        double xv[8], yv[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          xv[u] = R.x[r][min(i0 + u, kSumChunk - 1)][t];
-          yv[u] = R.y[r][min(i0 + u, kSumChunk - 1)][t];
-        }
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          if (i0 + u < n && !(ign && isnan(yv[u]))) {
-            sx = __dadd_rn(sx, xv[u]);
-            sy = __dadd_rn(sy, yv[u]);
-            ++cnt;
-          }
-        }
-      }
+      for (int o = 16; o > 0; o >>= 1) chunks = max(chunks, __shfl_xor_sync(0xffffffffu, chunks, o));
+      if (t == 0) chunks_s = chunks;
     }
-    cp_async_wait<0>();
-    if (mine) J.means[j] = make_double2(__ddiv_rn(sx, (double)cnt), __ddiv_rn(sy, (double)cnt));
+    __syncthreads();
+    const int64_t chunks = chunks_s;
+    if (chunks == 0) continue;
+    if (warp >= 2) {
+      // producers (x, then y): fill slot c % 3 with chunk c, signal chunk c - 1 once it landed
+      const double* src = warp == 2 ? J.px : J.py;
+      SumSlots& dst = warp == 2 ? R.x : R.y;
+      for (int64_t c = 0; c <= chunks; ++c) {
+        if (c < chunks) {
+          const int slot = (int)(c % kSumRing);
+          if (c >= kSumRing) named_bar_sync(kBarFree + slot);
+          const int64_t k = c * kSumChunk + t;
+#pragma unroll 8
+          for (int b = 0; b < 32; ++b)
+            if (k < n_s[b]) cp_async8(&dst[slot][t][b], src + lo_s[b] + k);
+          cp_async_commit();
+        }
+        if (c >= 1) {
+          if (c < chunks) cp_async_wait<1>();
+          else cp_async_wait<0>();
+          named_bar_arrive(kBarReady + (int)((c - 1) % kSumRing));
+        }
+      }
+    } else {
+      // consumers: thread t of warp 0 sums bucket jb + t's x values, of warp 1 its y values
+      const int64_t n = n_s[t];
+      const SumSlots& v = warp == 0 ? R.x : R.y;
+      double s = 0.0;
+      int64_t cnt = 0;
+      for (int64_t c = 0; c < chunks; ++c) {
+        const int slot = (int)(c % kSumRing);
+        named_bar_sync(kBarReady + slot);
+        const int nn = (int)max((int64_t)0, min((int64_t)kSumChunk, n - c * kSumChunk));
+        if (ign) sums_consume<true>(v, R.y, slot, t, nn, s, cnt);
+        else sums_consume<false>(v, R.y, slot, t, nn, s, cnt);
+        if (c + kSumRing < chunks) named_bar_arrive(kBarFree + slot);
+      }
+      if (!ign) cnt = n;
+      if (n > 0) reinterpret_cast<double*>(J.means)[2 * j + warp] = __ddiv_rn(s, (double)cnt);
+    }
   }
 }
 
@@ -413,6 +452,57 @@ __device__ __forceinline__ bool filt_ok(float v) {
   return a == 0.0f || (a >= 8.6736174e-19f && a <= 1.1529215e18f);
 }
 
+// The FP32 filter.  For previous pick a and third vertex m, with al, be the
+// FP32 roundings of xa - xm and ym - ya and (ax, ay) those of a relative to
+// the bucket's first point, a point p of the bucket (relative to the same
+// first point, FP32) gets est = |al (p.y - ay) - (ax - p.x) be| and the bound
+// err = 8u (|al| (|p.y| + |ay| + |p.y - ay|) + |be| (|p.x| + |ax| + |ax - p.x|))
+// + 4u est + 2^-120 (u = 2^-24) on est's distance from its exact binary64
+// area, valid while every input passes filt_ok.  A point whose est + err is
+// below a lower bound of the best exact area cannot be the pick.  Every
+// operation is rounded to nearest and none is fused, so the computed
+// est + err is a monotone function of p.x and p.y separately, which is what
+// lets a slice's bounding box bound all of its points at once.
+struct Filt {
+  float al, be, ax, ay;
+};
+
+__device__ __forceinline__ float filt_err(const Filt& F, float apx, float apy, float ad1, float ad2, float est) {
+  const float u8 = 4.7683716e-07f;   // 8 * 2^-24
+  const float u4 = 2.3841858e-07f;   // 4 * 2^-24
+  const float tiny = 7.5231638e-37f; // 2^-120
+  const float sy = __fadd_rn(__fadd_rn(apy, fabsf(F.ay)), ad1);
+  const float sx = __fadd_rn(__fadd_rn(apx, fabsf(F.ax)), ad2);
+  const float t = __fadd_rn(__fmul_rn(fabsf(F.al), sy), __fmul_rn(fabsf(F.be), sx));
+  return __fadd_rn(__fadd_rn(__fmul_rn(u8, t), __fmul_rn(u4, est)), tiny);
+}
+
+// The signed estimate al (py - ay) - (ax - px) be: non-decreasing in py when
+// al >= 0 (non-increasing otherwise) and in px when be >= 0.
+__device__ __forceinline__ float filt_signed(const Filt& F, float px, float py) {
+  return __fsub_rn(__fmul_rn(F.al, __fsub_rn(py, F.ay)), __fmul_rn(__fsub_rn(F.ax, px), F.be));
+}
+
+// est + err of one point.
+__device__ __forceinline__ float filt_point(const Filt& F, float2 p) {
+  const float est = fabsf(filt_signed(F, p.x, p.y));
+  return __fadd_rn(est, filt_err(F, fabsf(p.x), fabsf(p.y), fabsf(__fsub_rn(p.y, F.ay)),
+                                 fabsf(__fsub_rn(F.ax, p.x)), est));
+}
+
+// An upper bound of filt_point over every point of the box (x0, x1, y0, y1):
+// the signed estimate takes its extremes at two opposite corners, and each
+// term of err its largest value at an edge of the box.
+__device__ __forceinline__ float filt_box(const Filt& F, float4 bx) {
+  const float yh = F.al >= 0.0f ? bx.w : bx.z, yl = F.al >= 0.0f ? bx.z : bx.w;
+  const float xh = F.be >= 0.0f ? bx.y : bx.x, xl = F.be >= 0.0f ? bx.x : bx.y;
+  const float est = fmaxf(fabsf(filt_signed(F, xh, yh)), fabsf(filt_signed(F, xl, yl)));
+  const float ad1 = fmaxf(fabsf(__fsub_rn(bx.z, F.ay)), fabsf(__fsub_rn(bx.w, F.ay)));
+  const float ad2 = fmaxf(fabsf(__fsub_rn(F.ax, bx.x)), fabsf(__fsub_rn(F.ax, bx.y)));
+  const float apx = fmaxf(fabsf(bx.x), fabsf(bx.y)), apy = fmaxf(fabsf(bx.z), fabsf(bx.w));
+  return __fadd_rn(est, filt_err(F, apx, apy, ad1, ad2, est));
+}
+
 // The exact pick of bucket j = [lo, hi) after previous pick a, by one warp.
 // Every point first gets an FP32 estimate of its area and a rigorous bound
 // on the estimate's error (relative to the bucket's first point, where the
@@ -431,36 +521,28 @@ __device__ __noinline__ int64_t warp_pick(const LttbJob& J, int64_t j, int64_t l
   const float ax = __double2float_rn(__dsub_rn(xa, X0)), ay = __double2float_rn(__dsub_rn(ya, Y0));
   const bool fast = filt_ok(al) && filt_ok(be) && filt_ok(ax) && filt_ok(ay) && !isnan(dxm) && !isnan(dym) &&
                     !isinf(dxm) && !isinf(dym);
-  const float u8 = 4.7683716e-07f;   // 8 * 2^-24
-  const float u4 = 2.3841858e-07f;   // 4 * 2^-24
-  const float tiny = 7.5231638e-37f; // 2^-120
+  const Filt F{al, be, ax, ay};
   uint64_t bk = 0ull;
   int64_t bi = kIdxNone;
   bool done = false;
   if (fast) {
+    // a lower bound of the best area: the largest est - err (rounded down)
     float lmax = -INFINITY;
     bool bad = false;
     for (int64_t b = lo + lane; b < hi; b += 32) {
       const float2 p = J.p32[b];
       if (!(filt_ok(p.x) && filt_ok(p.y))) { bad = true; continue; }
-      const float d1 = p.y - ay, d2 = ax - p.x;
-      const float est = fabsf(al * d1 - d2 * be);
-      const float err = u8 * (fabsf(al) * (fabsf(p.y) + fabsf(ay) + fabsf(d1)) +
-                              fabsf(be) * (fabsf(p.x) + fabsf(ax) + fabsf(d2))) + u4 * est + tiny;
-      lmax = fmaxf(lmax, est - err);
+      const float est = fabsf(filt_signed(F, p.x, p.y));
+      const float err = filt_err(F, fabsf(p.x), fabsf(p.y), fabsf(__fsub_rn(p.y, F.ay)), fabsf(__fsub_rn(F.ax, p.x)),
+                                 est);
+      lmax = fmaxf(lmax, __fsub_rd(est, err));
     }
     if (!__any_sync(0xffffffffu, bad)) {
 #pragma unroll
       for (int o = 16; o; o >>= 1) lmax = fmaxf(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
-      for (int64_t b = lo + lane; b < hi; b += 32) {
-        const float2 p = J.p32[b];
-        const float d1 = p.y - ay, d2 = ax - p.x;
-        const float est = fabsf(al * d1 - d2 * be);
-        const float err = u8 * (fabsf(al) * (fabsf(p.y) + fabsf(ay) + fabsf(d1)) +
-                                fabsf(be) * (fabsf(p.x) + fabsf(ax) + fabsf(d2))) + u4 * est + tiny;
-        if (est + err >= lmax)
+      for (int64_t b = lo + lane; b < hi; b += 32)
+        if (filt_point(F, J.p32[b]) >= lmax)
           amax_merge(bk, bi, area_key(exact_area(xa, ya, dxm, dym, J.px[b], J.py[b]), J.nan), b);
-      }
       done = true;
     }
   }
@@ -522,6 +604,8 @@ __global__ void __launch_bounds__(kHullWarps * 32) k_hull(const LttbJob* __restr
     const int64_t s0 = lo + lane * c, s1 = min(s0 + c, hi);
     int n0 = 0, n1 = 0;
     int64_t bad = INT64_MAX;
+    float4 box = make_float4(INFINITY, -INFINITY, INFINITY, -INFINITY);   // empty: x0 > x1
+    bool box_ok = true;
     for (int64_t b0 = s0; b0 < s1; b0 += 8) {
       float2 pv[8];
 #pragma unroll
@@ -531,12 +615,19 @@ __global__ void __launch_bounds__(kHullWarps * 32) k_hull(const LttbJob* __restr
         const int64_t b = b0 + u;
         if (b >= s1) break;
         const float2 p = pv[u];
-        if (!(isfinite(p.x) && isfinite(p.y))) { bad = min(bad, b); continue; }
+        if (!(isfinite(p.x) && isfinite(p.y))) { bad = min(bad, b); box_ok = false; continue; }
+        box_ok = box_ok && filt_ok(p.x) && filt_ok(p.y);
+        box.x = fminf(box.x, p.x);
+        box.y = fmaxf(box.y, p.x);
+        box.z = fminf(box.z, p.y);
+        box.w = fmaxf(box.w, p.y);
         const int32_t r = (int32_t)(b - lo);
         hull_push(H, 0, lane, n0, p, r);
         hull_push(H, 1, lane, n1, p, r);
       }
     }
+    // the slice's box for k_htable; NaN marks a slice with a value the FP32 filter cannot take
+    J.box[j * 32 + lane] = box_ok ? box : make_float4(NAN, NAN, NAN, NAN);
 #pragma unroll
     for (int o = 16; o; o >>= 1) bad = min(bad, (int64_t)__shfl_xor_sync(0xffffffffu, bad, o));
     H.n[0][lane] = n0;
@@ -591,9 +682,6 @@ __global__ void __launch_bounds__(kTableWarps * 32) k_htable(const LttbJob* __re
   if (m <= B + 2) return;
   extern __shared__ __align__(16) float2 stage[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const float u8 = 4.7683716e-07f;   // 8 * 2^-24
-  const float u4 = 2.3841858e-07f;   // 4 * 2^-24
-  const float tiny = 7.5231638e-37f; // 2^-120
   for (int64_t j = blockIdx.x; j < B; j += gridDim.x) {
     const int64_t lo = bucket_start(j, m, B), hi = bucket_start(j + 1, m, B);
     const int64_t K = hi - lo;
@@ -602,12 +690,10 @@ __global__ void __launch_bounds__(kTableWarps * 32) k_htable(const LttbJob* __re
     if (staged)
       for (int64_t i = threadIdx.x; i < K; i += blockDim.x) stage[i] = J.p32[lo + i];
     __syncthreads();
-    bool any_bad = false;
-    for (int64_t i = lane; i < K; i += 32) {
-      const float2 p = staged ? stage[i] : J.p32[lo + i];
-      any_bad |= !(filt_ok(p.x) && filt_ok(p.y));
-    }
-    any_bad = __any_sync(0xffffffffu, any_bad);
+    // lane l's slice of the bucket (the slices k_hull used) and its box
+    const int64_t cs = (K + 31) / 32;
+    const float4 mybox = J.box[j * 32 + lane];
+    const bool any_bad = __any_sync(0xffffffffu, isnan(mybox.x));
     double xm, ym;
     if (j == B - 1) { xm = J.px[m - 1]; ym = J.py[m - 1]; }
     else { const double2 cm = J.means[j + 1]; xm = cm.x; ym = cm.y; }
@@ -643,15 +729,20 @@ __global__ void __launch_bounds__(kTableWarps * 32) k_htable(const LttbJob* __re
 #pragma unroll
         for (int o = 16; o; o >>= 1) best = fmax(best, __shfl_xor_sync(0xffffffffu, best, o));
         if (best >= 0.0) {
-          float L = __double2float_rd(best);
-          for (int64_t i = lane; i < K; i += 32) {
-            const float2 p = staged ? stage[i] : J.p32[lo + i];
-            const float d1 = p.y - ay, d2 = ax - p.x;
-            const float est = fabsf(al * d1 - d2 * be);
-            const float err = u8 * (fabsf(al) * (fabsf(p.y) + fabsf(ay) + fabsf(d1)) +
-                                    fabsf(be) * (fabsf(p.x) + fabsf(ax) + fabsf(d2))) + u4 * est + tiny;
-            if (est + err >= L)
-              amax_merge(bk, bi, area_key(exact_area(xa, ya, dxm, dym, J.px[lo + i], J.py[lo + i]), J.nan), lo + i);
+          // slices whose box can reach L, then their points that can
+          const float L = __double2float_rd(best);
+          const Filt F{al, be, ax, ay};
+          unsigned live = __ballot_sync(0xffffffffu, mybox.x <= mybox.y && filt_box(F, mybox) >= L);
+          while (live) {
+            const int l = __ffs(live) - 1;
+            live &= live - 1;
+            const int64_t r1 = min((int64_t)(l + 1) * cs, K);
+            for (int64_t i = (int64_t)l * cs + lane; i < r1; i += 32) {
+              const float2 p = staged ? stage[i] : J.p32[lo + i];
+              if (filt_point(F, p) >= L)
+                amax_merge(bk, bi, area_key(exact_area(xa, ya, dxm, dym, J.px[lo + i], J.py[lo + i]), J.nan),
+                           lo + i);
+            }
           }
           done = true;
         }
@@ -850,6 +941,7 @@ size_t lttb_job_scratch(int64_t m_max, int64_t B, int64_t K) {
     s += align_up((size_t)(B + 1) * kCandMax * 4, 256);           // candidate rows 0..B
     s += 2 * align_up((size_t)B * kCandMax * 4, 256);             // table, fslot
     s += align_up((size_t)B, 256);                                // chain flags
+    s += align_up((size_t)B * 32 * sizeof(float4), 256);          // slice boxes
   }
   return s;
 }
@@ -877,6 +969,8 @@ void lttb_job_bind(LttbJob& J, char* p, int64_t m_max) {
   J.fslot = reinterpret_cast<int32_t*>(p);
   p += align_up((size_t)J.B * kCandMax * 4, 256);
   J.chain = reinterpret_cast<uint8_t*>(p);
+  p += align_up((size_t)J.B, 256);
+  J.box = reinterpret_cast<float4*>(p);
 }
 
 tsds_status launch_points_jobs(const PointsJob* jobs_dev, int count, int64_t max_m, cudaStream_t st) {
@@ -915,7 +1009,7 @@ tsds_status run_lttb_jobs(const LttbJob* jobs_host, const LttbJob* jobs_dev, int
     const int ssmem = (int)sizeof(SumRing);
     TSDS_CK(cudaFuncSetAttribute(k_sums_wide, cudaFuncAttributeMaxDynamicSharedMemorySize, ssmem));
     note_launch();
-    k_sums_wide<<<dim3((unsigned)((max_B + 31) / 32), (unsigned)count), 32, ssmem, st>>>(jobs_dev);
+    k_sums_wide<<<dim3((unsigned)((max_B + 31) / 32), (unsigned)count), kSumThreads, ssmem, st>>>(jobs_dev);
     TSDS_CK(cudaGetLastError());
     int64_t hb = (max_B + kHullWarps - 1) / kHullWarps;
     if (hb > cap) hb = cap;

@@ -39,6 +39,7 @@ struct LttbJob {
   int32_t* cand;         // mode 2: B*kLttbCandMax candidate picks per bucket (relative, -1: none)
   int32_t* fslot;        // slot of the pick among the next step's inputs (mode 0: the table itself)
   uint8_t* chain;        // mode 2: per bucket, 1 when its mean needs the sequential sum (k_sums_wide)
+  float4* box;           // mode 2: per bucket, the FP32 bounding box of each of its 32 slices
   int32_t* comp;         // per segment of 32 steps and input slot: the slot after the segment (-1: leaves the table)
   int32_t* seg_start;    // per segment: its input slot, or -1 when the chain was replayed there directly
   int64_t* out;
