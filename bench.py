@@ -58,7 +58,7 @@ def parse():
     ap.add_argument("--n-out", type=int, default=N_OUT, help="n_out of the default step (profiling other bin sizes)")
     ap.add_argument("--stream-variant", default="auto", choices=["auto", "ring", "ldg", "seg"],
                     help="kernel variant of the streaming pass (tsds_stream_variant)")
-    ap.add_argument("--suite", default=None, choices=["dtypes", "config1", "lttb", "batched", "serve"],
+    ap.add_argument("--suite", default=None, choices=["dtypes", "config1", "lttb", "batched", "serve", "values"],
                     help="instead of the headline step, measure one of the other workloads and print one JSON line")
     return ap.parse_args()
 
@@ -208,6 +208,73 @@ def suite_batched(args):
             "config": {"workload": "4096 float32 random-walk series, lengths log-uniform [1e3, 1e7] (seed 3), "
                                    "n_out uniform [200, 4000] (multiple of 4), no x; actual total reported"},
             "results": res}
+
+
+def suite_values(args):
+    """Fused value gather on the headline workload (1e9 float32 random walk, int64 geometric x,
+    n_out = 2000) and on LTTB (1e7 float64 walk, n_out = 4000): the index-only call, the *_values
+    call (indices plus x and y values from the same kernels), and the unfused alternative (the
+    index call, then torch gathers of x and y by the indices over the full output buffer)."""
+    import torch
+
+    from paper_2307_05389_gb300 import binding, inputs
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    sp = binding.ctypes.c_void_p(stream.cuda_stream)
+    res = {}
+    cases = [("minmax", 1_000_000_000, "float32", True, 2000), ("m4", 1_000_000_000, "float32", True, 2000),
+             ("lttb", 10_000_000, "float64", False, 4000), ("minmaxlttb", 10_000_000, "float64", False, 4000)]
+    cache = {}
+    for algo, n, dt, with_x, n_out in cases:
+        key = (n, dt, with_x)
+        if key not in cache:
+            cache.clear()
+            torch.cuda.empty_cache()
+            y = inputs.random_walk_cuda(n, dt, seed=2, device=dev)
+            x = inputs.geometric_x_cuda(n, seed=2, device=dev) if with_x else None
+            cache[key] = (y, x)
+        y, x = cache[key]
+        # zeros: entries past the count (empty bins) stay a valid index for the torch gathers
+        out = torch.zeros(n_out, dtype=torch.int64, device=dev)
+        cnt = torch.empty(1, dtype=torch.int64, device=dev)
+        yo = torch.empty(n_out, dtype=y.dtype, device=dev)
+        xo = torch.empty(n_out, dtype=torch.int64, device=dev) if with_x else None
+        xp = x.data_ptr() if with_x else None
+        xd = binding.DTYPES["int64"] if with_x else 0
+        common = (xp, xd, y.data_ptr(), binding.DTYPES[dt], n, n_out)
+
+        def plain():
+            _raw_call(binding, algo, x, "int64" if with_x else None, y, dt, n, n_out, out, cnt, stream)
+
+        def fused():
+            tail = (out.data_ptr(), cnt.data_ptr(), xo.data_ptr() if with_x else None, yo.data_ptr(), sp)
+            if algo == "minmaxlttb":
+                r = binding.tsds_minmaxlttb_values(*common, 4, 0, *tail)
+            else:
+                r = {"minmax": binding.tsds_minmax_values, "m4": binding.tsds_m4_values,
+                     "lttb": binding.tsds_lttb_values}[algo](*common, 0, *tail)
+            if r != 0:
+                raise RuntimeError(binding.last_error())
+
+        def unfused():
+            plain()
+            torch.index_select(y, 0, out, out=yo)
+            if with_x:
+                torch.index_select(x, 0, out, out=xo)
+        for f in (plain, fused, unfused):
+            f()
+        reps = max(10, args.steps // 5)
+        t_plain, _ = _timed_calls(torch, stream, plain, reps)
+        t_fused, _ = _timed_calls(torch, stream, fused, reps)
+        t_unfused, _ = _timed_calls(torch, stream, unfused, reps)
+        torch.cuda.synchronize()
+        k = int(cnt.item())
+        same = bool(torch.equal(yo[:k], y[out[:k]]) and (not with_x or torch.equal(xo[:k], x[out[:k]])))
+        res[algo] = {"n": n, "y": dt, "x": "int64" if with_x else None, "n_out": n_out, "index_only_ms": t_plain,
+                     "fused_values_ms": t_fused, "index_then_torch_gather_ms": t_unfused,
+                     "fused_overhead_us": (t_fused - t_plain) * 1e3, "values_match": same}
+    return {"suite": "values", "unit": "ms", "config": {"workload": "headline MinMax/M4 (1e9 float32, int64 x, "
+            "n_out=2000) and LTTB/MinMaxLTTB(4) on a 1e7 float64 walk (n_out=4000)"}, "results": res}
 
 
 def suite_serve(args):
@@ -555,7 +622,7 @@ def main():
         import paper_2307_05389_gb300 as pkg
         pkg.load()
         fn = {"dtypes": suite_dtypes, "config1": suite_config1, "lttb": suite_lttb, "batched": suite_batched,
-              "serve": suite_serve}[args.suite]
+              "serve": suite_serve, "values": suite_values}[args.suite]
         clocks = ClockSampler(0)
         out = fn(args)
         out["clocks"] = clocks.stop()

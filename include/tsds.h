@@ -108,6 +108,29 @@ tsds_status tsds_minmaxlttb(const void* x, tsds_dtype x_dtype, const void* y,
                             int64_t minmax_ratio, tsds_nan_mode nan, int64_t* out,
                             int64_t* out_count, void* stream);
 
+/* The same four algorithms with the selected points' values gathered in the
+ * kernel that writes the indices, so that a plot gets (x, y) pairs without a
+ * further pass (Section 3, Listing 2: the selected indices are used to fetch
+ * the subset of the series that is drawn).  Besides out[i]: y_out[i] = y[out[i]] (raw
+ * elements of y_dtype) and x_out[i] = x[out[i]] (raw elements of x_dtype),
+ * for i < *out_count.  Either pointer may be NULL (no copy); x_out needs x
+ * (without x the index is the x value).  y_out / x_out are device buffers of
+ * the capacity out has, aligned to their element size; TSDS_EINVAL
+ * otherwise.  Other arguments, results and errors as in the plain calls. */
+tsds_status tsds_minmax_values(const void* x, tsds_dtype x_dtype, const void* y, tsds_dtype y_dtype,
+                               int64_t n, int64_t n_out, tsds_nan_mode nan, int64_t* out,
+                               int64_t* out_count, void* x_out, void* y_out, void* stream);
+tsds_status tsds_m4_values(const void* x, tsds_dtype x_dtype, const void* y, tsds_dtype y_dtype,
+                           int64_t n, int64_t n_out, tsds_nan_mode nan, int64_t* out,
+                           int64_t* out_count, void* x_out, void* y_out, void* stream);
+tsds_status tsds_lttb_values(const void* x, tsds_dtype x_dtype, const void* y, tsds_dtype y_dtype,
+                             int64_t n, int64_t n_out, tsds_nan_mode nan, int64_t* out,
+                             int64_t* out_count, void* x_out, void* y_out, void* stream);
+tsds_status tsds_minmaxlttb_values(const void* x, tsds_dtype x_dtype, const void* y, tsds_dtype y_dtype,
+                                   int64_t n, int64_t n_out, int64_t minmax_ratio, tsds_nan_mode nan,
+                                   int64_t* out, int64_t* out_count, void* x_out, void* y_out,
+                                   void* stream);
+
 /* ---- Batched form: many series of one dtype in one launch sequence.
  *
  * The paper parallelises one series over CPU threads (Section 2.2, the

@@ -16,6 +16,7 @@ from .binding import (  # noqa: F401
     TsdsError,
     Plan,
     downsample,
+    downsample_values,
     downsample_batched,
     downsample_host,
     tsds_batched,
@@ -28,6 +29,10 @@ from .binding import (  # noqa: F401
     load,
     tsds_lttb,
     tsds_lttb_means,
+    tsds_lttb_values,
+    tsds_m4_values,
+    tsds_minmax_values,
+    tsds_minmaxlttb_values,
     tsds_m4,
     tsds_minmax,
     tsds_minmaxlttb,

@@ -80,6 +80,12 @@ def load(path: str = LIB_PATH):
     lib.tsds_stream_variant.restype = c_int
     lib.tsds_lttb_means.argtypes = [p, c_int, p, c_int, i64, i64, c_int, p, p]
     lib.tsds_lttb_means.restype = c_int
+    for name in ("tsds_minmax_values", "tsds_m4_values", "tsds_lttb_values"):
+        f = getattr(lib, name)
+        f.argtypes = [p, c_int, p, c_int, i64, i64, c_int, p, p, p, p, p]
+        f.restype = c_int
+    lib.tsds_minmaxlttb_values.argtypes = [p, c_int, p, c_int, i64, i64, i64, c_int, p, p, p, p, p]
+    lib.tsds_minmaxlttb_values.restype = c_int
     _lib = lib
     return lib
 
@@ -135,6 +141,24 @@ def tsds_lttb(x, x_dtype, y, y_dtype, n, n_out, nan, out, out_count, stream):
 
 def tsds_lttb_means(x, x_dtype, y, y_dtype, n, n_out, nan, means, stream):
     return load().tsds_lttb_means(x, x_dtype, y, y_dtype, n, n_out, nan, means, stream)
+
+
+def tsds_minmax_values(x, x_dtype, y, y_dtype, n, n_out, nan, out, out_count, x_out, y_out, stream):
+    return load().tsds_minmax_values(x, x_dtype, y, y_dtype, n, n_out, nan, out, out_count, x_out, y_out, stream)
+
+
+def tsds_m4_values(x, x_dtype, y, y_dtype, n, n_out, nan, out, out_count, x_out, y_out, stream):
+    return load().tsds_m4_values(x, x_dtype, y, y_dtype, n, n_out, nan, out, out_count, x_out, y_out, stream)
+
+
+def tsds_lttb_values(x, x_dtype, y, y_dtype, n, n_out, nan, out, out_count, x_out, y_out, stream):
+    return load().tsds_lttb_values(x, x_dtype, y, y_dtype, n, n_out, nan, out, out_count, x_out, y_out, stream)
+
+
+def tsds_minmaxlttb_values(x, x_dtype, y, y_dtype, n, n_out, minmax_ratio, nan, out, out_count, x_out, y_out,
+                           stream):
+    return load().tsds_minmaxlttb_values(x, x_dtype, y, y_dtype, n, n_out, minmax_ratio, nan, out, out_count,
+                                         x_out, y_out, stream)
 
 
 def tsds_minmaxlttb(x, x_dtype, y, y_dtype, n, n_out, minmax_ratio, nan, out, out_count, stream):
@@ -442,6 +466,47 @@ def lttb_means(y, n_out, x=None, nan="propagate"):
     return means
 
 
+def downsample_values(algo, y, n_out, x=None, nan="propagate", minmax_ratio=4):
+    """Indices selected by `algo` with the selected points' values gathered in the same
+    launch: returns (indices, x_values or None, y_values), CUDA tensors trimmed to the count
+    (one device-to-host read of the count)."""
+    import torch
+    if not (y.is_cuda and y.dim() == 1 and y.is_contiguous()):
+        raise ValueError("y must be a contiguous 1-D CUDA tensor")
+    n = y.shape[0]
+    if x is not None and not (x.is_cuda and x.dim() == 1 and x.is_contiguous() and x.shape[0] == n):
+        raise ValueError("x must be a contiguous 1-D CUDA tensor as long as y")
+    dev = y.device
+    cap = out_capacity(algo, n, n_out)
+    out = torch.empty(cap, dtype=torch.int64, device=dev)
+    cnt = torch.empty(1, dtype=torch.int64, device=dev)
+    y_out = torch.empty(cap, dtype=y.dtype, device=dev)
+    x_out = torch.empty(cap, dtype=x.dtype, device=dev) if x is not None else None
+    st = torch.cuda.current_stream(dev)
+    xp = x.data_ptr() if x is not None else None
+    xd = DTYPES[_torch_dtype_name(x)] if x is not None else 0
+    args = (xp, xd, y.data_ptr(), DTYPES[_torch_dtype_name(y)], n, n_out)
+    tail = (out.data_ptr(), cnt.data_ptr(), x_out.data_ptr() if x_out is not None else None, y_out.data_ptr(),
+            ctypes.c_void_p(st.cuda_stream))
+    with torch.cuda.device(dev):
+        if algo == "minmax":
+            r = tsds_minmax_values(*args, NAN_MODES[nan], *tail)
+        elif algo == "m4":
+            r = tsds_m4_values(*args, NAN_MODES[nan], *tail)
+        elif algo == "lttb":
+            r = tsds_lttb_values(*args, NAN_MODES[nan], *tail)
+        elif algo == "minmaxlttb":
+            r = tsds_minmaxlttb_values(*args, minmax_ratio, NAN_MODES[nan], *tail)
+        else:
+            raise ValueError(f"unknown algorithm {algo!r}")
+    if r != 0:
+        raise TsdsError(r, last_error())
+    k = int(cnt.item())
+    if k < 0:
+        raise TsdsError(-k, "the streaming pass reported a device-side failure")
+    return out[:k], (x_out[:k] if x_out is not None else None), y_out[:k]
+
+
 def downsample(algo, y, n_out, x=None, nan="propagate", minmax_ratio=4, out=None, out_count=None,
                stream=None, sync=True):
     """Indices selected by `algo` ("minmax", "m4", "lttb", "minmaxlttb") on y (and x).
@@ -483,6 +548,8 @@ def downsample(algo, y, n_out, x=None, nan="propagate", minmax_ratio=4, out=None
     if not sync:
         return out, out_count
     k = int(out_count.item())
+    if k < 0:
+        raise TsdsError(-k, "the streaming pass reported a device-side failure")
     return out[:k]
 
 

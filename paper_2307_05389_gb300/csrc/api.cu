@@ -172,7 +172,7 @@ static BinnedLayout binned_layout(int64_t nb, int64_t windows) {
 // with idx_bias added to every index.
 tsds_status run_binned_series(const void* x, tsds_dtype x_dtype, const void* y, tsds_dtype y_dtype,
                               int64_t n, int64_t nb, tsds_nan_mode nan, Algo algo, int64_t* out,
-                              int64_t* out_count, int64_t idx_bias, cudaStream_t st) {
+                              int64_t* out_count, int64_t idx_bias, cudaStream_t st, const Gather* g) {
   if (small_call(n, nb, y_dtype)) {
     // a small call: one launch (after the edge search when x is given)
     const size_t o_res = align_up((size_t)(nb + 1) * 8, 256);
@@ -192,6 +192,7 @@ tsds_status run_binned_series(const void* x, tsds_dtype x_dtype, const void* y, 
     S.out = out;
     S.out_count = out_count;
     S.idx_bias = idx_bias;
+    if (g) S.g = *g;
     if (x) TSDS_CK(launch_edges(nullptr, 1, &S, true, x_dtype, nb, st));
     void* tok;
     timing_begin(st, &tok);
@@ -231,6 +232,7 @@ tsds_status run_binned_series(const void* x, tsds_dtype x_dtype, const void* y, 
   S.out = out;
   S.out_count = out_count;
   S.idx_bias = idx_bias;
+  if (g) S.g = *g;
   TSDS_CK(launch_edges(nullptr, 1, &S, x != nullptr, x_dtype, nb, st));
   void* tok;
   timing_begin(st, &tok);
@@ -243,11 +245,34 @@ tsds_status run_binned_series(const void* x, tsds_dtype x_dtype, const void* y, 
   return TSDS_OK;
 }
 
+// Checks the optional value outputs and fills g (null g when there are none).
+static tsds_status gather_args(const void* x, tsds_dtype x_dtype, tsds_dtype y_dtype, void* x_out, void* y_out,
+                               Gather& g, const Gather*& gp) {
+  gp = nullptr;
+  if (!x_out && !y_out) return TSDS_OK;
+  if (x_out && !x) return fail(TSDS_EINVAL, "x_out needs x (without x the index is the x value)");
+  g.y_size = (int)dtype_size(y_dtype);
+  g.x_size = x ? (int)dtype_size(x_dtype) : 0;
+  if (y_out && reinterpret_cast<uintptr_t>(y_out) % (uintptr_t)g.y_size != 0)
+    return fail(TSDS_EINVAL, "y_out is not aligned to its %d-byte elements", g.y_size);
+  if (x_out && reinterpret_cast<uintptr_t>(x_out) % (uintptr_t)g.x_size != 0)
+    return fail(TSDS_EINVAL, "x_out is not aligned to its %d-byte elements", g.x_size);
+  g.y_out = y_out;
+  g.x_out = x_out;
+  gp = &g;
+  return TSDS_OK;
+}
+
 static tsds_status run_binned(Algo algo, const void* x, tsds_dtype x_dtype, const void* y,
                               tsds_dtype y_dtype, int64_t n, int64_t n_out, tsds_nan_mode nan,
-                              int64_t* out, int64_t* out_count, void* stream) {
+                              int64_t* out, int64_t* out_count, void* stream, void* x_out = nullptr,
+                              void* y_out = nullptr) {
   g_err[0] = 0;
   tsds_status s = check_common(x, x_dtype, y, y_dtype, n, nan, out, out_count);
+  if (s != TSDS_OK) return s;
+  Gather g;
+  const Gather* gp;
+  s = gather_args(x, x_dtype, y_dtype, x_out, y_out, g, gp);
   if (s != TSDS_OK) return s;
   const int per_bin = algo == ALGO_MINMAX ? 2 : 4;
   if (n_out < per_bin || n_out % per_bin != 0)
@@ -259,10 +284,10 @@ static tsds_status run_binned(Algo algo, const void* x, tsds_dtype x_dtype, cons
     return TSDS_OK;
   }
   if (n_out >= n) {
-    TSDS_CK(launch_iota(out, n, out_count, st));
+    TSDS_CK(launch_iota(out, n, out_count, st, y, x, gp));
     return TSDS_OK;
   }
-  return run_binned_series(x, x_dtype, y, y_dtype, n, n_out / per_bin, nan, algo, out, out_count, 0, st);
+  return run_binned_series(x, x_dtype, y, y_dtype, n, n_out / per_bin, nan, algo, out, out_count, 0, st, gp);
 }
 
 }  // namespace tsds
@@ -283,27 +308,74 @@ tsds_status tsds_m4(const void* x, tsds_dtype x_dtype, const void* y, tsds_dtype
   return run_binned(ALGO_M4, x, x_dtype, y, y_dtype, n, n_out, nan, out, out_count, stream);
 }
 
-tsds_status tsds_lttb(const void* x, tsds_dtype x_dtype, const void* y, tsds_dtype y_dtype,
-                      int64_t n, int64_t n_out, tsds_nan_mode nan, int64_t* out,
-                      int64_t* out_count, void* stream) {
+static tsds_status lttb_entry(const void* x, tsds_dtype x_dtype, const void* y, tsds_dtype y_dtype, int64_t n,
+                              int64_t n_out, tsds_nan_mode nan, int64_t* out, int64_t* out_count, void* stream,
+                              void* x_out, void* y_out) {
   g_err[0] = 0;
   tsds_status s = check_common(x, x_dtype, y, y_dtype, n, nan, out, out_count);
   if (s != TSDS_OK) return s;
   if (n_out < 3) return fail(TSDS_EINVAL, "LTTB needs n_out >= 3 (got %lld)", (long long)n_out);
-  return run_lttb(x, x_dtype, y, y_dtype, n, n_out, nan, out, out_count, static_cast<cudaStream_t>(stream));
+  Gather g;
+  const Gather* gp;
+  s = gather_args(x, x_dtype, y_dtype, x_out, y_out, g, gp);
+  if (s != TSDS_OK) return s;
+  return run_lttb(x, x_dtype, y, y_dtype, n, n_out, nan, out, out_count, static_cast<cudaStream_t>(stream),
+                  nullptr, gp);
 }
 
-tsds_status tsds_minmaxlttb(const void* x, tsds_dtype x_dtype, const void* y, tsds_dtype y_dtype,
-                            int64_t n, int64_t n_out, int64_t minmax_ratio, tsds_nan_mode nan,
-                            int64_t* out, int64_t* out_count, void* stream) {
+static tsds_status minmaxlttb_entry(const void* x, tsds_dtype x_dtype, const void* y, tsds_dtype y_dtype,
+                                    int64_t n, int64_t n_out, int64_t minmax_ratio, tsds_nan_mode nan, int64_t* out,
+                                    int64_t* out_count, void* stream, void* x_out, void* y_out) {
   g_err[0] = 0;
   tsds_status s = check_common(x, x_dtype, y, y_dtype, n, nan, out, out_count);
   if (s != TSDS_OK) return s;
   if (n_out < 3) return fail(TSDS_EINVAL, "MinMaxLTTB needs n_out >= 3 (got %lld)", (long long)n_out);
   if (minmax_ratio < 1) return fail(TSDS_EINVAL, "minmax_ratio must be >= 1 (got %lld)", (long long)minmax_ratio);
   if (minmax_ratio > (INT64_MAX / 4) / n_out) return fail(TSDS_EINVAL, "n_out * minmax_ratio overflows");
+  Gather g;
+  const Gather* gp;
+  s = gather_args(x, x_dtype, y_dtype, x_out, y_out, g, gp);
+  if (s != TSDS_OK) return s;
   return run_minmaxlttb(x, x_dtype, y, y_dtype, n, n_out, minmax_ratio, nan, out, out_count,
-                        static_cast<cudaStream_t>(stream));
+                        static_cast<cudaStream_t>(stream), gp);
+}
+
+tsds_status tsds_lttb(const void* x, tsds_dtype x_dtype, const void* y, tsds_dtype y_dtype,
+                      int64_t n, int64_t n_out, tsds_nan_mode nan, int64_t* out,
+                      int64_t* out_count, void* stream) {
+  return lttb_entry(x, x_dtype, y, y_dtype, n, n_out, nan, out, out_count, stream, nullptr, nullptr);
+}
+
+tsds_status tsds_minmaxlttb(const void* x, tsds_dtype x_dtype, const void* y, tsds_dtype y_dtype,
+                            int64_t n, int64_t n_out, int64_t minmax_ratio, tsds_nan_mode nan,
+                            int64_t* out, int64_t* out_count, void* stream) {
+  return minmaxlttb_entry(x, x_dtype, y, y_dtype, n, n_out, minmax_ratio, nan, out, out_count, stream, nullptr,
+                          nullptr);
+}
+
+tsds_status tsds_minmax_values(const void* x, tsds_dtype x_dtype, const void* y, tsds_dtype y_dtype, int64_t n,
+                               int64_t n_out, tsds_nan_mode nan, int64_t* out, int64_t* out_count, void* x_out,
+                               void* y_out, void* stream) {
+  return run_binned(ALGO_MINMAX, x, x_dtype, y, y_dtype, n, n_out, nan, out, out_count, stream, x_out, y_out);
+}
+
+tsds_status tsds_m4_values(const void* x, tsds_dtype x_dtype, const void* y, tsds_dtype y_dtype, int64_t n,
+                           int64_t n_out, tsds_nan_mode nan, int64_t* out, int64_t* out_count, void* x_out,
+                           void* y_out, void* stream) {
+  return run_binned(ALGO_M4, x, x_dtype, y, y_dtype, n, n_out, nan, out, out_count, stream, x_out, y_out);
+}
+
+tsds_status tsds_lttb_values(const void* x, tsds_dtype x_dtype, const void* y, tsds_dtype y_dtype, int64_t n,
+                             int64_t n_out, tsds_nan_mode nan, int64_t* out, int64_t* out_count, void* x_out,
+                             void* y_out, void* stream) {
+  return lttb_entry(x, x_dtype, y, y_dtype, n, n_out, nan, out, out_count, stream, x_out, y_out);
+}
+
+tsds_status tsds_minmaxlttb_values(const void* x, tsds_dtype x_dtype, const void* y, tsds_dtype y_dtype, int64_t n,
+                                   int64_t n_out, int64_t minmax_ratio, tsds_nan_mode nan, int64_t* out,
+                                   int64_t* out_count, void* x_out, void* y_out, void* stream) {
+  return minmaxlttb_entry(x, x_dtype, y, y_dtype, n, n_out, minmax_ratio, nan, out, out_count, stream, x_out,
+                          y_out);
 }
 
 tsds_status tsds_lttb_means(const void* x, tsds_dtype x_dtype, const void* y, tsds_dtype y_dtype,

@@ -141,6 +141,28 @@ __device__ __forceinline__ int64_t warp_lower_bound(int64_t lo, int64_t hi, Pred
   return hi;
 }
 
+// Fused value gather -------------------------------------------------------
+// dst[pos] = src[idx] for raw elements of `size` bytes (1, 2, 4 or 8).
+__device__ __forceinline__ void gather_elem(void* dst, int64_t pos, const void* src, int64_t idx, int size) {
+  switch (size) {
+    case 1: static_cast<uint8_t*>(dst)[pos] = static_cast<const uint8_t*>(src)[idx]; break;
+    case 2: static_cast<uint16_t*>(dst)[pos] = static_cast<const uint16_t*>(src)[idx]; break;
+    case 4: static_cast<uint32_t*>(dst)[pos] = static_cast<const uint32_t*>(src)[idx]; break;
+    default: static_cast<uint64_t*>(dst)[pos] = static_cast<const uint64_t*>(src)[idx]; break;
+  }
+}
+
+__device__ __forceinline__ void gather_point(const Gather& g, int64_t pos, const void* y, const void* x, int64_t idx) {
+  if (g.y_out) gather_elem(g.y_out, pos, y, idx, g.y_size);
+  if (g.x_out) gather_elem(g.x_out, pos, x, idx, g.x_size);
+}
+
+// out[pos] = v + bias, with the values of point v of the series beside it.
+__device__ __forceinline__ void emit_point(const SeriesDev& S, int64_t pos, int64_t v) {
+  S.out[pos] = v + S.idx_bias;
+  gather_point(S.g, pos, S.y, S.x, v);
+}
+
 // Load helpers -------------------------------------------------------------
 template <class T>
 __device__ __forceinline__ T ldg_elem(const T* p) { return __ldg(p); }

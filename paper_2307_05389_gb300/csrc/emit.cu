@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit(const SeriesDev* __restri
   int64_t off = warp_tot[warp] + incl - local;
   for (int64_t b = b0; b < b1; ++b) {
     const int k = bin_select<ALGO>(S, b, v);
-    for (int i = 0; i < k; ++i) S.out[off + i] = v[i] + S.idx_bias;
+    for (int i = 0; i < k; ++i) emit_point(S, off + i, v[i]);
     off += k;
   }
   if (tid == 0 && S.out_count) *S.out_count = total_sh;
@@ -161,7 +161,7 @@ __global__ void __launch_bounds__(kTileThreads) k_emit_write(SeriesDev S, const 
   int64_t v[4];
   for (int64_t b = b0; b < b1; ++b) {
     const int k = bin_select<ALGO>(S, b, v);
-    for (int i = 0; i < k; ++i) S.out[off + i] = v[i] + S.idx_bias;
+    for (int i = 0; i < k; ++i) emit_point(S, off + i, v[i]);
     off += k;
   }
   if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0 && S.out_count) *S.out_count = base + total;

@@ -13,6 +13,16 @@ constexpr int kStreamThreads = 256;   // 8 warps per CTA
 
 enum Algo : int { ALGO_MINMAX = 0, ALGO_M4 = 1 };
 
+// Optional fused value gather: beside each index the kernel that writes
+// out[i] also copies the selected point's raw y element to y_out[i] and its
+// raw x element to x_out[i] (either pointer may be null).
+struct Gather {
+  void* y_out;
+  void* x_out;
+  int y_size;
+  int x_size;
+};
+
 // One series as the binned kernels see it.  For a single call there is one;
 // the batched launch passes an array.
 struct SeriesDev {
@@ -29,6 +39,7 @@ struct SeriesDev {
   int64_t idx_bias;   // added to every index written (1 for the MinMaxLTTB interior)
   const unsigned long long* status;  // device status word of the streaming pass (null: none);
                                      // non-zero makes emit report -status as the count
+  Gather g;           // values written beside the indices (y[v], x[v] for index v + idx_bias)
 };
 
 // Partial argmin/argmax of one bin piece: ordered 64-bit keys plus indices.
@@ -135,8 +146,9 @@ constexpr int64_t kEmitTiledMinBins = 16384;
 int64_t emit_tiles(int64_t nb);
 cudaError_t launch_emit_tiled(const SeriesDev& single, Algo algo, int64_t* tile_count, cudaStream_t st);
 
-// out[i] = i + offset for i < n, *count = n.
-cudaError_t launch_iota(int64_t* out, int64_t n, int64_t* count, cudaStream_t st);
+// out[i] = i for i < n, *count = n; with a gather, y_out[i] = y[i] and x_out[i] = x[i].
+cudaError_t launch_iota(int64_t* out, int64_t n, int64_t* count, cudaStream_t st, const void* y = nullptr,
+                        const void* x = nullptr, const Gather* g = nullptr);
 
 int device_sm_count();
 

@@ -49,6 +49,13 @@ __device__ __forceinline__ int64_t bucket_start(int64_t j, int64_t m, int64_t B)
 
 __device__ __forceinline__ int64_t out_index(const LttbJob& J, int64_t k) { return J.R ? J.R[k] : k + J.bias; }
 
+// out[pos] = the series index of point k, with its values beside it.
+__device__ __forceinline__ void lttb_emit(const LttbJob& J, int64_t pos, int64_t k) {
+  const int64_t i = out_index(J, k);
+  J.out[pos] = i;
+  gather_point(J.g, pos, J.ysrc, J.xsrc, i);
+}
+
 __device__ __forceinline__ double load_as_f64(const void* p, int dt, int64_t i) {
   switch (dt) {
     case TSDS_I8: return (double)static_cast<const int8_t*>(p)[i];
@@ -344,7 +351,10 @@ __device__ __forceinline__ bool exact_finish(const ExactSum& e, int cnt, double&
 
 // p32[k] = point k relative to its bucket's first point, rounded to FP32: a
 // warp per bucket, coalesced.  The same pass adds the bucket up exactly
-// (ExactSum) and writes its mean, or flags the bucket for k_sums_wide.
+// (ExactSum) and writes its mean, or flags the bucket for k_sums_wide.  When
+// x is the index, k - start is an integer below 2^53: its FP32 rounding comes
+// straight from the integer, and the x sum is an integer sum, exact while the
+// bucket's indices add up to less than 2^53.
 __global__ void k_p32(const LttbJob* __restrict__ jobs) {
   const LttbJob J = jobs[blockIdx.y];
   if (J.mode != 2) return;
@@ -352,6 +362,7 @@ __global__ void k_p32(const LttbJob* __restrict__ jobs) {
   if (m <= B + 2) return;
   const int lane = threadIdx.x & 31;
   const bool ign = J.nan == TSDS_NAN_IGNORE;
+  const bool xi = J.x_index != 0;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t j = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); j < B; j += warps) {
     const int64_t lo = bucket_start(j, m, B), hi = bucket_start(j + 1, m, B);
@@ -359,24 +370,29 @@ __global__ void k_p32(const LttbJob* __restrict__ jobs) {
     ExactSum ex, ey;
     exact_init(ex);
     exact_init(ey);
+    unsigned long long isum = 0;             // x sum when x is the index (wraps only when unused)
     bool bad = hi - lo > (int64_t)1 << 30;
+    const bool small = hi - lo < (int64_t)1 << 31;   // offsets fit an int
     int cnt = 0;
     for (int64_t k0 = lo + lane; k0 < hi; k0 += 128) {
       double xv[4], yv[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const int64_t k = k0 + 32 * u;
-        xv[u] = k < hi ? J.px[k] : 0.0;
+        xv[u] = !xi && k < hi ? J.px[k] : 0.0;
         yv[u] = k < hi ? J.py[k] : 0.0;
       }
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const int64_t k = k0 + 32 * u;
         if (k < hi) {
-          J.p32[k] = make_float2(__double2float_rn(__dsub_rn(xv[u], X0)), __double2float_rn(__dsub_rn(yv[u], Y0)));
+          const float fx = !xi ? __double2float_rn(__dsub_rn(xv[u], X0))
+                           : small ? __int2float_rn((int)(k - lo)) : __ll2float_rn(k - lo);
+          J.p32[k] = make_float2(fx, __double2float_rn(__dsub_rn(yv[u], Y0)));
           if (!(ign && isnan(yv[u]))) {
             ++cnt;
-            exact_add(ex, xv[u], bad);
+            if (xi) isum += (unsigned long long)k;
+            else exact_add(ex, xv[u], bad);
             exact_add(ey, yv[u], bad);
           }
         }
@@ -386,7 +402,16 @@ __global__ void k_p32(const LttbJob* __restrict__ jobs) {
     cnt = (int)__reduce_add_sync(0xffffffffu, (unsigned)cnt);
     bad = __any_sync(0xffffffffu, bad) || cnt == 0;
     double sx = 0.0, sy = 0.0;
-    const bool okx = exact_finish(ex, cnt, sx);
+    bool okx;
+    if (xi) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) isum += __shfl_xor_sync(0xffffffffu, isum, o);
+      // every partial sum is at most hi * cnt: below 2^53 they are all exact binary64 additions
+      okx = (double)hi * (double)cnt < 9007199254740992.0;
+      sx = __ll2double_rn((long long)isum);
+    } else {
+      okx = exact_finish(ex, cnt, sx);
+    }
     const bool oky = exact_finish(ey, cnt, sy);
     const bool exact = !bad && okx && oky;
     if (lane == 0) {
@@ -437,7 +462,7 @@ __global__ void __launch_bounds__(32) k_chase(const LttbJob* __restrict__ jobs) 
   const int lane = threadIdx.x & 31;
   const int64_t m = job_m(J), B = J.B;
   if (m <= B + 2) {
-    for (int64_t i = lane; i < m; i += 32) J.out[i] = out_index(J, i);
+    for (int64_t i = lane; i < m; i += 32) lttb_emit(J, i, i);
     if (lane == 0) *J.out_count = m;
   }
 }
@@ -555,13 +580,18 @@ __device__ __noinline__ int64_t warp_pick(const LttbJob& J, int64_t j, int64_t l
 
 // Candidates of every bucket, one warp per bucket: each lane builds the upper
 // and lower hulls of its slice of the bucket (Andrew's monotone chain over the
-// FP32 points, x ascending), then pairs of neighbouring slice hulls are merged
+// FP32 points, x ascending, after the Akl-Toussaint test against the
+// bucket's extreme points has set aside the points that cannot be vertices),
+// then pairs of neighbouring slice hulls are merged
 // in five rounds (lane 2i takes lane 2i+1's lists, lane 4i lane 4i+2's, ...),
 // all stacks in shared memory.  Lane 0 writes candidate row j+1 (the row the
 // step after bucket j reads): the first point, the first non-finite point,
 // then hull vertices, at most kCandMax, -1 after.  A stack that would
 // overflow replaces its top, so an unusually long hull only yields fewer
-// useful candidates (the chase then computes those steps directly).
+// useful candidates (the chase then computes those steps directly).  The
+// candidates only steer the work: the tables scan every point a candidate's
+// bound cannot exclude, so FP32 hulls that miss a vertex cost time, not
+// correctness.
 constexpr int kHullWarps = 4;
 constexpr int kSliceStack = 24;    // per lane and hull
 
@@ -577,16 +607,31 @@ __device__ __forceinline__ float cross3(float2 o, float2 a, float2 b) {
 }
 
 // Pushes (p, r) onto column `col` of stack h (upper: pops on left or straight
-// turns, lower: on right or straight turns).
-__device__ __forceinline__ void hull_push(HullWarp& H, int h, int col, int& n, float2 p, int32_t r) {
+// turns, lower: on right or straight turns).  t1 and t2 mirror the stack's
+// top two points in registers, so a push that pops nothing reads no shared
+// memory.
+__device__ __forceinline__ void hull_push(HullWarp& H, int h, int col, int& n, float2& t1, float2& t2, float2 p,
+                                          int32_t r) {
   while (n >= 2) {
-    const float c = cross3(H.p[h][n - 2][col], H.p[h][n - 1][col], p);
-    if (h == 0 ? c >= 0.0f : c <= 0.0f) --n;
-    else break;
+    const float c = cross3(t2, t1, p);
+    if (h == 0 ? c >= 0.0f : c <= 0.0f) {
+      --n;
+      t1 = t2;
+      if (n >= 2) t2 = H.p[h][n - 2][col];
+    } else {
+      break;
+    }
   }
-  if (n == kSliceStack) --n;
+  if (n == kSliceStack) {      // full: the new point replaces the top
+    H.p[h][n - 1][col] = p;
+    H.r[h][n - 1][col] = r;
+    t1 = p;
+    return;
+  }
   H.p[h][n][col] = p;
   H.r[h][n][col] = r;
+  t2 = t1;
+  t1 = p;
   ++n;
 }
 
@@ -602,7 +647,40 @@ __global__ void __launch_bounds__(kHullWarps * 32) k_hull(const LttbJob* __restr
     const int64_t lo = bucket_start(j, m, B), hi = bucket_start(j + 1, m, B);
     const int64_t c = (hi - lo + 31) / 32;
     const int64_t s0 = lo + lane * c, s1 = min(s0 + c, hi);
+    // Akl-Toussaint: with F, L the bucket's first and last finite points and T, D
+    // its highest and lowest, a point strictly below the polyline F-T-L is no
+    // vertex of the upper hull, one strictly above F-D-L none of the lower hull
+    int64_t kf = INT64_MAX, kl = -1, kt = INT64_MAX, kd = INT64_MAX;
+    float ty = -INFINITY, dy = INFINITY;
+    for (int64_t k0 = lo + lane; k0 < hi; k0 += 128) {
+      float2 pv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) pv[u] = k0 + 32 * u < hi ? J.p32[k0 + 32 * u] : make_float2(NAN, NAN);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int64_t k = k0 + 32 * u;
+        const float2 p = pv[u];
+        if (!(isfinite(p.x) && isfinite(p.y))) continue;
+        kf = min(kf, k);
+        kl = max(kl, k);
+        if (p.y > ty || (p.y == ty && k < kt)) { ty = p.y; kt = k; }
+        if (p.y < dy || (p.y == dy && k < kd)) { dy = p.y; kd = k; }
+      }
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+      kf = min(kf, (int64_t)__shfl_xor_sync(0xffffffffu, kf, o));
+      kl = max(kl, (int64_t)__shfl_xor_sync(0xffffffffu, kl, o));
+      const float ty2 = __shfl_xor_sync(0xffffffffu, ty, o), dy2 = __shfl_xor_sync(0xffffffffu, dy, o);
+      const int64_t kt2 = __shfl_xor_sync(0xffffffffu, kt, o), kd2 = __shfl_xor_sync(0xffffffffu, kd, o);
+      if (ty2 > ty || (ty2 == ty && kt2 < kt)) { ty = ty2; kt = kt2; }
+      if (dy2 < dy || (dy2 == dy && kd2 < kd)) { dy = dy2; kd = kd2; }
+    }
+    const bool some = kl >= 0;
+    const float2 pF = some ? J.p32[kf] : make_float2(0.f, 0.f), pL = some ? J.p32[kl] : pF;
+    const float2 pT = some ? J.p32[kt] : pF, pD = some ? J.p32[kd] : pF;
     int n0 = 0, n1 = 0;
+    float2 u1 = make_float2(0.f, 0.f), u2 = u1, l1 = u1, l2 = u1;   // tops of the two stacks
     int64_t bad = INT64_MAX;
     float4 box = make_float4(INFINITY, -INFINITY, INFINITY, -INFINITY);   // empty: x0 > x1
     bool box_ok = true;
@@ -622,8 +700,10 @@ __global__ void __launch_bounds__(kHullWarps * 32) k_hull(const LttbJob* __restr
         box.z = fminf(box.z, p.y);
         box.w = fmaxf(box.w, p.y);
         const int32_t r = (int32_t)(b - lo);
-        hull_push(H, 0, lane, n0, p, r);
-        hull_push(H, 1, lane, n1, p, r);
+        const float cu = p.x <= pT.x ? cross3(pF, pT, p) : cross3(pT, pL, p);
+        const float cl = p.x <= pD.x ? cross3(pF, pD, p) : cross3(pD, pL, p);
+        if (!(cu < 0.0f)) hull_push(H, 0, lane, n0, u1, u2, p, r);
+        if (!(cl > 0.0f)) hull_push(H, 1, lane, n1, l1, l2, p, r);
       }
     }
     // the slice's box for k_htable; NaN marks a slice with a value the FP32 filter cannot take
@@ -638,26 +718,46 @@ __global__ void __launch_bounds__(kHullWarps * 32) k_hull(const LttbJob* __restr
         const int src = lane + d;
         for (int h = 0; h < 2; ++h) {
           int n = H.n[h][lane];
+          float2 t1 = make_float2(0.f, 0.f), t2 = t1;
+          if (n >= 1) t1 = H.p[h][n - 1][lane];
+          if (n >= 2) t2 = H.p[h][n - 2][lane];
           const int ns = H.n[h][src];
-          for (int i = 0; i < ns; ++i) hull_push(H, h, lane, n, H.p[h][i][src], H.r[h][i][src]);
+          for (int i = 0; i < ns; ++i) hull_push(H, h, lane, n, t1, t2, H.p[h][i][src], H.r[h][i][src]);
           H.n[h][lane] = n;
         }
       }
     }
     __syncwarp();
-    if (lane == 0 && j + 1 <= B) {
-      int32_t* row = J.cand + (j + 1) * kCandMax;
-      int nc = 0;
-      auto add = [&](int32_t r) {
-        for (int i = 0; i < nc; ++i)
-          if (row[i] == r) return;
-        if (nc < kCandMax) row[nc++] = r;
+    if (j + 1 <= B) {
+      // the list 0, [first non-finite point], upper hull, lower hull (lane 0's
+      // merged stacks); its first occurrences, at most kCandMax, in order
+      static_assert(kCandMax == 32 && 2 + 2 * kSliceStack <= 64, "one row per warp, two entries per lane");
+      const int nu = H.n[0][0], nl = H.n[1][0];
+      const int hb = bad < hi ? 1 : 0;
+      const int total = 1 + hb + nu + nl;
+      auto entry = [&](int e) -> int32_t {
+        if (e == 0) return 0;
+        if (hb && e == 1) return (int32_t)(bad - lo);
+        e -= 1 + hb;
+        return e < nu ? H.r[0][e][0] : H.r[1][e - nu][0];
       };
-      add(0);
-      if (bad < hi) add((int32_t)(bad - lo));
-      for (int h = 0; h < 2; ++h)
-        for (int i = 0; i < H.n[h][0]; ++i) add(H.r[h][i][0]);
-      for (int i = nc; i < kCandMax; ++i) row[i] = -1;
+      int32_t v[2];
+      bool keep[2];
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const int e = lane + 32 * q;
+        keep[q] = e < total;
+        v[q] = keep[q] ? entry(e) : -1;
+        for (int f = 0; keep[q] && f < e; ++f)
+          if (entry(f) == v[q]) keep[q] = false;
+      }
+      const unsigned k0 = __ballot_sync(0xffffffffu, keep[0]), k1 = __ballot_sync(0xffffffffu, keep[1]);
+      const unsigned below = (1u << lane) - 1u;
+      const int p0 = __popc(k0 & below), p1 = __popc(k0) + __popc(k1 & below);
+      int32_t* row = J.cand + (j + 1) * kCandMax;
+      if (keep[0] && p0 < kCandMax) row[p0] = v[0];
+      if (keep[1] && p1 < kCandMax) row[p1] = v[1];
+      if (lane >= __popc(k0) + __popc(k1)) row[lane] = -1;
     }
     __syncwarp();
   }
@@ -719,19 +819,27 @@ __global__ void __launch_bounds__(kTableWarps * 32) k_htable(const LttbJob* __re
                         !isnan(dym) && !isinf(dxm) && !isinf(dym);
       bool done = false;
       if (fast) {
-        // lower bound from the exact areas of the bucket's own candidates
-        double best = -1.0;
+        // lower bound: the exact area of the bucket's own candidate with the
+        // largest FP32 estimate
+        const Filt F{al, be, ax, ay};
+        float e = -1.0f;
         if (own >= 0) {
-          const double ar = exact_area(xa, ya, dxm, dym, J.px[lo + own], J.py[lo + own]);
-          if (isfinite(ar)) best = ar;
-          amax_merge(bk, bi, area_key(ar, J.nan), lo + own);
+          const float2 p = staged ? stage[own] : J.p32[lo + own];
+          e = fabsf(filt_signed(F, p.x, p.y));
         }
+        float emax = e;
 #pragma unroll
-        for (int o = 16; o; o >>= 1) best = fmax(best, __shfl_xor_sync(0xffffffffu, best, o));
+        for (int o = 16; o; o >>= 1) emax = fmaxf(emax, __shfl_xor_sync(0xffffffffu, emax, o));
+        const unsigned who = __ballot_sync(0xffffffffu, own >= 0 && e == emax);
+        const int32_t r_best = __shfl_sync(0xffffffffu, own, who ? __ffs(who) - 1 : 0);
+        double best = -1.0;
+        if (who) {
+          const double ar = exact_area(xa, ya, dxm, dym, J.px[lo + r_best], J.py[lo + r_best]);
+          if (isfinite(ar)) best = ar;
+        }
         if (best >= 0.0) {
           // slices whose box can reach L, then their points that can
           const float L = __double2float_rd(best);
-          const Filt F{al, be, ax, ay};
           unsigned live = __ballot_sync(0xffffffffu, mybox.x <= mybox.y && filt_box(F, mybox) >= L);
           while (live) {
             const int l = __ffs(live) - 1;
@@ -834,7 +942,7 @@ __global__ void __launch_bounds__(32) k_chain_seg(const LttbJob* __restrict__ jo
     cp_async_commit();
   };
   for (int b = 0; b < kChaseRing - 1; ++b) issue(b);
-  if (lane == 0) J.out[0] = out_index(J, 0);
+  if (lane == 0) lttb_emit(J, 0, 0);
   int32_t s = 0;        // input slot of the current segment (-1: the previous pick is not a table input)
   int64_t a = 0;        // the previous pick, when s < 0
   for (int64_t b = 0; b < nblk; ++b) {
@@ -859,7 +967,7 @@ __global__ void __launch_bounds__(32) k_chain_seg(const LttbJob* __restrict__ jo
         int32_t rel;
         if (s >= 0) rel = J.table[j * W + s];
         else rel = (int32_t)(warp_pick(J, j, lo, hi, a, m, B, lane) - lo);
-        if (lane == 0) J.out[j + 1] = out_index(J, lo + rel);
+        if (lane == 0) lttb_emit(J, j + 1, lo + rel);
         a = lo + rel;
         s = j + 1 < B ? next_slot(J, j, rel, lane) : 0;
         lo = hi;
@@ -868,7 +976,7 @@ __global__ void __launch_bounds__(32) k_chain_seg(const LttbJob* __restrict__ jo
     __syncwarp();
   }
   if (lane == 0) {
-    J.out[B + 1] = out_index(J, m - 1);
+    lttb_emit(J, B + 1, m - 1);
     *J.out_count = B + 2;
   }
 }
@@ -898,7 +1006,7 @@ __global__ void __launch_bounds__(kSegWarpsC * 32) k_replay(const LttbJob* __res
       s = fr[w][t][s];
       s = (s >= 0 && s < W) ? s : 0;   // only the last step's slot can be outside the table
     }
-    if (lane < len) J.out[j0 + lane + 1] = out_index(J, bucket_start(j0 + lane, m, B) + mine);
+    if (lane < len) lttb_emit(J, j0 + lane + 1, bucket_start(j0 + lane, m, B) + mine);
     __syncwarp();
   }
 }
@@ -1049,8 +1157,8 @@ tsds_status run_lttb_jobs(const LttbJob* jobs_host, const LttbJob* jobs_dev, int
 // set, otherwise m_host; m_max bounds it), writing R[pick] (or pick) to out.
 static tsds_status lttb_points_core(const double* px, const double* py, const int64_t* m_dev, int64_t m_host,
                                     int64_t m_max, int64_t n_out, tsds_nan_mode nan, const int64_t* R,
-                                    int64_t* out, int64_t* out_count, cudaStream_t st,
-                                    double* means_out = nullptr) {
+                                    int64_t* out, int64_t* out_count, cudaStream_t st, bool x_index,
+                                    double* means_out, const void* y, const void* x, const Gather* g) {
   LttbJob J;
   memset(&J, 0, sizeof J);
   J.px = px;
@@ -1063,6 +1171,12 @@ static tsds_status lttb_points_core(const double* px, const double* py, const in
   J.R = R;
   J.out = out;
   J.out_count = out_count;
+  J.x_index = x_index ? 1 : 0;
+  if (g) {
+    J.g = *g;
+    J.ysrc = y;
+    J.xsrc = x;
+  }
   Scratch s;
   const size_t js = lttb_job_scratch(m_max, J.B, J.K);
   TSDS_CK(scratch_alloc(s, js + align_up(sizeof(LttbJob), 256), st));
@@ -1099,13 +1213,13 @@ static tsds_status points(const void* x, tsds_dtype x_dtype, const void* y, tsds
 
 tsds_status run_lttb(const void* x, tsds_dtype x_dtype, const void* y, tsds_dtype y_dtype, int64_t n,
                      int64_t n_out, tsds_nan_mode nan, int64_t* out, int64_t* out_count, cudaStream_t st,
-                     double* means_out) {
+                     double* means_out, const Gather* g) {
   if (n == 0) {
     TSDS_CK(cudaMemsetAsync(out_count, 0, sizeof(int64_t), st));
     return TSDS_OK;
   }
   if (n_out >= n) {
-    TSDS_CK(launch_iota(out, n, out_count, st));
+    TSDS_CK(launch_iota(out, n, out_count, st, y, x, g));
     return TSDS_OK;
   }
   Scratch s;
@@ -1115,25 +1229,26 @@ tsds_status run_lttb(const void* x, tsds_dtype x_dtype, const void* y, tsds_dtyp
   double* px = reinterpret_cast<double*>(static_cast<char*>(s.p) + pb);
   tsds_status r = points(x, x_dtype, y, y_dtype, nullptr, nullptr, n, n, px, py, st);
   if (r != TSDS_OK) return r;
-  return lttb_points_core(px, py, nullptr, n, n, n_out, nan, nullptr, out, out_count, st, means_out);
+  return lttb_points_core(px, py, nullptr, n, n, n_out, nan, nullptr, out, out_count, st, x == nullptr, means_out,
+                          y, x, g);
 }
 
 tsds_status run_minmaxlttb(const void* x, tsds_dtype x_dtype, const void* y, tsds_dtype y_dtype,
                            int64_t n, int64_t n_out, int64_t minmax_ratio, tsds_nan_mode nan,
-                           int64_t* out, int64_t* out_count, cudaStream_t st) {
+                           int64_t* out, int64_t* out_count, cudaStream_t st, const Gather* g) {
   if (n == 0) {
     TSDS_CK(cudaMemsetAsync(out_count, 0, sizeof(int64_t), st));
     return TSDS_OK;
   }
   if (n_out >= n) {
-    TSDS_CK(launch_iota(out, n, out_count, st));
+    TSDS_CK(launch_iota(out, n, out_count, st, y, x, g));
     return TSDS_OK;
   }
   const int64_t n_sel = 2 * ((n_out * minmax_ratio) / 2);
   const int64_t n_in = n - 2;
   if (n_sel >= n_in) {
     // the preselection keeps every interior point: plain LTTB
-    return run_lttb(x, x_dtype, y, y_dtype, n, n_out, nan, out, out_count, st);
+    return run_lttb(x, x_dtype, y, y_dtype, n, n_out, nan, out, out_count, st, nullptr, g);
   }
   const int64_t m_max = n_sel + 2;
   Scratch s;
@@ -1154,7 +1269,7 @@ tsds_status run_minmaxlttb(const void* x, tsds_dtype x_dtype, const void* y, tsd
   TSDS_CK(cudaGetLastError());
   r = points(x, x_dtype, y, y_dtype, R, counts + 1, 0, m_max, px, py, st);
   if (r != TSDS_OK) return r;
-  return lttb_points_core(px, py, counts + 1, 0, m_max, n_out, nan, R, out, out_count, st);
+  return lttb_points_core(px, py, counts + 1, 0, m_max, n_out, nan, R, out, out_count, st, false, nullptr, y, x, g);
 }
 
 }  // namespace tsds

@@ -9,16 +9,17 @@ tsds_status fail(tsds_status s, const char* fmt, ...);
 
 tsds_status run_binned_series(const void* x, tsds_dtype x_dtype, const void* y, tsds_dtype y_dtype,
                               int64_t n, int64_t nb, tsds_nan_mode nan, Algo algo, int64_t* out,
-                              int64_t* out_count, int64_t idx_bias, cudaStream_t st);
+                              int64_t* out_count, int64_t idx_bias, cudaStream_t st, const Gather* g = nullptr);
 
 // means_out (optional, device): the averages of buckets 1..B-1 as (x, y) pairs
+// g (optional): values written beside the indices
 tsds_status run_lttb(const void* x, tsds_dtype x_dtype, const void* y, tsds_dtype y_dtype, int64_t n,
                      int64_t n_out, tsds_nan_mode nan, int64_t* out, int64_t* out_count, cudaStream_t st,
-                     double* means_out = nullptr);
+                     double* means_out = nullptr, const Gather* g = nullptr);
 
 tsds_status run_minmaxlttb(const void* x, tsds_dtype x_dtype, const void* y, tsds_dtype y_dtype,
                            int64_t n, int64_t n_out, int64_t minmax_ratio, tsds_nan_mode nan,
-                           int64_t* out, int64_t* out_count, cudaStream_t st);
+                           int64_t* out, int64_t* out_count, cudaStream_t st, const Gather* g = nullptr);
 
 // One LTTB problem over m binary64 points (see lttb.cu).
 struct LttbJob {
@@ -31,6 +32,7 @@ struct LttbJob {
   int nan;
   int mode;              // 0: transition table over whole buckets (K <= kLttbTableMaxK),
                          // 2: transition table over each bucket's hull candidates
+  int x_index;           // 1: px[k] == k (no x, every point kept)
   const int64_t* R;      // point -> output index (null: index + bias)
   int64_t bias;
   double2* means;        // B+1 entries
@@ -44,6 +46,9 @@ struct LttbJob {
   int32_t* seg_start;    // per segment: its input slot, or -1 when the chain was replayed there directly
   int64_t* out;
   int64_t* out_count;
+  const void* ysrc;      // with g: the series the output indices point into
+  const void* xsrc;
+  Gather g;              // values written beside the indices (null pointers: none)
 };
 
 // Gathers points as binary64: px[k] = x[i] or i, py[k] = y[i], i = R[k] or k.

@@ -23,6 +23,8 @@
 
 #include <mutex>
 
+#include <string.h>
+
 #include "internal.h"
 
 namespace tsds {
@@ -147,6 +149,7 @@ extern "C" tsds_status tsds_minmax_noalloc(const void* x, tsds_dtype x_dtype, co
   // keeps whatever the previous call left in it
   NA_CK(cudaMemsetAsync(base + off_cnt, 0, off_first - off_cnt, st));
   SeriesDev S;
+  memset(&S, 0, sizeof S);
   S.y = y;
   S.x = x;
   S.n = n;

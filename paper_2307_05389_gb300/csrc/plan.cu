@@ -132,7 +132,7 @@ cudaError_t launch_window_map(const SeriesDev* s_dev, int count, int32_t* win_se
 __global__ void k_iota_batched(const SeriesDev* sd) {
   const SeriesDev S = sd[blockIdx.x];
   if (S.nb != 0) return;
-  for (int64_t i = threadIdx.x; i < S.n; i += blockDim.x) S.out[i] = i + S.idx_bias;
+  for (int64_t i = threadIdx.x; i < S.n; i += blockDim.x) emit_point(S, i, i);
   if (threadIdx.x == 0) *S.out_count = S.n;
 }
 
@@ -142,19 +142,23 @@ cudaError_t launch_iota_batched(const SeriesDev* s_dev, int count, cudaStream_t 
   return cudaGetLastError();
 }
 
-__global__ void k_iota(int64_t* out, int64_t n, int64_t* count) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+__global__ void k_iota(int64_t* out, int64_t n, int64_t* count, const void* y, const void* x, Gather g) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     out[i] = i;
+    gather_point(g, i, y, x, i);
+  }
   if (blockIdx.x == 0 && threadIdx.x == 0 && count) *count = n;
 }
 
-cudaError_t launch_iota(int64_t* out, int64_t n, int64_t* count, cudaStream_t st) {
+cudaError_t launch_iota(int64_t* out, int64_t n, int64_t* count, cudaStream_t st, const void* y, const void* x,
+                        const Gather* g) {
   int64_t blocks = (n + 255) / 256;
   if (blocks < 1) blocks = 1;
   int cap = device_sm_count() * 8;
   if (blocks > cap) blocks = cap;
+  Gather none{nullptr, nullptr, 0, 0};
   note_launch();
-  k_iota<<<(unsigned)blocks, 256, 0, st>>>(out, n, count);
+  k_iota<<<(unsigned)blocks, 256, 0, st>>>(out, n, count, y, x, g ? *g : none);
   return cudaGetLastError();
 }
 

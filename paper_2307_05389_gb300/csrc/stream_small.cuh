@@ -104,7 +104,7 @@ __global__ void __launch_bounds__(kSmallThreads) k_small(SeriesDev S, unsigned* 
   int64_t off = warp_tot[warp] + incl - local;
   for (int64_t q = b0; q < b1; ++q) {
     const int k = small_select<ALGO>(S, q, v);
-    for (int i = 0; i < k; ++i) S.out[off + i] = v[i] + S.idx_bias;
+    for (int i = 0; i < k; ++i) emit_point(S, off + i, v[i]);
     off += k;
   }
   if (threadIdx.x == 0 && S.out_count) *S.out_count = total;

@@ -106,3 +106,16 @@ def test_series_array_matches_the_struct_layout():
     assert (s.x, s.y, s.n, s.n_out, s.out, s.out_count) == (0x9100, 0x2000, 101, 12, 0x20040, 0x30008)
     a = binding._series_array(ys, [8, 12, 16], None, outs, counts)
     assert (a[:, 0] == 0).all()
+
+
+def test_value_outputs_are_checked_on_the_host(lib):
+    """x_out without x, and value buffers not aligned to their elements, are
+    rejected before anything runs."""
+    y, out, cnt = 1 << 20, 1 << 21, 1 << 22
+    for fn in (binding.tsds_minmax_values, binding.tsds_m4_values, binding.tsds_lttb_values):
+        assert fn(None, 0, y, 9, 100, 8, 0, out, cnt, 1 << 23, None, None) == 1      # x_out, no x
+        assert "x_out" in pkg.last_error()
+        assert fn(None, 0, y, 9, 100, 8, 0, out, cnt, None, (1 << 23) + 2, None) == 1  # float32 y_out
+        assert "aligned" in pkg.last_error()
+        assert fn(1 << 24, 3, y, 9, 100, 8, 0, out, cnt, (1 << 23) + 4, None, None) == 1  # int64 x_out
+    assert binding.tsds_minmaxlttb_values(None, 0, y, 9, 100, 8, 4, 0, out, cnt, 1 << 23, None, None) == 1
