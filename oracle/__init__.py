@@ -59,7 +59,7 @@ def _load():
     lib.orc_bin_edges.restype = i64
     lib.orc_argminmax.argtypes = [p, c_int, i64, i64, c_int, p, p]
     lib.orc_argminmax.restype = c_int
-    for name in ("orc_minmax", "orc_m4", "orc_lttb"):
+    for name in ("orc_minmax", "orc_m4", "orc_lttb", "orc_everynth"):
         f = getattr(lib, name)
         f.argtypes = [p, c_int, p, c_int, i64, i64, c_int, p]
         f.restype = i64
@@ -123,6 +123,10 @@ def lttb(x, y, n_out, nan="propagate"):
     return _call("orc_lttb", x, y, n_out, nan)
 
 
+def everynth(x, y, n_out, nan="propagate"):
+    return _call("orc_everynth", x, y, n_out, nan)
+
+
 def minmaxlttb(x, y, n_out, minmax_ratio=4, nan="propagate"):
     return _call("orc_minmaxlttb", x, y, n_out, nan, extra=(minmax_ratio,))
 
@@ -136,6 +140,8 @@ def downsample(algo, x, y, n_out, nan="propagate", minmax_ratio=4):
         return lttb(x, y, n_out, nan)
     if algo == "minmaxlttb":
         return minmaxlttb(x, y, n_out, minmax_ratio, nan)
+    if algo == "everynth":
+        return everynth(x, y, n_out, nan)
     raise ValueError(algo)
 
 

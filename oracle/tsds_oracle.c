@@ -269,6 +269,24 @@ int64_t orc_m4(const void* x, int x_dtype, const void* y, int y_dtype, int64_t n
   return binned(x, x_dtype, y, y_dtype, n, n_out, nan_mode, out, 4);
 }
 
+/* EveryNth (Section 1 names it; the reading here): n_out bins laid out as
+ * MinMax/M4 lay them out (index space without x, equal-width x ranges with
+ * x), and the first point of every non-empty bin. */
+int64_t orc_everynth(const void* x, int x_dtype, const void* y, int y_dtype, int64_t n,
+                     int64_t n_out, int nan_mode, int64_t* out) {
+  (void)nan_mode;
+  if (!args_ok(x, x_dtype, y, y_dtype, n) || n_out < 1) return ORC_EINVAL;
+  if (n_out >= n) return all_indices(n, out);
+  int64_t* s = (int64_t*)malloc((size_t)(n_out + 1) * sizeof(int64_t));
+  if (!s) return ORC_EINVAL;
+  orc_bin_edges(x, x_dtype, n, n_out, s);
+  int64_t cnt = 0;
+  for (int64_t b = 0; b < n_out; ++b)
+    if (s[b] < s[b + 1]) out[cnt++] = s[b];
+  free(s);
+  return cnt;
+}
+
 /* ---------------------------------------------------------------- LTTB */
 
 /* Bucket j of B over points 1..m-2 starts at 1 + floor(j*(m-2)/B). */

@@ -53,6 +53,11 @@ int64_t orc_lttb(const void* x, int x_dtype, const void* y, int y_dtype, int64_t
 int64_t orc_minmaxlttb(const void* x, int x_dtype, const void* y, int y_dtype, int64_t n,
                        int64_t n_out, int64_t minmax_ratio, int nan_mode, int64_t* out);
 
+/* EveryNth (reading): the first point of each non-empty bin of the MinMax/M4
+ * bin layout with n_out bins; n_out >= 1. */
+int64_t orc_everynth(const void* x, int x_dtype, const void* y, int y_dtype, int64_t n,
+                     int64_t n_out, int nan_mode, int64_t* out);
+
 /* The LTTB bucket chain on points already converted to binary64 (px may be
  * NULL: x = index).  Exposed so the tests can pin the chain on hand-built
  * point sets. */

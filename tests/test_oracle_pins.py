@@ -514,3 +514,65 @@ def test_lttb_means_rejects_undefined_shapes():
     for n_out in (2, 10, 11):
         with pytest.raises(oracle.OracleError):
             oracle.lttb_means(None, y, n_out)
+
+
+# ----------------------------------------------------------------------------- EveryNth
+
+@pytest.mark.parametrize("n,n_out", [(11, 3), (1000, 7), (1001, 1000), (100_003, 999), (10 ** 6, 4000)])
+def test_everynth_closed_form_without_x(n, n_out):
+    """No x: the first index of each of n_out equal index bins, ceil(i(n-1)/n_out):
+    exactly n_out strictly increasing picks starting at 0 (exact integer arithmetic)."""
+    y = np.zeros(n, dtype=np.float32)
+    got = oracle.everynth(None, y, n_out)
+    exp = [-((-i * (n - 1)) // n_out) for i in range(n_out)]
+    np.testing.assert_array_equal(got, exp)
+    assert got[0] == 0 and np.all(np.diff(got) >= 1)
+
+
+def test_everynth_brute_force_integer_x():
+    """Sorted integer x with gaps and repeats: bin i is {j : (x_j - x_0) n_out in
+    [i span, (i+1) span)}; the pick is its first j, scanned exactly."""
+    rng = np.random.default_rng(41)
+    for trial in range(200):
+        n = int(rng.integers(2, 60))
+        n_out = int(rng.integers(1, n))
+        xs = np.cumsum(rng.integers(0, 4, size=n)).astype(np.int64)
+        xs[0] = 0
+        exp = [s for s, e in zip(bf_edges_int_x(xs.tolist(), n_out)[:-1], bf_edges_int_x(xs.tolist(), n_out)[1:])
+               if s < e]
+        got = oracle.everynth(xs, np.zeros(n), n_out)
+        np.testing.assert_array_equal(got, exp, err_msg=f"trial {trial}")
+
+
+@pytest.mark.parametrize("x_dtype", ["int64", "float64", "uint32"])
+def test_everynth_equal_x_matches_no_x(x_dtype):
+    n = 50_001
+    y = inputs.random_walk(n, "float32", 3)
+    for n_out in (10, 999, 5000):
+        np.testing.assert_array_equal(oracle.everynth(np.arange(n).astype(x_dtype), y, n_out),
+                                      oracle.everynth(None, y, n_out))
+
+
+def test_everynth_is_the_first_pick_of_each_m4_bin():
+    """With the same bins (M4 with 4 n_out), EveryNth is the first M4 pick of each
+    non-empty bin: a subset of M4 of one pick per bin."""
+    n = 20_011
+    y = inputs.random_walk(n, "float32", 4)
+    x = inputs.geometric_x(n, 4)
+    for xx in (None, x):
+        for n_out in (7, 250, 3000):
+            e = oracle.everynth(xx, y, n_out)
+            m4 = oracle.m4(xx, y, 4 * n_out)
+            assert set(e.tolist()) <= set(m4.tolist())
+            s = oracle.bin_edges(xx, n, n_out)
+            assert len(e) == int(np.sum(s[1:] > s[:-1]))
+
+
+def test_everynth_degenerate_shapes():
+    y = np.arange(5, dtype=np.float64)
+    np.testing.assert_array_equal(oracle.everynth(None, y, 5), np.arange(5))
+    np.testing.assert_array_equal(oracle.everynth(None, y, 9), np.arange(5))
+    np.testing.assert_array_equal(oracle.everynth(None, y, 1), [0])
+    assert len(oracle.everynth(None, y[:0], 3)) == 0
+    with pytest.raises(oracle.OracleError):
+        oracle.everynth(None, y, 0)
