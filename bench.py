@@ -86,7 +86,8 @@ def _raw_call(binding, algo, x, x_dtype, y, y_dtype, n, n_out, out, cnt, stream,
         r = binding.tsds_minmaxlttb(xp, xd, y.data_ptr(), binding.DTYPES[y_dtype], n, n_out, ratio, nan,
                                     out.data_ptr(), cnt.data_ptr(), sp)
     else:
-        fn = {"minmax": binding.tsds_minmax, "m4": binding.tsds_m4, "lttb": binding.tsds_lttb}[algo]
+        fn = {"minmax": binding.tsds_minmax, "m4": binding.tsds_m4, "lttb": binding.tsds_lttb,
+              "everynth": binding.tsds_everynth}[algo]
         r = fn(xp, xd, y.data_ptr(), binding.DTYPES[y_dtype], n, n_out, nan, out.data_ptr(), cnt.data_ptr(), sp)
     if r != 0:
         raise RuntimeError(binding.last_error())
@@ -223,6 +224,7 @@ def suite_values(args):
     sp = binding.ctypes.c_void_p(stream.cuda_stream)
     res = {}
     cases = [("minmax", 1_000_000_000, "float32", True, 2000), ("m4", 1_000_000_000, "float32", True, 2000),
+             ("everynth", 1_000_000_000, "float32", True, 2000),
              ("lttb", 10_000_000, "float64", False, 4000), ("minmaxlttb", 10_000_000, "float64", False, 4000)]
     cache = {}
     for algo, n, dt, with_x, n_out in cases:
@@ -252,7 +254,8 @@ def suite_values(args):
                 r = binding.tsds_minmaxlttb_values(*common, 4, 0, *tail)
             else:
                 r = {"minmax": binding.tsds_minmax_values, "m4": binding.tsds_m4_values,
-                     "lttb": binding.tsds_lttb_values}[algo](*common, 0, *tail)
+                     "lttb": binding.tsds_lttb_values, "everynth": binding.tsds_everynth_values}[algo](*common, 0,
+                                                                                                     *tail)
             if r != 0:
                 raise RuntimeError(binding.last_error())
 
@@ -373,7 +376,8 @@ def suite_serve(args):
 
 
 def suite_config1(args):
-    """10^6-point float32 random walk (seed 0), no x, n_out = 1000: latency of each algorithm."""
+    """10^6-point float32 random walk (seed 0), no x, n_out = 1000: latency of each algorithm
+    (EveryNth included: the paper reports it as constant time, Section 4)."""
     import torch
 
     from paper_2307_05389_gb300 import binding, inputs
@@ -384,7 +388,7 @@ def suite_config1(args):
     out = torch.empty(n_out, dtype=torch.int64, device=dev)
     cnt = torch.empty(1, dtype=torch.int64, device=dev)
     res = {}
-    for algo in ("minmax", "m4", "lttb", "minmaxlttb"):
+    for algo in ("minmax", "m4", "lttb", "minmaxlttb", "everynth"):
         f = lambda: _raw_call(binding, algo, None, None, y, "float32", n, n_out, out, cnt, stream)
         for _ in range(5):
             f()

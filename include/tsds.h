@@ -108,7 +108,17 @@ tsds_status tsds_minmaxlttb(const void* x, tsds_dtype x_dtype, const void* y,
                             int64_t minmax_ratio, tsds_nan_mode nan, int64_t* out,
                             int64_t* out_count, void* stream);
 
-/* The same four algorithms with the selected points' values gathered in the
+/* EveryNth (Section 1 names it among the algorithms; reading): the n_out bins
+ * MinMax/M4 lay out (index space without x: bin i starts at
+ * ceil(i(n-1)/n_out); equal-width x ranges with x) and the first point of
+ * every non-empty bin, so exactly n_out points without x.  No y value is
+ * read (y is still required, for a uniform interface, and nan is accepted
+ * and unused).  n >= 0; n_out >= 1. */
+tsds_status tsds_everynth(const void* x, tsds_dtype x_dtype, const void* y, tsds_dtype y_dtype,
+                          int64_t n, int64_t n_out, tsds_nan_mode nan, int64_t* out,
+                          int64_t* out_count, void* stream);
+
+/* The same algorithms with the selected points' values gathered in the
  * kernel that writes the indices, so that a plot gets (x, y) pairs without a
  * further pass (Section 3, Listing 2: the selected indices are used to fetch
  * the subset of the series that is drawn).  Besides out[i]: y_out[i] = y[out[i]] (raw
@@ -130,6 +140,9 @@ tsds_status tsds_minmaxlttb_values(const void* x, tsds_dtype x_dtype, const void
                                    int64_t n, int64_t n_out, int64_t minmax_ratio, tsds_nan_mode nan,
                                    int64_t* out, int64_t* out_count, void* x_out, void* y_out,
                                    void* stream);
+tsds_status tsds_everynth_values(const void* x, tsds_dtype x_dtype, const void* y, tsds_dtype y_dtype,
+                                 int64_t n, int64_t n_out, tsds_nan_mode nan, int64_t* out,
+                                 int64_t* out_count, void* x_out, void* y_out, void* stream);
 
 /* ---- Batched form: many series of one dtype in one launch sequence.
  *

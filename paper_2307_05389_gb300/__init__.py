@@ -1,5 +1,5 @@
-"""GB300-native downsampling for line-chart visualisation: MinMax, M4, LTTB and
-MinMaxLTTB (the algorithms of tsdownsample, arXiv 2307.05389) as hand-written
+"""GB300-native downsampling for line-chart visualisation: MinMax, M4, LTTB,
+MinMaxLTTB and EveryNth (the algorithms of tsdownsample, arXiv 2307.05389) as hand-written
 sm_103a CUDA kernels behind a C ABI (include/tsds.h).
 
 ``binding`` holds the ctypes entry points (same names as the C ABI) and the
@@ -8,6 +8,7 @@ seeded synthetic series used by the tests and the benchmark.
 """
 from .binding import (  # noqa: F401
     DTYPES,
+    EveryNthDownsampler,
     M4Downsampler,
     LTTBDownsampler,
     MinMaxDownsampler,
@@ -27,6 +28,8 @@ from .binding import (  # noqa: F401
     tsds_plan_info,
     last_error,
     load,
+    tsds_everynth,
+    tsds_everynth_values,
     tsds_lttb,
     tsds_lttb_means,
     tsds_lttb_values,

@@ -43,7 +43,7 @@ def load(path: str = LIB_PATH):
         raise RuntimeError(f"{path} is missing: build it with `python -m paper_2307_05389_gb300.build`")
     lib = ctypes.CDLL(path)
     p, i64, c_int = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
-    for name in ("tsds_minmax", "tsds_m4", "tsds_lttb"):
+    for name in ("tsds_minmax", "tsds_m4", "tsds_lttb", "tsds_everynth"):
         f = getattr(lib, name)
         f.argtypes = [p, c_int, p, c_int, i64, i64, c_int, p, p, p]
         f.restype = c_int
@@ -80,7 +80,7 @@ def load(path: str = LIB_PATH):
     lib.tsds_stream_variant.restype = c_int
     lib.tsds_lttb_means.argtypes = [p, c_int, p, c_int, i64, i64, c_int, p, p]
     lib.tsds_lttb_means.restype = c_int
-    for name in ("tsds_minmax_values", "tsds_m4_values", "tsds_lttb_values"):
+    for name in ("tsds_minmax_values", "tsds_m4_values", "tsds_lttb_values", "tsds_everynth_values"):
         f = getattr(lib, name)
         f.argtypes = [p, c_int, p, c_int, i64, i64, c_int, p, p, p, p, p]
         f.restype = c_int
@@ -137,6 +137,14 @@ def tsds_m4(x, x_dtype, y, y_dtype, n, n_out, nan, out, out_count, stream):
 
 def tsds_lttb(x, x_dtype, y, y_dtype, n, n_out, nan, out, out_count, stream):
     return load().tsds_lttb(x, x_dtype, y, y_dtype, n, n_out, nan, out, out_count, stream)
+
+
+def tsds_everynth(x, x_dtype, y, y_dtype, n, n_out, nan, out, out_count, stream):
+    return load().tsds_everynth(x, x_dtype, y, y_dtype, n, n_out, nan, out, out_count, stream)
+
+
+def tsds_everynth_values(x, x_dtype, y, y_dtype, n, n_out, nan, out, out_count, x_out, y_out, stream):
+    return load().tsds_everynth_values(x, x_dtype, y, y_dtype, n, n_out, nan, out, out_count, x_out, y_out, stream)
 
 
 def tsds_lttb_means(x, x_dtype, y, y_dtype, n, n_out, nan, means, stream):
@@ -495,6 +503,8 @@ def downsample_values(algo, y, n_out, x=None, nan="propagate", minmax_ratio=4):
             r = tsds_m4_values(*args, NAN_MODES[nan], *tail)
         elif algo == "lttb":
             r = tsds_lttb_values(*args, NAN_MODES[nan], *tail)
+        elif algo == "everynth":
+            r = tsds_everynth_values(*args, NAN_MODES[nan], *tail)
         elif algo == "minmaxlttb":
             r = tsds_minmaxlttb_values(*args, minmax_ratio, NAN_MODES[nan], *tail)
         else:
@@ -509,7 +519,7 @@ def downsample_values(algo, y, n_out, x=None, nan="propagate", minmax_ratio=4):
 
 def downsample(algo, y, n_out, x=None, nan="propagate", minmax_ratio=4, out=None, out_count=None,
                stream=None, sync=True):
-    """Indices selected by `algo` ("minmax", "m4", "lttb", "minmaxlttb") on y (and x).
+    """Indices selected by `algo` ("minmax", "m4", "lttb", "minmaxlttb", "everynth") on y (and x).
 
     y and x are 1-D CUDA tensors (contiguous).  With sync=True the result is
     trimmed to the selected count (one device-to-host read of the count);
@@ -539,6 +549,8 @@ def downsample(algo, y, n_out, x=None, nan="propagate", minmax_ratio=4, out=None
             r = tsds_m4(*args, *tail)
         elif algo == "lttb":
             r = tsds_lttb(*args, *tail)
+        elif algo == "everynth":
+            r = tsds_everynth(*args, *tail)
         elif algo == "minmaxlttb":
             r = tsds_minmaxlttb(*args, minmax_ratio, *tail)
         else:
@@ -593,6 +605,10 @@ class _Downsampler:
 
 class MinMaxDownsampler(_Downsampler):
     algo = "minmax"
+
+
+class EveryNthDownsampler(_Downsampler):
+    algo = "everynth"
 
 
 class M4Downsampler(_Downsampler):

@@ -245,6 +245,31 @@ tsds_status run_binned_series(const void* x, tsds_dtype x_dtype, const void* y, 
   return TSDS_OK;
 }
 
+// EveryNth: the bin starts (index space or x space, as for MinMax/M4) with
+// n_out bins, then the emit of the first point of every non-empty bin.
+static tsds_status run_everynth(const void* x, tsds_dtype x_dtype, int64_t n, int64_t nb, int64_t* out,
+                                int64_t* out_count, cudaStream_t st, const void* y, const Gather* g) {
+  const bool tiled = nb >= kEmitTiledMinBins;
+  const size_t o_tiles = align_up((size_t)(nb + 1) * 8, 256);
+  Scratch s;
+  TSDS_CK(scratch_alloc(s, o_tiles + (tiled ? align_up((size_t)emit_tiles(nb) * 8, 256) : 0), st));
+  char* base = static_cast<char*>(s.p);
+  SeriesDev S;
+  memset(&S, 0, sizeof S);
+  S.y = y;
+  S.x = x;
+  S.n = n;
+  S.nb = nb;
+  S.edges = reinterpret_cast<int64_t*>(base);
+  S.out = out;
+  S.out_count = out_count;
+  if (g) S.g = *g;
+  TSDS_CK(launch_edges(nullptr, 1, &S, x != nullptr, x_dtype, nb, st));
+  if (tiled) TSDS_CK(launch_emit_tiled(S, ALGO_EVERYNTH, reinterpret_cast<int64_t*>(base + o_tiles), st));
+  else TSDS_CK(launch_emit(nullptr, 1, S, ALGO_EVERYNTH, st));
+  return TSDS_OK;
+}
+
 // Checks the optional value outputs and fills g (null g when there are none).
 static tsds_status gather_args(const void* x, tsds_dtype x_dtype, tsds_dtype y_dtype, void* x_out, void* y_out,
                                Gather& g, const Gather*& gp) {
@@ -274,10 +299,10 @@ static tsds_status run_binned(Algo algo, const void* x, tsds_dtype x_dtype, cons
   const Gather* gp;
   s = gather_args(x, x_dtype, y_dtype, x_out, y_out, g, gp);
   if (s != TSDS_OK) return s;
-  const int per_bin = algo == ALGO_MINMAX ? 2 : 4;
+  const int per_bin = algo == ALGO_MINMAX ? 2 : algo == ALGO_M4 ? 4 : 1;
   if (n_out < per_bin || n_out % per_bin != 0)
     return fail(TSDS_EINVAL, "%s needs n_out to be a positive multiple of %d (got %lld)",
-                algo == ALGO_MINMAX ? "MinMax" : "M4", per_bin, (long long)n_out);
+                algo == ALGO_MINMAX ? "MinMax" : algo == ALGO_M4 ? "M4" : "EveryNth", per_bin, (long long)n_out);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (n == 0) {
     TSDS_CK(cudaMemsetAsync(out_count, 0, sizeof(int64_t), st));
@@ -287,6 +312,7 @@ static tsds_status run_binned(Algo algo, const void* x, tsds_dtype x_dtype, cons
     TSDS_CK(launch_iota(out, n, out_count, st, y, x, gp));
     return TSDS_OK;
   }
+  if (algo == ALGO_EVERYNTH) return run_everynth(x, x_dtype, n, n_out, out, out_count, st, y, gp);
   return run_binned_series(x, x_dtype, y, y_dtype, n, n_out / per_bin, nan, algo, out, out_count, 0, st, gp);
 }
 
@@ -351,6 +377,17 @@ tsds_status tsds_minmaxlttb(const void* x, tsds_dtype x_dtype, const void* y, ts
                             int64_t* out, int64_t* out_count, void* stream) {
   return minmaxlttb_entry(x, x_dtype, y, y_dtype, n, n_out, minmax_ratio, nan, out, out_count, stream, nullptr,
                           nullptr);
+}
+
+tsds_status tsds_everynth(const void* x, tsds_dtype x_dtype, const void* y, tsds_dtype y_dtype, int64_t n,
+                          int64_t n_out, tsds_nan_mode nan, int64_t* out, int64_t* out_count, void* stream) {
+  return run_binned(ALGO_EVERYNTH, x, x_dtype, y, y_dtype, n, n_out, nan, out, out_count, stream);
+}
+
+tsds_status tsds_everynth_values(const void* x, tsds_dtype x_dtype, const void* y, tsds_dtype y_dtype, int64_t n,
+                                 int64_t n_out, tsds_nan_mode nan, int64_t* out, int64_t* out_count, void* x_out,
+                                 void* y_out, void* stream) {
+  return run_binned(ALGO_EVERYNTH, x, x_dtype, y, y_dtype, n, n_out, nan, out, out_count, stream, x_out, y_out);
 }
 
 tsds_status tsds_minmax_values(const void* x, tsds_dtype x_dtype, const void* y, tsds_dtype y_dtype, int64_t n,

@@ -1,7 +1,7 @@
 // emit.cu -- turns per-bin selections into the output index list.
 //
-// MinMax emits {argmin, argmax} of each non-empty bin and M4 emits {first,
-// argmin, argmax, last} (Section 1); each bin's selections are written once
+// MinMax emits {argmin, argmax} of each non-empty bin, M4 {first, argmin,
+// argmax, last} and EveryNth {first} (Section 1); each bin's selections are written once
 // each, in increasing order, and bins follow each other, so the output is
 // strictly increasing.  Empty bins (possible with gaps in x) emit nothing,
 // which is why fewer than n_out indices can come back (Section 2.3 footnote).
@@ -19,6 +19,10 @@ template <int ALGO>
 __device__ __forceinline__ int bin_select(const SeriesDev& S, int64_t b, int64_t (&v)[4]) {
   const int64_t lo = __ldg(S.edges + b), hi = __ldg(S.edges + b + 1);
   if (hi <= lo) return 0;
+  if (ALGO == ALGO_EVERYNTH) {
+    v[0] = lo;
+    return 1;
+  }
   const int64_t mn = S.res[2 * b], mx = S.res[2 * b + 1];
   int k = 0;
   if (ALGO == ALGO_MINMAX) {
@@ -176,6 +180,9 @@ cudaError_t launch_emit_tiled(const SeriesDev& single, Algo algo, int64_t* tile_
   if (algo == ALGO_MINMAX) {
     k_emit_count<ALGO_MINMAX><<<(unsigned)tiles, kTileThreads, 0, st>>>(single, tile_count);
     k_emit_write<ALGO_MINMAX><<<(unsigned)tiles, kTileThreads, 0, st>>>(single, tile_count);
+  } else if (algo == ALGO_EVERYNTH) {
+    k_emit_count<ALGO_EVERYNTH><<<(unsigned)tiles, kTileThreads, 0, st>>>(single, tile_count);
+    k_emit_write<ALGO_EVERYNTH><<<(unsigned)tiles, kTileThreads, 0, st>>>(single, tile_count);
   } else {
     k_emit_count<ALGO_M4><<<(unsigned)tiles, kTileThreads, 0, st>>>(single, tile_count);
     k_emit_write<ALGO_M4><<<(unsigned)tiles, kTileThreads, 0, st>>>(single, tile_count);
@@ -192,6 +199,8 @@ cudaError_t launch_emit(const SeriesDev* s_dev, int count, const SeriesDev& sing
   note_launch();
   if (algo == ALGO_MINMAX)
     k_emit<ALGO_MINMAX><<<count, (unsigned)threads, 0, st>>>(arr, single);
+  else if (algo == ALGO_EVERYNTH)
+    k_emit<ALGO_EVERYNTH><<<count, (unsigned)threads, 0, st>>>(arr, single);
   else
     k_emit<ALGO_M4><<<count, (unsigned)threads, 0, st>>>(arr, single);
   return cudaGetLastError();

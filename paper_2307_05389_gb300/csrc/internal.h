@@ -11,7 +11,8 @@ namespace tsds {
 constexpr int64_t kWindowBytes = 64 * 1024;
 constexpr int kStreamThreads = 256;   // 8 warps per CTA
 
-enum Algo : int { ALGO_MINMAX = 0, ALGO_M4 = 1 };
+// EVERYNTH: the first point of each non-empty bin (no argmin/argmax pass).
+enum Algo : int { ALGO_MINMAX = 0, ALGO_M4 = 1, ALGO_EVERYNTH = 2 };
 
 // Optional fused value gather: beside each index the kernel that writes
 // out[i] also copies the selected point's raw y element to y_out[i] and its

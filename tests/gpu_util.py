@@ -4,7 +4,7 @@ import numpy as np
 
 from paper_2307_05389_gb300 import binding
 
-ALGOS = ("minmax", "m4", "lttb", "minmaxlttb")
+ALGOS = ("minmax", "m4", "lttb", "minmaxlttb", "everynth")
 
 
 class DevArray:
@@ -41,7 +41,8 @@ def call(algo, x, y, n_out, nan="propagate", ratio=4, stream=None, out_cap=None,
     if algo == "minmaxlttb":
         r = binding.tsds_minmaxlttb(*common, ratio, nm, out.data_ptr(), cnt.data_ptr(), sp)
     else:
-        fn = {"minmax": binding.tsds_minmax, "m4": binding.tsds_m4, "lttb": binding.tsds_lttb}[algo]
+        fn = {"minmax": binding.tsds_minmax, "m4": binding.tsds_m4, "lttb": binding.tsds_lttb,
+              "everynth": binding.tsds_everynth}[algo]
         r = fn(*common, nm, out.data_ptr(), cnt.data_ptr(), sp)
     if r != 0:
         return r, None

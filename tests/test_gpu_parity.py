@@ -302,3 +302,26 @@ def test_segmented_tiny_and_mixed_bins(dtype, nan, stream_variant):
     for n_out in (400, 4000, 40_000):
         check("minmax", x.astype(np.int64), y, n_out, nan)
         check("m4", x.astype(np.int64), y, n_out, nan)
+
+
+@pytest.mark.parametrize("x_dtype", [None, "int64", "float64", "uint8", "float16", "int32"])
+def test_everynth(x_dtype):
+    """EveryNth: index-space and x-space bins, a single bin, the tiled emit
+    (>= 16384 bins), n_out >= n, n = 0, and x with long runs of equal values
+    (empty bins)."""
+    n = 300_007
+    y = inputs.random_walk(n, "float32", 7)
+    if x_dtype is None:
+        x = None
+    elif x_dtype in ("uint8", "float16"):
+        x = np.sort(np.random.default_rng(7).integers(0, 200, n)).astype(x_dtype)
+    elif x_dtype == "float64":
+        x = inputs.exponential_x(n, 7)
+    else:
+        x = inputs.geometric_x(n, 7).astype(x_dtype) if x_dtype == "int64" else \
+            np.sort(np.random.default_rng(7).integers(-10**9, 10**9, n)).astype(np.int32)
+    for n_out in (1, 7, 2000, 40_000):
+        check("everynth", x, y, n_out)
+    check("everynth", None if x is None else x[:500], y[:500], 500)
+    check("everynth", None if x is None else x[:500], y[:500], 501)
+    check("everynth", None if x is None else x[:0], y[:0], 10)

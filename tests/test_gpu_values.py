@@ -16,7 +16,8 @@ from gpu_util import DevArray
 
 pytestmark = pytest.mark.gpu
 
-FNS = {"minmax": binding.tsds_minmax_values, "m4": binding.tsds_m4_values, "lttb": binding.tsds_lttb_values}
+FNS = {"minmax": binding.tsds_minmax_values, "m4": binding.tsds_m4_values, "lttb": binding.tsds_lttb_values,
+       "everynth": binding.tsds_everynth_values}
 
 
 def call_values(algo, x, y, n_out, nan="propagate", ratio=4, want_x=True):
@@ -116,3 +117,14 @@ def test_downsample_values_helper():
     assert torch.equal(yv, y[idx]) and torch.equal(xv, x[idx])
     idx, xv, yv = binding.downsample_values("minmaxlttb", y, 400)
     assert xv is None and torch.equal(yv, y[idx])
+
+
+@pytest.mark.parametrize("dtype", ["uint8", "float16", "float64"])
+def test_everynth_values(dtype):
+    n = 400_003
+    y = inputs.random_walk(n, dtype, 8) if np.dtype(dtype).kind == "f" else inputs.quarter_range(n, dtype, 8)
+    x = inputs.exponential_x(n, 8)
+    for n_out in (1000, 30_000):
+        check("everynth", None, y, n_out)
+        check("everynth", x, y, n_out)
+    check("everynth", x[:100], y[:100], 100)
