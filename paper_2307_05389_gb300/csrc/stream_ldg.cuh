@@ -15,24 +15,77 @@ constexpr int kCH = 8;                   // steps between index resolutions
 // ---------------------------------------------------------------------------
 // One bin piece [a, b) of a series, reduced by one warp.
 // ---------------------------------------------------------------------------
+// Element offset (from the first body element) of the first element of the
+// vectors v of step t that matches `target`, or -1.
 template <class P, bool MIN>
-__device__ __noinline__ int find_first_g(const uint4* __restrict__ vp, int nvec, int t, int lane,
-                                       typename P::Acc target) {
-  // element offset (from the first body element) of the first match in step t
+__device__ __forceinline__ int find_in_step(const uint4 (&v)[kU], int nvec, int t, int lane,
+                                            typename P::Acc target) {
   using T = typename P::T;
   const int vb = t * (32 * kU) + lane;
-#pragma unroll 1
+#pragma unroll
   for (int u = 0; u < kU; ++u) {
     const int vi = vb + u * 32;
-    if (vi >= nvec) break;
-    const uint4 v = ldg_vec(vp + vi);
+    if (vi < nvec) {
 #pragma unroll
-    for (int e = 0; e < P::E; ++e) {
-      const T val = vec_elem<T, P::E>(v, e);
-      if (MIN ? P::match_min(val, target) : P::match_max(val, target)) return vi * P::E + e;
+      for (int e = 0; e < P::E; ++e) {
+        const T val = vec_elem<T, P::E>(v[u], e);
+        if (MIN ? P::match_min(val, target) : P::match_max(val, target)) return vi * P::E + e;
+      }
     }
   }
   return -1;
+}
+
+// The same after re-reading step t (all of its vectors are requested before
+// any is searched, so the re-read costs one round trip).
+template <class P, bool MIN>
+__device__ __noinline__ int find_first_g(const uint4* __restrict__ vp, int nvec, int t, int lane,
+                                         typename P::Acc target) {
+  const int vb = t * (32 * kU) + lane;
+  uint4 v[kU];
+#pragma unroll
+  for (int u = 0; u < kU; ++u) v[u] = vb + u * 32 < nvec ? ldg_vec(vp + vb + u * 32) : make_uint4(0u, 0u, 0u, 0u);
+  return find_in_step<P, MIN>(v, nvec, t, lane, target);
+}
+
+// A piece whose body is a single step: the head, tail and body loads are all
+// issued before any is used, and the body's indices come straight from the
+// registers (no re-read).  Kept out of line so that the main loop's register
+// allocation does not carry it.
+template <class P>
+__device__ __noinline__ Cand one_step(const typename P::T* __restrict__ y, int64_t a, int64_t ia, int64_t ib,
+                                      int64_t b, int lane) {
+  using T = typename P::T;
+  using Acc = typename P::Acc;
+  const uint4* __restrict__ vp = reinterpret_cast<const uint4*>(y + ia);
+  const int nv = (int)((ib - ia) / P::E);
+  const bool has_h = a + lane < ia, has_t = ib + lane < b;   // fewer than 16 bytes each side
+  T he{}, te{};
+  if (has_h) he = ldg_elem<T>(y + a + lane);
+  if (has_t) te = ldg_elem<T>(y + ib + lane);
+  uint4 v[kU];
+#pragma unroll
+  for (int u = 0; u < kU; ++u) v[u] = lane + u * 32 < nv ? ldg_vec(vp + lane + u * 32) : make_uint4(0u, 0u, 0u, 0u);
+  Cand c;
+  cand_init(c);
+  if (lane < nv) {
+#pragma unroll
+    for (int u = 1; u < kU; ++u)
+      if (lane + u * 32 >= nv) v[u] = v[0];
+    Acc mn, mx;
+    P::group(v, mn, mx);
+    cand_merge_min(c, P::key_min(mn), ia + find_in_step<P, true>(v, nv, 0, lane, mn));
+    cand_merge_max(c, P::key_max(mx), ia + find_in_step<P, false>(v, nv, 0, lane, mx));
+  }
+  if (has_h) {
+    cand_merge_min(c, P::elem_key_min(he), a + lane);
+    cand_merge_max(c, P::elem_key_max(he), a + lane);
+  }
+  if (has_t) {
+    cand_merge_min(c, P::elem_key_min(te), ib + lane);
+    cand_merge_max(c, P::elem_key_max(te), ib + lane);
+  }
+  return c;
 }
 
 template <class P>
@@ -51,6 +104,11 @@ __device__ __forceinline__ Cand piece_ldg(const typename P::T* __restrict__ y, i
   if (ia > b) ia = b;
   const int64_t nvec = (b - ia) / E;
   const int64_t ib = ia + nvec * E;
+  if (nvec <= 32 * kU) {
+    c = one_step<P>(y, a, ia, ib, b, lane);
+    cand_warp_reduce(c);
+    return c;
+  }
   for (int64_t i = a + lane; i < ia; i += 32) {
     const T e = ldg_elem<T>(y + i);
     cand_merge_min(c, P::elem_key_min(e), i);
@@ -62,7 +120,7 @@ __device__ __forceinline__ Cand piece_ldg(const typename P::T* __restrict__ y, i
     cand_merge_max(c, P::elem_key_max(e), i);
   }
 
-  if (nvec > 0) {
+  {
     // a piece never exceeds one window, so step and vector numbers fit in 32 bits
     const uint4* __restrict__ vp = reinterpret_cast<const uint4*>(y + ia);
     const int nv = (int)nvec;
@@ -124,11 +182,14 @@ k_argminmax_ldg(const SeriesDev* __restrict__ sd, SeriesDev single, const int32_
   const int lane = threadIdx.x & 31;
   if (total_dev) total_windows = *total_dev;
   if (first_dev) w_first = *first_dev;
+  // a warp claims its next window as soon as it starts on one, so the claim's
+  // round trip overlaps the work
+  unsigned long long wu = 0;
+  if (lane == 0) wu = atomicAdd(&work->next_window, 1ull);
   for (;;) {
-    unsigned long long wu = 0;
-    if (lane == 0) wu = atomicAdd(&work->next_window, 1ull);
     const int64_t w = w_first + (int64_t)__shfl_sync(0xffffffffu, wu, 0);
     if (w >= total_windows) break;
+    if (lane == 0) wu = atomicAdd(&work->next_window, 1ull);
     SeriesDev S = MULTI ? sd[win_series[w]] : single;
     const T* __restrict__ y = static_cast<const T*>(S.y);
     const int64_t* __restrict__ edges = S.edges;
