@@ -816,9 +816,11 @@ static cudaError_t launch_var(const SeriesDev* s_dev, const SeriesDev& single, c
   const int64_t welems = cfg.window_bytes / (int64_t)sizeof(typename P::T);
   note_launch();
   if constexpr (VAR == STREAM_LDG) {
+    const int prefetch = cfg.mean_bin_bytes > 0 && cfg.mean_bin_bytes < kPrefetchMaxBinBytes ? 1 : 0;
     k_argminmax_ldg<P, NM, MULTI><<<(unsigned)blocks, threads, 0, st>>>(s_dev, single, win_series, total_windows, fp,
                                                                         lp, work, welems, cfg.total_windows_dev,
-                                                                        cfg.window_first, cfg.window_first_dev);
+                                                                        cfg.window_first, cfg.window_first_dev,
+                                                                        prefetch);
   } else if constexpr (VAR == STREAM_SEG) {
     k_argminmax_seg<P, NM, MULTI><<<(unsigned)blocks, threads, 0, st>>>(s_dev, single, win_series, total_windows, fp,
                                                                         lp, work, welems, cfg.total_windows_dev,

@@ -11,6 +11,20 @@
 
 constexpr int kStreamThreadsLdg = 256;   // 8 warps per CTA
 constexpr int kCH = 8;                   // steps between index resolutions
+constexpr int kPrefetchAhead = 8192;     // bytes of the window requested into L2 ahead of the loads
+// Prefetch pays when pieces are short (each costs a few round trips of its
+// own) and costs when they are long (steps already stream at the copy rate):
+// on for launches whose bytes-weighted mean bin is below this.
+constexpr int64_t kPrefetchMaxBinBytes = 128 * 1024;
+
+// Requests the 2 KB of y that start kPrefetchAhead bytes past base + off into
+// L2 (lane l the 64 bytes at 64 l), never at or past base + room; a hint with
+// no register cost, so the loads of the next bins and steps find their lines
+// in L2.
+__device__ __forceinline__ void prefetch_ahead(const char* base, int off, int room, int lane) {
+  const int q = off + kPrefetchAhead + 64 * lane;
+  if (q < room) asm volatile("prefetch.global.L2 [%0];" ::"l"(base + q));
+}
 
 // ---------------------------------------------------------------------------
 // One bin piece [a, b) of a series, reduced by one warp.
@@ -88,8 +102,10 @@ __device__ __noinline__ Cand one_step(const typename P::T* __restrict__ y, int64
   return c;
 }
 
+// room (optional): bytes from y + a to the end of the window holding the
+// piece, which is prefetched ahead within that window (0: no prefetch)
 template <class P>
-__device__ __forceinline__ Cand piece_ldg(const typename P::T* __restrict__ y, int64_t a, int64_t b) {
+__device__ __forceinline__ Cand piece_ldg(const typename P::T* __restrict__ y, int64_t a, int64_t b, int room = 0) {
   using T = typename P::T;
   using Acc = typename P::Acc;
   constexpr int E = P::E;
@@ -104,6 +120,13 @@ __device__ __forceinline__ Cand piece_ldg(const typename P::T* __restrict__ y, i
   if (ia > b) ia = b;
   const int64_t nvec = (b - ia) / E;
   const int64_t ib = ia + nvec * E;
+  if (room > 0) {
+    // the bytes kPrefetchAhead past this piece (the following pieces of the
+    // window), at most 16 KB, requested before the piece's own loads
+    const char* pbase = reinterpret_cast<const char*>(y + a);
+    const int pbytes = (int)min((int64_t)16384, (b - a) * (int64_t)sizeof(T));
+    for (int off = 0; off < pbytes; off += 2048) prefetch_ahead(pbase, off, room, lane);
+  }
   if (nvec <= 32 * kU) {
     c = one_step<P>(y, a, ia, ib, b, lane);
     cand_warp_reduce(c);
@@ -177,7 +200,7 @@ __global__ void __launch_bounds__(kStreamThreadsLdg, MULTI ? 3 : 4)
 k_argminmax_ldg(const SeriesDev* __restrict__ sd, SeriesDev single, const int32_t* __restrict__ win_series,
             int64_t total_windows, Piece* __restrict__ first_piece, Piece* __restrict__ last_piece,
             WorkCounters* __restrict__ work, int64_t welems, const int64_t* __restrict__ total_dev,
-            int64_t w_first, const int64_t* __restrict__ first_dev) {
+            int64_t w_first, const int64_t* __restrict__ first_dev, int prefetch) {
   using T = typename P::T;
   const int lane = threadIdx.x & 31;
   if (total_dev) total_windows = *total_dev;
@@ -197,6 +220,14 @@ k_argminmax_ldg(const SeriesDev* __restrict__ sd, SeriesDev single, const int32_
     const int64_t k = w - S.win_base;
     const int64_t ws = k * welems;
     const int64_t we = min(ws + welems, S.n);
+    // with prefetch (launches of small and mid-size bins): the window's first
+    // lines into L2 while its first bin is searched
+    if (prefetch) {
+      const int wroom = (int)((we - ws) * (int64_t)sizeof(T));
+#pragma unroll
+      for (int q = 0; q < kPrefetchAhead / 2048; ++q)
+        prefetch_ahead(reinterpret_cast<const char*>(y + ws), 2048 * q - kPrefetchAhead, wroom, lane);
+    }
     // the bin holding ws: the last b with edges[b] <= ws
     int64_t b = warp_lower_bound(1, nb + 1, [&](int64_t j) { return __ldg(edges + j) > ws; }) - 1;
     int64_t lo = __ldg(edges + b);
@@ -207,7 +238,7 @@ k_argminmax_ldg(const SeriesDev* __restrict__ sd, SeriesDev single, const int32_
         const int64_t hi = __shfl_sync(0xffffffffu, my_hi, q);
         if (hi > lo) {
           const int64_t pa = max(lo, ws), pb = min(hi, we);
-          Cand c = piece_ldg<P>(y, pa, pb);
+          Cand c = piece_ldg<P>(y, pa, pb, prefetch ? (int)((we - pa) * (int64_t)sizeof(T)) : 0);
           bin_result<P, NM>(S, b, lo, hi, k, welems, c, first_piece, last_piece, lane);
         }
         lo = hi;
