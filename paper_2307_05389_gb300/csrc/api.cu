@@ -174,11 +174,14 @@ tsds_status run_binned_series(const void* x, tsds_dtype x_dtype, const void* y, 
                               int64_t n, int64_t nb, tsds_nan_mode nan, Algo algo, int64_t* out,
                               int64_t* out_count, int64_t idx_bias, cudaStream_t st, const Gather* g) {
   if (small_call(n, nb, y_dtype)) {
-    // a small call: one launch (after the edge search when x is given)
+    // a warp per bin: one launch (after the edge search when x is given), then
+    // the emit kernels when there are too many bins for the last CTA to emit
+    const bool emit = nb <= kSmallEmitMaxBins;
     const size_t o_res = align_up((size_t)(nb + 1) * 8, 256);
     const size_t o_done = o_res + align_up((size_t)nb * 16, 256);
+    const size_t o_tiles = o_done + 256;
     Scratch s;
-    TSDS_CK(scratch_alloc(s, o_done + 256, st));
+    TSDS_CK(scratch_alloc(s, o_tiles + align_up((size_t)emit_tiles(nb) * 8, 256), st));
     char* base = static_cast<char*>(s.p);
     TSDS_CK(cudaMemsetAsync(base + o_done, 0, sizeof(unsigned), st));
     SeriesDev S;
@@ -196,11 +199,15 @@ tsds_status run_binned_series(const void* x, tsds_dtype x_dtype, const void* y, 
     if (x) TSDS_CK(launch_edges(nullptr, 1, &S, true, x_dtype, nb, st));
     void* tok;
     timing_begin(st, &tok);
-    TSDS_CK(launch_small(S, y_dtype, nan, algo, x != nullptr, reinterpret_cast<unsigned*>(base + o_done), st));
+    TSDS_CK(launch_small(S, y_dtype, nan, algo, x != nullptr, reinterpret_cast<unsigned*>(base + o_done), emit, st));
     timing_end(st, tok);
+    if (!emit) {
+      if (nb >= kEmitTiledMinBins) TSDS_CK(launch_emit_tiled(S, algo, reinterpret_cast<int64_t*>(base + o_tiles), st));
+      else TSDS_CK(launch_emit(nullptr, 1, S, algo, st));
+    }
     return TSDS_OK;
   }
-  // Window size: 64 KB for large inputs; smaller (down to 8 KB, a multiple of
+  // Window size: 64 KB for large inputs; smaller (down to 4 KB, a multiple of
   // the 4 KB ring chunk) when fewer windows than about twice the resident
   // warps would leave SMs idle.
   StreamConfig cfg;
@@ -209,7 +216,7 @@ tsds_status run_binned_series(const void* x, tsds_dtype x_dtype, const void* y, 
     const int64_t bytes = n * dtype_size(y_dtype);
     const int64_t warps = (int64_t)device_sm_count() * 3 * 4;
     int64_t wb = (bytes / (2 * warps) + 4095) / 4096 * 4096;
-    cfg.window_bytes = wb < 8192 ? 8192 : (wb > kWindowBytes ? kWindowBytes : wb);
+    cfg.window_bytes = wb < 4096 ? 4096 : (wb > kWindowBytes ? kWindowBytes : wb);
   }
   const int64_t welems = cfg.window_bytes / dtype_size(y_dtype);
   const int64_t windows = (n + welems - 1) / welems;

@@ -898,13 +898,16 @@ cudaError_t launch_argminmax_sm(const SeriesDev& single, int64_t total_windows, 
 }
 
 bool small_call(int64_t n, int64_t nb, tsds_dtype y_dtype) {
-  return nb >= 1 && nb <= kSmallMaxBins && n * dtype_size(y_dtype) <= kSmallMaxBinBytes * nb;
+  const int64_t bytes = n * dtype_size(y_dtype);
+  if (nb < 1 || bytes > kSmallMaxBytes || bytes > kSmallMaxBinBytes * nb || variant_override() != STREAM_AUTO)
+    return false;
+  return nb <= 4096 || bytes >= 512 * nb;
 }
 
 cudaError_t launch_small(const SeriesDev& S, tsds_dtype y_dtype, tsds_nan_mode nan, Algo algo, bool has_x,
-                         unsigned* done, cudaStream_t st) {
+                         unsigned* done, bool emit, cudaStream_t st) {
   const bool ign = nan == TSDS_NAN_IGNORE;
-#define TSDS_SMALL(POL, NM) launch_small_pol<POL, NM>(S, algo, has_x, done, st)
+#define TSDS_SMALL(POL, NM) launch_small_pol<POL, NM>(S, algo, has_x, done, emit, st)
   switch (y_dtype) {
     case TSDS_I8: return TSDS_SMALL(PolSmallInt<int8_t>, 0);
     case TSDS_U8: return TSDS_SMALL(PolSmallInt<uint8_t>, 0);

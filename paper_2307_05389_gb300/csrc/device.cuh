@@ -141,6 +141,21 @@ __device__ __forceinline__ int64_t warp_lower_bound(int64_t lo, int64_t hi, Pred
   return hi;
 }
 
+// floor(a*b/c) and ceil(a*b/c) for non-negative a, b and positive c with a*b
+// below 2^127: one 64-bit division when a and b are below 2^32 (the product
+// then fits 64 bits), the 128-bit one otherwise.
+__device__ __forceinline__ uint64_t muldiv_floor(uint64_t a, uint64_t b, uint64_t c) {
+  if (((a | b) >> 32) == 0) return (a * b) / c;
+  return (uint64_t)(((unsigned __int128)a * b) / c);
+}
+__device__ __forceinline__ uint64_t muldiv_ceil(uint64_t a, uint64_t b, uint64_t c) {
+  if (((a | b) >> 32) == 0) {
+    const uint64_t p = a * b;
+    return p / c + (p % c != 0 ? 1 : 0);
+  }
+  return (uint64_t)(((unsigned __int128)a * b + c - 1) / c);
+}
+
 // Fused value gather -------------------------------------------------------
 // dst[pos] = src[idx] for raw elements of `size` bytes (1, 2, 4 or 8).
 __device__ __forceinline__ void gather_elem(void* dst, int64_t pos, const void* src, int64_t idx, int size) {

@@ -123,12 +123,19 @@ cudaError_t launch_argminmax_sm(const SeriesDev& single, int64_t total_windows, 
                                 Piece* last_piece, WorkCounters* work, tsds_dtype y_dtype, tsds_nan_mode nan,
                                 const StreamConfig& cfg, int sm_count, cudaStream_t st);
 
-// Small single-series calls (n*sizeof(y) <= 64 KB per bin, at most 4096
-// bins): the whole MinMax/M4 pipeline in one launch (index-bin starts in the
-// kernel, x-space starts from launch_edges first); `done` is a zeroed counter.
+// Single-series calls with bins of at most 64 KB on average and at most
+// 256 MB of y (either at most 4096 bins, or bins of at least 512 bytes, where
+// a warp per bin beats the segmented pass) and no explicit streaming
+// variant: a warp per bin in one launch (index-bin starts in the kernel,
+// x-space starts from launch_edges first).  With emit (at most
+// kSmallEmitMaxBins bins) the last CTA also emits, with `done` a zeroed
+// counter; otherwise launch_emit / launch_emit_tiled follow.
+constexpr int64_t kSmallMaxBinBytes = 64 * 1024;
+constexpr int64_t kSmallMaxBytes = 256ll << 20;
+constexpr int64_t kSmallEmitMaxBins = 1024;
 bool small_call(int64_t n, int64_t nb, tsds_dtype y_dtype);
 cudaError_t launch_small(const SeriesDev& S, tsds_dtype y_dtype, tsds_nan_mode nan, Algo algo, bool has_x,
-                         unsigned* done, cudaStream_t st);
+                         unsigned* done, bool emit, cudaStream_t st);
 
 // A kernel whose barrier wait nothing satisfies, bounded by `rounds`; writes
 // the status it ends with (TSDS_ETIMEOUT) to *status.
@@ -143,7 +150,7 @@ cudaError_t launch_emit(const SeriesDev* s_dev, int count, const SeriesDev& sing
 
 // The same for one series with many bins, over tiles of bins on many CTAs
 // (tile_count: emit_tiles(nb) int64 of scratch).
-constexpr int64_t kEmitTiledMinBins = 16384;
+constexpr int64_t kEmitTiledMinBins = 4096;
 int64_t emit_tiles(int64_t nb);
 cudaError_t launch_emit_tiled(const SeriesDev& single, Algo algo, int64_t* tile_count, cudaStream_t st);
 

@@ -44,7 +44,7 @@ typedef unsigned __int128 u128;
 __device__ __forceinline__ int64_t job_m(const LttbJob& J) { return J.m_dev ? *J.m_dev : J.m_host; }
 
 __device__ __forceinline__ int64_t bucket_start(int64_t j, int64_t m, int64_t B) {
-  return 1 + (int64_t)(((u128)j * (u128)(m - 2)) / (u128)B);
+  return 1 + (int64_t)muldiv_floor((uint64_t)j, (uint64_t)(m - 2), (uint64_t)B);
 }
 
 __device__ __forceinline__ int64_t out_index(const LttbJob& J, int64_t k) { return J.R ? J.R[k] : k + J.bias; }
@@ -114,30 +114,6 @@ __global__ void k_points(const PointsJob* __restrict__ jobs) {
   }
 }
 
-// means[j] for buckets 1..B-1 (the third vertex of steps 0..B-2): binary64
-// sums in index order divided once by the count.  Small buckets (table mode):
-// a thread per bucket.
-__global__ void k_means(const LttbJob* __restrict__ jobs) {
-  const LttbJob J = jobs[blockIdx.y];
-  if (J.mode != 0) return;
-  const int64_t m = job_m(J), B = J.B;
-  if (m <= B + 2) return;
-  const bool ign = J.nan == TSDS_NAN_IGNORE;
-  for (int64_t j = 1 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < B; j += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t lo = bucket_start(j, m, B), hi = bucket_start(j + 1, m, B);
-    double sx = 0.0, sy = 0.0;
-    int64_t c = 0;
-    for (int64_t k = lo; k < hi; ++k) {
-      const double yk = J.py[k];
-      if (ign && isnan(yk)) continue;
-      sx = __dadd_rn(sx, J.px[k]);
-      sy = __dadd_rn(sy, yk);
-      ++c;
-    }
-    J.means[j] = make_double2(__ddiv_rn(sx, (double)c), __ddiv_rn(sy, (double)c));
-  }
-}
-
 __device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((unsigned)__cvta_generic_to_shared(smem)), "l"(gmem)
                : "memory");
@@ -157,8 +133,8 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-// Hull-table mode, larger buckets.  Most buckets get their mean from k_p32
-// (exact sums, below); a bucket it flags takes the sequential sum here, one
+// Buckets whose mean needs the sequential sum (flagged by k_means or k_p32,
+// which give every other bucket its mean from exact sums, below) take it here, one
 // chain per bucket and coordinate.  A CTA covers 32 buckets with four warps,
 // one per SM sub-partition: two producer warps stream the flagged buckets'
 // x and y values through a ring of three 32-point chunks in shared memory
@@ -214,9 +190,9 @@ __device__ __forceinline__ void sums_consume(const SumSlots& v, const SumSlots& 
   }
 }
 
-__global__ void __launch_bounds__(kSumThreads) k_sums_wide(const LttbJob* __restrict__ jobs) {
+__global__ void __launch_bounds__(kSumThreads) k_sums_wide(const LttbJob* __restrict__ jobs, int mode) {
   const LttbJob J = jobs[blockIdx.y];
-  if (J.mode != 2) return;
+  if (J.mode != mode) return;
   const int64_t m = job_m(J), B = J.B;
   if (m <= B + 2) return;
   extern __shared__ __align__(16) unsigned char sum_smem[];
@@ -294,12 +270,14 @@ __global__ void __launch_bounds__(kSumThreads) k_sums_wide(const LttbJob* __rest
 struct ExactSum {
   unsigned long long acc;   // two's complement, units of 2^s
   int s, top;
+  bool nan;                 // a NaN was added: the sum is NaN in any order
 };
 
 __device__ __forceinline__ void exact_init(ExactSum& e) {
   e.acc = 0ull;
   e.s = 4096;
   e.top = -4096;
+  e.nan = false;
 }
 
 __device__ __forceinline__ void exact_add(ExactSum& e, double v, bool& bad) {
@@ -307,7 +285,8 @@ __device__ __forceinline__ void exact_add(ExactSum& e, double v, bool& bad) {
   const int eb = (int)((b >> 52) & 0x7ff);
   unsigned long long M = b & 0xfffffffffffffull;
   if (eb == 0x7ff) {
-    bad = true;
+    if (M != 0ull) e.nan = true;
+    else bad = true;                                     // an infinity: order may matter (overflow)
     return;
   }
   if (eb == 0 && M == 0ull) return;                      // a zero adds nothing
@@ -325,8 +304,13 @@ __device__ __forceinline__ void exact_add(ExactSum& e, double v, bool& bad) {
   e.acc += (b >> 63) ? (0ull - w) : w;
 }
 
-// The warp's exact sum of one coordinate, or false when the bound fails.
+// The warp's exact sum of one coordinate (NaN when a NaN was added), or
+// false when the bound fails.
 __device__ __forceinline__ bool exact_finish(const ExactSum& e, int cnt, double& out) {
+  if (__any_sync(0xffffffffu, e.nan)) {
+    out = __longlong_as_double(0x7ff8000000000000ll);
+    return true;
+  }
   const int L = __reduce_min_sync(0xffffffffu, e.s + 8192) - 8192;
   const int T = __reduce_max_sync(0xffffffffu, e.top + 8192) - 8192;
   unsigned long long a = e.acc << min(e.s - L, 63);
@@ -347,6 +331,46 @@ __device__ __forceinline__ bool exact_finish(const ExactSum& e, int cnt, double&
   }
   out = __dmul_rn(r, __longlong_as_double((long long)(e2 + 1023) << 52));
   return true;
+}
+
+// means[j] for buckets 1..B-1 (the third vertex of steps 0..B-2): binary64
+// sums in index order divided once by the count.  Small buckets (table mode,
+// at most 32 points): a warp per bucket, a lane per point, the exact integer
+// sum (ExactSum) when no addition of the index-order sum can round; other
+// buckets are flagged for the sequential sums of k_sums_wide.
+__global__ void k_means(const LttbJob* __restrict__ jobs) {
+  const LttbJob J = jobs[blockIdx.y];
+  if (J.mode != 0) return;
+  const int64_t m = job_m(J), B = J.B;
+  if (m <= B + 2) return;
+  const bool ign = J.nan == TSDS_NAN_IGNORE;
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t j = 1 + (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); j < B; j += warps) {
+    const int64_t lo = bucket_start(j, m, B), hi = bucket_start(j + 1, m, B);
+    const int n = (int)(hi - lo);          // at most 32 in table mode
+    const bool has = lane < n;
+    const double x = has ? J.px[lo + lane] : 0.0, y = has ? J.py[lo + lane] : 0.0;
+    const bool inc = has && !(ign && isnan(y));
+    const int cnt = __popc(__ballot_sync(0xffffffffu, inc));
+    ExactSum ex, ey;
+    exact_init(ex);
+    exact_init(ey);
+    bool bad = cnt == 0;
+    if (inc) {
+      exact_add(ex, x, bad);
+      exact_add(ey, y, bad);
+    }
+    bad = __any_sync(0xffffffffu, bad);
+    double sx = 0.0, sy = 0.0;
+    const bool okx = exact_finish(ex, cnt, sx);
+    const bool oky = exact_finish(ey, cnt, sy);
+    const bool exact = !bad && okx && oky;
+    if (lane == 0) {
+      J.chain[j] = exact ? 0 : 1;
+      if (exact) J.means[j] = make_double2(__ddiv_rn(sx, (double)cnt), __ddiv_rn(sy, (double)cnt));
+    }
+  }
 }
 
 // p32[k] = point k relative to its bucket's first point, rounded to FP32: a
@@ -423,39 +447,6 @@ __global__ void k_p32(const LttbJob* __restrict__ jobs) {
 
 // ---------------------------------------------------------------- table mode
 
-// table[j*K + ai] = (pick in bucket j) - start(j) when the previous pick is
-// point start(j-1) + ai (for j = 0 the previous pick is point 0, slot 0).
-// One warp per bucket; lanes are the candidates b.
-__global__ void k_table(const LttbJob* __restrict__ jobs) {
-  const LttbJob J = jobs[blockIdx.y];
-  if (J.mode != 0) return;
-  const int64_t m = job_m(J), B = J.B;
-  if (m <= B + 2) return;
-  const int lane = threadIdx.x & 31;
-  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t j = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); j < B; j += warps) {
-    const int64_t lo = bucket_start(j, m, B), hi = bucket_start(j + 1, m, B);
-    double xm, ym;
-    if (j == B - 1) { xm = J.px[m - 1]; ym = J.py[m - 1]; }
-    else { const double2 c = J.means[j + 1]; xm = c.x; ym = c.y; }
-    const int64_t b = lo + lane;
-    const bool has_b = b < hi;
-    const double xb = has_b ? J.px[b] : 0.0, yb = has_b ? J.py[b] : 0.0;
-    int64_t alo, ahi;
-    if (j == 0) { alo = 0; ahi = 1; }
-    else { alo = bucket_start(j - 1, m, B); ahi = lo; }
-    for (int64_t a = alo; a < ahi; ++a) {
-      const double xa = J.px[a], ya = J.py[a];
-      const double dxm = __dsub_rn(xa, xm), dym = __dsub_rn(ym, ya);
-      uint64_t k = 0ull;
-      int64_t idx = kIdxNone;
-      if (has_b) { k = area_key(exact_area(xa, ya, dxm, dym, xb, yb), J.nan); idx = b; }
-      amax_warp(k, idx);
-      if (lane == 0) J.table[j * J.K + (a - alo)] = (int32_t)((k == 0ull ? lo : idx) - lo);
-    }
-  }
-}
-
 // Jobs whose points are all kept return every index.
 __global__ void __launch_bounds__(32) k_chase(const LttbJob* __restrict__ jobs) {
   const LttbJob J = jobs[blockIdx.x];
@@ -526,6 +517,93 @@ __device__ __forceinline__ float filt_box(const Filt& F, float4 bx) {
   const float ad2 = fmaxf(fabsf(__fsub_rn(F.ax, bx.x)), fabsf(__fsub_rn(F.ax, bx.y)));
   const float apx = fmaxf(fabsf(bx.x), fabsf(bx.y)), apy = fmaxf(fabsf(bx.z), fabsf(bx.w));
   return __fadd_rn(est, filt_err(F, apx, apy, ad1, ad2, est));
+}
+
+// table[j*K + ai] = (pick in bucket j) - start(j) when the previous pick is
+// point start(j-1) + ai (for j = 0 the previous pick is point 0, slot 0).
+// One warp per bucket; lanes are the candidates b.  The FP32 filter (filt_err above) decides most
+// steps without binary64 arithmetic: when exactly one candidate's upper bound
+// reaches the best lower bound, that candidate is the pick.  Otherwise (a tie
+// or near-tie, or a value the filter cannot take) every candidate gets its
+// exact binary64 area.  The binary64 work left is per bucket, not per step:
+// the FP32 copies of the bucket's points (lanes = b) and of the previous
+// bucket's points and their differences from the third vertex (lanes = a).
+__global__ void k_table(const LttbJob* __restrict__ jobs) {
+  const LttbJob J = jobs[blockIdx.y];
+  if (J.mode != 0) return;
+  const int64_t m = job_m(J), B = J.B;
+  if (m <= B + 2) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t j = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); j < B; j += warps) {
+    const int64_t lo = bucket_start(j, m, B), hi = bucket_start(j + 1, m, B);
+    double xm, ym;
+    if (j == B - 1) { xm = J.px[m - 1]; ym = J.py[m - 1]; }
+    else { const double2 c = J.means[j + 1]; xm = c.x; ym = c.y; }
+    const double X0 = J.px[lo], Y0 = J.py[lo];
+    const int64_t b = lo + lane;
+    const bool has_b = b < hi;
+    const double xb = has_b ? J.px[b] : 0.0, yb = has_b ? J.py[b] : 0.0;
+    const float2 pb = make_float2(__double2float_rn(__dsub_rn(xb, X0)), __double2float_rn(__dsub_rn(yb, Y0)));
+    // NaN candidates have NaN areas; the others must suit the filter
+    const bool nanb = has_b && (isnan(xb) || isnan(yb));
+    const bool candb = has_b && !nanb;
+    const bool pts_ok = __all_sync(0xffffffffu, !candb || (filt_ok(pb.x) && filt_ok(pb.y)));
+    const unsigned nan_mask = __ballot_sync(0xffffffffu, nanb);
+    const unsigned cand_mask = __ballot_sync(0xffffffffu, candb);
+    const bool prop = J.nan == TSDS_NAN_PROPAGATE;
+    int64_t alo, ahi;
+    if (j == 0) { alo = 0; ahi = 1; }
+    else { alo = bucket_start(j - 1, m, B); ahi = lo; }
+    // lane l: the previous pick a = alo + l
+    const bool has_a = alo + lane < ahi;
+    const double xa_l = has_a ? J.px[alo + lane] : 0.0, ya_l = has_a ? J.py[alo + lane] : 0.0;
+    const double dxm_l = __dsub_rn(xa_l, xm), dym_l = __dsub_rn(ym, ya_l);
+    const float al_l = __double2float_rn(dxm_l), be_l = __double2float_rn(dym_l);
+    const float ax_l = __double2float_rn(__dsub_rn(xa_l, X0)), ay_l = __double2float_rn(__dsub_rn(ya_l, Y0));
+    const bool fast_l = pts_ok && filt_ok(al_l) && filt_ok(be_l) && filt_ok(ax_l) && filt_ok(ay_l) &&
+                        isfinite(dxm_l) && isfinite(dym_l);
+    // a NaN difference from the third vertex makes every area NaN: the first
+    // candidate (NaN-propagate: first NaN; NaN-ignore: no winner, first index)
+    const bool anan_l = isnan(dxm_l) || isnan(dym_l);
+    const int ka = (int)(ahi - alo);
+    for (int ai = 0; ai < ka; ++ai) {
+      int32_t pick = -1;
+      if (__shfl_sync(0xffffffffu, anan_l, ai)) {
+        pick = 0;
+      } else if (__shfl_sync(0xffffffffu, fast_l, ai) && prop && nan_mask) {
+        pick = __ffs(nan_mask) - 1;   // every other area is finite here: the first NaN wins
+      } else if (__shfl_sync(0xffffffffu, fast_l, ai) && !cand_mask) {
+        pick = 0;                     // NaN-ignore, only NaN candidates: no winner
+      } else if (__shfl_sync(0xffffffffu, fast_l, ai)) {
+        const Filt F{__shfl_sync(0xffffffffu, al_l, ai), __shfl_sync(0xffffffffu, be_l, ai),
+                     __shfl_sync(0xffffffffu, ax_l, ai), __shfl_sync(0xffffffffu, ay_l, ai)};
+        float lowb = -INFINITY, upb = -INFINITY;
+        if (candb) {
+          const float est = fabsf(filt_signed(F, pb.x, pb.y));
+          const float err = filt_err(F, fabsf(pb.x), fabsf(pb.y), fabsf(__fsub_rn(pb.y, F.ay)),
+                                     fabsf(__fsub_rn(F.ax, pb.x)), est);
+          lowb = __fsub_rd(est, err);
+          upb = __fadd_rn(est, err);
+        }
+        float L = lowb;
+#pragma unroll
+        for (int o = 16; o; o >>= 1) L = fmaxf(L, __shfl_xor_sync(0xffffffffu, L, o));
+        const unsigned pass = __ballot_sync(0xffffffffu, candb && upb >= L);
+        if (__popc(pass) == 1) pick = __ffs(pass) - 1;
+      }
+      if (pick < 0) {
+        const double xa = __shfl_sync(0xffffffffu, xa_l, ai), ya = __shfl_sync(0xffffffffu, ya_l, ai);
+        const double dxm = __shfl_sync(0xffffffffu, dxm_l, ai), dym = __shfl_sync(0xffffffffu, dym_l, ai);
+        uint64_t k = 0ull;
+        int64_t idx = kIdxNone;
+        if (has_b) { k = area_key(exact_area(xa, ya, dxm, dym, xb, yb), J.nan); idx = b; }
+        amax_warp(k, idx);
+        pick = (int32_t)((k == 0ull ? lo : idx) - lo);
+      }
+      if (lane == 0) J.table[j * J.K + ai] = pick;
+    }
+  }
 }
 
 // The exact pick of bucket j = [lo, hi) after previous pick a, by one warp.
@@ -1044,6 +1122,7 @@ size_t lttb_job_scratch(int64_t m_max, int64_t B, int64_t K) {
   s += align_up((size_t)nseg * kSeg * 4, 256) + align_up((size_t)nseg * 4, 256);   // comp, seg_start
   if (lttb_mode(K) == 0) {
     s += align_up((size_t)B * (size_t)K * 4, 256);
+    s += align_up((size_t)B, 256);                                // chain flags
   } else {
     s += align_up((size_t)m_max * sizeof(float2), 256);           // p32
     s += align_up((size_t)(B + 1) * kCandMax * 4, 256);           // candidate rows 0..B
@@ -1066,6 +1145,8 @@ void lttb_job_bind(LttbJob& J, char* p, int64_t m_max) {
   if (J.mode == 0) {
     J.table = reinterpret_cast<int32_t*>(p);
     J.fslot = J.table;
+    p += align_up((size_t)J.B * (size_t)J.K * 4, 256);
+    J.chain = reinterpret_cast<uint8_t*>(p);
     return;
   }
   J.p32 = reinterpret_cast<float2*>(p);
@@ -1088,6 +1169,16 @@ tsds_status launch_points_jobs(const PointsJob* jobs_dev, int count, int64_t max
   return TSDS_OK;
 }
 
+// The sequential sums of the flagged buckets of the jobs in `mode`.
+static tsds_status launch_sums(const LttbJob* jobs_dev, int count, int64_t max_B, int mode, cudaStream_t st) {
+  const int ssmem = (int)sizeof(SumRing);
+  TSDS_CK(cudaFuncSetAttribute(k_sums_wide, cudaFuncAttributeMaxDynamicSharedMemorySize, ssmem));
+  note_launch();
+  k_sums_wide<<<dim3((unsigned)((max_B + 31) / 32), (unsigned)count), kSumThreads, ssmem, st>>>(jobs_dev, mode);
+  TSDS_CK(cudaGetLastError());
+  return TSDS_OK;
+}
+
 tsds_status run_lttb_jobs(const LttbJob* jobs_host, const LttbJob* jobs_dev, int count, int64_t max_B,
                           int64_t max_m, cudaStream_t st) {
   bool any_table = false, any_hull = false;
@@ -1095,8 +1186,12 @@ tsds_status run_lttb_jobs(const LttbJob* jobs_host, const LttbJob* jobs_dev, int
   const int64_t cap = (int64_t)device_sm_count() * 16;
   if (any_table) {
     note_launch();
-    k_means<<<dim3(grid_for(max_B, 4), (unsigned)count), 256, 0, st>>>(jobs_dev);
+    k_means<<<dim3(grid_for(max_B * 32, 8), (unsigned)count), 256, 0, st>>>(jobs_dev);   // a warp per bucket
     TSDS_CK(cudaGetLastError());
+    {
+      const tsds_status r = launch_sums(jobs_dev, count, max_B, 0, st);
+      if (r != TSDS_OK) return r;
+    }
     int64_t blocks = (max_B + 7) / 8;
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
@@ -1114,11 +1209,10 @@ tsds_status run_lttb_jobs(const LttbJob* jobs_host, const LttbJob* jobs_dev, int
     note_launch();
     k_p32<<<dim3((unsigned)pb, (unsigned)count), 256, 0, st>>>(jobs_dev);
     TSDS_CK(cudaGetLastError());
-    const int ssmem = (int)sizeof(SumRing);
-    TSDS_CK(cudaFuncSetAttribute(k_sums_wide, cudaFuncAttributeMaxDynamicSharedMemorySize, ssmem));
-    note_launch();
-    k_sums_wide<<<dim3((unsigned)((max_B + 31) / 32), (unsigned)count), kSumThreads, ssmem, st>>>(jobs_dev);
-    TSDS_CK(cudaGetLastError());
+    {
+      const tsds_status r = launch_sums(jobs_dev, count, max_B, 2, st);
+      if (r != TSDS_OK) return r;
+    }
     int64_t hb = (max_B + kHullWarps - 1) / kHullWarps;
     if (hb > cap) hb = cap;
     if (hb < 1) hb = 1;

@@ -25,8 +25,7 @@ __global__ void k_edges_index(const SeriesDev* sd, SeriesDev single, int count) 
     if (i == nb) {
       v = S.n;
     } else {
-      u128 num = (u128)i * (u128)(S.n - 1);
-      v = (int64_t)((num + (u128)nb - 1) / (u128)nb);
+      v = (int64_t)muldiv_ceil((uint64_t)i, (uint64_t)(S.n - 1), (uint64_t)nb);
     }
     S.edges[i] = v;
   }

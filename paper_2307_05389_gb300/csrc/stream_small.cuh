@@ -1,19 +1,18 @@
-// stream_small.cuh -- the whole MinMax/M4 pipeline of a small single-series
-// call in one launch (included by argminmax.cu after the other variants).
+// stream_small.cuh -- the MinMax/M4 pass of a single series with small bins
+// as a warp per bin (included by argminmax.cu after the other variants).
 //
-// For an input of a few MB the window machinery is all latency: claiming
-// windows, searching bin starts, publishing pieces, and separate launches for
-// the bin starts and the emit step.  Here one warp takes one bin (at most
-// kSmallMaxBinBytes of it, a few register-streaming steps): index-bin starts
-// are computed in place (x-space starts come from the edge kernel), the warp
-// reduces its bin and writes its selections, and the CTA whose arrival on a
-// device counter is the last one emits the sorted output of every bin (a
-// block-wide scan, as the emit kernel does).
+// For an input of up to a few hundred MB in bins of at most 64 KB the window
+// machinery is all latency: claiming windows, searching bin starts,
+// publishing pieces, and separate launches for the bin starts and the emit
+// step.  Here one warp takes one bin (a few register-streaming steps):
+// index-bin starts are computed in place (x-space starts come from the edge
+// kernel), the warp reduces its bin and writes its selections, and with few
+// bins the CTA whose arrival on a device counter is the last one emits the
+// sorted output of every bin (a block-wide scan, as the emit kernel does);
+// with more, the emit kernels follow.
 #pragma once
 
 constexpr int kSmallThreads = 256;          // 8 warps, 8 bins per CTA
-constexpr int64_t kSmallMaxBins = 4096;
-constexpr int64_t kSmallMaxBinBytes = 64 * 1024;
 
 // A bin's selections for the emit, read with loads that bypass L1 (the
 // selections were written by other CTAs of the same launch).
@@ -36,7 +35,7 @@ __device__ __forceinline__ int small_select(const SeriesDev& S, int64_t b, int64
   return k;
 }
 
-template <class P, int NM, int ALGO, bool HASX>
+template <class P, int NM, int ALGO, bool HASX, bool EMIT>
 __global__ void __launch_bounds__(kSmallThreads) k_small(SeriesDev S, unsigned* __restrict__ done) {
   using T = typename P::T;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -48,9 +47,8 @@ __global__ void __launch_bounds__(kSmallThreads) k_small(SeriesDev S, unsigned* 
       lo = __ldg(S.edges + b);
       hi = __ldg(S.edges + b + 1);
     } else {
-      const u128 nm1 = (u128)(S.n - 1);
-      lo = (int64_t)(((u128)b * nm1 + (u128)nb - 1) / (u128)nb);
-      hi = b + 1 == nb ? S.n : (int64_t)(((u128)(b + 1) * nm1 + (u128)nb - 1) / (u128)nb);
+      lo = (int64_t)muldiv_ceil((uint64_t)b, (uint64_t)(S.n - 1), (uint64_t)nb);
+      hi = b + 1 == nb ? S.n : (int64_t)muldiv_ceil((uint64_t)(b + 1), (uint64_t)(S.n - 1), (uint64_t)nb);
       if (lane == 0) {
         S.edges[b] = lo;
         if (b + 1 == nb) S.edges[nb] = S.n;
@@ -65,6 +63,7 @@ __global__ void __launch_bounds__(kSmallThreads) k_small(SeriesDev S, unsigned* 
       }
     }
   }
+  if (!EMIT) return;   // many bins: the emit kernels run next
   // the last CTA to arrive emits every bin
   __shared__ unsigned last;
   __threadfence();
@@ -110,16 +109,24 @@ __global__ void __launch_bounds__(kSmallThreads) k_small(SeriesDev S, unsigned* 
   if (threadIdx.x == 0 && S.out_count) *S.out_count = total;
 }
 
+template <class P, int NM, bool EMIT>
+static void launch_small_emit(const SeriesDev& S, Algo algo, bool has_x, unsigned* done, unsigned blocks,
+                              cudaStream_t st) {
+  if (algo == ALGO_MINMAX) {
+    if (has_x) k_small<P, NM, ALGO_MINMAX, true, EMIT><<<blocks, kSmallThreads, 0, st>>>(S, done);
+    else k_small<P, NM, ALGO_MINMAX, false, EMIT><<<blocks, kSmallThreads, 0, st>>>(S, done);
+  } else {
+    if (has_x) k_small<P, NM, ALGO_M4, true, EMIT><<<blocks, kSmallThreads, 0, st>>>(S, done);
+    else k_small<P, NM, ALGO_M4, false, EMIT><<<blocks, kSmallThreads, 0, st>>>(S, done);
+  }
+}
+
 template <class P, int NM>
-static cudaError_t launch_small_pol(const SeriesDev& S, Algo algo, bool has_x, unsigned* done, cudaStream_t st) {
+static cudaError_t launch_small_pol(const SeriesDev& S, Algo algo, bool has_x, unsigned* done, bool emit,
+                                    cudaStream_t st) {
   const unsigned blocks = (unsigned)((S.nb + kSmallThreads / 32 - 1) / (kSmallThreads / 32));
   note_launch();
-  if (algo == ALGO_MINMAX) {
-    if (has_x) k_small<P, NM, ALGO_MINMAX, true><<<blocks, kSmallThreads, 0, st>>>(S, done);
-    else k_small<P, NM, ALGO_MINMAX, false><<<blocks, kSmallThreads, 0, st>>>(S, done);
-  } else {
-    if (has_x) k_small<P, NM, ALGO_M4, true><<<blocks, kSmallThreads, 0, st>>>(S, done);
-    else k_small<P, NM, ALGO_M4, false><<<blocks, kSmallThreads, 0, st>>>(S, done);
-  }
+  if (emit) launch_small_emit<P, NM, true>(S, algo, has_x, done, blocks, st);
+  else launch_small_emit<P, NM, false>(S, algo, has_x, done, blocks, st);
   return cudaGetLastError();
 }

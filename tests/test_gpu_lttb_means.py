@@ -81,6 +81,10 @@ def test_means_specials_and_quantised_nan():
     check(None, inputs.ties_and_specials(n, "float32", 8), 300, "ignore")
     check(None, inputs.quantised_nan(n, 9), 900, "propagate")
     check(None, inputs.quantised_nan(n, 9), 900, "ignore")
+    # table mode (buckets of at most 32 points): warp sums and the sequential fallback
+    for nan in ("propagate", "ignore"):
+        check(None, inputs.ties_and_specials(n, "float64", 11), 20_000, nan)
+        check(None, inputs.quantised_nan(n, 12), 5_000, nan)
 
 
 def test_means_at_the_exactness_bound():

@@ -307,7 +307,7 @@ def test_segmented_tiny_and_mixed_bins(dtype, nan, stream_variant):
 @pytest.mark.parametrize("x_dtype", [None, "int64", "float64", "uint8", "float16", "int32"])
 def test_everynth(x_dtype):
     """EveryNth: index-space and x-space bins, a single bin, the tiled emit
-    (>= 16384 bins), n_out >= n, n = 0, and x with long runs of equal values
+    (>= 4096 bins), n_out >= n, n = 0, and x with long runs of equal values
     (empty bins)."""
     n = 300_007
     y = inputs.random_walk(n, "float32", 7)

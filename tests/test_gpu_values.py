@@ -67,7 +67,7 @@ def test_binned_values_every_path(dtype, algo):
     y_big = inputs.random_walk(big, dtype, 2) if np.dtype(dtype).kind == "f" else inputs.quarter_range(big, dtype, 2)
     check(algo, None, y_small, 400)                      # one-launch small path
     check(algo, None, y_big, 2000)                       # windowed pass, per-series emit
-    check(algo, None, y_big, 80_000)                     # tiled emit (>= 16384 bins)
+    check(algo, None, y_big, 80_000)                     # tiled emit (>= 4096 bins)
     check(algo, None, y_small[:300], 400)                # n_out >= n
     if np.dtype(dtype).kind == "f":
         check(algo, None, y_small, 400, nan="ignore")
