@@ -899,9 +899,33 @@ cudaError_t launch_argminmax_sm(const SeriesDev& single, int64_t total_windows, 
 
 bool small_call(int64_t n, int64_t nb, tsds_dtype y_dtype) {
   const int64_t bytes = n * dtype_size(y_dtype);
-  if (nb < 1 || bytes > kSmallMaxBytes || bytes > kSmallMaxBinBytes * nb || variant_override() != STREAM_AUTO)
-    return false;
-  return nb <= 4096 || bytes >= 512 * nb;
+  if (nb < 1 || bytes > kSmallMaxBinBytes * nb || variant_override() != STREAM_AUTO) return false;
+  // measured on GB300: up to 256 MB a warp per bin wins from 512-byte bins
+  // on; beyond, from 8 KB bins (below that the windowed pass keeps up)
+  if (bytes <= kSmallMaxBytes) return nb <= 4096 || bytes >= 512 * nb;
+  return bytes >= 8192 * nb;
+}
+
+cudaError_t launch_bins_multi(const SeriesDev* s_dev, const int32_t* cta_series, int64_t ctas, tsds_dtype y_dtype,
+                              tsds_nan_mode nan, cudaStream_t st) {
+  if (ctas <= 0) return cudaSuccess;
+  const bool ign = nan == TSDS_NAN_IGNORE;
+#define TSDS_BINS(POL, NM) launch_bins_multi_pol<POL, NM>(s_dev, cta_series, ctas, st)
+  switch (y_dtype) {
+    case TSDS_I8: return TSDS_BINS(PolSmallInt<int8_t>, 0);
+    case TSDS_U8: return TSDS_BINS(PolSmallInt<uint8_t>, 0);
+    case TSDS_I16: return TSDS_BINS(PolSmallInt<int16_t>, 0);
+    case TSDS_U16: return TSDS_BINS(PolSmallInt<uint16_t>, 0);
+    case TSDS_I32: return TSDS_BINS(PolInt32<int32_t>, 0);
+    case TSDS_U32: return TSDS_BINS(PolInt32<uint32_t>, 0);
+    case TSDS_I64: return TSDS_BINS(PolI64, 0);
+    case TSDS_U64: return TSDS_BINS(PolU64, 0);
+    case TSDS_F16: return ign ? TSDS_BINS(PolF16<1>, 1) : TSDS_BINS(PolF16<0>, 0);
+    case TSDS_F32: return ign ? TSDS_BINS(PolF32<1>, 1) : TSDS_BINS(PolF32<0>, 0);
+    case TSDS_F64: return ign ? TSDS_BINS(PolF64Ign, 1) : TSDS_BINS(PolF64Prop, 0);
+    default: return cudaErrorInvalidValue;
+  }
+#undef TSDS_BINS
 }
 
 cudaError_t launch_small(const SeriesDev& S, tsds_dtype y_dtype, tsds_nan_mode nan, Algo algo, bool has_x,

@@ -42,14 +42,18 @@ struct BatchLayout {
   int64_t count = 0;
   int64_t total_nb = 0, max_nb = 0, total_windows = 0, y_bytes = 0;
   int64_t mean_bin_bytes = 0;  // bytes-weighted mean bin size of the binned series
-  // Series whose bins are small (below seg_max_bin_bytes) form the second
-  // group: their windows are numbered after all others, from split_windows on,
-  // so that one launch of each variant can take its own range.
-  std::vector<uint8_t> small_bins;
-  int64_t split_windows = 0;
+  int64_t mean_bin_bytes0 = 0, mean_bin_bytes1 = 0;   // the same over groups 0 and 1
+  // Series groups of the automatic variant: 0 large bins (register streaming
+  // over windows), 1 small bins below seg_max_bin_bytes (segmented, windows
+  // numbered after group 0's, from split_windows on), 2 bins from there up to
+  // kSmallMaxBinBytes (a warp per bin, mid_ctas CTAs, no windows).  With an
+  // explicit variant every series is cut into windows.
+  std::vector<uint8_t> group;
+  int64_t split_windows = 0, mid_ctas = 0;
+  bool auto_groups = true;     // how the current numbering was made
   bool any_full = false;       // some series returns every index
   size_t off_desc = 0, off_edges = 0, off_res = 0, off_cnt = 0, off_work = 0, off_map = 0, off_first = 0,
-         off_last = 0, total = 0;
+         off_last = 0, off_ctas = 0, total = 0;
   std::vector<SeriesDev> host; // descriptors (scratch pointers set by bind_layout)
   std::vector<int64_t> nb_before;  // bins of the series before each one
 };
@@ -87,20 +91,32 @@ static tsds_status check_series(tsds_algo algo, const tsds_series* s, int64_t co
   return TSDS_OK;
 }
 
-// Window bases for windows of welems elements: the series with large bins
-// first, then those with small bins (from split_windows on).
-static void number_windows(BatchLayout& L, int64_t welems) {
-  int64_t win = 0;
+// Window bases for windows of welems elements: group 0 first, then group 1
+// (from split_windows on); with auto_groups, group 2 gets CTA bases instead.
+static void number_windows(BatchLayout& L, int64_t welems, bool auto_groups) {
+  int64_t win = 0, cta = 0;
+  L.auto_groups = auto_groups;
   for (int pass = 0; pass < 2; ++pass) {
     if (pass == 1) L.split_windows = win;
     for (size_t i = 0; i < L.host.size(); ++i) {
       SeriesDev& d = L.host[i];
-      if (L.small_bins[i] != pass) continue;
+      const int g = auto_groups ? L.group[i] : 0;
+      if (g == 2) {
+        if (pass == 0) {
+          d.mode = 1;
+          d.win_base = cta;
+          cta += (d.nb + kBinsPerCta - 1) / kBinsPerCta;
+        }
+        continue;
+      }
+      if (g != pass) continue;
+      d.mode = 0;
       d.win_base = win;
       if (d.nb > 0) win += (d.n + welems - 1) / welems;
     }
   }
   L.total_windows = win;
+  L.mid_ctas = cta;
 }
 
 // Layout for the smallest window size a plan may try (most windows).
@@ -113,8 +129,8 @@ static BatchLayout make_layout(tsds_algo algo, const tsds_series* s, int64_t cou
   L.host.resize((size_t)count);
   L.nb_before.resize((size_t)count);
   int64_t nb_sum = 0;
-  double wsum = 0.0, wbin = 0.0;
-  L.small_bins.assign((size_t)count, 0);
+  double wsum = 0.0, wbin = 0.0, gsum[3] = {0.0, 0.0, 0.0}, gbin[3] = {0.0, 0.0, 0.0};
+  L.group.assign((size_t)count, 0);
   for (int64_t i = 0; i < count; ++i) {
     const tsds_series& q = s[i];
     SeriesDev& d = L.host[(size_t)i];
@@ -134,13 +150,21 @@ static BatchLayout make_layout(tsds_algo algo, const tsds_series* s, int64_t cou
       const double bytes = (double)q.n * (double)dtype_size(y_dtype);
       wsum += bytes;
       wbin += bytes * (bytes / (double)d.nb);
-      L.small_bins[(size_t)i] = bytes / (double)d.nb < (double)seg_max_bin_bytes(dtype_size(y_dtype));
+      const double bin = bytes / (double)d.nb;
+      const int g = bin < (double)seg_max_bin_bytes(dtype_size(y_dtype)) ? 1 : bin <= (double)kSmallMaxBinBytes ? 2 : 0;
+      L.group[(size_t)i] = (uint8_t)g;
+      gsum[g] += bytes;
+      gbin[g] += bytes * bin;
     }
     L.y_bytes += q.n * dtype_size(y_dtype);
   }
   L.mean_bin_bytes = wsum > 0.0 ? (int64_t)(wbin / wsum) : 0;
-  number_windows(L, welems);
+  L.mean_bin_bytes0 = gsum[0] > 0.0 ? (int64_t)(gbin[0] / gsum[0]) : 0;
+  L.mean_bin_bytes1 = gsum[1] > 0.0 ? (int64_t)(gbin[1] / gsum[1]) : 0;
+  number_windows(L, welems, false);                 // every series windowed: the most windows
   const int64_t win_sum = L.total_windows;
+  number_windows(L, welems, true);
+  const int64_t ctas = L.mid_ctas;
   L.total_nb = nb_sum;
   size_t o = 0;
   L.off_desc = o;  o = up256(o + (size_t)count * sizeof(SeriesDev));
@@ -151,13 +175,15 @@ static BatchLayout make_layout(tsds_algo algo, const tsds_series* s, int64_t cou
   L.off_map = o;   o = up256(o + (size_t)win_sum * 4);
   L.off_first = o; o = up256(o + (size_t)win_sum * sizeof(Piece));
   L.off_last = o;  o = up256(o + (size_t)win_sum * sizeof(Piece));
+  L.off_ctas = o;  o = up256(o + (size_t)ctas * 4);
   L.total = o;
   return L;
 }
 
 // Points the descriptors' scratch pointers into `base` and recomputes the
-// window bases for `window_bytes` (which must be >= the layout's).
-static void bind_layout(BatchLayout& L, char* base, tsds_dtype y_dtype, int64_t window_bytes) {
+// window bases for `window_bytes` (which must be >= the layout's) and the
+// launch shape's variant.
+static void bind_layout(BatchLayout& L, char* base, tsds_dtype y_dtype, int64_t window_bytes, int variant) {
   for (size_t i = 0; i < L.host.size(); ++i) {
     SeriesDev& d = L.host[i];
     const int64_t before = L.nb_before[i];
@@ -167,11 +193,23 @@ static void bind_layout(BatchLayout& L, char* base, tsds_dtype y_dtype, int64_t 
     d.cnt = reinterpret_cast<uint32_t*>(base + L.off_cnt) + before;
     d.status = &reinterpret_cast<WorkCounters*>(base + L.off_work)->status;
   }
-  number_windows(L, window_bytes / dtype_size(y_dtype));
+  number_windows(L, window_bytes / dtype_size(y_dtype), variant == STREAM_AUTO);
 }
 
-static void rebase_windows(BatchLayout& L, tsds_dtype y_dtype, int64_t window_bytes) {
-  number_windows(L, window_bytes / dtype_size(y_dtype));
+static void rebase_windows(BatchLayout& L, tsds_dtype y_dtype, int64_t window_bytes, int variant) {
+  number_windows(L, window_bytes / dtype_size(y_dtype), variant == STREAM_AUTO);
+}
+
+// The window map and (automatic variant) the CTA map of the current numbering.
+static tsds_status launch_maps(const BatchLayout& L, char* base, tsds_dtype y_dtype, int64_t window_bytes,
+                               cudaStream_t st) {
+  const SeriesDev* sd = reinterpret_cast<const SeriesDev*>(base + L.off_desc);
+  if (L.total_windows > 0)
+    BT_CK(launch_window_map(sd, (int)L.count, reinterpret_cast<int32_t*>(base + L.off_map), y_dtype, st,
+                            window_bytes));
+  if (L.auto_groups && L.mid_ctas > 0)
+    BT_CK(launch_cta_map(sd, (int)L.count, reinterpret_cast<int32_t*>(base + L.off_ctas), st));
+  return TSDS_OK;
 }
 
 // Side stream and events a plan uses to run the two launches of a split pass
@@ -181,10 +219,11 @@ struct Fork {
   cudaEvent_t fork = nullptr, join = nullptr;
 };
 
-// The kernel sequence of one execution (descriptors and window map in place).
-// With the automatic variant and series of both kinds, the streaming pass is
-// two launches: register streaming over the large-bin series' windows and the
-// segmented kernel over the small-bin ones (each with its own work counter).
+// The kernel sequence of one execution (descriptors, window and CTA maps in
+// place).  With the automatic variant the pass is a launch per series group:
+// a warp per bin for mid-size bins, register streaming over the large-bin
+// series' windows and the segmented kernel over the small-bin ones (each
+// windowed launch with its own work counter).
 static tsds_status enqueue(const BatchLayout& L, char* base, tsds_algo algo, bool has_x, tsds_dtype x_dtype,
                            tsds_dtype y_dtype, tsds_nan_mode nan, const StreamConfig& shape, cudaStream_t st,
                            const Fork& fk = Fork()) {
@@ -202,27 +241,36 @@ static tsds_status enqueue(const BatchLayout& L, char* base, tsds_algo algo, boo
     WorkCounters* work = reinterpret_cast<WorkCounters*>(base + L.off_work);
     void* tok;
     timing_begin(st, &tok);
-    const bool split = cfg.variant == STREAM_AUTO && L.split_windows > 0 && L.split_windows < L.total_windows;
-    if (!split) {
-      BT_CK(launch_argminmax(sd, (int)L.count, none, map, L.total_windows, fp, lp, work, y_dtype, nan, st, cfg));
-    } else {
+    if (cfg.variant == STREAM_AUTO && L.auto_groups) {
+      // group 2 a warp per bin; group 0 register streaming over [0, split_windows);
+      // group 1 segmented over [split_windows, total), side by side with group 0
+      if (L.mid_ctas > 0)
+        BT_CK(launch_bins_multi(sd, reinterpret_cast<const int32_t*>(base + L.off_ctas), L.mid_ctas, y_dtype, nan,
+                                st));
       StreamConfig big = cfg, small = cfg;
       big.variant = STREAM_LDG;
+      big.mean_bin_bytes = L.mean_bin_bytes0;
       small.variant = STREAM_SEG;
+      small.mean_bin_bytes = L.mean_bin_bytes1;
       small.window_first = L.split_windows;
+      const bool g0 = L.split_windows > 0, g1 = L.total_windows > L.split_windows;
       cudaStream_t st2 = st;
-      if (fk.side) {
+      if (g0 && g1 && fk.side) {
         BT_CK(cudaEventRecord(fk.fork, st));
         BT_CK(cudaStreamWaitEvent(fk.side, fk.fork, 0));
         st2 = fk.side;
       }
-      BT_CK(launch_argminmax(sd, (int)L.count, none, map, L.total_windows, fp, lp, work + 1, y_dtype, nan, st2,
-                             small));
-      BT_CK(launch_argminmax(sd, (int)L.count, none, map, L.split_windows, fp, lp, work, y_dtype, nan, st, big));
-      if (fk.side) {
+      if (g1)
+        BT_CK(launch_argminmax(sd, (int)L.count, none, map, L.total_windows, fp, lp, work + 1, y_dtype, nan, st2,
+                               small));
+      if (g0)
+        BT_CK(launch_argminmax(sd, (int)L.count, none, map, L.split_windows, fp, lp, work, y_dtype, nan, st, big));
+      if (st2 != st) {
         BT_CK(cudaEventRecord(fk.join, fk.side));
         BT_CK(cudaStreamWaitEvent(st, fk.join, 0));
       }
+    } else if (L.total_windows > 0) {
+      BT_CK(launch_argminmax(sd, (int)L.count, none, map, L.total_windows, fp, lp, work, y_dtype, nan, st, cfg));
     }
     timing_end(st, tok);
     BT_CK(launch_emit(sd, (int)L.count, none, algo == TSDS_ALGO_MINMAX ? ALGO_MINMAX : ALGO_M4, st));
@@ -232,12 +280,11 @@ static tsds_status enqueue(const BatchLayout& L, char* base, tsds_algo algo, boo
 }
 
 static tsds_status upload(BatchLayout& L, char* base, tsds_dtype y_dtype, const StreamConfig& cfg, cudaStream_t st) {
-  rebase_windows(L, y_dtype, cfg.window_bytes);
+  rebase_windows(L, y_dtype, cfg.window_bytes, cfg.variant);
   BT_CK(cudaMemcpyAsync(base + L.off_desc, L.host.data(), L.host.size() * sizeof(SeriesDev),
                         cudaMemcpyHostToDevice, st));
-  if (L.total_windows > 0)
-    BT_CK(launch_window_map(reinterpret_cast<const SeriesDev*>(base + L.off_desc), (int)L.count,
-                            reinterpret_cast<int32_t*>(base + L.off_map), y_dtype, st, cfg.window_bytes));
+  const tsds_status s = launch_maps(L, base, y_dtype, cfg.window_bytes, st);
+  if (s != TSDS_OK) return s;
   // the host copy may be freed or reused once the upload has been consumed
   BT_CK(cudaStreamSynchronize(st));
   return TSDS_OK;
@@ -268,7 +315,7 @@ static std::string tune_key(tsds_algo algo, tsds_dtype y_dtype, bool has_x, cons
   char k[128];
   int bin_class = 0;
   for (int64_t b = std::max<int64_t>(L.mean_bin_bytes, 1); b > 1; b >>= 1) ++bin_class;
-  snprintf(k, sizeof k, "s3_a%d_y%d_x%d_b%d_c%d_m%d", (int)algo, (int)y_dtype, has_x ? 1 : 0, bytes_class,
+  snprintf(k, sizeof k, "s4_a%d_y%d_x%d_b%d_c%d_m%d", (int)algo, (int)y_dtype, has_x ? 1 : 0, bytes_class,
            count_class, bin_class);
   return k;
 }
@@ -359,12 +406,11 @@ tsds_status tsds_batched(tsds_algo algo, const tsds_series* series, int64_t coun
   Scratch sc;
   BT_CK(scratch_alloc(sc, L.total, st));
   char* base = static_cast<char*>(sc.p);
-  bind_layout(L, base, y_dtype, cfg.window_bytes);
+  bind_layout(L, base, y_dtype, cfg.window_bytes, cfg.variant);
   BT_CK(cudaMemcpyAsync(base + L.off_desc, L.host.data(), L.host.size() * sizeof(SeriesDev),
                         cudaMemcpyHostToDevice, st));
-  if (L.total_windows > 0)
-    BT_CK(launch_window_map(reinterpret_cast<const SeriesDev*>(base + L.off_desc), (int)L.count,
-                            reinterpret_cast<int32_t*>(base + L.off_map), y_dtype, st, cfg.window_bytes));
+  s = launch_maps(L, base, y_dtype, cfg.window_bytes, st);
+  if (s != TSDS_OK) return s;
   s = enqueue(L, base, algo, batch_has_x(series, count), x_dtype, y_dtype, nan, cfg, st);
   if (s != TSDS_OK) return s;
   // the pageable descriptor copy was staged by the runtime before cudaMemcpyAsync returned
@@ -392,7 +438,7 @@ tsds_status tsds_plan_create(tsds_plan* plan, tsds_algo algo, const tsds_series*
     delete p;
     return fail(TSDS_ENOMEM, "tsds_plan_create: cudaMalloc(%zu): %s", P->L.total, cudaGetErrorString(e));
   }
-  bind_layout(P->L, P->base, y_dtype, kCandidates[0].window_bytes);
+  bind_layout(P->L, P->base, y_dtype, kCandidates[0].window_bytes, kCandidates[0].variant);
   if (cudaStreamCreateWithFlags(&P->fork.side, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&P->fork.fork, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&P->fork.join, cudaEventDisableTiming) != cudaSuccess) {
@@ -473,8 +519,8 @@ tsds_status tsds_plan_info(tsds_plan plan, int64_t* window_bytes, int* ctas_per_
   if (variant) {
     StreamConfig c = P->cfg;
     c.mean_bin_bytes = P->L.mean_bin_bytes;
-    const bool split = c.variant == STREAM_AUTO && P->L.split_windows > 0 && P->L.split_windows < P->L.total_windows;
-    *variant = split ? STREAM_AUTO : stream_variant_for(c, dtype_size(P->y_dtype));
+    // the automatic variant runs a launch per group
+    *variant = c.variant == STREAM_AUTO ? STREAM_AUTO : stream_variant_for(c, dtype_size(P->y_dtype));
   }
   return TSDS_OK;
 }

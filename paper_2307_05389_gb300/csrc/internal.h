@@ -41,6 +41,8 @@ struct SeriesDev {
   const unsigned long long* status;  // device status word of the streaming pass (null: none);
                                      // non-zero makes emit report -status as the count
   Gather g;           // values written beside the indices (y[v], x[v] for index v + idx_bias)
+  int32_t mode;       // batched: 0 the series is cut into windows; 1 a warp per bin, and
+                      // win_base is its first CTA in that launch (kBinsPerCta bins each)
 };
 
 // Partial argmin/argmax of one bin piece: ordered 64-bit keys plus indices.
@@ -123,10 +125,10 @@ cudaError_t launch_argminmax_sm(const SeriesDev& single, int64_t total_windows, 
                                 Piece* last_piece, WorkCounters* work, tsds_dtype y_dtype, tsds_nan_mode nan,
                                 const StreamConfig& cfg, int sm_count, cudaStream_t st);
 
-// Single-series calls with bins of at most 64 KB on average and at most
-// 256 MB of y (either at most 4096 bins, or bins of at least 512 bytes, where
-// a warp per bin beats the segmented pass) and no explicit streaming
-// variant: a warp per bin in one launch (index-bin starts in the kernel,
+// Single-series calls with bins of at most 64 KB on average, no explicit
+// streaming variant, and either at most 256 MB of y (at most 4096 bins, or
+// bins of at least 512 bytes) or bins of at least 8 KB: a warp per bin in one
+// launch (index-bin starts in the kernel,
 // x-space starts from launch_edges first).  With emit (at most
 // kSmallEmitMaxBins bins) the last CTA also emits, with `done` a zeroed
 // counter; otherwise launch_emit / launch_emit_tiled follow.
@@ -140,6 +142,13 @@ cudaError_t launch_small(const SeriesDev& S, tsds_dtype y_dtype, tsds_nan_mode n
 // A kernel whose barrier wait nothing satisfies, bounded by `rounds`; writes
 // the status it ends with (TSDS_ETIMEOUT) to *status.
 cudaError_t launch_wait_probe(unsigned long long* status, unsigned rounds, cudaStream_t st);
+
+// Batched series in mode 1: a warp per bin over CTAs of kBinsPerCta bins
+// (cta_series maps each CTA to its series; launch_cta_map fills it).
+constexpr int kBinsPerCta = 8;
+cudaError_t launch_cta_map(const SeriesDev* s_dev, int count, int32_t* cta_series, cudaStream_t st);
+cudaError_t launch_bins_multi(const SeriesDev* s_dev, const int32_t* cta_series, int64_t ctas, tsds_dtype y_dtype,
+                              tsds_nan_mode nan, cudaStream_t st);
 
 // Every series with nb == 0 gets 0..n-1 (its n_out >= n) and *out_count = n.
 cudaError_t launch_iota_batched(const SeriesDev* s_dev, int count, cudaStream_t st);

@@ -115,7 +115,7 @@ cudaError_t launch_edges(const SeriesDev* s_dev, int count, const SeriesDev* s_h
 
 __global__ void k_window_map(const SeriesDev* sd, int32_t* win_series, int64_t welems) {
   const SeriesDev S = sd[blockIdx.x];
-  if (S.nb <= 0) return;
+  if (S.nb <= 0 || S.mode != 0) return;
   int64_t k = (S.n + welems - 1) / welems;
   for (int64_t w = threadIdx.x; w < k; w += blockDim.x) win_series[S.win_base + w] = (int32_t)blockIdx.x;
 }
@@ -124,6 +124,20 @@ cudaError_t launch_window_map(const SeriesDev* s_dev, int count, int32_t* win_se
                               tsds_dtype y_dtype, cudaStream_t st, int64_t window_bytes) {
   note_launch();
   k_window_map<<<count, 256, 0, st>>>(s_dev, win_series, window_bytes / dtype_size(y_dtype));
+  return cudaGetLastError();
+}
+
+// cta_series[win_base + c] = the series, for each CTA c of a series in mode 1.
+__global__ void k_cta_map(const SeriesDev* sd, int32_t* cta_series) {
+  const SeriesDev S = sd[blockIdx.x];
+  if (S.nb <= 0 || S.mode != 1) return;
+  const int64_t ctas = (S.nb + kBinsPerCta - 1) / kBinsPerCta;
+  for (int64_t c = threadIdx.x; c < ctas; c += blockDim.x) cta_series[S.win_base + c] = (int32_t)blockIdx.x;
+}
+
+cudaError_t launch_cta_map(const SeriesDev* s_dev, int count, int32_t* cta_series, cudaStream_t st) {
+  note_launch();
+  k_cta_map<<<count, 256, 0, st>>>(s_dev, cta_series);
   return cudaGetLastError();
 }
 

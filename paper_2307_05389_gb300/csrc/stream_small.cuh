@@ -130,3 +130,34 @@ static cudaError_t launch_small_pol(const SeriesDev& S, Algo algo, bool has_x, u
   else launch_small_emit<P, NM, false>(S, algo, has_x, done, blocks, st);
   return cudaGetLastError();
 }
+
+// Batched series in mode 1 (bins of a few hundred bytes to 64 KB): CTA c
+// takes bins kBinsPerCta*(c - win_base) .. of series cta_series[c], a warp
+// each, with the bin starts the edge kernel wrote; the per-series emit runs
+// after it.
+template <class P, int NM>
+__global__ void __launch_bounds__(kSmallThreads) k_bins_multi(const SeriesDev* __restrict__ sd,
+                                                              const int32_t* __restrict__ cta_series) {
+  using T = typename P::T;
+  static_assert(kSmallThreads / 32 == kBinsPerCta, "a warp per bin");
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const SeriesDev S = sd[cta_series[blockIdx.x]];
+  const int64_t b = ((int64_t)blockIdx.x - S.win_base) * kBinsPerCta + warp;
+  if (b >= S.nb) return;
+  const int64_t lo = __ldg(S.edges + b), hi = __ldg(S.edges + b + 1);
+  if (hi <= lo) return;
+  Cand c = piece_ldg<P>(static_cast<const T*>(S.y), lo, hi);
+  finish_bin<P, NM>(c, lo);
+  if (lane == 0) {
+    S.res[2 * b] = c.imin;
+    S.res[2 * b + 1] = c.imax;
+  }
+}
+
+template <class P, int NM>
+static cudaError_t launch_bins_multi_pol(const SeriesDev* sd, const int32_t* cta_series, int64_t ctas,
+                                         cudaStream_t st) {
+  note_launch();
+  k_bins_multi<P, NM><<<(unsigned)ctas, kSmallThreads, 0, st>>>(sd, cta_series);
+  return cudaGetLastError();
+}

@@ -118,18 +118,20 @@ def test_batched_rejects_mixed_x_and_bad_n_out():
 @pytest.mark.parametrize("graph", [False, True])
 @pytest.mark.parametrize("algo", ["minmax", "m4"])
 def test_split_pass_small_and_large_bins(graph, algo):
-    """A batch whose series fall on both sides of the small-bin threshold runs
-    the streaming pass as two launches (one per kernel variant, side by side in
-    a plan); every series must still match the oracle, bins cut by windows
-    included."""
+    """A batch with series in all three groups of the automatic variant (bins
+    of tens of bytes: segmented windows; a few KB: a warp per bin; hundreds
+    of KB: register-streaming windows) runs a launch per group; every series
+    must still match the oracle, bins cut by windows included."""
     rng = np.random.default_rng(21)
     ys, n_outs = [], []
     for i in range(24):
-        if i % 2:
+        if i % 3 == 1:
             n = int(rng.integers(20_000, 90_000)); n_out = 4000    # bins of tens of bytes
+        elif i % 3 == 2:
+            n = int(rng.integers(100_000, 400_000)); n_out = 400   # bins of a few KB
         else:
-            n = int(rng.integers(300_000, 900_000)); n_out = 40    # bins of tens of KB
-        ys.append(inputs.ties_and_specials(n, "float32", seed=100 + i) if i % 3 == 0 else
+            n = int(rng.integers(2_000_000, 3_000_000)); n_out = 40    # bins of hundreds of KB
+        ys.append(inputs.ties_and_specials(n, "float32", seed=100 + i) if i % 4 == 0 else
                   inputs.random_walk(n, "float32", seed=100 + i))
         n_outs.append(n_out)
     n_outs = np.array(n_outs)
