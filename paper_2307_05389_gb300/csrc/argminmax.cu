@@ -907,10 +907,10 @@ bool small_call(int64_t n, int64_t nb, tsds_dtype y_dtype) {
 }
 
 cudaError_t launch_bins_multi(const SeriesDev* s_dev, const int32_t* cta_series, int64_t ctas, tsds_dtype y_dtype,
-                              tsds_nan_mode nan, cudaStream_t st) {
+                              tsds_nan_mode nan, cudaStream_t st, const int64_t* ctas_dev) {
   if (ctas <= 0) return cudaSuccess;
   const bool ign = nan == TSDS_NAN_IGNORE;
-#define TSDS_BINS(POL, NM) launch_bins_multi_pol<POL, NM>(s_dev, cta_series, ctas, st)
+#define TSDS_BINS(POL, NM) launch_bins_multi_pol<POL, NM>(s_dev, cta_series, ctas, ctas_dev, st)
   switch (y_dtype) {
     case TSDS_I8: return TSDS_BINS(PolSmallInt<int8_t>, 0);
     case TSDS_U8: return TSDS_BINS(PolSmallInt<uint8_t>, 0);

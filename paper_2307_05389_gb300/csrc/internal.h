@@ -147,8 +147,9 @@ cudaError_t launch_wait_probe(unsigned long long* status, unsigned rounds, cudaS
 // (cta_series maps each CTA to its series; launch_cta_map fills it).
 constexpr int kBinsPerCta = 8;
 cudaError_t launch_cta_map(const SeriesDev* s_dev, int count, int32_t* cta_series, cudaStream_t st);
+// ctas_dev (optional): the actual number of CTAs, read on the device (ctas is then a bound)
 cudaError_t launch_bins_multi(const SeriesDev* s_dev, const int32_t* cta_series, int64_t ctas, tsds_dtype y_dtype,
-                              tsds_nan_mode nan, cudaStream_t st);
+                              tsds_nan_mode nan, cudaStream_t st, const int64_t* ctas_dev = nullptr);
 
 // Every series with nb == 0 gets 0..n-1 (its n_out >= n) and *out_count = n.
 cudaError_t launch_iota_batched(const SeriesDev* s_dev, int count, cudaStream_t st);

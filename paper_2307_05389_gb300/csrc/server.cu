@@ -127,26 +127,32 @@ __global__ void k_resolve(const QueryDev* __restrict__ qd, SeriesDev* __restrict
   D.idx_bias = S.idx_bias;
   D.out = S.out;
   D.out_count = S.out_count;
-  windows[q] = S.nb > 0 ? (S.n + welems - 1) / welems : 0;
-  // bins under the small-bin size go to the segmented launch
-  small[q] = (S.nb > 0 && S.n * y_size < small_bin_bytes * S.nb) ? 1 : 0;
+  // bins under the small-bin size go to the segmented launch, bins from there
+  // to kSmallMaxBinBytes to a warp per bin (mode 1, no windows), larger ones
+  // to the register-streaming launch
+  const int64_t bytes = S.n * y_size;
+  const int8_t g = S.nb <= 0 ? 0 : bytes < small_bin_bytes * S.nb ? 1 : bytes <= kSmallMaxBinBytes * S.nb ? 2 : 0;
+  small[q] = g;
+  D.mode = g == 2 ? 1 : 0;
+  windows[q] = S.nb > 0 && g != 2 ? (S.n + welems - 1) / welems : 0;
   Q.info[1] = L;
   Q.info[2] = lo;
 }
 
 // Window bases of the queries: those with large bins first, then those with
 // small bins; total[0] = all windows, total[1] = the large-bin windows (where
-// the small-bin range starts).  One CTA.
+// the small-bin range starts).  Queries in mode 1 get CTA bases instead, and
+// total[2] = their CTAs.  One CTA.
 __global__ void k_scan_windows(SeriesDev* __restrict__ sd, const int64_t* __restrict__ windows,
                                const int8_t* __restrict__ small, int count, int64_t* __restrict__ total) {
-  __shared__ int64_t part[2][1024];
+  __shared__ int64_t part[3][1024];
   const int t = threadIdx.x;
   const int per = (count + blockDim.x - 1) / blockDim.x;
   const int a = min(t * per, count), b = min(a + per, count);
-  int64_t s0 = 0, s1 = 0;
-  for (int i = a; i < b; ++i) (small[i] ? s1 : s0) += windows[i];
-  part[0][t] = s0;
-  part[1][t] = s1;
+  int64_t s[3] = {0, 0, 0};
+  for (int i = a; i < b; ++i)
+    s[small[i]] += small[i] == 2 ? (sd[i].nb + kBinsPerCta - 1) / kBinsPerCta : windows[i];
+  for (int g = 0; g < 3; ++g) part[g][t] = s[g];
   __syncthreads();
   if (t == 0) {
     int64_t run = 0;
@@ -155,12 +161,16 @@ __global__ void k_scan_windows(SeriesDev* __restrict__ sd, const int64_t* __rest
       for (int i = 0; i < (int)blockDim.x; ++i) { const int64_t v = part[g][i]; part[g][i] = run; run += v; }
     }
     total[0] = run;
+    run = 0;
+    for (int i = 0; i < (int)blockDim.x; ++i) { const int64_t v = part[2][i]; part[2][i] = run; run += v; }
+    total[2] = run;
   }
   __syncthreads();
-  int64_t r0 = part[0][t], r1 = part[1][t];
+  int64_t r[3] = {part[0][t], part[1][t], part[2][t]};
   for (int i = a; i < b; ++i) {
-    if (small[i]) { sd[i].win_base = r1; r1 += windows[i]; }
-    else { sd[i].win_base = r0; r0 += windows[i]; }
+    const int g = small[i];
+    sd[i].win_base = r[g];
+    r[g] += g == 2 ? (sd[i].nb + kBinsPerCta - 1) / kBinsPerCta : windows[i];
   }
 }
 
@@ -321,13 +331,14 @@ tsds_status launch_batch(const Server& S, Slot& sl, const std::vector<tsds_query
   const size_t off_q = 0, off_sd = off_q + sz_q, off_ljobs = off_sd + sz_s, off_pjobs = off_ljobs + sz_l;
   const size_t in_bytes = off_pjobs + sz_p;
   size_t o = up256(in_bytes);
-  const size_t off_win = o; o = up256(o + (size_t)count * 8 + 16);   // windows, total, large-bin windows
+  const size_t off_win = o; o = up256(o + (size_t)count * 8 + 24);   // windows; all, large-bin windows; CTAs
   const size_t off_small = o; o = up256(o + (size_t)count);
   std::vector<size_t> off_edges(count), off_res(count), off_cnt(count), off_R(count), off_lt(count);
-  int64_t max_nb = 0, win_ub = 0;
+  int64_t max_nb = 0, win_ub = 0, cta_ub = 0;
   for (int i = 0; i < count; ++i) {
     const int64_t nb = nb_of(qs[i]);
     max_nb = std::max(max_nb, nb);
+    cta_ub += (nb + kBinsPerCta - 1) / kBinsPerCta;
     off_edges[i] = o; o = up256(o + (size_t)(nb + 1) * 8);
     off_res[i] = o;   o = up256(o + (size_t)nb * 16);
     win_ub += (ser[i].n * ys + window_bytes - 1) / window_bytes + 1;
@@ -340,6 +351,7 @@ tsds_status launch_batch(const Server& S, Slot& sl, const std::vector<tsds_query
   const size_t off_map = o;   o = up256(o + (size_t)win_ub * 4);
   const size_t off_first = o; o = up256(o + (size_t)win_ub * sizeof(Piece));
   const size_t off_last = o;  o = up256(o + (size_t)win_ub * sizeof(Piece));
+  const size_t off_ctas = o;  o = up256(o + (size_t)cta_ub * 4);
   // results: per query n_out indices then kInfoSlots info words, contiguous for one copy back
   const size_t off_out = o;
   sl.out_off.assign(count, 0);
@@ -465,6 +477,7 @@ tsds_status launch_batch(const Server& S, Slot& sl, const std::vector<tsds_query
   k_scan_windows<<<1, 1024, 0, st>>>(dsd, windows, small, count, total_dev);
   SV_CK(cudaGetLastError());
   SV_CK(launch_window_map(dsd, count, reinterpret_cast<int32_t*>(base + off_map), S.y_dtype, st, window_bytes));
+  SV_CK(launch_cta_map(dsd, count, reinterpret_cast<int32_t*>(base + off_ctas), st));
   SV_CK(launch_edges(dsd, count, nullptr, has_x, S.x_dtype, max_nb, st));
   SeriesDev none;
   memset(&none, 0, sizeof none);
@@ -478,6 +491,9 @@ tsds_status launch_batch(const Server& S, Slot& sl, const std::vector<tsds_query
   Piece* fp = reinterpret_cast<Piece*>(base + off_first);
   Piece* lp = reinterpret_cast<Piece*>(base + off_last);
   WorkCounters* work = reinterpret_cast<WorkCounters*>(base + off_work);
+  // mid-size bins: a warp per bin over the CTAs counted on the device
+  SV_CK(launch_bins_multi(dsd, reinterpret_cast<const int32_t*>(base + off_ctas), std::max<int64_t>(cta_ub, 1), S.y_dtype,
+                          nan, st, total_dev + 2));
   StreamConfig big;
   big.variant = STREAM_LDG;
   big.total_windows_dev = can_split ? total_dev + 1 : total_dev;

@@ -137,10 +137,12 @@ static cudaError_t launch_small_pol(const SeriesDev& S, Algo algo, bool has_x, u
 // after it.
 template <class P, int NM>
 __global__ void __launch_bounds__(kSmallThreads) k_bins_multi(const SeriesDev* __restrict__ sd,
-                                                              const int32_t* __restrict__ cta_series) {
+                                                              const int32_t* __restrict__ cta_series,
+                                                              const int64_t* __restrict__ ctas_dev) {
   using T = typename P::T;
   static_assert(kSmallThreads / 32 == kBinsPerCta, "a warp per bin");
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (ctas_dev && (int64_t)blockIdx.x >= *ctas_dev) return;   // a grid sized by a bound
   const SeriesDev S = sd[cta_series[blockIdx.x]];
   const int64_t b = ((int64_t)blockIdx.x - S.win_base) * kBinsPerCta + warp;
   if (b >= S.nb) return;
@@ -156,8 +158,8 @@ __global__ void __launch_bounds__(kSmallThreads) k_bins_multi(const SeriesDev* _
 
 template <class P, int NM>
 static cudaError_t launch_bins_multi_pol(const SeriesDev* sd, const int32_t* cta_series, int64_t ctas,
-                                         cudaStream_t st) {
+                                         const int64_t* ctas_dev, cudaStream_t st) {
   note_launch();
-  k_bins_multi<P, NM><<<(unsigned)ctas, kSmallThreads, 0, st>>>(sd, cta_series);
+  k_bins_multi<P, NM><<<(unsigned)ctas, kSmallThreads, 0, st>>>(sd, cta_series, ctas_dev);
   return cudaGetLastError();
 }
