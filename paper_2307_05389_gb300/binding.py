@@ -567,23 +567,49 @@ def downsample(algo, y, n_out, x=None, nan="propagate", minmax_ratio=4, out=None
 
 def downsample_host(algos, y, n_out, x=None, nan="propagate", minmax_ratio=4, device="cuda",
                     y_dev=None, x_dev=None):
-    """Host-buffer form: copies y (and x) from host memory to the device once
-    (asynchronously when the host tensors are pinned), runs each algorithm in
-    `algos` on the GPU and copies each index list back.  Returns a list of
-    CPU int64 tensors.  y_dev / x_dev may supply preallocated device buffers
-    to copy into."""
+    """Host-buffer form: copies y from host memory to the device once
+    (asynchronously when the host tensor is pinned), runs each algorithm in
+    `algos` on the GPU and copies each index list back.  A pinned x is read in
+    place by the bin search of MinMax, M4 and EveryNth (which probes only
+    about log2(n) values per bin); otherwise x is copied too.  Returns a list
+    of CPU int64 tensors.  y_dev / x_dev may supply preallocated device
+    buffers to copy into."""
     import torch
     st = torch.cuda.current_stream(device)
     yd = y_dev if y_dev is not None else torch.empty_like(y, device=device)
     yd.copy_(y, non_blocking=True)
-    xd = None
+    xp, xd = None, 0
     if x is not None:
-        xd = x_dev if x_dev is not None else torch.empty_like(x, device=device)
-        xd.copy_(x, non_blocking=True)
+        if x.is_pinned() and all(a in ("minmax", "m4", "everynth") for a in algos):
+            # page-locked x is read in place: the bin search probes about log2(n)
+            # elements per bin, so x is not copied (the device reads pinned host
+            # memory through its unified address)
+            xp = x.data_ptr()
+        else:
+            xdev = x_dev if x_dev is not None else torch.empty_like(x, device=device)
+            xdev.copy_(x, non_blocking=True)
+            xp = xdev.data_ptr()
+        xd = DTYPES[_torch_dtype_name(x)]
+    fns = {"minmax": tsds_minmax, "m4": tsds_m4, "lttb": tsds_lttb, "everynth": tsds_everynth}
+    n = yd.shape[0]
     res = []
     for algo in algos:
-        out, cnt = downsample(algo, yd, n_out, x=xd, nan=nan, minmax_ratio=minmax_ratio, stream=st, sync=False)
+        out = torch.empty(out_capacity(algo, n, n_out), dtype=torch.int64, device=yd.device)
+        cnt = torch.empty(1, dtype=torch.int64, device=yd.device)
+        args = (xp, xd, yd.data_ptr(), DTYPES[_torch_dtype_name(yd)], n, n_out)
+        tail = (NAN_MODES[nan], out.data_ptr(), cnt.data_ptr(), ctypes.c_void_p(st.cuda_stream))
+        with torch.cuda.device(yd.device):
+            if algo == "minmaxlttb":
+                r = tsds_minmaxlttb(*args, minmax_ratio, *tail)
+            elif algo in fns:
+                r = fns[algo](*args, *tail)
+            else:
+                raise ValueError(f"unknown algorithm {algo!r}")
+        if r != 0:
+            raise TsdsError(r, last_error())
         k = int(cnt.item())
+        if k < 0:
+            raise TsdsError(-k, "the streaming pass reported a device-side failure")
         res.append(out[:k].cpu())
     return res
 

@@ -128,3 +128,20 @@ def test_everynth_values(dtype):
         check("everynth", None, y, n_out)
         check("everynth", x, y, n_out)
     check("everynth", x[:100], y[:100], 100)
+
+
+def test_downsample_host_pinned_x_read_in_place():
+    """downsample_host with page-locked host buffers: y is copied, a pinned x
+    is searched in place; the indices equal the oracle's."""
+    import torch
+    n = 400_003
+    y = inputs.random_walk(n, "float32", 9)
+    x = inputs.geometric_x(n, 9)
+    yh = torch.from_numpy(y).pin_memory()
+    xh = torch.from_numpy(x).pin_memory()
+    res = binding.downsample_host(["minmax", "m4", "everynth"], yh, 2000, x=xh)
+    for algo, got in zip(["minmax", "m4", "everynth"], res):
+        np.testing.assert_array_equal(got.numpy(), oracle.downsample(algo, x, y, 2000))
+    res = binding.downsample_host(["minmaxlttb", "lttb"], yh, 2000, x=xh)   # x copied for the LTTB family
+    for algo, got in zip(["minmaxlttb", "lttb"], res):
+        np.testing.assert_array_equal(got.numpy(), oracle.downsample(algo, x, y, 2000))
