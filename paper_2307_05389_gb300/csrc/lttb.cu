@@ -983,7 +983,15 @@ __global__ void __launch_bounds__(kSegWarpsC * 32) k_compose(const LttbJob* __re
   for (int64_t seg = (int64_t)blockIdx.x * kSegWarpsC + w; seg < nseg; seg += (int64_t)gridDim.x * kSegWarpsC) {
     const int64_t j0 = seg * kSeg;
     const int len = (int)min((int64_t)kSeg, B - j0);
-    for (int t = 0; t < len; ++t) rows[w][t][lane] = lane < W ? J.fslot[(j0 + t) * W + lane] : -1;
+    // the segment's rows, eight loads in flight per lane
+    for (int t0 = 0; t0 < len; t0 += 8) {
+      int32_t v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = (t0 + u < len && lane < W) ? J.fslot[(j0 + t0 + u) * W + lane] : -1;
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (t0 + u < len) rows[w][t0 + u][lane] = v[u];
+    }
     __syncwarp();
     int32_t cur = lane;
     for (int t = 0; t < len; ++t) {
@@ -1000,6 +1008,24 @@ __device__ __forceinline__ int32_t next_slot(const LttbJob& J, int64_t j, int32_
   if (J.mode == 0) return rel;
   const unsigned hit = __ballot_sync(0xffffffffu, J.cand[(j + 1) * kCandMax + lane] == rel);
   return hit ? __ffs(hit) - 1 : -1;
+}
+
+// Walks segment `seg` step by step from input slot s (or, for s < 0, from
+// the previous pick a), writing its picks; leaves s and a at the segment's end.
+__device__ __noinline__ void walk_segment(const LttbJob& J, int64_t seg, int64_t m, int64_t B, int W, int lane,
+                                          int32_t& s, int64_t& a) {
+  const int64_t j0 = seg * kSeg, j1 = min(j0 + kSeg, B);
+  int64_t lo = bucket_start(j0, m, B);
+  for (int64_t j = j0; j < j1; ++j) {
+    const int64_t hi = bucket_start(j + 1, m, B);
+    int32_t rel;
+    if (s >= 0) rel = J.table[j * W + s];
+    else rel = (int32_t)(warp_pick(J, j, lo, hi, a, m, B, lane) - lo);
+    if (lane == 0) lttb_emit(J, j + 1, lo + rel);
+    a = lo + rel;
+    s = j + 1 < B ? next_slot(J, j, rel, lane) : 0;
+    lo = hi;
+  }
 }
 
 __global__ void __launch_bounds__(32) k_chain_seg(const LttbJob* __restrict__ jobs) {
@@ -1028,28 +1054,13 @@ __global__ void __launch_bounds__(32) k_chain_seg(const LttbJob* __restrict__ jo
     cp_async_wait<kChaseRing - 1>();
     __syncwarp();
     const int n = (int)min((int64_t)kBlk, nseg - b * kBlk);
+    const int32_t* blk = ring[b % kChaseRing];
     for (int t = 0; t < n; ++t) {
       const int64_t seg = b * kBlk + t;
-      const int32_t nxt = s >= 0 ? ring[b % kChaseRing][t * kSeg + s] : -1;
-      if (nxt >= 0) {
-        if (lane == 0) J.seg_start[seg] = s;
-        s = nxt;
-        continue;
-      }
-      // the path leaves the tables inside this segment: walk it here
-      if (lane == 0) J.seg_start[seg] = -1;
-      const int64_t j0 = seg * kSeg, j1 = min(j0 + kSeg, B);
-      int64_t lo = bucket_start(j0, m, B);
-      for (int64_t j = j0; j < j1; ++j) {
-        const int64_t hi = bucket_start(j + 1, m, B);
-        int32_t rel;
-        if (s >= 0) rel = J.table[j * W + s];
-        else rel = (int32_t)(warp_pick(J, j, lo, hi, a, m, B, lane) - lo);
-        if (lane == 0) lttb_emit(J, j + 1, lo + rel);
-        a = lo + rel;
-        s = j + 1 < B ? next_slot(J, j, rel, lane) : 0;
-        lo = hi;
-      }
+      const int32_t nxt = s >= 0 ? blk[t * kSeg + s] : -1;
+      if (lane == 0) J.seg_start[seg] = nxt >= 0 ? s : -1;
+      if (nxt >= 0) s = nxt;
+      else walk_segment(J, seg, m, B, W, lane, s, a);   // the path leaves the tables in this segment
     }
     __syncwarp();
   }
@@ -1072,9 +1083,21 @@ __global__ void __launch_bounds__(kSegWarpsC * 32) k_replay(const LttbJob* __res
     if (s < 0) continue;   // written by k_chain_seg
     const int64_t j0 = seg * kSeg;
     const int len = (int)min((int64_t)kSeg, B - j0);
-    for (int t = 0; t < len; ++t) {
-      pr[w][t][lane] = lane < W ? J.table[(j0 + t) * W + lane] : 0;
-      fr[w][t][lane] = lane < W ? J.fslot[(j0 + t) * W + lane] : 0;
+    for (int t0 = 0; t0 < len; t0 += 8) {
+      int32_t pv[8], fv[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const bool ok = t0 + u < len && lane < W;
+        pv[u] = ok ? J.table[(j0 + t0 + u) * W + lane] : 0;
+        fv[u] = ok ? J.fslot[(j0 + t0 + u) * W + lane] : 0;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        if (t0 + u < len) {
+          pr[w][t0 + u][lane] = pv[u];
+          fr[w][t0 + u][lane] = fv[u];
+        }
+      }
     }
     __syncwarp();
     int32_t mine = 0;
