@@ -242,20 +242,18 @@ static tsds_status enqueue(const BatchLayout& L, char* base, tsds_algo algo, boo
     void* tok;
     timing_begin(st, &tok);
     if (cfg.variant == STREAM_AUTO && L.auto_groups) {
-      // group 2 a warp per bin; group 0 register streaming over [0, split_windows);
-      // group 1 segmented over [split_windows, total), side by side with group 0
-      if (L.mid_ctas > 0)
-        BT_CK(launch_bins_multi(sd, reinterpret_cast<const int32_t*>(base + L.off_ctas), L.mid_ctas, y_dtype, nan,
-                                st));
+      // group 1 (segmented windows [split_windows, total)) on the plan's side
+      // stream, beside group 2 (a warp per bin) and then group 0 (register
+      // streaming over [0, split_windows)) on the caller's stream
       StreamConfig big = cfg, small = cfg;
       big.variant = STREAM_LDG;
       big.mean_bin_bytes = L.mean_bin_bytes0;
       small.variant = STREAM_SEG;
       small.mean_bin_bytes = L.mean_bin_bytes1;
       small.window_first = L.split_windows;
-      const bool g0 = L.split_windows > 0, g1 = L.total_windows > L.split_windows;
+      const bool g0 = L.split_windows > 0, g1 = L.total_windows > L.split_windows, g2 = L.mid_ctas > 0;
       cudaStream_t st2 = st;
-      if (g0 && g1 && fk.side) {
+      if (g1 && (g0 || g2) && fk.side) {
         BT_CK(cudaEventRecord(fk.fork, st));
         BT_CK(cudaStreamWaitEvent(fk.side, fk.fork, 0));
         st2 = fk.side;
@@ -263,6 +261,9 @@ static tsds_status enqueue(const BatchLayout& L, char* base, tsds_algo algo, boo
       if (g1)
         BT_CK(launch_argminmax(sd, (int)L.count, none, map, L.total_windows, fp, lp, work + 1, y_dtype, nan, st2,
                                small));
+      if (g2)
+        BT_CK(launch_bins_multi(sd, reinterpret_cast<const int32_t*>(base + L.off_ctas), L.mid_ctas, y_dtype, nan,
+                                st));
       if (g0)
         BT_CK(launch_argminmax(sd, (int)L.count, none, map, L.split_windows, fp, lp, work, y_dtype, nan, st, big));
       if (st2 != st) {

@@ -193,7 +193,8 @@ cudaError_t launch_emit_tiled(const SeriesDev& single, Algo algo, int64_t* tile_
 cudaError_t launch_emit(const SeriesDev* s_dev, int count, const SeriesDev& single, Algo algo,
                         cudaStream_t st) {
   const SeriesDev* arr = (count > 1 || s_dev) ? s_dev : nullptr;
-  int64_t threads = kEmitThreads;
+  // a batch: 256 threads per series, so that eight series' CTAs share an SM
+  int64_t threads = arr ? 256 : kEmitThreads;
   if (!arr && single.nb < 1024) threads = ((single.nb + 31) / 32) * 32;
   if (threads < 32) threads = 32;
   note_launch();
