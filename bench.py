@@ -56,6 +56,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--n-out", type=int, default=N_OUT, help="n_out of the default step (profiling other bin sizes)")
+    ap.add_argument("--batch-count", type=int, default=4096, help="series in the batched suite (smaller for profiling)")
     ap.add_argument("--stream-variant", default="auto", choices=["auto", "ring", "ldg", "seg"],
                     help="kernel variant of the streaming pass (tsds_stream_variant)")
     ap.add_argument("--suite", default=None, choices=["dtypes", "config1", "lttb", "batched", "serve", "values"],
@@ -152,7 +153,7 @@ def suite_batched(args):
     from paper_2307_05389_gb300 import binding, inputs
     dev = torch.device("cuda", 0)
     stream = torch.cuda.current_stream(dev)
-    count = 4096
+    count = args.batch_count
     lens = inputs.batch_lengths(count, seed=3)
     n_outs = inputs.batch_n_out(count, seed=3)
     total = int(lens.sum())
