@@ -41,6 +41,23 @@ ALGOS = ("minmax", "m4")
 METRIC = "input GB/s and % of GB300 HBM peak per algorithm"
 WORKLOAD = ("single series n=1e9 float32 random walk with int64 sorted non-equidistant x "
             "(geometric(0.5) gaps), n_out=2000, MinMax + M4")
+
+
+def workload_name(n, n_out):
+    """The default step's workload, or the same recipe at other sizes (profiling runs)."""
+    if n == N_DEFAULT and n_out == N_OUT:
+        return WORKLOAD
+    return (f"single series n={n:.4g} float32 random walk with int64 sorted non-equidistant x "
+            f"(geometric(0.5) gaps), n_out={n_out}, MinMax + M4")
+
+
+def l2_note(n):
+    gb = n * 4 / 1e9
+    if n * 4 > 129e6:
+        return f"inputs larger than L2 ({gb:.4g} GB y, {2 * gb:.4g} GB x); no flush"
+    return f"y ({gb:.4g} GB) fits in L2: not an HBM measurement"
+
+
 FALLBACK_HBM = 6800.0
 
 
@@ -777,8 +794,8 @@ def main():
             "warmup": max(3, args.warmup), "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "impl": "native",
-            "config": {"workload": WORKLOAD, "n": n, "n_out": args.n_out, "algorithms": list(ALGOS),
-                       "x": "int64", "y": "float32", "l2": "inputs larger than L2 (4 GB y, 8 GB x); no flush",
+            "config": {"workload": workload_name(n, args.n_out), "n": n, "n_out": args.n_out,
+                       "algorithms": list(ALGOS), "x": "int64", "y": "float32", "l2": l2_note(n),
                        "parallelism": f"{world} independent series (one per GPU)" if world > 1 else "single GPU"},
             "pct_of_hbm_peak": 100.0 * value / world / peak,
             "per_algo": per_algo,

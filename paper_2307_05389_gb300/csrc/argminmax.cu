@@ -122,10 +122,10 @@ struct PolF32 {
   __device__ static bool match(T e, Acc t) { return isnan(t) ? isnan(e) : e == t; }
   __device__ static bool match_min(T e, Acc t) { return match(e, t); }
   __device__ static bool match_max(T e, Acc t) { return match(e, t); }
-  __device__ static uint64_t key_min(Acc a) { return fkey_min<NM>((double)a); }
-  __device__ static uint64_t key_max(Acc a) { return fkey_max<NM>((double)a); }
-  __device__ static uint64_t elem_key_min(T e) { return fkey_min<NM>((double)e); }
-  __device__ static uint64_t elem_key_max(T e) { return fkey_max<NM>((double)e); }
+  __device__ static uint64_t key_min(Acc a) { return f32key_min<NM>(a); }
+  __device__ static uint64_t key_max(Acc a) { return f32key_max<NM>(a); }
+  __device__ static uint64_t elem_key_min(T e) { return f32key_min<NM>(e); }
+  __device__ static uint64_t elem_key_max(T e) { return f32key_max<NM>(e); }
 };
 
 // float16: packed half2 min/max, then one FP32 comparison per group.
@@ -165,10 +165,10 @@ struct PolF16 {
   __device__ static bool match(T e, Acc t) { float f = __half2float(e); return isnan(t) ? isnan(f) : f == t; }
   __device__ static bool match_min(T e, Acc t) { return match(e, t); }
   __device__ static bool match_max(T e, Acc t) { return match(e, t); }
-  __device__ static uint64_t key_min(Acc a) { return fkey_min<NM>((double)a); }
-  __device__ static uint64_t key_max(Acc a) { return fkey_max<NM>((double)a); }
-  __device__ static uint64_t elem_key_min(T e) { return fkey_min<NM>((double)__half2float(e)); }
-  __device__ static uint64_t elem_key_max(T e) { return fkey_max<NM>((double)__half2float(e)); }
+  __device__ static uint64_t key_min(Acc a) { return f32key_min<NM>(a); }
+  __device__ static uint64_t key_max(Acc a) { return f32key_max<NM>(a); }
+  __device__ static uint64_t elem_key_min(T e) { return f32key_min<NM>(__half2float(e)); }
+  __device__ static uint64_t elem_key_max(T e) { return f32key_max<NM>(__half2float(e)); }
 };
 
 // 8- and 16-bit integers: widen to 16-bit lanes (PRMT) and reduce with packed

@@ -66,6 +66,25 @@ __device__ __forceinline__ uint64_t fkey_max(double d) {
   return f64_bits_key(f64_bits(d));
 }
 
+// The same order for float32 (and float16 widened to float32) straight from
+// its bits, with integer operations only: -0 as +0, negative values below
+// positive ones, NaN as in fkey_*.  Finite keys lie strictly between 0 and
+// kKeyMax, like the binary64 ones.
+__device__ __forceinline__ uint64_t f32_bits_key(uint32_t b) {
+  if (b == 0x80000000u) b = 0u;
+  return (b & 0x80000000u) ? (uint64_t)(~b) : (uint64_t)(b | 0x80000000u);
+}
+template <int NAN_MODE>
+__device__ __forceinline__ uint64_t f32key_min(float f) {
+  const uint32_t b = __float_as_uint(f);
+  return (b & 0x7fffffffu) > 0x7f800000u ? nan_key_min<NAN_MODE>() : f32_bits_key(b);
+}
+template <int NAN_MODE>
+__device__ __forceinline__ uint64_t f32key_max(float f) {
+  const uint32_t b = __float_as_uint(f);
+  return (b & 0x7fffffffu) > 0x7f800000u ? nan_key_max<NAN_MODE>() : f32_bits_key(b);
+}
+
 __device__ __forceinline__ uint64_t skey(int64_t v) { return (uint64_t)v ^ kSign64; }
 __device__ __forceinline__ uint64_t ukey(uint64_t v) { return v; }
 
