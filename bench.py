@@ -127,6 +127,7 @@ def suite_dtypes(args):
     x_n = 0
     out = torch.empty(N_OUT, dtype=torch.int64, device=dev)
     cnt = torch.empty(1, dtype=torch.int64, device=dev)
+    rpeak = None
     for d in inputs.DTYPES:
         size = np.dtype(d).itemsize
         n = 4_000_000_000 // size
@@ -137,6 +138,8 @@ def suite_dtypes(args):
             x = inputs.geometric_x_cuda(n, seed=2, device=dev)
             x_n = n
         torch.cuda.synchronize()
+        if rpeak is None:
+            rpeak = read_peak(pkg, torch, y, stream)
         row = {"n": n}
         for algo in ALGOS:
             f = lambda: _raw_call(binding, algo, x, "int64", y, d, n, N_OUT, out, cnt, stream)
@@ -148,13 +151,17 @@ def suite_dtypes(args):
             pkg.tsds_timing_enable(False)
             km, kl = pkg.tsds_timing_read()
             b = step_bytes(n)[algo] - n * 4 + n * size
+            kgb = n * size / (km / kl / 1e3) / 1e9
             row[algo] = {"call_ms": med, "call_GBps": b / (med / 1e3) / 1e9,
-                         "kernel_GBps": n * size / (km / kl / 1e3) / 1e9,
+                         "kernel_GBps": kgb,
                          "pct_of_hbm_peak": 100.0 * b / (med / 1e3) / 1e9 / peak}
+            if rpeak:
+                row[algo]["kernel_pct_of_read_peak"] = 100.0 * kgb / rpeak
         res[d] = row
         del y
         torch.cuda.empty_cache()
     return {"suite": "dtypes", "metric": METRIC, "unit": "GB/s", "peak": peak, "peak_source": peak_src,
+            "read_peak": rpeak,
             "config": {"workload": "per dtype: n*itemsize = 4e9, quarter-range uniform values, int64 geometric x, "
                                    "n_out=2000, MinMax + M4", "reps": args.steps}, "results": res}
 
@@ -543,6 +550,28 @@ def kernel_traffic():
         return None
 
 
+def read_peak(pkg, torch, y, stream, reps=10):
+    """Read-only streaming ceiling: median GB/s of the library's read probe
+    (tsds_read_stream: every byte once, 16-byte loads) over the resident y."""
+    per16 = max(1, 16 // y.element_size())
+    buf = y[: (y.numel() // per16) * per16]
+    nbytes = buf.numel() * buf.element_size()
+    if nbytes == 0:
+        return None
+    sink = torch.zeros(1, dtype=torch.int64, device=y.device)
+    for _ in range(2):
+        pkg.read_stream(buf, sink, stream)
+    times = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        pkg.read_stream(buf, sink, stream)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    return nbytes / (statistics.median(times) / 1e3) / 1e9
+
+
 # ----------------------------------------------------------------------------- clocks
 
 class ClockSampler:
@@ -739,6 +768,8 @@ def main():
                        "kernel_ms": km / max(kl, 1), "kernel_GBps": n * 4 / (km / max(kl, 1) / 1e3) / 1e9,
                        "pct_of_hbm_peak": 100.0 * per[a] / (call_ms / 1e3) / 1e9 / peak}
 
+    rpeak = read_peak(pkg, torch, y, stream)
+
     # ---- end to end through the public API with pinned host buffers
     e2e = None
     if not args.no_e2e:
@@ -803,7 +834,11 @@ def main():
                          "frac": achieved / peak, "traffic": kernel_traffic(),
                          "kernel": stream_kernel_name(n, args.n_out, args.stream_variant),
                          "bytes_per_launch": n * 4, "launches_timed": kern_launches,
-                         "peak_source": f"{peak_src} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"},
+                         "peak_source": f"{peak_src} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+                         "read_peak": None if rpeak is None else {
+                             "value": rpeak, "frac": achieved / rpeak,
+                             "source": "tsds_read_stream over the resident y (each byte read once, "
+                                       "16-byte loads), median of 10 launches, same call"}},
             "clocks": clk,
             "e2e": e2e,
             "cpu_baseline": cpu,

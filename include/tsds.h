@@ -347,6 +347,19 @@ int tsds_stream_variant(int variant);
  * event query fails. */
 tsds_status tsds_timing_read(double* total_ms, int64_t* launches);
 
+/* Measurement aid: the read-only streaming ceiling.  The per-bin pass reads
+ * each y element once and writes next to nothing (Section 2.1: one pass over
+ * the data, bound by memory), so besides the copy bandwidth its speed is set
+ * against this kernel, which does only that: it reads the `bytes` bytes at
+ * `buf` (device memory, 16-byte aligned, bytes a multiple of 16) once with
+ * 16-byte loads over a grid of a few CTAs per SM and XORs the XOR of all its
+ * 8-byte little-endian words into *sink (one device uint64, not cleared
+ * first).  The XOR makes every load observable.  Enqueued on `stream`;
+ * bytes == 0 launches nothing.  TSDS_EINVAL (nothing launched) when bytes is
+ * negative or not a multiple of 16, buf is null or misaligned with bytes > 0,
+ * or sink is null. */
+tsds_status tsds_read_stream(const void* buf, int64_t bytes, uint64_t* sink, void* stream);
+
 /* Diagnostic: the bucket averages an LTTB call with the same arguments uses
  * (Section 1: the third point of each step's triangle is the average of the
  * next bucket).  Bucket j of B = n_out - 2 covers points

@@ -44,4 +44,6 @@ from .binding import (  # noqa: F401
     tsds_kernel_launches,
     tsds_timing_enable,
     tsds_timing_read,
+    tsds_read_stream,
+    read_stream,
 )

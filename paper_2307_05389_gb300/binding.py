@@ -86,6 +86,8 @@ def load(path: str = LIB_PATH):
         f.restype = c_int
     lib.tsds_minmaxlttb_values.argtypes = [p, c_int, p, c_int, i64, i64, i64, c_int, p, p, p, p, p]
     lib.tsds_minmaxlttb_values.restype = c_int
+    lib.tsds_read_stream.argtypes = [p, i64, p, p]
+    lib.tsds_read_stream.restype = c_int
     _lib = lib
     return lib
 
@@ -119,6 +121,26 @@ def tsds_timing_read():
     if r != 0:
         raise TsdsError(r, last_error())
     return ms.value, k.value
+
+
+def tsds_read_stream(buf, nbytes, sink, stream):
+    return load().tsds_read_stream(buf, nbytes, sink, stream)
+
+
+def read_stream(buf, sink, stream=None) -> None:
+    """Reads every byte of the CUDA tensor `buf` once (the read-only streaming ceiling) and
+    XORs the XOR of its 8-byte words into the one-element int64 CUDA tensor `sink`."""
+    import torch
+    if not buf.is_cuda or not buf.is_contiguous():
+        raise ValueError("buf must be a contiguous CUDA tensor")
+    if sink.dtype != torch.int64 or sink.numel() < 1 or sink.device != buf.device:
+        raise ValueError("sink must be an int64 tensor on buf's device")
+    nbytes = buf.numel() * buf.element_size()
+    st = stream if stream is not None else torch.cuda.current_stream(buf.device)
+    with torch.cuda.device(buf.device):
+        r = tsds_read_stream(buf.data_ptr(), nbytes, sink.data_ptr(), ctypes.c_void_p(st.cuda_stream))
+    if r != 0:
+        raise TsdsError(r, last_error())
 
 
 def last_error() -> str:

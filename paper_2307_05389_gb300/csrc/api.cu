@@ -472,6 +472,17 @@ tsds_status tsds_check_wait_timeout(unsigned rounds, void* stream) {
 
 void tsds_timing_enable(int on) { g_timing.store(on ? 1 : 0); }
 
+tsds_status tsds_read_stream(const void* buf, int64_t bytes, uint64_t* sink, void* stream) {
+  if (bytes < 0 || bytes % 16 != 0)
+    return fail(TSDS_EINVAL, "tsds_read_stream: bytes must be a non-negative multiple of 16 (got %lld)",
+                (long long)bytes);
+  if (!sink) return fail(TSDS_EINVAL, "tsds_read_stream: sink is null");
+  if (bytes > 0 && (!buf || (reinterpret_cast<uintptr_t>(buf) & 15) != 0))
+    return fail(TSDS_EINVAL, "tsds_read_stream: buf must be a non-null 16-byte aligned pointer");
+  TSDS_CK(launch_read_stream(buf, bytes, sink, static_cast<cudaStream_t>(stream)));
+  return TSDS_OK;
+}
+
 tsds_status tsds_timing_read(double* total_ms, int64_t* launches) {
   std::vector<TimedLaunch> done;
   {

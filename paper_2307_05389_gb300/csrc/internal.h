@@ -170,6 +170,10 @@ cudaError_t launch_iota(int64_t* out, int64_t n, int64_t* count, cudaStream_t st
 
 int device_sm_count();
 
+// Reads bytes (a multiple of 16) at buf (16-byte aligned) once, 16 bytes per
+// load, and XORs the XOR of its 8-byte words into *sink.
+cudaError_t launch_read_stream(const void* buf, int64_t bytes, uint64_t* sink, cudaStream_t st);
+
 // Counts every kernel this library launches (reported by tsds_kernel_launches).
 void note_launch(int kernels = 1);
 

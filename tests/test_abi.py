@@ -119,3 +119,19 @@ def test_value_outputs_are_checked_on_the_host(lib):
         assert "aligned" in pkg.last_error()
         assert fn(1 << 24, 3, y, 9, 100, 8, 0, out, cnt, (1 << 23) + 4, None, None) == 1  # int64 x_out
     assert binding.tsds_minmaxlttb_values(None, 0, y, 9, 100, 8, 4, 0, out, cnt, 1 << 23, None, None) == 1
+
+
+def test_read_stream_arguments_are_checked_on_the_host(lib):
+    """The read-only streaming probe rejects bad sizes and pointers before any
+    launch; zero bytes launch nothing."""
+    buf, sink = 1 << 20, 1 << 21
+    assert binding.tsds_read_stream(buf, -16, sink, None) == 1
+    assert binding.tsds_read_stream(buf, 24, sink, None) == 1           # not a multiple of 16
+    assert "multiple of 16" in pkg.last_error()
+    assert binding.tsds_read_stream(buf, 32, None, None) == 1           # no sink
+    assert binding.tsds_read_stream(buf + 8, 32, sink, None) == 1       # misaligned
+    assert binding.tsds_read_stream(None, 32, sink, None) == 1
+    assert "aligned" in pkg.last_error()
+    before = pkg.tsds_kernel_launches()
+    assert binding.tsds_read_stream(None, 0, sink, None) == 0
+    assert pkg.tsds_kernel_launches() == before
