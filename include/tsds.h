@@ -14,8 +14,10 @@
  *    the caller.  The library never frees them, never keeps them past the
  *    call's completion on the stream and never copies y or x.
  *  - y holds n elements of y_dtype; x is NULL (equally spaced points, Section
- *    2.3) or holds n elements of x_dtype sorted non-decreasing (not checked).
- *    Both must be aligned to their element size.
+ *    2.3) or holds n elements of x_dtype sorted non-decreasing, with no NaN.
+ *    That order is checked only in checked mode (tsds_checked); otherwise an
+ *    x out of order gives unspecified indices.  Both must be aligned to their
+ *    element size.
  *  - out must have room for n_out indices (for MinMaxLTTB also n_out); when
  *    n_out >= n it receives 0..n-1 and needs room for n.  *out_count (a device
  *    int64) receives the number of indices written.  With x, empty bins select
@@ -346,6 +348,19 @@ int tsds_stream_variant(int variant);
  * number to *launches (may be NULL), and forgets them.  TSDS_ECUDA if an
  * event query fails. */
 tsds_status tsds_timing_read(double* total_ms, int64_t* launches);
+
+/* Checked mode.  When on, every entry point that takes x (the single-series
+ * calls and their *_values forms, tsds_lttb_means, tsds_batched,
+ * tsds_plan_create, tsds_server_add_series) first verifies on the device that
+ * x is sorted non-decreasing with no NaN (one extra read of x), waits for the
+ * answer on the call's stream (the legacy default stream for
+ * tsds_server_add_series) and returns TSDS_EINVAL, naming the first position
+ * i where x[i] is NaN or x[i] > x[i+1], before launching anything else.
+ * tsds_minmax_noalloc is never checked (it takes no scratch).  The mode starts
+ * on when the environment variable TSDS_CHECKED is set to anything but "0"
+ * when the library loads.  on = 0 or 1 sets the mode, on < 0 leaves it;
+ * returns the mode before the call. */
+int tsds_checked(int on);
 
 /* Measurement aid: the read-only streaming ceiling.  The per-bin pass reads
  * each y element once and writes next to nothing (Section 2.1: one pass over

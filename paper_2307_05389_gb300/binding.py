@@ -88,6 +88,8 @@ def load(path: str = LIB_PATH):
     lib.tsds_minmaxlttb_values.restype = c_int
     lib.tsds_read_stream.argtypes = [p, i64, p, p]
     lib.tsds_read_stream.restype = c_int
+    lib.tsds_checked.argtypes = [c_int]
+    lib.tsds_checked.restype = c_int
     _lib = lib
     return lib
 
@@ -121,6 +123,12 @@ def tsds_timing_read():
     if r != 0:
         raise TsdsError(r, last_error())
     return ms.value, k.value
+
+
+def tsds_checked(on: int = -1) -> int:
+    """Checked mode (x sortedness verified on the device before each call that takes x):
+    on = 0/1 sets it, on < 0 only queries; returns the previous mode."""
+    return int(load().tsds_checked(int(on)))
 
 
 def tsds_read_stream(buf, nbytes, sink, stream):

@@ -2,6 +2,7 @@
 // stream-ordered scratch pool, and the launch sequence of each algorithm.
 #include <cuda_runtime.h>
 #include <stdarg.h>
+#include <stdlib.h>
 #include <stdio.h>
 #include <string.h>
 
@@ -142,6 +143,32 @@ static tsds_status check_common(const void* x, int x_dtype, const void* y, int y
     return fail(TSDS_EINVAL, "y is not aligned to its element size");
   if (x && (reinterpret_cast<uintptr_t>(x) % dtype_size((tsds_dtype)x_dtype)) != 0)
     return fail(TSDS_EINVAL, "x is not aligned to its element size");
+  return TSDS_OK;
+}
+
+// ---------------------------------------------------------------- checked mode
+
+static int checked_from_env() {
+  const char* e = getenv("TSDS_CHECKED");
+  return (e && e[0] && strcmp(e, "0") != 0) ? 1 : 0;
+}
+static std::atomic<int> g_checked{checked_from_env()};
+
+bool checked_mode() { return g_checked.load() != 0; }
+
+tsds_status check_sorted_x(const char* who, const void* x, tsds_dtype xd, int64_t n, cudaStream_t st) {
+  if (!checked_mode() || !x || n <= 0) return TSDS_OK;
+  Scratch sc;
+  TSDS_CK(scratch_alloc(sc, 256, st));
+  unsigned long long* word = static_cast<unsigned long long*>(sc.p);
+  TSDS_CK(cudaMemsetAsync(word, 0xff, sizeof *word, st));
+  TSDS_CK(launch_check_sorted(x, xd, n, word, st));
+  unsigned long long bad = 0;
+  TSDS_CK(cudaMemcpyAsync(&bad, word, sizeof bad, cudaMemcpyDeviceToHost, st));
+  TSDS_CK(cudaStreamSynchronize(st));
+  if (bad != ~0ull)
+    return fail(TSDS_EINVAL, "%s: x is not sorted non-decreasing (NaN or x[i] > x[i+1] at i = %llu; checked mode)",
+                who, bad);
   return TSDS_OK;
 }
 
@@ -311,6 +338,8 @@ static tsds_status run_binned(Algo algo, const void* x, tsds_dtype x_dtype, cons
     return fail(TSDS_EINVAL, "%s needs n_out to be a positive multiple of %d (got %lld)",
                 algo == ALGO_MINMAX ? "MinMax" : algo == ALGO_M4 ? "M4" : "EveryNth", per_bin, (long long)n_out);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  s = check_sorted_x(algo == ALGO_MINMAX ? "MinMax" : algo == ALGO_M4 ? "M4" : "EveryNth", x, x_dtype, n, st);
+  if (s != TSDS_OK) return s;
   if (n == 0) {
     TSDS_CK(cudaMemsetAsync(out_count, 0, sizeof(int64_t), st));
     return TSDS_OK;
@@ -352,6 +381,8 @@ static tsds_status lttb_entry(const void* x, tsds_dtype x_dtype, const void* y, 
   const Gather* gp;
   s = gather_args(x, x_dtype, y_dtype, x_out, y_out, g, gp);
   if (s != TSDS_OK) return s;
+  s = check_sorted_x("LTTB", x, x_dtype, n, static_cast<cudaStream_t>(stream));
+  if (s != TSDS_OK) return s;
   return run_lttb(x, x_dtype, y, y_dtype, n, n_out, nan, out, out_count, static_cast<cudaStream_t>(stream),
                   nullptr, gp);
 }
@@ -368,6 +399,8 @@ static tsds_status minmaxlttb_entry(const void* x, tsds_dtype x_dtype, const voi
   Gather g;
   const Gather* gp;
   s = gather_args(x, x_dtype, y_dtype, x_out, y_out, g, gp);
+  if (s != TSDS_OK) return s;
+  s = check_sorted_x("MinMaxLTTB", x, x_dtype, n, static_cast<cudaStream_t>(stream));
   if (s != TSDS_OK) return s;
   return run_minmaxlttb(x, x_dtype, y, y_dtype, n, n_out, minmax_ratio, nan, out, out_count,
                         static_cast<cudaStream_t>(stream), gp);
@@ -435,6 +468,8 @@ tsds_status tsds_lttb_means(const void* x, tsds_dtype x_dtype, const void* y, ts
   int64_t* out = static_cast<int64_t*>(sc.p);
   tsds_status s = check_common(x, x_dtype, y, y_dtype, n, nan, out, out + n_out);
   if (s != TSDS_OK) return s;
+  s = check_sorted_x("tsds_lttb_means", x, x_dtype, n, st);
+  if (s != TSDS_OK) return s;
   return run_lttb(x, x_dtype, y, y_dtype, n, n_out, nan, out, out + n_out, st, means);
 }
 
@@ -471,6 +506,11 @@ tsds_status tsds_check_wait_timeout(unsigned rounds, void* stream) {
 }
 
 void tsds_timing_enable(int on) { g_timing.store(on ? 1 : 0); }
+
+int tsds_checked(int on) {
+  if (on < 0) return g_checked.load();
+  return g_checked.exchange(on ? 1 : 0);
+}
 
 tsds_status tsds_read_stream(const void* buf, int64_t bytes, uint64_t* sink, void* stream) {
   if (bytes < 0 || bytes % 16 != 0)

@@ -91,6 +91,26 @@ static tsds_status check_series(tsds_algo algo, const tsds_series* s, int64_t co
   return TSDS_OK;
 }
 
+// Checked mode: every series' x in order, one check launch per series and a
+// single wait for all of them.
+static tsds_status check_batch_sorted(const tsds_series* s, int64_t count, tsds_dtype x_dtype, cudaStream_t st) {
+  if (!checked_mode() || !batch_has_x(s, count)) return TSDS_OK;
+  Scratch sc;
+  BT_CK(scratch_alloc(sc, (size_t)count * sizeof(unsigned long long), st));
+  unsigned long long* words = static_cast<unsigned long long*>(sc.p);
+  BT_CK(cudaMemsetAsync(words, 0xff, (size_t)count * sizeof(unsigned long long), st));
+  for (int64_t i = 0; i < count; ++i)
+    if (s[i].n > 0) BT_CK(launch_check_sorted(s[i].x, x_dtype, s[i].n, words + i, st));
+  std::vector<unsigned long long> bad((size_t)count);
+  BT_CK(cudaMemcpyAsync(bad.data(), words, (size_t)count * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+  BT_CK(cudaStreamSynchronize(st));
+  for (int64_t i = 0; i < count; ++i)
+    if (bad[(size_t)i] != ~0ull)
+      return fail(TSDS_EINVAL, "batched: series %lld: x is not sorted non-decreasing (NaN or x[i] > x[i+1] at i = %llu; "
+                  "checked mode)", (long long)i, bad[(size_t)i]);
+  return TSDS_OK;
+}
+
 // Window bases for windows of welems elements: group 0 first, then group 1
 // (from split_windows on); with auto_groups, group 2 gets CTA bases instead.
 static void number_windows(BatchLayout& L, int64_t welems, bool auto_groups) {
@@ -402,6 +422,8 @@ tsds_status tsds_batched(tsds_algo algo, const tsds_series* series, int64_t coun
   tsds_status s = check_series(algo, series, count, x_dtype, y_dtype, nan);
   if (s != TSDS_OK) return s;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  s = check_batch_sorted(series, count, x_dtype, st);
+  if (s != TSDS_OK) return s;
   const StreamConfig cfg;
   BatchLayout L = make_layout(algo, series, count, y_dtype, cfg.window_bytes);
   Scratch sc;
@@ -426,6 +448,8 @@ tsds_status tsds_plan_create(tsds_plan* plan, tsds_algo algo, const tsds_series*
   if (s != TSDS_OK) return s;
   if (flags & ~(TSDS_PLAN_GRAPH | TSDS_PLAN_AUTOTUNE)) return fail(TSDS_EINVAL, "tsds_plan_create: unknown flags");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  s = check_batch_sorted(series, count, x_dtype, st);
+  if (s != TSDS_OK) return s;
   tsds_plan_s* p = new tsds_plan_s();
   PlanImpl* P = &p->impl;
   P->algo = algo;

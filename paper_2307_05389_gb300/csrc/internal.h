@@ -170,6 +170,20 @@ cudaError_t launch_iota(int64_t* out, int64_t n, int64_t* count, cudaStream_t st
 
 int device_sm_count();
 
+// Checked mode (tsds_checked, TSDS_CHECKED=1): every entry point that takes x
+// first verifies on the device that it is sorted non-decreasing with no NaN,
+// waits for the answer and returns TSDS_EINVAL before launching anything else.
+bool checked_mode();
+// The smallest out-of-order position of x goes to *first_bad (left as is when
+// x is in order).
+cudaError_t launch_check_sorted(const void* x, tsds_dtype xd, int64_t n, unsigned long long* first_bad,
+                                cudaStream_t st);
+// TSDS_OK when checked mode is off, x is null, or x[0..n) is in order;
+// otherwise TSDS_EINVAL naming `who` and the first bad index.  Synchronises st
+// when it checks.
+tsds_status check_sorted_x(const char* who, const void* x, tsds_dtype xd, int64_t n, cudaStream_t st);
+tsds_status fail(tsds_status s, const char* fmt, ...);
+
 // Reads bytes (a multiple of 16) at buf (16-byte aligned) once, 16 bytes per
 // load, and XORs the XOR of its 8-byte words into *sink.
 cudaError_t launch_read_stream(const void* buf, int64_t bytes, uint64_t* sink, cudaStream_t st);

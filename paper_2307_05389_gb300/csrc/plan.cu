@@ -175,4 +175,57 @@ cudaError_t launch_iota(int64_t* out, int64_t n, int64_t* count, cudaStream_t st
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- checked mode
+
+// The bin searches need x sorted non-decreasing (Section 3: x gives the
+// position of each point on the horizontal axis).  Element i is out of order
+// when it is NaN or larger than element i+1; the smallest such i lands in
+// *first_bad (left untouched when x is in order).
+template <class X>
+__device__ __forceinline__ bool x_gt(X a, X b) { return a > b; }
+template <>
+__device__ __forceinline__ bool x_gt<__half>(__half a, __half b) { return __half2float(a) > __half2float(b); }
+template <class X>
+__device__ __forceinline__ bool x_nan(X) { return false; }
+template <>
+__device__ __forceinline__ bool x_nan<__half>(__half a) { return __hisnan(a); }
+template <>
+__device__ __forceinline__ bool x_nan<float>(float a) { return isnan(a); }
+template <>
+__device__ __forceinline__ bool x_nan<double>(double a) { return isnan(a); }
+
+template <class X>
+__global__ void k_check_sorted(const X* __restrict__ x, int64_t n, unsigned long long* first_bad) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const X a = x[i];
+    const bool bad = x_nan<X>(a) || (i + 1 < n && x_gt<X>(a, x[i + 1]));
+    if (bad) atomicMin(first_bad, (unsigned long long)i);
+  }
+}
+
+cudaError_t launch_check_sorted(const void* x, tsds_dtype xd, int64_t n, unsigned long long* first_bad,
+                                cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  const int64_t need = (n + 255) / 256;
+  const int64_t full = (int64_t)device_sm_count() * 8;
+  const unsigned grid = (unsigned)(need < full ? need : full);
+  note_launch();
+  switch (xd) {
+    case TSDS_I8: k_check_sorted<<<grid, 256, 0, st>>>(static_cast<const int8_t*>(x), n, first_bad); break;
+    case TSDS_I16: k_check_sorted<<<grid, 256, 0, st>>>(static_cast<const int16_t*>(x), n, first_bad); break;
+    case TSDS_I32: k_check_sorted<<<grid, 256, 0, st>>>(static_cast<const int32_t*>(x), n, first_bad); break;
+    case TSDS_I64: k_check_sorted<<<grid, 256, 0, st>>>(static_cast<const int64_t*>(x), n, first_bad); break;
+    case TSDS_U8: k_check_sorted<<<grid, 256, 0, st>>>(static_cast<const uint8_t*>(x), n, first_bad); break;
+    case TSDS_U16: k_check_sorted<<<grid, 256, 0, st>>>(static_cast<const uint16_t*>(x), n, first_bad); break;
+    case TSDS_U32: k_check_sorted<<<grid, 256, 0, st>>>(static_cast<const uint32_t*>(x), n, first_bad); break;
+    case TSDS_U64: k_check_sorted<<<grid, 256, 0, st>>>(static_cast<const uint64_t*>(x), n, first_bad); break;
+    case TSDS_F16: k_check_sorted<<<grid, 256, 0, st>>>(static_cast<const __half*>(x), n, first_bad); break;
+    case TSDS_F32: k_check_sorted<<<grid, 256, 0, st>>>(static_cast<const float*>(x), n, first_bad); break;
+    case TSDS_F64: k_check_sorted<<<grid, 256, 0, st>>>(static_cast<const double*>(x), n, first_bad); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
 }  // namespace tsds

@@ -689,6 +689,10 @@ tsds_status tsds_server_add_series(tsds_server h, const void* x, const void* y, 
   if (!h || !id) return fail(TSDS_EINVAL, "tsds_server_add_series: NULL argument");
   Server& S = h->s;
   if (n < 0 || (n > 0 && !y)) return fail(TSDS_EINVAL, "tsds_server_add_series: bad series");
+  if (x && dtype_valid(S.x_dtype)) {
+    const tsds_status c = check_sorted_x("tsds_server_add_series", x, S.x_dtype, n, nullptr);
+    if (c != TSDS_OK) return c;
+  }
   std::lock_guard<std::mutex> lk(S.mu);
   if (!S.series.empty() && (S.series[0].x != nullptr) != (x != nullptr))
     return fail(TSDS_EINVAL, "tsds_server_add_series: either every series has x or none");

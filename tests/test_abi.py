@@ -135,3 +135,28 @@ def test_read_stream_arguments_are_checked_on_the_host(lib):
     before = pkg.tsds_kernel_launches()
     assert binding.tsds_read_stream(None, 0, sink, None) == 0
     assert pkg.tsds_kernel_launches() == before
+
+
+def test_checked_mode_toggle(lib):
+    """tsds_checked sets and reports the mode; negative arguments only query."""
+    prev = pkg.tsds_checked(-1)
+    try:
+        assert pkg.tsds_checked(1) == prev
+        assert pkg.tsds_checked(-1) == 1
+        assert pkg.tsds_checked(0) == 1
+        assert pkg.tsds_checked(-5) == 0
+    finally:
+        pkg.tsds_checked(prev)
+
+
+@pytest.mark.parametrize("value,want", [("1", 1), ("yes", 1), ("0", 0), ("", 0)])
+def test_checked_mode_from_environment(value, want):
+    """TSDS_CHECKED turns the mode on at load for any value but "0" (and empty)."""
+    import subprocess
+    import sys
+    code = ("import paper_2307_05389_gb300 as p; p.load(); print(p.tsds_checked(-1))")
+    env = dict(os.environ, TSDS_CHECKED=value)
+    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=120,
+                       cwd=os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    assert r.returncode == 0, r.stderr
+    assert int(r.stdout.strip().splitlines()[-1]) == want
