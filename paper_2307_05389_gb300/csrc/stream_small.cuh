@@ -35,6 +35,18 @@ __device__ __forceinline__ int small_select(const SeriesDev& S, int64_t b, int64
   return k;
 }
 
+// A warp owns its whole bin and reads it in 2 KB steps, one round trip each.
+// Before the first step it asks L2 for the bin's bytes from 2 KB on, up to
+// kBinPrefetchBytes, so that the later steps find them there (a hint: the
+// addresses stay inside the bin).
+constexpr int64_t kBinPrefetchBytes = 16384;
+template <class T>
+__device__ __forceinline__ void prefetch_bin(const T* y, int64_t lo, int64_t hi, int lane) {
+  const char* base = reinterpret_cast<const char*>(y + lo);
+  const int64_t end = min((hi - lo) * (int64_t)sizeof(T), kBinPrefetchBytes);
+  for (int64_t q = 2048 + 128 * lane; q < end; q += 4096) asm volatile("prefetch.global.L2 [%0];" ::"l"(base + q));
+}
+
 template <class P, int NM, int ALGO, bool HASX, bool EMIT>
 __global__ void __launch_bounds__(kSmallThreads) k_small(SeriesDev S, unsigned* __restrict__ done) {
   using T = typename P::T;
@@ -55,6 +67,7 @@ __global__ void __launch_bounds__(kSmallThreads) k_small(SeriesDev S, unsigned* 
       }
     }
     if (hi > lo) {
+      prefetch_bin(static_cast<const T*>(S.y), lo, hi, lane);
       Cand c = piece_ldg<P>(static_cast<const T*>(S.y), lo, hi);
       finish_bin<P, NM>(c, lo);
       if (lane == 0) {
@@ -148,6 +161,7 @@ __global__ void __launch_bounds__(kSmallThreads) k_bins_multi(const SeriesDev* _
   if (b >= S.nb) return;
   const int64_t lo = __ldg(S.edges + b), hi = __ldg(S.edges + b + 1);
   if (hi <= lo) return;
+  prefetch_bin(static_cast<const T*>(S.y), lo, hi, lane);
   Cand c = piece_ldg<P>(static_cast<const T*>(S.y), lo, hi);
   finish_bin<P, NM>(c, lo);
   if (lane == 0) {
