@@ -1,6 +1,6 @@
 // probe.cu -- a read-only streaming kernel: the ceiling a pass that reads each
 // byte once and writes almost nothing can reach on this device (the per-bin
-// argmin/argmax pass reads y once, Section 2.1, and is judged against it
+// argmin/argmax pass reads y once, Section 2.1, and is compared with it
 // beside the copy bandwidth).
 #include <stdint.h>
 

@@ -29,7 +29,7 @@ def lib():
     return pkg.load()
 
 
-def test_header_declares_the_survey_entry_points():
+def test_header_declares_the_core_entry_points():
     names = declared_functions()
     for n in ("tsds_minmax", "tsds_m4", "tsds_lttb", "tsds_minmaxlttb", "tsds_last_error", "tsds_shutdown"):
         assert n in names
