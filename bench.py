@@ -463,10 +463,29 @@ def suite_lttb(args):
             f()
             issue = (time.perf_counter() - t0) * 1e3
             torch.cuda.synchronize()
+            # the same 64 series as one batched call (tsds_batched_minmaxlttb)
+            outs, counts = binding.batch_buffers(series, [n_out] * 64, dev)
+
+            def fb():
+                binding.downsample_batched("minmaxlttb", series, [n_out] * 64, nan=nm, outs=outs, counts=counts,
+                                           minmax_ratio=r)
+            fb()
+            torch.cuda.synchronize()
+            same = True
+            c = counts.cpu().tolist()
+            for k, srs in enumerate(series):
+                _raw_call(binding, "minmaxlttb", None, None, srs, "float64", srs.numel(), n_out, out, cnt, stream,
+                          nan=nan, ratio=r)
+                torch.cuda.synchronize()
+                same &= int(cnt.item()) == c[k] and torch.equal(out[:c[k]], outs[k][:c[k]])
+            bmed, _ = _timed_calls(torch, stream, fb, 5)
             res[f"minmaxlttb_r{r}_{nm}"] = {"ms_64_series": med, "GBps": 1e8 * 8 / (med / 1e3) / 1e9,
-                                            "host_issue_ms": issue}
+                                            "host_issue_ms": issue, "batched_ms_64_series": bmed,
+                                            "batched_GBps": 1e8 * 8 / (bmed / 1e3) / 1e9,
+                                            "batched_identical": bool(same)}
     return {"suite": "lttb", "unit": "ms", "config": {"workload": "LTTB: float64/float32 random walks, n_out=4000; "
-            "MinMaxLTTB: 64 x 1.5625e6 float64 quantised to 256 levels with 1% NaN, one call per series"},
+            "MinMaxLTTB: 64 x 1.5625e6 float64 quantised to 256 levels with 1% NaN, one call per series and "
+            "one batched call for all 64"},
             "results": res}
 
 

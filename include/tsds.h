@@ -176,6 +176,19 @@ typedef struct {
 tsds_status tsds_batched(tsds_algo algo, const tsds_series* series, int64_t count,
                          tsds_dtype x_dtype, tsds_dtype y_dtype, tsds_nan_mode nan, void* stream);
 
+/* MinMaxLTTB of every series in `series` (a host array of `count`
+ * descriptors; n_out >= 3 each, minmax_ratio and nan shared) in one launch
+ * sequence, asynchronously on `stream`: the MinMax preselection of every
+ * series' interior shares the binned launches, and the LTTB pass of every
+ * series runs as one job of each LTTB kernel (Section 1: the preselection
+ * keeps LTTB's cost low; Section 2.2: many series at once instead of one at
+ * a time).  Each series' indices and count are exactly those of
+ * tsds_minmaxlttb on that series.  1 <= count <= 65535.  The descriptors are
+ * staged from pageable memory, so the call may wait for earlier work on
+ * `stream` before it returns.  TSDS_EINVAL names the offending series. */
+tsds_status tsds_batched_minmaxlttb(const tsds_series* series, int64_t count, tsds_dtype x_dtype,
+                                    tsds_dtype y_dtype, int64_t minmax_ratio, tsds_nan_mode nan, void* stream);
+
 /* A plan keeps a batch's descriptors and scratch resident so the same batch
  * (same buffers; their contents may change between executions) can be
  * downsampled again with one call.  Flags: */

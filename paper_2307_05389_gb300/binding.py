@@ -56,6 +56,8 @@ def load(path: str = LIB_PATH):
     lib.tsds_version.argtypes = []
     lib.tsds_version.restype = ctypes.c_char_p
     lib.tsds_batched.argtypes = [c_int, p, i64, c_int, c_int, c_int, p]
+    lib.tsds_batched_minmaxlttb.argtypes = [p, i64, c_int, c_int, i64, c_int, p]
+    lib.tsds_batched_minmaxlttb.restype = c_int
     lib.tsds_batched.restype = c_int
     lib.tsds_plan_create.argtypes = [ctypes.POINTER(p), c_int, p, i64, c_int, c_int, c_int, c_int, p]
     lib.tsds_plan_create.restype = c_int
@@ -271,10 +273,14 @@ def batch_buffers(ys, n_outs, device):
     return outs, counts
 
 
+def tsds_batched_minmaxlttb(series, count, x_dtype, y_dtype, minmax_ratio, nan, stream):
+    return load().tsds_batched_minmaxlttb(series, count, x_dtype, y_dtype, minmax_ratio, nan, stream)
+
+
 def downsample_batched(algo, ys, n_outs, xs=None, nan="propagate", stream=None, outs=None, counts=None,
-                       y_dtype=None, x_dtype=None):
-    """MinMax/M4 of every CUDA tensor in `ys` in one launch sequence.  Returns
-    (outs, counts) device tensors (outs[i][:counts[i]] are series i's indices)."""
+                       y_dtype=None, x_dtype=None, minmax_ratio=4):
+    """MinMax, M4 or MinMaxLTTB of every CUDA tensor in `ys` in one launch sequence.
+    Returns (outs, counts) device tensors (outs[i][:counts[i]] are series i's indices)."""
     import torch
     dev = ys[0].device
     if outs is None or counts is None:
@@ -284,8 +290,12 @@ def downsample_batched(algo, ys, n_outs, xs=None, nan="propagate", stream=None, 
     yd = DTYPES[y_dtype or _torch_dtype_name(ys[0])]
     xd = DTYPES[x_dtype or _torch_dtype_name(xs[0])] if xs is not None else 0
     with torch.cuda.device(dev):
-        r = tsds_batched(ALGO_CODES[algo], _array_ptr(arr), len(ys), xd, yd, NAN_MODES[nan],
-                         ctypes.c_void_p(st.cuda_stream))
+        if algo == "minmaxlttb":
+            r = tsds_batched_minmaxlttb(_array_ptr(arr), len(ys), xd, yd, int(minmax_ratio), NAN_MODES[nan],
+                                        ctypes.c_void_p(st.cuda_stream))
+        else:
+            r = tsds_batched(ALGO_CODES[algo], _array_ptr(arr), len(ys), xd, yd, NAN_MODES[nan],
+                             ctypes.c_void_p(st.cuda_stream))
     if r != 0:
         raise TsdsError(r, last_error())
     return outs, counts

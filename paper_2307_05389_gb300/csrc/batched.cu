@@ -93,7 +93,7 @@ static tsds_status check_series(tsds_algo algo, const tsds_series* s, int64_t co
 
 // Checked mode: every series' x in order, one check launch per series and a
 // single wait for all of them.
-static tsds_status check_batch_sorted(const tsds_series* s, int64_t count, tsds_dtype x_dtype, cudaStream_t st) {
+tsds_status check_batch_sorted(const tsds_series* s, int64_t count, tsds_dtype x_dtype, cudaStream_t st) {
   if (!checked_mode() || !batch_has_x(s, count)) return TSDS_OK;
   Scratch sc;
   BT_CK(scratch_alloc(sc, (size_t)count * sizeof(unsigned long long), st));

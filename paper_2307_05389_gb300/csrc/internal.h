@@ -183,6 +183,9 @@ cudaError_t launch_check_sorted(const void* x, tsds_dtype xd, int64_t n, unsigne
 // when it checks.
 tsds_status check_sorted_x(const char* who, const void* x, tsds_dtype xd, int64_t n, cudaStream_t st);
 tsds_status fail(tsds_status s, const char* fmt, ...);
+// Checked mode over a batch: every series' x in order (one wait for all);
+// TSDS_EINVAL names the series and the position.
+tsds_status check_batch_sorted(const tsds_series* s, int64_t count, tsds_dtype x_dtype, cudaStream_t st);
 
 // Reads bytes (a multiple of 16) at buf (16-byte aligned) once, 16 bytes per
 // load, and XORs the XOR of its 8-byte words into *sink.

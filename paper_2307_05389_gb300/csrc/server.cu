@@ -52,6 +52,7 @@ struct QueryDev {
   int64_t* out;       // n_out entries
   int64_t* info;      // [count, L, lo, k, m] (count = selected indices)
   int64_t* R;         // MinMaxLTTB points (global indices)
+  int64_t* user_count;  // device-output batches: the caller's count word (null for the server)
 };
 
 constexpr int kInfoSlots = 8;
@@ -195,8 +196,13 @@ __global__ void k_close_queries(const QueryDev* __restrict__ qd, int count) {
   Q.info[4] = m;
 }
 
-// Copies the LTTB count into the query's result count (MinMaxLTTB writes its
-// count through the job's out_count, which points at info[0]).
+// Device-output batches: each query's count goes to the caller's count word.
+__global__ void k_copy_counts(const QueryDev* __restrict__ qd, int count) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= count) return;
+  const QueryDev Q = qd[q];
+  if (Q.user_count) *Q.user_count = Q.info[0];
+}
 }  // namespace tsds
 
 using namespace tsds;
@@ -313,9 +319,14 @@ int64_t lttb_m_max(const tsds_query& q) { return std::max(2 * ((q.n_out * q.minm
 
 // Enqueues one batch on the slot's stream.  Called without the server lock:
 // everything it needs from the server is in `qs` and `ser` (the series of
-// each query) and the server's fixed dtypes.
+// each query) and the server's fixed dtypes.  With dev_out (one batched call
+// rather than the server), query i writes its indices to dev_out[i] and its
+// count to dev_count[i] on the device, the descriptors are staged from
+// pageable memory, and nothing is copied back.
 tsds_status launch_batch(const Server& S, Slot& sl, const std::vector<tsds_query>& qs,
-                         const std::vector<SeriesHost>& ser, bool has_x, char* err, size_t errlen) {
+                         const std::vector<SeriesHost>& ser, bool has_x, char* err, size_t errlen,
+                         int64_t* const* dev_out = nullptr, int64_t* const* dev_count = nullptr) {
+  const bool device_out = dev_out != nullptr;
   const int count = (int)qs.size();
   const int64_t window_bytes = kWindowBytes;
   const int64_t ys = dtype_size(S.y_dtype);
@@ -359,8 +370,8 @@ tsds_status launch_batch(const Server& S, Slot& sl, const std::vector<tsds_query
   size_t words = 0;
   for (int i = 0; i < count; ++i) {
     sl.out_off[i] = words;
-    sl.n_outs[i] = qs[i].n_out;
-    words += (size_t)qs[i].n_out + kInfoSlots;
+    sl.n_outs[i] = device_out ? 0 : qs[i].n_out;
+    words += (size_t)sl.n_outs[i] + kInfoSlots;
   }
   o = up256(o + words * 8);
   int64_t lt_max_B = 0, lt_max_m = 0;
@@ -375,15 +386,19 @@ tsds_status launch_batch(const Server& S, Slot& sl, const std::vector<tsds_query
   }
   const size_t total = o;
 
-  // ---- pinned staging (the slot is idle, so its buffers are free)
-  if (sl.pin_in_cap < in_bytes) {
+  // ---- staging: pinned for the server (the slot is idle, so its buffers are
+  // free), pageable for a one-shot batched call
+  std::vector<char> pageable;
+  if (device_out) {
+    pageable.assign(in_bytes, 0);
+  } else if (sl.pin_in_cap < in_bytes) {
     if (sl.pin_in) cudaFreeHost(sl.pin_in);
     sl.pin_in = nullptr;
     sl.pin_in_cap = 0;
     SV_CK(cudaMallocHost(&sl.pin_in, in_bytes * 2));
     sl.pin_in_cap = in_bytes * 2;
   }
-  if (sl.pin_out_cap < words) {
+  if (!device_out && sl.pin_out_cap < words) {
     if (sl.pin_out) cudaFreeHost(sl.pin_out);
     sl.pin_out = nullptr;
     sl.pin_out_cap = 0;
@@ -395,7 +410,7 @@ tsds_status launch_batch(const Server& S, Slot& sl, const std::vector<tsds_query
   Scratch scr;   // returned to the library pool in stream order when this function returns
   SV_CK(scratch_alloc(scr, total, sl.st));
   char* base = static_cast<char*>(scr.p);
-  char* stage = static_cast<char*>(sl.pin_in);
+  char* stage = device_out ? pageable.data() : static_cast<char*>(sl.pin_in);
   QueryDev* hq = reinterpret_cast<QueryDev*>(stage + off_q);
   SeriesDev* hs = reinterpret_cast<SeriesDev*>(stage + off_sd);
   LttbJob* hl = reinterpret_cast<LttbJob*>(stage + off_ljobs);
@@ -417,8 +432,9 @@ tsds_status launch_batch(const Server& S, Slot& sl, const std::vector<tsds_query
     d.hi = q.hi;
     d.n_out = q.n_out;
     d.n_sel = q.algo == 2 ? 2 * ((q.n_out * q.minmax_ratio) / 2) : 0;
-    d.out = outbase + sl.out_off[i];
-    d.info = outbase + sl.out_off[i] + q.n_out;
+    d.out = device_out ? dev_out[i] : outbase + sl.out_off[i];
+    d.info = outbase + sl.out_off[i] + sl.n_outs[i];
+    d.user_count = device_out ? dev_count[i] : nullptr;
     d.R = q.algo == 2 ? reinterpret_cast<int64_t*>(base + off_R[i]) : nullptr;
     SeriesDev& s = hs[i];
     memset(&s, 0, sizeof s);   // k_resolve fills the range-dependent fields
@@ -516,6 +532,12 @@ tsds_status launch_batch(const Server& S, Slot& sl, const std::vector<tsds_query
     if (r != TSDS_OK) { snprintf(err, errlen, "points: %s", tsds_last_error()); return r; }
     r = run_lttb_jobs(hl, reinterpret_cast<const LttbJob*>(base + off_ljobs), nlt, lt_max_B, lt_max_m, st);
     if (r != TSDS_OK) { snprintf(err, errlen, "lttb: %s", tsds_last_error()); return r; }
+  }
+  if (device_out) {
+    note_launch();
+    k_copy_counts<<<(count + 255) / 256, 256, 0, st>>>(dq, count);
+    SV_CK(cudaGetLastError());
+    return TSDS_OK;
   }
   SV_CK(cudaMemcpyAsync(sl.pin_out, outbase, words * 8, cudaMemcpyDeviceToHost, st));
   SV_CK(cudaLaunchHostFunc(st, on_batch_done, &sl));
@@ -818,6 +840,67 @@ tsds_status tsds_server_destroy(tsds_server h) {
     delete sl;
   }
   delete h;
+  return TSDS_OK;
+}
+
+tsds_status tsds_batched_minmaxlttb(const tsds_series* series, int64_t count, tsds_dtype x_dtype, tsds_dtype y_dtype,
+                                    int64_t minmax_ratio, tsds_nan_mode nan, void* stream) {
+  if (count < 1 || count > 65535)
+    return fail(TSDS_EINVAL, "tsds_batched_minmaxlttb: count must be in [1, 65535] (got %lld)", (long long)count);
+  if (!series) return fail(TSDS_EINVAL, "tsds_batched_minmaxlttb: series is NULL");
+  if (!dtype_valid(y_dtype)) return fail(TSDS_EINVAL, "tsds_batched_minmaxlttb: unknown y dtype %d", (int)y_dtype);
+  if (nan != TSDS_NAN_PROPAGATE && nan != TSDS_NAN_IGNORE)
+    return fail(TSDS_EINVAL, "tsds_batched_minmaxlttb: unknown NaN mode %d", (int)nan);
+  if (minmax_ratio < 1) return fail(TSDS_EINVAL, "tsds_batched_minmaxlttb: minmax_ratio must be >= 1");
+  bool has_x = false;
+  for (int64_t i = 0; i < count; ++i)
+    if (series[i].n > 0) { has_x = series[i].x != nullptr; break; }
+  if (has_x && !dtype_valid(x_dtype)) return fail(TSDS_EINVAL, "tsds_batched_minmaxlttb: unknown x dtype %d", (int)x_dtype);
+  for (int64_t i = 0; i < count; ++i) {
+    const tsds_series& q = series[i];
+    if (q.n < 0) return fail(TSDS_EINVAL, "tsds_batched_minmaxlttb: series %lld: n < 0", (long long)i);
+    if (q.n > 0 && (q.x != nullptr) != has_x)
+      return fail(TSDS_EINVAL, "tsds_batched_minmaxlttb: series %lld: either every non-empty series has x or none",
+                  (long long)i);
+    if (q.n_out < 3) return fail(TSDS_EINVAL, "tsds_batched_minmaxlttb: series %lld: n_out must be >= 3", (long long)i);
+    if (minmax_ratio > (INT64_MAX / 4) / q.n_out)
+      return fail(TSDS_EINVAL, "tsds_batched_minmaxlttb: series %lld: n_out * minmax_ratio overflows", (long long)i);
+    if ((q.n > 0 && (!q.y || !q.out)) || !q.out_count)
+      return fail(TSDS_EINVAL, "tsds_batched_minmaxlttb: series %lld: NULL buffer", (long long)i);
+    if (reinterpret_cast<uintptr_t>(q.y) % dtype_size(y_dtype) ||
+        (has_x && reinterpret_cast<uintptr_t>(q.x) % dtype_size(x_dtype)))
+      return fail(TSDS_EINVAL, "tsds_batched_minmaxlttb: series %lld: x or y not aligned to its element size",
+                  (long long)i);
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  tsds_status c = check_batch_sorted(series, count, x_dtype, st);
+  if (c != TSDS_OK) return c;
+  Server S;
+  S.x_dtype = has_x ? x_dtype : TSDS_F64;
+  S.y_dtype = y_dtype;
+  std::vector<tsds_query> qs((size_t)count);
+  std::vector<SeriesHost> ser((size_t)count);
+  std::vector<int64_t*> outs((size_t)count), counts((size_t)count);
+  for (int64_t i = 0; i < count; ++i) {
+    const tsds_series& in = series[i];
+    tsds_query& q = qs[(size_t)i];
+    memset(&q, 0, sizeof q);
+    q.series = i;
+    q.algo = TSDS_ALGO_MINMAXLTTB;
+    q.nan = nan;
+    q.lo = 0;
+    q.hi = in.n;
+    q.n_out = in.n_out;
+    q.minmax_ratio = minmax_ratio;
+    ser[(size_t)i] = SeriesHost{has_x ? in.x : nullptr, in.y, in.n};
+    outs[(size_t)i] = in.out;
+    counts[(size_t)i] = in.out_count;
+  }
+  Slot sl;
+  sl.st = st;
+  char err[256] = "";
+  const tsds_status r = launch_batch(S, sl, qs, ser, has_x, err, sizeof err, outs.data(), counts.data());
+  if (r != TSDS_OK) return fail(r, "tsds_batched_minmaxlttb: %s", err);
   return TSDS_OK;
 }
 

@@ -160,3 +160,37 @@ def test_checked_mode_from_environment(value, want):
                        cwd=os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
     assert r.returncode == 0, r.stderr
     assert int(r.stdout.strip().splitlines()[-1]) == want
+
+
+def test_batched_minmaxlttb_arguments_are_checked_on_the_host(lib):
+    """tsds_batched_minmaxlttb rejects bad batches before anything runs and names the series."""
+    import numpy as np
+    y, out, cnt = 1 << 20, 1 << 24, 1 << 28
+
+    def arr(rows):
+        a = np.zeros((len(rows), 6), dtype=np.uint64)
+        for i, r in enumerate(rows):
+            a[i] = r
+        return a
+
+    good = [0, y, 1000, 100, out, cnt]
+    f = binding.tsds_batched_minmaxlttb
+    a = arr([good, good])
+    assert f(binding._array_ptr(a), 0, 0, 9, 4, 0, None) == 1                       # count 0
+    assert f(None, 2, 0, 9, 4, 0, None) == 1                                         # no series
+    assert f(binding._array_ptr(a), 2, 0, 9, 0, 0, None) == 1                        # ratio 0
+    assert "minmax_ratio" in pkg.last_error()
+    assert f(binding._array_ptr(a), 2, 0, 11, 4, 0, None) == 1                       # y dtype
+    assert f(binding._array_ptr(a), 2, 0, 9, 4, 2, None) == 1                        # NaN mode
+    b = arr([good, [0, y, 1000, 2, out, cnt]])
+    assert f(binding._array_ptr(b), 2, 0, 9, 4, 0, None) == 1                        # n_out < 3
+    assert "series 1" in pkg.last_error()
+    b = arr([good, [0, y, 1000, 100, out, 0]])
+    assert f(binding._array_ptr(b), 2, 0, 9, 4, 0, None) == 1                        # no count word
+    b = arr([good, [1 << 30, y, 1000, 100, out, cnt]])
+    assert f(binding._array_ptr(b), 2, 3, 9, 4, 0, None) == 1                        # x on one series only
+    b = arr([good, [0, y + 2, 1000, 100, out, cnt]])
+    assert f(binding._array_ptr(b), 2, 0, 9, 4, 0, None) == 1                        # misaligned float32 y
+    b = arr([good, [0, y, 1000, 1 << 40, out, cnt]])
+    assert f(binding._array_ptr(b), 2, 0, 9, 1 << 40, 0, None) == 1                  # n_out * ratio overflows
+    assert "overflows" in pkg.last_error()

@@ -11,7 +11,8 @@ times, on outputs the oracle computes one by one.
 * The batched workload (4096 series, 17.7 GB, a resident autotuned plan with a
   CUDA graph): sampled series against the oracle, whole outputs.
 * Plain LTTB on 10^7 points and MinMaxLTTB on the 64 quantised NaN series of
-  1.5625e6 points: whole outputs against the oracle.
+  1.5625e6 points, one call per series and one batched call for all 64: whole
+  outputs against the oracle.
 
 Inputs are generated exactly as bench.py generates them (same seeds)."""
 import ctypes
@@ -172,3 +173,21 @@ def test_minmaxlttb_quantised_nan_series(nan):
             got = binding.downsample("minmaxlttb", dy, 4000, nan=nan, minmax_ratio=r).cpu().numpy()
             want = oracle.minmaxlttb(None, y, 4000, r, nan)
             assert np.array_equal(got, want), f"series {i} ratio {r}"
+
+
+@pytest.mark.parametrize("nan", ["propagate", "ignore"])
+def test_batched_minmaxlttb_quantised_nan_series(nan):
+    """The same 64 series as one tsds_batched_minmaxlttb call per ratio: eight sampled
+    series against the oracle, whole outputs."""
+    import torch
+    series = [inputs.quantised_nan(1_562_500, seed=4 + i) for i in range(64)]
+    dev = [torch.from_numpy(y).cuda() for y in series]
+    rng = np.random.default_rng(15)
+    pick = sorted(rng.choice(64, 8, replace=False).tolist())
+    for r in (2, 4, 30):
+        outs, counts = binding.downsample_batched("minmaxlttb", dev, [4000] * 64, nan=nan, minmax_ratio=r)
+        torch.cuda.synchronize()
+        c = counts.cpu().numpy()
+        for i in pick:
+            want = oracle.minmaxlttb(None, series[i], 4000, r, nan)
+            assert np.array_equal(outs[i][:int(c[i])].cpu().numpy(), want), f"series {i} ratio {r}"
