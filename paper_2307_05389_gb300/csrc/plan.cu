@@ -48,7 +48,16 @@ __device__ __forceinline__ double x_as_f64<__half>(const __half* x, int64_t j) {
   return (double)__half2float(ldg_elem<__half>(x + j));
 }
 
-template <class X, bool FLOATX>
+// With many bins the edges are found in two launches: PHASE 1 searches all of
+// x for every kEdgeGroup-th edge, PHASE 2 searches each other edge only
+// between the two group edges around it.  Both the integer rule and the
+// binary64 rule give edge values non-decreasing in i, so for sorted x edge i
+// of group k lies in [s_{kG}, s_{(k+1)G}] (s_nb = n).  PHASE 0 is the single
+// launch for calls with few bins (every edge over all of x).
+constexpr int64_t kEdgeGroup = 32;
+constexpr int64_t kEdgesTwoLevelMinBins = 4096;
+
+template <class X, bool FLOATX, int PHASE>
 __global__ void k_edges_x(const SeriesDev* sd, SeriesDev single, int count) {
   const SeriesDev S = count == 1 && sd == nullptr ? single : sd[blockIdx.y];
   const int64_t nb = S.nb;
@@ -57,23 +66,47 @@ __global__ void k_edges_x(const SeriesDev* sd, SeriesDev single, int count) {
   const int64_t n = S.n;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t warps_total = (int64_t)gridDim.x * (blockDim.x >> 5);
-  if (blockIdx.x == 0 && threadIdx.x == 0) { S.edges[0] = 0; S.edges[nb] = n; }
-  for (int64_t i = 1 + (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; i < nb; i += warps_total) {
+  if (PHASE != 2 && blockIdx.x == 0 && threadIdx.x == 0) { S.edges[0] = 0; S.edges[nb] = n; }
+  const int64_t step = PHASE == 1 ? kEdgeGroup : 1;
+  for (int64_t i = step + ((int64_t)blockIdx.x * (blockDim.x >> 5) + warp) * step; i < nb; i += warps_total * step) {
+    if (PHASE == 2 && i % kEdgeGroup == 0) continue;
+    int64_t lo = 0, hi = n;
+    if (PHASE == 2) {
+      const int64_t g = i - i % kEdgeGroup;
+      lo = S.edges[g];
+      hi = g + kEdgeGroup < nb ? S.edges[g + kEdgeGroup] : n;
+    }
     int64_t e;
     if constexpr (FLOATX) {
       double x0 = x_as_f64<X>(x, 0);
       double xl = x_as_f64<X>(x, n - 1);
       double span = __dsub_rn(xl, x0);
       double edge = __dadd_rn(x0, __ddiv_rn(__dmul_rn(span, (double)i), (double)nb));
-      e = warp_lower_bound(0, n, [&](int64_t j) { return x_as_f64<X>(x, j) >= edge; });
+      e = warp_lower_bound(lo, hi, [&](int64_t j) { return x_as_f64<X>(x, j) >= edge; });
     } else {
       X x0 = __ldg(x);
       u128 span = XInt<X>::off(x, n - 1, x0);
       u128 rhs = (u128)i * span;
-      e = warp_lower_bound(0, n, [&](int64_t j) { return XInt<X>::off(x, j, x0) * (u128)nb >= rhs; });
+      e = warp_lower_bound(lo, hi, [&](int64_t j) { return XInt<X>::off(x, j, x0) * (u128)nb >= rhs; });
     }
     if (lane == 0) S.edges[i] = e;
   }
+}
+
+template <class X, bool FLOATX>
+static void launch_edges_x(dim3 grid, int threads, const SeriesDev* arr, const SeriesDev& single, int count,
+                           int64_t max_nb, cudaStream_t st) {
+  if (max_nb < kEdgesTwoLevelMinBins) {
+    note_launch();
+    k_edges_x<X, FLOATX, 0><<<grid, threads, 0, st>>>(arr, single, count);
+    return;
+  }
+  int64_t cblocks = (max_nb / kEdgeGroup + 7) / 8;
+  if (cblocks < 1) cblocks = 1;
+  if (cblocks > 65535) cblocks = 65535;
+  note_launch(2);
+  k_edges_x<X, FLOATX, 1><<<dim3((unsigned)cblocks, grid.y), threads, 0, st>>>(arr, single, count);
+  k_edges_x<X, FLOATX, 2><<<grid, threads, 0, st>>>(arr, single, count);
 }
 
 cudaError_t launch_edges(const SeriesDev* s_dev, int count, const SeriesDev* s_host_single,
@@ -95,19 +128,18 @@ cudaError_t launch_edges(const SeriesDev* s_dev, int count, const SeriesDev* s_h
   if (blocks < 1) blocks = 1;
   if (blocks > 65535) blocks = 65535;
   dim3 grid((unsigned)blocks, (unsigned)count);
-  note_launch();
   switch (x_dtype) {
-    case TSDS_I8: k_edges_x<int8_t, false><<<grid, threads, 0, st>>>(arr, single, count); break;
-    case TSDS_I16: k_edges_x<int16_t, false><<<grid, threads, 0, st>>>(arr, single, count); break;
-    case TSDS_I32: k_edges_x<int32_t, false><<<grid, threads, 0, st>>>(arr, single, count); break;
-    case TSDS_I64: k_edges_x<int64_t, false><<<grid, threads, 0, st>>>(arr, single, count); break;
-    case TSDS_U8: k_edges_x<uint8_t, false><<<grid, threads, 0, st>>>(arr, single, count); break;
-    case TSDS_U16: k_edges_x<uint16_t, false><<<grid, threads, 0, st>>>(arr, single, count); break;
-    case TSDS_U32: k_edges_x<uint32_t, false><<<grid, threads, 0, st>>>(arr, single, count); break;
-    case TSDS_U64: k_edges_x<uint64_t, false><<<grid, threads, 0, st>>>(arr, single, count); break;
-    case TSDS_F16: k_edges_x<__half, true><<<grid, threads, 0, st>>>(arr, single, count); break;
-    case TSDS_F32: k_edges_x<float, true><<<grid, threads, 0, st>>>(arr, single, count); break;
-    case TSDS_F64: k_edges_x<double, true><<<grid, threads, 0, st>>>(arr, single, count); break;
+    case TSDS_I8: launch_edges_x<int8_t, false>(grid, threads, arr, single, count, max_nb, st); break;
+    case TSDS_I16: launch_edges_x<int16_t, false>(grid, threads, arr, single, count, max_nb, st); break;
+    case TSDS_I32: launch_edges_x<int32_t, false>(grid, threads, arr, single, count, max_nb, st); break;
+    case TSDS_I64: launch_edges_x<int64_t, false>(grid, threads, arr, single, count, max_nb, st); break;
+    case TSDS_U8: launch_edges_x<uint8_t, false>(grid, threads, arr, single, count, max_nb, st); break;
+    case TSDS_U16: launch_edges_x<uint16_t, false>(grid, threads, arr, single, count, max_nb, st); break;
+    case TSDS_U32: launch_edges_x<uint32_t, false>(grid, threads, arr, single, count, max_nb, st); break;
+    case TSDS_U64: launch_edges_x<uint64_t, false>(grid, threads, arr, single, count, max_nb, st); break;
+    case TSDS_F16: launch_edges_x<__half, true>(grid, threads, arr, single, count, max_nb, st); break;
+    case TSDS_F32: launch_edges_x<float, true>(grid, threads, arr, single, count, max_nb, st); break;
+    case TSDS_F64: launch_edges_x<double, true>(grid, threads, arr, single, count, max_nb, st); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

@@ -148,3 +148,20 @@ def test_split_pass_small_and_large_bins(graph, algo):
     got = results(outs, counts)
     for i, y in enumerate(ys):
         np.testing.assert_array_equal(got[i], oracle.downsample(algo, None, y, int(n_outs[i])))
+
+
+@pytest.mark.parametrize("algo", ["minmax", "m4"])
+def test_batched_with_x_and_many_bins(algo):
+    """A batch whose largest series has thousands of x-space bins takes the two-level edge
+    search for every series, including those with a handful of bins."""
+    ys, xs, _ = make_batch(9, 24, with_x=True, max_len=300_000)
+    rng = np.random.default_rng(10)
+    per = 2 if algo == "minmax" else 4
+    n_outs = rng.choice([4, 8, 60, 400, 4000, 20_000, 60_000], len(ys)).astype(np.int64)
+    n_outs[5] = 32_768 * per // 2         # the long series: >= 4096 bins either way
+    n_outs = (n_outs // per) * per
+    outs, counts = binding.downsample_batched(algo, to_dev(ys), n_outs, xs=to_dev(xs))
+    got = results(outs, counts)
+    for i, y in enumerate(ys):
+        exp = oracle.downsample(algo, xs[i], y, int(n_outs[i]))
+        np.testing.assert_array_equal(got[i], exp, err_msg=f"series {i} n={len(y)} n_out={n_outs[i]}")

@@ -129,6 +129,26 @@ def test_constant_and_monotone():
     check("minmax", None, y[::-1].copy(), 100)
 
 
+@pytest.mark.parametrize("nb", [4095, 4096, 4097, 4096 + 31, 4096 + 33, 65 * 32, 20_000])
+@pytest.mark.parametrize("x_kind", ["int64", "float64", "gap", "runs"])
+def test_many_x_bins_two_level_edges(nb, x_kind):
+    """From 4096 x-space bins on, the edges come from a coarse search for every 32nd edge and a
+    fine search between coarse neighbours: bin counts around that threshold and around group
+    ends, with uniform, gapped and run-heavy x."""
+    n = 200_003
+    y = inputs.random_walk(n, "float32", seed=21)
+    if x_kind == "int64":
+        x = inputs.geometric_x(n, seed=22)
+    elif x_kind == "float64":
+        x = inputs.exponential_x(n, seed=22)
+    elif x_kind == "gap":
+        x = np.concatenate([np.arange(n // 3), np.arange(n - n // 3) + 10 ** 12]).astype(np.int64)
+    else:
+        x = np.sort(np.random.default_rng(23).integers(0, 3000, n)).astype(np.int64)
+    check("minmax", x, y, 2 * nb)
+    check("m4", x, y, 4 * nb)
+
+
 def test_x_all_equal_and_gaps():
     n = 100_000
     y = inputs.random_walk(n, "float32", seed=5)
