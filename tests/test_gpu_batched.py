@@ -152,8 +152,7 @@ def test_split_pass_small_and_large_bins(graph, algo):
 
 @pytest.mark.parametrize("algo", ["minmax", "m4"])
 def test_batched_with_x_and_many_bins(algo):
-    """A batch whose largest series has thousands of x-space bins takes the two-level edge
-    search for every series, including those with a handful of bins."""
+    """A batch mixing series with thousands of x-space bins and series with a handful."""
     ys, xs, _ = make_batch(9, 24, with_x=True, max_len=300_000)
     rng = np.random.default_rng(10)
     per = 2 if algo == "minmax" else 4

@@ -132,9 +132,9 @@ def test_constant_and_monotone():
 @pytest.mark.parametrize("nb", [4095, 4096, 4097, 4096 + 31, 4096 + 33, 65 * 32, 20_000])
 @pytest.mark.parametrize("x_kind", ["int64", "float64", "gap", "runs"])
 def test_many_x_bins_two_level_edges(nb, x_kind):
-    """From 4096 x-space bins on, the edges come from a coarse search for every 32nd edge and a
-    fine search between coarse neighbours: bin counts around that threshold and around group
-    ends, with uniform, gapped and run-heavy x."""
+    """From 4096 x-space bins of at most 512 points on, a single series' edges come from a
+    coarse search for every 32nd edge and a fine search between coarse neighbours: bin counts
+    around that threshold and around group ends, with uniform, gapped and run-heavy x."""
     n = 200_003
     y = inputs.random_walk(n, "float32", seed=21)
     if x_kind == "int64":
