@@ -362,6 +362,14 @@ int tsds_stream_variant(int variant);
  * event query fails. */
 tsds_status tsds_timing_read(double* total_ms, int64_t* launches);
 
+/* Failure injection for tests: the next `count` device allocations the
+ * library makes (its stream-ordered scratch and the memory of a new plan)
+ * fail as if the device were out of memory, without allocating, and the
+ * calls that needed them return TSDS_ENOMEM.  Work a call had already
+ * enqueued before the failed allocation still runs; its outputs are then
+ * unspecified.  count <= 0 clears the injection. */
+void tsds_inject_alloc_failures(int count);
+
 /* Checked mode.  When on, every entry point that takes x (the single-series
  * calls and their *_values forms, tsds_lttb_means, tsds_batched,
  * tsds_plan_create, tsds_server_add_series) first verifies on the device that

@@ -92,6 +92,8 @@ def load(path: str = LIB_PATH):
     lib.tsds_read_stream.restype = c_int
     lib.tsds_checked.argtypes = [c_int]
     lib.tsds_checked.restype = c_int
+    lib.tsds_inject_alloc_failures.argtypes = [c_int]
+    lib.tsds_inject_alloc_failures.restype = None
     _lib = lib
     return lib
 
@@ -131,6 +133,12 @@ def tsds_checked(on: int = -1) -> int:
     """Checked mode (x sortedness verified on the device before each call that takes x):
     on = 0/1 sets it, on < 0 only queries; returns the previous mode."""
     return int(load().tsds_checked(int(on)))
+
+
+def tsds_inject_alloc_failures(count: int) -> None:
+    """Failure injection for tests: the next `count` device allocations of the library fail
+    (the calls return TSDS_ENOMEM); count <= 0 clears it."""
+    load().tsds_inject_alloc_failures(int(count))
 
 
 def tsds_read_stream(buf, nbytes, sink, stream):

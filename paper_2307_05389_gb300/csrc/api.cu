@@ -11,6 +11,8 @@
 #include <mutex>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "internal.h"
 #include "lttb.h"
 
@@ -75,10 +77,22 @@ int device_sm_count() {
   return s ? s->sm_count : 148;
 }
 
+// Failure injection (tsds_inject_alloc_failures): the next g_fail_allocs
+// device allocations report cudaErrorMemoryAllocation without allocating.
+static std::atomic<int> g_fail_allocs{0};
+
+bool take_injected_alloc_failure() {
+  int v = g_fail_allocs.load();
+  while (v > 0)
+    if (g_fail_allocs.compare_exchange_weak(v, v - 1)) return true;
+  return false;
+}
+
 cudaError_t scratch_alloc(Scratch& s, size_t bytes, cudaStream_t st) {
   cudaError_t e;
   DevState* d = dev_state(&e);
   if (!d) return e;
+  if (take_injected_alloc_failure()) return cudaErrorMemoryAllocation;
   s.st = st;
   if (bytes == 0) bytes = 256;
   return cudaMallocFromPoolAsync(&s.p, bytes, d->pool, st);
@@ -145,6 +159,15 @@ static tsds_status check_common(const void* x, int x_dtype, const void* y, int y
     return fail(TSDS_EINVAL, "x is not aligned to its element size");
   return TSDS_OK;
 }
+
+// ---------------------------------------------------------------- NVTX
+
+// A named NVTX range around each public call (visible in Nsight tools; a
+// no-op when no tool is attached).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
 
 // ---------------------------------------------------------------- checked mode
 
@@ -361,12 +384,14 @@ extern "C" {
 tsds_status tsds_minmax(const void* x, tsds_dtype x_dtype, const void* y, tsds_dtype y_dtype,
                         int64_t n, int64_t n_out, tsds_nan_mode nan, int64_t* out,
                         int64_t* out_count, void* stream) {
+  NvtxRange nvtx_("tsds_minmax");
   return run_binned(ALGO_MINMAX, x, x_dtype, y, y_dtype, n, n_out, nan, out, out_count, stream);
 }
 
 tsds_status tsds_m4(const void* x, tsds_dtype x_dtype, const void* y, tsds_dtype y_dtype,
                     int64_t n, int64_t n_out, tsds_nan_mode nan, int64_t* out,
                     int64_t* out_count, void* stream) {
+  NvtxRange nvtx_("tsds_m4");
   return run_binned(ALGO_M4, x, x_dtype, y, y_dtype, n, n_out, nan, out, out_count, stream);
 }
 
@@ -409,54 +434,63 @@ static tsds_status minmaxlttb_entry(const void* x, tsds_dtype x_dtype, const voi
 tsds_status tsds_lttb(const void* x, tsds_dtype x_dtype, const void* y, tsds_dtype y_dtype,
                       int64_t n, int64_t n_out, tsds_nan_mode nan, int64_t* out,
                       int64_t* out_count, void* stream) {
+  NvtxRange nvtx_("tsds_lttb");
   return lttb_entry(x, x_dtype, y, y_dtype, n, n_out, nan, out, out_count, stream, nullptr, nullptr);
 }
 
 tsds_status tsds_minmaxlttb(const void* x, tsds_dtype x_dtype, const void* y, tsds_dtype y_dtype,
                             int64_t n, int64_t n_out, int64_t minmax_ratio, tsds_nan_mode nan,
                             int64_t* out, int64_t* out_count, void* stream) {
+  NvtxRange nvtx_("tsds_minmaxlttb");
   return minmaxlttb_entry(x, x_dtype, y, y_dtype, n, n_out, minmax_ratio, nan, out, out_count, stream, nullptr,
                           nullptr);
 }
 
 tsds_status tsds_everynth(const void* x, tsds_dtype x_dtype, const void* y, tsds_dtype y_dtype, int64_t n,
                           int64_t n_out, tsds_nan_mode nan, int64_t* out, int64_t* out_count, void* stream) {
+  NvtxRange nvtx_("tsds_everynth");
   return run_binned(ALGO_EVERYNTH, x, x_dtype, y, y_dtype, n, n_out, nan, out, out_count, stream);
 }
 
 tsds_status tsds_everynth_values(const void* x, tsds_dtype x_dtype, const void* y, tsds_dtype y_dtype, int64_t n,
                                  int64_t n_out, tsds_nan_mode nan, int64_t* out, int64_t* out_count, void* x_out,
                                  void* y_out, void* stream) {
+  NvtxRange nvtx_("tsds_everynth_values");
   return run_binned(ALGO_EVERYNTH, x, x_dtype, y, y_dtype, n, n_out, nan, out, out_count, stream, x_out, y_out);
 }
 
 tsds_status tsds_minmax_values(const void* x, tsds_dtype x_dtype, const void* y, tsds_dtype y_dtype, int64_t n,
                                int64_t n_out, tsds_nan_mode nan, int64_t* out, int64_t* out_count, void* x_out,
                                void* y_out, void* stream) {
+  NvtxRange nvtx_("tsds_minmax_values");
   return run_binned(ALGO_MINMAX, x, x_dtype, y, y_dtype, n, n_out, nan, out, out_count, stream, x_out, y_out);
 }
 
 tsds_status tsds_m4_values(const void* x, tsds_dtype x_dtype, const void* y, tsds_dtype y_dtype, int64_t n,
                            int64_t n_out, tsds_nan_mode nan, int64_t* out, int64_t* out_count, void* x_out,
                            void* y_out, void* stream) {
+  NvtxRange nvtx_("tsds_m4_values");
   return run_binned(ALGO_M4, x, x_dtype, y, y_dtype, n, n_out, nan, out, out_count, stream, x_out, y_out);
 }
 
 tsds_status tsds_lttb_values(const void* x, tsds_dtype x_dtype, const void* y, tsds_dtype y_dtype, int64_t n,
                              int64_t n_out, tsds_nan_mode nan, int64_t* out, int64_t* out_count, void* x_out,
                              void* y_out, void* stream) {
+  NvtxRange nvtx_("tsds_lttb_values");
   return lttb_entry(x, x_dtype, y, y_dtype, n, n_out, nan, out, out_count, stream, x_out, y_out);
 }
 
 tsds_status tsds_minmaxlttb_values(const void* x, tsds_dtype x_dtype, const void* y, tsds_dtype y_dtype, int64_t n,
                                    int64_t n_out, int64_t minmax_ratio, tsds_nan_mode nan, int64_t* out,
                                    int64_t* out_count, void* x_out, void* y_out, void* stream) {
+  NvtxRange nvtx_("tsds_minmaxlttb_values");
   return minmaxlttb_entry(x, x_dtype, y, y_dtype, n, n_out, minmax_ratio, nan, out, out_count, stream, x_out,
                           y_out);
 }
 
 tsds_status tsds_lttb_means(const void* x, tsds_dtype x_dtype, const void* y, tsds_dtype y_dtype,
                             int64_t n, int64_t n_out, tsds_nan_mode nan, double* means, void* stream) {
+  NvtxRange nvtx_("tsds_lttb_means");
   g_err[0] = 0;
   if (!means) return fail(TSDS_EINVAL, "tsds_lttb_means: means is NULL");
   if (n_out < 3 || n_out >= n)
@@ -507,12 +541,15 @@ tsds_status tsds_check_wait_timeout(unsigned rounds, void* stream) {
 
 void tsds_timing_enable(int on) { g_timing.store(on ? 1 : 0); }
 
+void tsds_inject_alloc_failures(int count) { g_fail_allocs.store(count > 0 ? count : 0); }
+
 int tsds_checked(int on) {
   if (on < 0) return g_checked.load();
   return g_checked.exchange(on ? 1 : 0);
 }
 
 tsds_status tsds_read_stream(const void* buf, int64_t bytes, uint64_t* sink, void* stream) {
+  NvtxRange nvtx_("tsds_read_stream");
   if (bytes < 0 || bytes % 16 != 0)
     return fail(TSDS_EINVAL, "tsds_read_stream: bytes must be a non-negative multiple of 16 (got %lld)",
                 (long long)bytes);

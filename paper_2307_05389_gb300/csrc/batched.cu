@@ -26,6 +26,7 @@
 namespace tsds {
 
 tsds_status fail(tsds_status s, const char* fmt, ...);
+bool take_injected_alloc_failure();   // failure injection of the library's allocations (api.cu)
 
 #define BT_CK(call)                                                                      \
   do {                                                                                   \
@@ -458,7 +459,7 @@ tsds_status tsds_plan_create(tsds_plan* plan, tsds_algo algo, const tsds_series*
   P->nan = nan;
   P->has_x = batch_has_x(series, count);
   P->L = make_layout(algo, series, count, y_dtype, kCandidates[0].window_bytes);
-  cudaError_t e = cudaMalloc(&P->base, P->L.total);
+  cudaError_t e = take_injected_alloc_failure() ? cudaErrorMemoryAllocation : cudaMalloc(&P->base, P->L.total);
   if (e != cudaSuccess) {
     delete p;
     return fail(TSDS_ENOMEM, "tsds_plan_create: cudaMalloc(%zu): %s", P->L.total, cudaGetErrorString(e));
