@@ -76,7 +76,7 @@ typedef enum { TSDS_NAN_PROPAGATE = 0, TSDS_NAN_IGNORE = 1 } tsds_nan_mode;
 typedef enum {
   TSDS_OK = 0,
   TSDS_EINVAL = 1,    /* an argument outside what the algorithm defines */
-  TSDS_ENOMEM = 2,    /* the scratch pool could not grow */
+  TSDS_ENOMEM = 2,    /* device memory could not be allocated (scratch pool, plan) */
   TSDS_ECUDA = 3,     /* a CUDA runtime call or kernel launch failed */
   TSDS_ETIMEOUT = 4,  /* a bounded device-side wait ran out */
   TSDS_EINTERNAL = 5  /* a device-side consistency check failed */
@@ -183,7 +183,8 @@ tsds_status tsds_batched(tsds_algo algo, const tsds_series* series, int64_t coun
  * series runs as one job of each LTTB kernel (Section 1: the preselection
  * keeps LTTB's cost low; Section 2.2: many series at once instead of one at
  * a time).  Each series' indices and count are exactly those of
- * tsds_minmaxlttb on that series.  1 <= count <= 65535.  The descriptors are
+ * tsds_minmaxlttb on that series, and each out needs the room that call's
+ * out needs (n_out indices, or n when n_out >= n).  1 <= count <= 65535.  The descriptors are
  * staged from pageable memory, so the call may wait for earlier work on
  * `stream` before it returns.  TSDS_EINVAL names the offending series. */
 tsds_status tsds_batched_minmaxlttb(const tsds_series* series, int64_t count, tsds_dtype x_dtype,
