@@ -198,6 +198,35 @@ def test_float_x_edges_only_differ_from_exact_rule_at_near_ties():
                     assert all(abs(fx[j] - e) <= tol for j in range(lo, hi)), (trial, nb, i)
 
 
+@pytest.mark.parametrize("x_dtype", ["int64", "uint64", "int8", "uint16", "float16", "float32", "float64"])
+def test_edges_never_decrease_with_the_bin_index(x_dtype):
+    """Bin starts are non-decreasing in the bin index under both the exact integer rule and the
+    rounded binary64 rule (each operation is monotone), for sorted x of every kind: long runs of
+    equal values, spans near the dtype's limits, rounding-heavy float steps.  So edge i lies
+    between the edges of any two bin indices around it, which lets a search for it start from
+    coarser edges."""
+    rng = np.random.default_rng(61)
+    dt = np.dtype(x_dtype)
+    for trial in range(6):
+        n = int(rng.integers(2, 5000))
+        if dt.kind == "f":
+            hi = float(np.finfo(dt).max) / (4 if trial % 2 else 1e6)
+            x = np.sort(rng.uniform(-hi, hi, n)).astype(dt)
+            if trial == 5:
+                x = np.sort(rng.integers(0, 7, n)).astype(dt)     # runs of equal values
+        else:
+            info = np.iinfo(dt)
+            lo, top = (int(info.min), int(info.max)) if trial % 2 else (0, int(info.max) // 3)
+            x = np.sort(rng.integers(lo, top, n, endpoint=True, dtype=dt))
+            if trial == 5:
+                x = np.sort(rng.integers(lo, lo + 5, n, dtype=dt))
+        x = np.sort(x)
+        for nb in (1, 2, 31, 32, 33, 1000, 5000):
+            e = oracle.bin_edges(x, n, nb)
+            assert e[0] == 0 and e[-1] == n
+            assert np.all(np.diff(e) >= 0), f"{x_dtype} n={n} nb={nb}"
+
+
 @pytest.mark.parametrize("x_dtype", ["int64", "int32", "uint32", "uint64", "float64", "float32"])
 def test_equal_x_matches_no_x_edges(x_dtype):
     """Section 2.2: an equally sampled x gives the same output as no x."""
