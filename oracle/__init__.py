@@ -51,7 +51,9 @@ def _load():
     global _lib
     if _lib is not None:
         return _lib
-    lib = ctypes.CDLL(build())
+    # TSDS_ORACLE_LIB loads another build of the same source instead (the
+    # mutation test compiles copies with one planted mistake each)
+    lib = ctypes.CDLL(os.environ.get("TSDS_ORACLE_LIB") or build())
     p, i64, c_int = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
     lib.orc_f16_to_f64.argtypes = [ctypes.c_uint16]
     lib.orc_f16_to_f64.restype = ctypes.c_double
