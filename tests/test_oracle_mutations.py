@@ -41,6 +41,29 @@ MUTATIONS = [
     # LTTB buckets laid out over m-1 points instead of m-2
     ("return 1 + (int64_t)(((u128)j * (u128)(m - 2)) / (u128)B);",
      "return 1 + (int64_t)(((u128)j * (u128)(m - 1)) / (u128)B);"),
+    # integer x edges: strict instead of reaching the edge
+    ("if (int_offset(x, dt, mid) * (u128)nb >= rhs) hi = mid; else lo = mid + 1;",
+     "if (int_offset(x, dt, mid) * (u128)nb > rhs) hi = mid; else lo = mid + 1;"),
+    # float x edges: strict instead of reaching the edge
+    ("if (get_f(x, dt, mid) >= e) hi = mid; else lo = mid + 1;", "if (get_f(x, dt, mid) > e) hi = mid; else lo = mid + 1;"),
+    # NaN-propagate: the last NaN of a bin instead of the first
+    ("if (y_isnan(y, y_dtype, i)) { *imin = i; *imax = i; return 0; }",
+     "if (y_isnan(y, y_dtype, i)) { *imin = i; *imax = i; }"),
+    # tie rule for the maximum
+    ("if (y_less(y, y_dtype, mx, i)) mx = i;   /* strict: the earliest maximum stays */",
+     "if (!y_less(y, y_dtype, i, mx)) mx = i;"),
+    # an all-NaN bin (NaN-ignore) selects its last index
+    ("if (mn < 0) { mn = lo; mx = lo; }", "if (mn < 0) { mn = hi - 1; mx = hi - 1; }"),
+    # uint64 x offsets taken as signed differences
+    ("return (u128)(get_u(x, dt, j) - get_u(x, dt, 0));",
+     "return (u128)(__int128)((int64_t)get_u(x, dt, j) - (int64_t)get_u(x, dt, 0));"),
+    # LTTB NaN-propagate: the last NaN area wins
+    ("if (nan_mode == ORC_NAN_PROPAGATE && !best_is_nan) { best = b; best_is_nan = 1; }",
+     "if (nan_mode == ORC_NAN_PROPAGATE) { best = b; best_is_nan = 1; }"),
+    # MinMaxLTTB preselection size rounded up
+    ("int64_t n_sel = 2 * ((n_out * minmax_ratio) / 2);", "int64_t n_sel = 2 * ((n_out * minmax_ratio + 1) / 2);"),
+    # LTTB area: the wrong vertex in the first term
+    ("double t1 = (xa - xm) * (py[b] - ya);", "double t1 = (xa - xm) * (py[b] - ym);"),
 ]
 
 
