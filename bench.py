@@ -12,8 +12,10 @@ Metric: input GB/s = algorithmic input bytes / time, where a step's bytes are
 n*4 for each of the two algorithms plus the x reads of the bin-edge searches
 ((nb+1)*ceil(log2 n)*8 per algorithm).  The line also reports the roofline of
 the dominant kernel (the streaming argmin/argmax, n*4 bytes per launch, timed
-by CUDA events on its stream), an end-to-end figure through the public API
-with pinned host buffers, and the CPU oracle timed on a bounded sample.
+by CUDA events on its stream) against the measured copy bandwidth and against
+a read-only streaming ceiling measured in the same run (tsds_read_stream over
+the resident y), an end-to-end figure through the public API with pinned host
+buffers, and the CPU oracle timed on a bounded sample.
 
 --impl reference times the CPU oracle itself on the host cores (the paper's
 own implementation is CPU code that is not available here).
