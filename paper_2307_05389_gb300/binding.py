@@ -112,6 +112,8 @@ STREAM_VARIANTS = {"auto": 0, "ring": 1, "ldg": 2, "seg": 3}
 def tsds_stream_variant(variant) -> str:
     """Sets the streaming-pass kernel variant ("auto", "ring", "ldg", "seg" or 0..3)
     for later calls; returns the previous one by name."""
+    if isinstance(variant, str) and variant not in STREAM_VARIANTS:
+        raise ValueError(f"unknown stream variant {variant!r}")
     v = STREAM_VARIANTS[variant] if isinstance(variant, str) else int(variant)
     prev = load().tsds_stream_variant(v)
     if prev < 0:

@@ -194,3 +194,25 @@ def test_batched_minmaxlttb_arguments_are_checked_on_the_host(lib):
     b = arr([good, [0, y, 1000, 1 << 40, out, cnt]])
     assert f(binding._array_ptr(b), 2, 0, 9, 1 << 40, 0, None) == 1                  # n_out * ratio overflows
     assert "overflows" in pkg.last_error()
+
+
+def test_binding_rejects_host_tensors_and_bad_shapes_before_any_call(lib):
+    """The torch-facing helpers check their tensors on the host: CPU tensors, 2-D tensors, an x
+    of another length and unknown names raise before anything reaches the library."""
+    torch = pytest.importorskip("torch")
+    y = torch.zeros(100, dtype=torch.float32)
+    before = pkg.tsds_kernel_launches()
+    for algo in ("minmax", "m4", "lttb", "minmaxlttb", "everynth"):
+        with pytest.raises(ValueError):
+            binding.downsample(algo, y, 10)                       # host tensor
+        with pytest.raises(ValueError):
+            binding.downsample_values(algo, y, 10)
+    with pytest.raises(ValueError):
+        binding.downsample("minmax", y.reshape(10, 10), 4)
+    with pytest.raises(ValueError):
+        binding.read_stream(y, torch.zeros(1, dtype=torch.int64))
+    with pytest.raises(ValueError):
+        binding.tsds_stream_variant("fastest")
+    with pytest.raises(TypeError):
+        binding.MinMaxDownsampler().downsample(y, y, y, n_out=4)
+    assert pkg.tsds_kernel_launches() == before
