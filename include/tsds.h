@@ -15,8 +15,9 @@
  *    call's completion on the stream and never copies y or x.
  *  - y holds n elements of y_dtype; x is NULL (equally spaced points, Section
  *    2.3) or holds n elements of x_dtype sorted non-decreasing, with no NaN.
- *    That order is checked only in checked mode (tsds_checked); otherwise an
- *    x out of order gives unspecified indices.  Both must be aligned to their
+ *    That order is checked only in checked mode (tsds_checked), which
+ *    rejects an x out of order; without it such an x is outside the contract
+ *    and the call's behaviour is undefined.  Both must be aligned to their
  *    element size.
  *  - out must have room for n_out indices (for MinMaxLTTB also n_out); when
  *    n_out >= n it receives 0..n-1 and needs room for n.  *out_count (a device
