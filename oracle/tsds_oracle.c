@@ -229,15 +229,19 @@ static int64_t all_indices(int64_t n, int64_t* out) {
   return n;
 }
 
-/* per_bin = 2 (MinMax) or 4 (M4) selections per bin. */
-static int64_t binned(const void* x, int x_dtype, const void* y, int y_dtype, int64_t n,
-                      int64_t n_out, int nan_mode, int64_t* out, int per_bin) {
+/* The output of bins [b0, b1) with per_bin = 2 (MinMax) or 4 (M4) selections
+ * per bin, the bins laid out over the whole series.  Each bin's selections
+ * depend on that bin alone (Section 2.2 runs bins on separate threads), so
+ * the output of all nb bins is the concatenation of these pieces in bin
+ * order. */
+static int64_t binned_range(const void* x, int x_dtype, const void* y, int y_dtype, int64_t n,
+                            int64_t n_out, int nan_mode, int64_t* out, int per_bin, int64_t b0, int64_t b1) {
   int64_t nb = n_out / per_bin;
   int64_t* s = (int64_t*)malloc((size_t)(nb + 1) * sizeof(int64_t));
   if (!s) return ORC_EINVAL;
   orc_bin_edges(x, x_dtype, n, nb, s);
   int64_t cnt = 0;
-  for (int64_t b = 0; b < nb; ++b) {
+  for (int64_t b = b0; b < b1; ++b) {
     int64_t lo = s[b], hi = s[b + 1];
     if (lo >= hi) continue;                 /* empty bin: nothing selected */
     int64_t mn, mx;
@@ -255,6 +259,11 @@ static int64_t binned(const void* x, int x_dtype, const void* y, int y_dtype, in
   return cnt;
 }
 
+static int64_t binned(const void* x, int x_dtype, const void* y, int y_dtype, int64_t n,
+                      int64_t n_out, int nan_mode, int64_t* out, int per_bin) {
+  return binned_range(x, x_dtype, y, y_dtype, n, n_out, nan_mode, out, per_bin, 0, n_out / per_bin);
+}
+
 int64_t orc_minmax(const void* x, int x_dtype, const void* y, int y_dtype, int64_t n,
                    int64_t n_out, int nan_mode, int64_t* out) {
   if (!args_ok(x, x_dtype, y, y_dtype, n) || n_out < 2 || n_out % 2 != 0) return ORC_EINVAL;
@@ -267,6 +276,14 @@ int64_t orc_m4(const void* x, int x_dtype, const void* y, int y_dtype, int64_t n
   if (!args_ok(x, x_dtype, y, y_dtype, n) || n_out < 4 || n_out % 4 != 0) return ORC_EINVAL;
   if (n_out >= n) return all_indices(n, out);
   return binned(x, x_dtype, y, y_dtype, n, n_out, nan_mode, out, 4);
+}
+
+int64_t orc_binned_range(int per_bin, const void* x, int x_dtype, const void* y, int y_dtype, int64_t n,
+                         int64_t n_out, int nan_mode, int64_t b0, int64_t b1, int64_t* out) {
+  if (per_bin != 2 && per_bin != 4) return ORC_EINVAL;
+  if (!args_ok(x, x_dtype, y, y_dtype, n) || n_out < per_bin || n_out % per_bin != 0 || n_out >= n) return ORC_EINVAL;
+  if (b0 < 0 || b1 < b0 || b1 > n_out / per_bin) return ORC_EINVAL;
+  return binned_range(x, x_dtype, y, y_dtype, n, n_out, nan_mode, out, per_bin, b0, b1);
 }
 
 /* EveryNth (Section 1 names it; the reading here): n_out bins laid out as

@@ -53,6 +53,13 @@ int64_t orc_lttb(const void* x, int x_dtype, const void* y, int y_dtype, int64_t
 int64_t orc_minmaxlttb(const void* x, int x_dtype, const void* y, int y_dtype, int64_t n,
                        int64_t n_out, int64_t minmax_ratio, int nan_mode, int64_t* out);
 
+/* The part of the MinMax (per_bin 2) or M4 (per_bin 4) output that bins
+ * [b0, b1) select, with the bins laid out over the whole series (n_out < n).
+ * Bins are independent, so the full output is the concatenation of these
+ * parts over consecutive bin ranges.  out must hold per_bin*(b1-b0) indices. */
+int64_t orc_binned_range(int per_bin, const void* x, int x_dtype, const void* y, int y_dtype, int64_t n,
+                         int64_t n_out, int nan_mode, int64_t b0, int64_t b1, int64_t* out);
+
 /* EveryNth (reading): the first point of each non-empty bin of the MinMax/M4
  * bin layout with n_out bins; n_out >= 1. */
 int64_t orc_everynth(const void* x, int x_dtype, const void* y, int y_dtype, int64_t n,

@@ -62,6 +62,9 @@ MUTATIONS = [
      "if (nan_mode == ORC_NAN_PROPAGATE) { best = b; best_is_nan = 1; }"),
     # MinMaxLTTB preselection size rounded up
     ("int64_t n_sel = 2 * ((n_out * minmax_ratio) / 2);", "int64_t n_sel = 2 * ((n_out * minmax_ratio + 1) / 2);"),
+    # bin ranges: the range starts at bin 0 whatever b0 is
+    ("return binned_range(x, x_dtype, y, y_dtype, n, n_out, nan_mode, out, per_bin, b0, b1);",
+     "return binned_range(x, x_dtype, y, y_dtype, n, n_out, nan_mode, out, per_bin, 0, b1);"),
     # LTTB area: the wrong vertex in the first term
     ("double t1 = (xa - xm) * (py[b] - ya);", "double t1 = (xa - xm) * (py[b] - ym);"),
 ]

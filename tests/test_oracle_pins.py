@@ -290,6 +290,57 @@ def test_minmax_m4_brute_force_int_x(x_dtype):
             np.testing.assert_array_equal(oracle.m4(x, y, n_out), bf_binned(y, bf_edges_int_x(xs, n_out // 4), 4, "propagate"))
 
 
+@pytest.mark.parametrize("dtype", ["int8", "uint16", "float32", "float64"])
+@pytest.mark.parametrize("nan", ["propagate", "ignore"])
+def test_binned_range_brute_force_tiny(dtype, nan):
+    """Bins [b0, b1) of the whole-series layout select exactly what brute force
+    selects in those bins (edges by exhaustive scan, extrema by numpy)."""
+    rng = np.random.default_rng(23)
+    for trial in range(25):
+        n = int(rng.integers(3, 40))
+        y = inputs.ties_and_specials(n, dtype, seed=100 + trial)
+        for algo, per in (("minmax", 2), ("m4", 4)):
+            for nb in (1, 2, 3, 5, 9):
+                n_out = nb * per
+                if n_out >= n:
+                    continue
+                s = bf_edges_index(n, nb)
+                b0 = int(rng.integers(0, nb + 1))
+                b1 = int(rng.integers(b0, nb + 1))
+                got = oracle.binned_range(algo, None, y, n_out, b0, b1, nan)
+                np.testing.assert_array_equal(got, bf_binned(y, s[b0:b1 + 1], per, nan))
+
+
+@pytest.mark.parametrize("x_dtype", ["int64", "int16", "float64"])
+def test_binned_range_concatenation_is_the_whole_output(x_dtype):
+    """Cutting the bins anywhere (also inside runs of equal x, where bins are
+    empty) and concatenating the parts in bin order gives the whole output."""
+    rng = np.random.default_rng(24)
+    for trial in range(20):
+        n = int(rng.integers(50, 3000))
+        gaps = rng.choice([0, 0, 1, 2, 40], size=n - 1)
+        x = np.concatenate([[0], np.cumsum(gaps)]).astype(x_dtype)
+        y = inputs.random_walk(n, "float32", seed=200 + trial)
+        y[rng.integers(0, n, 3)] = np.nan
+        for algo, per in (("minmax", 2), ("m4", 4)):
+            for nan in ("propagate", "ignore"):
+                n_out = per * int(rng.integers(1, max(2, n // (2 * per))))
+                whole = oracle.downsample(algo, x, y, n_out, nan)
+                nb = n_out // per
+                cuts = sorted({0, nb, *rng.integers(0, nb + 1, size=3).tolist()})
+                parts = [oracle.binned_range(algo, x, y, n_out, a, b, nan) for a, b in zip(cuts, cuts[1:])]
+                np.testing.assert_array_equal(np.concatenate(parts), whole)
+                np.testing.assert_array_equal(oracle.binned_threads(algo, x, y, n_out, nan, threads=5), whole)
+
+
+def test_binned_range_rejects_undefined_ranges():
+    y = np.arange(100, dtype=np.float32)
+    for args in (("minmax", None, y, 10, -1, 3), ("minmax", None, y, 10, 3, 2), ("minmax", None, y, 10, 0, 6),
+                 ("m4", None, y, 10, 0, 1), ("minmax", None, y, 100, 0, 1)):
+        with pytest.raises(oracle.OracleError):
+            oracle.binned_range(*args)
+
+
 def check_invariants(idx, n, n_out, algo):
     assert idx.dtype == np.int64
     assert np.all(np.diff(idx) > 0), "strictly increasing and unique"
