@@ -2,12 +2,11 @@
 times, on outputs the oracle computes one by one.
 
 * The headline workload (10^9 float32 random walk, int64 geometric x, n_out =
-  2000, MinMax and M4) and the per-dtype workloads (4 GB of y each): sampled
-  bins.  The oracle places each sampled bin (its own bin rule, Section 2.3,
-  evaluated on x_0, x_{n-1} and a window of x around the bin start, the window
-  checked to contain the answer) and takes its argmin/argmax (Section 2.1);
-  the GPU's indices inside that bin must be exactly the oracle's.  The whole
-  output must be strictly increasing, in range and at most n_out long.
+  2000, MinMax and M4) and the per-dtype workloads (4 GB of y each, all eleven
+  dtypes): whole outputs against the oracle on host copies of the same bytes.
+* The served workload's shape (resident 10^8-point float32 series with float64
+  x, viewport queries spanning 10^6 to 10^8 points, every served algorithm,
+  both NaN modes): every query's whole result against the oracle on its range.
 * The batched workload (4096 series, 17.7 GB, a resident autotuned plan with a
   CUDA graph): sampled series against the oracle, whole outputs.
 * Plain LTTB on 10^7 points and MinMaxLTTB on the 64 quantised NaN series of
@@ -26,7 +25,6 @@ from paper_2307_05389_gb300 import binding, inputs
 pytestmark = pytest.mark.gpu
 
 N_OUT = 2000
-WINDOW = 1 << 20          # x elements on each side of a sampled bin start
 
 
 def _host(t, dtype):
@@ -34,13 +32,13 @@ def _host(t, dtype):
     return t.cpu().numpy().view(np.dtype(dtype))
 
 
-def _raw(algo, x, y, y_dtype, n, n_out, nan="propagate"):
+def _raw(algo, x, y, y_dtype, n, n_out, nan="propagate", x_dtype="int64"):
     import torch
     out = torch.full((n_out + 8,), -7, dtype=torch.int64, device=y.device)
     cnt = torch.full((1,), -1, dtype=torch.int64, device=y.device)
     st = torch.cuda.current_stream(y.device)
     fn = {"minmax": binding.tsds_minmax, "m4": binding.tsds_m4}[algo]
-    r = fn(x.data_ptr() if x is not None else None, binding.DTYPES["int64"] if x is not None else 0,
+    r = fn(x.data_ptr() if x is not None else None, binding.DTYPES[x_dtype] if x is not None else 0,
            y.data_ptr(), binding.DTYPES[y_dtype], n, n_out, binding.NAN_MODES[nan], out.data_ptr(),
            cnt.data_ptr(), ctypes.c_void_p(st.cuda_stream))
     assert r == 0, binding.last_error()
@@ -51,74 +49,46 @@ def _raw(algo, x, y, y_dtype, n, n_out, nan="propagate"):
     return res[:k]
 
 
-def _bin_start(x_dev, n, nb, i):
-    """Start of bin i by the oracle's bin rule, from x_0, x_{n-1} and a window of x."""
-    if i == 0:
-        return 0
-    if i == nb:
-        return n
-    c = int(round(i * n / nb))
-    a, b = max(1, c - WINDOW), min(n - 1, c + WINDOW)
-    sub = np.concatenate([_host(x_dev[:1], "int64"), _host(x_dev[a:b], "int64"), _host(x_dev[n - 1:], "int64")])
-    p = int(oracle.bin_edges(sub, len(sub), nb)[i])
-    # the answer lies strictly inside the window: x[a] is below the edge and some
-    # element of the window reaches it, so the global first index is a + p - 1
-    assert 1 < p <= b - a, f"bin {i}: edge outside the sampled window"
-    return a + p - 1
+def _whole_outputs_match(x, y, y_dtype, n, seed_note):
+    """MinMax and M4 at n_out = 2000 on the device, then the oracle on host copies of
+    the same bytes (its bins split over host threads, each part the single-threaded
+    oracle), compared index for index."""
+    import torch
+    got = {algo: _raw(algo, x, y, y_dtype, n, N_OUT) for algo in ("minmax", "m4")}
+    yh = _host(y, y_dtype)
+    xh = _host(x, "int64")
+    for algo, g in got.items():
+        want = oracle.binned_threads(algo, xh, yh, N_OUT)
+        assert len(want) == len(g), f"{algo} {seed_note}: {len(g)} indices, oracle {len(want)}"
+        bad = np.flatnonzero(g != want)
+        assert bad.size == 0, f"{algo} {seed_note}: first difference at output {bad[:1]}"
+    del yh, xh
+    torch.cuda.empty_cache()
 
 
-def _check_sampled_bins(algo, out, x_dev, y_dev, y_dtype, n, n_out, bins, nan="propagate"):
-    nb = n_out // (2 if algo == "minmax" else 4)
-    assert np.all(np.diff(out) > 0) and out[0] >= 0 and out[-1] < n
-    for i in bins:
-        if x_dev is None:
-            e = oracle.bin_edges(None, n, nb)
-            lo, hi = int(e[i]), int(e[i + 1])
-        else:
-            lo, hi = _bin_start(x_dev, n, nb, i), _bin_start(x_dev, n, nb, i + 1)
-        got = out[(out >= lo) & (out < hi)]
-        if hi == lo:
-            assert got.size == 0
-            continue
-        a, b = oracle.argminmax(_host(y_dev[lo:hi], y_dtype), 0, hi - lo, nan)
-        want = {lo + a, lo + b}
-        if algo == "m4":
-            want |= {lo, hi - 1}
-        assert list(got) == sorted(want), f"{algo} bin {i} [{lo}, {hi})"
-
-
-def _sample(nb, seed, k=14):
-    rng = np.random.default_rng(seed)
-    return sorted({0, nb - 1, *rng.choice(nb, size=k, replace=False).tolist()})
-
-
-def test_headline_workload_sampled_bins():
-    """10^9 float32 random walk (seed 2), int64 geometric x (seed 2), n_out = 2000."""
+def test_headline_workload_whole_output():
+    """10^9 float32 random walk (seed 2), int64 geometric x (seed 2), n_out = 2000: every
+    index of both outputs."""
     import torch
     n = 10 ** 9
     y = inputs.random_walk_cuda(n, "float32", seed=2)
     x = inputs.geometric_x_cuda(n, seed=2)
     torch.cuda.synchronize()
-    for algo in ("minmax", "m4"):
-        out = _raw(algo, x, y, "float32", n, N_OUT)
-        nb = N_OUT // (2 if algo == "minmax" else 4)
-        _check_sampled_bins(algo, out, x, y, "float32", n, N_OUT, _sample(nb, seed=11))
+    _whole_outputs_match(x, y, "float32", n, "1e9 float32 random walk")
     del x, y
     torch.cuda.empty_cache()
 
 
-@pytest.mark.parametrize("dtype", ["int8", "uint16", "float16", "float64"])
-def test_dtype_workloads_sampled_bins(dtype):
-    """4 GB of quarter-range y per dtype (seed 2) with int64 geometric x (seed 2)."""
+@pytest.mark.parametrize("dtype", inputs.DTYPES)
+def test_dtype_workloads_whole_output(dtype):
+    """4 GB of quarter-range y per dtype (seed 2; float32 here is the uniform case) with int64
+    geometric x (seed 2), n_out = 2000: every index of both outputs."""
     import torch
     n = 4_000_000_000 // np.dtype(dtype).itemsize
     y = inputs.quarter_range_cuda(n, dtype, seed=2)
     x = inputs.geometric_x_cuda(n, seed=2)
     torch.cuda.synchronize()
-    for algo in ("minmax", "m4"):
-        out = _raw(algo, x, y, dtype, n, N_OUT)
-        nb = N_OUT // (2 if algo == "minmax" else 4)
-        _check_sampled_bins(algo, out, x, y, dtype, n, N_OUT, _sample(nb, seed=12, k=6))
+    _whole_outputs_match(x, y, dtype, n, f"4 GB {dtype}")
     del x, y
     torch.cuda.empty_cache()
 
@@ -191,3 +161,64 @@ def test_batched_minmaxlttb_quantised_nan_series(nan):
         for i in pick:
             want = oracle.minmaxlttb(None, series[i], 4000, r, nan)
             assert np.array_equal(outs[i][:int(c[i])].cpu().numpy(), want), f"series {i} ratio {r}"
+
+
+def test_served_workload_resident_1e8_series():
+    """The served workload's shape: four resident 10^8-point float32 random walks (the
+    serving benchmark's first four, seeds 500..503) with float64 x = cumsum(exponential(1))
+    (seeds 600..603), one of them with 1 % of its points set to NaN so that the two NaN modes
+    differ.  48 viewport queries spanning 10^6 to 10^8 points (log-uniform; 36 as x ranges,
+    12 as index ranges), n_out in {500, 1000, 2000, 4000}, MinMax / M4 / MinMaxLTTB(4), both
+    NaN modes, all submitted at once to a server shaped like the benchmark's (4 streams,
+    batches of up to 256, 8 GiB budget).  Each whole result must equal the oracle on the range
+    its query selects, shifted to the whole series."""
+    import concurrent.futures as cf
+
+    import torch
+    nser, n = 4, 100_000_000
+    ys = [inputs.random_walk_cuda(n, "float32", seed=500 + i) for i in range(nser)]
+    xs = [inputs.exponential_x_cuda(n, seed=600 + i) for i in range(nser)]
+    torch.cuda.synchronize()
+    yh = [_host(y, "float32") for y in ys]
+    xh = [_host(x, "float64") for x in xs]
+    rng = np.random.default_rng(16)
+    nan_at = rng.choice(n, size=n // 100, replace=False)
+    yh[3] = yh[3].copy()
+    yh[3][nan_at] = np.nan
+    ys[3].copy_(torch.from_numpy(yh[3]))
+    srv = binding.Server("float32", "float64", streams=4, max_batch=256, memory_budget=8 << 30)
+    try:
+        ids = [srv.add_series(y, x) for y, x in zip(ys, xs)]
+        qs = []
+        for k in range(48):
+            s = int(rng.integers(0, nser))
+            span = int(10 ** rng.uniform(6, 8))
+            start = int(rng.integers(0, n - span + 1))
+            q = dict(sid=s, algo=("minmax", "m4", "minmaxlttb")[k % 3], n_out=int(rng.choice([500, 1000, 2000, 4000])),
+                     nan=("propagate", "ignore")[(k // 3) % 2])
+            if k % 4 == 3:
+                q["index_range"] = (start, start + span)
+            else:
+                q["x_range"] = (float(xh[s][start]), float(xh[s][start + span - 1]))
+            qs.append(q)
+        tickets = [srv.submit(ids[q["sid"]], q["algo"], q["n_out"], x_range=q.get("x_range"),
+                              index_range=q.get("index_range"), nan=q["nan"]) for q in qs]
+        got = [srv.result(t)[0] for t in tickets]
+    finally:
+        srv.close()
+
+    def want(q):
+        x, y = xh[q["sid"]], yh[q["sid"]]
+        if "x_range" in q:
+            lo = int(np.searchsorted(x, q["x_range"][0], "left"))
+            hi = int(np.searchsorted(x, q["x_range"][1], "right"))
+        else:
+            lo, hi = q["index_range"]
+        return oracle.downsample(q["algo"], x[lo:hi], y[lo:hi], q["n_out"], nan=q["nan"], minmax_ratio=4) + lo
+
+    with cf.ThreadPoolExecutor(16) as ex:
+        wants = list(ex.map(want, qs))
+    for q, g, w in zip(qs, got, wants):
+        assert np.array_equal(g, w), f"query {q}: {len(g)} indices, oracle {len(w)}"
+    del ys, xs
+    torch.cuda.empty_cache()
