@@ -304,7 +304,9 @@ tsds_status tsds_server_destroy(tsds_server server);
  *    about 8 GB of y fit).
  *  - The first call on a device, with that device current, looks up the
  *    array's device address (cudaGetSymbolAddress); make that first call
- *    before any stream capture.
+ *    before any stream capture.  The address is kept until tsds_shutdown:
+ *    after a reset of the device (cudaDeviceReset) call tsds_shutdown
+ *    before the next call, so that the address is looked up again.
  *  - Every call shares the one array and clears the parts that must start at
  *    zero; calls whose work overlaps on the GPU (other streams, other
  *    threads) race on it and give wrong results.  Serialise them. */
@@ -315,8 +317,11 @@ tsds_status tsds_minmax_noalloc(const void* x, tsds_dtype x_dtype, const void* y
 /* Message for the calling thread's last failed call ("" if none). */
 const char* tsds_last_error(void);
 
-/* Releases the scratch pools of every device the library touched.  Work
- * still queued on streams must have completed.  Later calls re-create them. */
+/* Releases the scratch pools of every device the library touched and forgets
+ * the per-device state (the static scratch address of tsds_minmax_noalloc,
+ * launch-shape caches).  Work still queued on streams must have completed.
+ * Later calls re-create them.  Call it after a device reset before using the
+ * library on that device again. */
 void tsds_shutdown(void);
 
 /* Library version, "major.minor.patch". */

@@ -521,6 +521,8 @@ void tsds_shutdown(void) {
   }
   g_dev.clear();
   cudaSetDevice(cur);
+  noalloc_forget_devices();
+  forget_stream_occupancy();
 }
 
 const char* tsds_version(void) { return "0.1.0"; }

@@ -757,23 +757,47 @@ cudaError_t launch_wait_probe(unsigned long long* status, unsigned rounds, cudaS
 typedef unsigned __int128 u128;
 #include "stream_small.cuh"
 
+// Resident CTAs per SM of each streaming kernel, cached per device (and
+// cleared by tsds_shutdown).  The ring kernel's 64 KB of dynamic shared memory
+// is opted into here, once per device, with the device current.
+constexpr int kOccDevices = 64;
+static std::atomic<unsigned> g_occ_epoch{1};
+
+void forget_stream_occupancy() { g_occ_epoch.fetch_add(1); }
+
 template <class P, int NM, bool MULTI, int VAR>
-static int stream_occupancy() {
-  static int occ = 0;
-  if (occ == 0) {
-    cudaError_t e;
-    if constexpr (VAR == STREAM_LDG) {
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_argminmax_ldg<P, NM, MULTI>, kStreamThreadsLdg, 0);
-    } else if constexpr (VAR == STREAM_SEG) {
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_argminmax_seg<P, NM, MULTI>, kSegThreads, 0);
-    } else {
-      auto kern = k_argminmax<P, NM, MULTI>;
-      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kRingSmemBytes);
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kRingThreads, kRingSmemBytes);
+static cudaError_t stream_occupancy(int* occ_out) {
+  // per device: the epoch the cached value belongs to (high 32 bits) and the value
+  static std::atomic<unsigned long long> cache[kOccDevices];
+  int d = 0;
+  cudaError_t e = cudaGetDevice(&d);
+  if (e != cudaSuccess) return e;
+  const unsigned epoch = g_occ_epoch.load();
+  std::atomic<unsigned long long>* slot = (d >= 0 && d < kOccDevices) ? &cache[d] : nullptr;
+  if (slot) {
+    const unsigned long long c = slot->load();
+    if ((unsigned)(c >> 32) == epoch && (int)(c & 0xffffffffu) > 0) {
+      *occ_out = (int)(c & 0xffffffffu);
+      return cudaSuccess;
     }
-    if (e != cudaSuccess || occ < 1) occ = 1;
   }
-  return occ;
+  int occ = 0;
+  if constexpr (VAR == STREAM_LDG) {
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_argminmax_ldg<P, NM, MULTI>, kStreamThreadsLdg, 0);
+  } else if constexpr (VAR == STREAM_SEG) {
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_argminmax_seg<P, NM, MULTI>, kSegThreads, 0);
+  } else {
+    auto kern = k_argminmax<P, NM, MULTI>;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kRingSmemBytes);
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kRingThreads, kRingSmemBytes);
+  }
+  if (e != cudaSuccess) return e;
+  if (occ < 1) occ = 1;
+  // concurrent first calls compute the same value; either store is fine
+  if (slot) slot->store(((unsigned long long)epoch << 32) | (unsigned)occ);
+  *occ_out = occ;
+  return cudaSuccess;
 }
 
 // Process-wide override of the per-launch choice (tsds_stream_variant; at
@@ -805,7 +829,9 @@ template <class P, int NM, int VAR, bool MULTI>
 static cudaError_t launch_var(const SeriesDev* s_dev, const SeriesDev& single, const int32_t* win_series,
                               int64_t total_windows, Piece* fp, Piece* lp, WorkCounters* work,
                               const StreamConfig& cfg, int sm_count, cudaStream_t st) {
-  const int occ = stream_occupancy<P, NM, MULTI, VAR>();
+  int occ = 1;
+  const cudaError_t oe = stream_occupancy<P, NM, MULTI, VAR>(&occ);
+  if (oe != cudaSuccess) return oe;
   const int per = (cfg.ctas_per_sm > 0 && cfg.ctas_per_sm < occ) ? cfg.ctas_per_sm : occ;
   const int threads = VAR == STREAM_LDG ? kStreamThreadsLdg : VAR == STREAM_SEG ? kSegThreads : kRingThreads;
   const int warps_per_cta = threads / 32;

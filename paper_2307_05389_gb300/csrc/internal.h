@@ -170,6 +170,11 @@ cudaError_t launch_iota(int64_t* out, int64_t n, int64_t* count, cudaStream_t st
 
 int device_sm_count();
 
+// tsds_shutdown: drop the per-device state kept outside the scratch pools
+// (the static scratch address of tsds_minmax_noalloc, the occupancy caches).
+void noalloc_forget_devices();
+void forget_stream_occupancy();
+
 // Checked mode (tsds_checked, TSDS_CHECKED=1): every entry point that takes x
 // first verifies on the device that it is sorted non-decreasing with no NaN,
 // waits for the answer and returns TSDS_EINVAL before launching anything else.

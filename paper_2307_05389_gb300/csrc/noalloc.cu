@@ -72,6 +72,17 @@ cudaError_t noalloc_device(NoallocDevice** out) {
 
 size_t up256(size_t v) { return (v + 255) / 256 * 256; }
 
+}  // namespace
+
+// Forgets every looked-up address (tsds_shutdown): after a device reset the
+// old address would be stale, so the next call looks it up again.
+void noalloc_forget_devices() {
+  std::lock_guard<std::mutex> lk(g_na_mu);
+  for (auto& d : g_na_dev) d = NoallocDevice{};
+}
+
+namespace {
+
 __global__ void k_iota_na(int64_t* out, int64_t n, int64_t* count) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     out[i] = i;
