@@ -76,7 +76,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--n-out", type=int, default=N_OUT, help="n_out of the default step (profiling other bin sizes)")
     ap.add_argument("--batch-count", type=int, default=4096, help="series in the batched suite (smaller for profiling)")
-    ap.add_argument("--stream-variant", default="auto", choices=["auto", "ring", "ldg", "seg"],
+    ap.add_argument("--stream-variant", default="auto", choices=["auto", "ring", "ldg", "seg", "grp"],
                     help="kernel variant of the streaming pass (tsds_stream_variant)")
     ap.add_argument("--suite", default=None, choices=["dtypes", "config1", "lttb", "batched", "serve", "values"],
                     help="instead of the headline step, measure one of the other workloads and print one JSON line")

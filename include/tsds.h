@@ -111,6 +111,25 @@ tsds_status tsds_minmaxlttb(const void* x, tsds_dtype x_dtype, const void* y,
                             int64_t minmax_ratio, tsds_nan_mode nan, int64_t* out,
                             int64_t* out_count, void* stream);
 
+/* Part of MinMax / M4 by bin range (Section 2.2: bins are independent, which
+ * is what lets the paper run them on separate threads).  With the bins laid
+ * out over the whole series exactly as tsds_minmax / tsds_m4 lay them out
+ * (nb = n_out/2 or n_out/4), writes what bins [bin_lo, bin_hi) select, in
+ * order, to out (capacity 2*(bin_hi-bin_lo) or 4*(bin_hi-bin_lo) indices, global
+ * into the whole series) and the count to *out_count.  Concatenating the
+ * outputs of consecutive ranges that cover [0, nb) gives the whole output, so
+ * ranks that each hold the series can split its bins and gather the lists
+ * (the Python helper paper_2307_05389_gb300.shard does this).  Only the y of
+ * the range's bins is read.  TSDS_EINVAL when n_out is not a valid MinMax/M4
+ * n_out, when n_out >= n (the output is every index, with no bins), or when
+ * the range is not inside [0, nb); bin_lo == bin_hi writes a count of 0. */
+tsds_status tsds_minmax_bins(const void* x, tsds_dtype x_dtype, const void* y, tsds_dtype y_dtype,
+                             int64_t n, int64_t n_out, int64_t bin_lo, int64_t bin_hi, tsds_nan_mode nan,
+                             int64_t* out, int64_t* out_count, void* stream);
+tsds_status tsds_m4_bins(const void* x, tsds_dtype x_dtype, const void* y, tsds_dtype y_dtype,
+                         int64_t n, int64_t n_out, int64_t bin_lo, int64_t bin_hi, tsds_nan_mode nan,
+                         int64_t* out, int64_t* out_count, void* stream);
+
 /* EveryNth (Section 1 names it among the algorithms; reading): the n_out bins
  * MinMax/M4 lay out (index space without x: bin i starts at
  * ceil(i(n-1)/n_out); equal-width x ranges with x) and the first point of
@@ -349,18 +368,26 @@ tsds_status tsds_check_wait_timeout(unsigned rounds, void* stream);
 
 /* Kernel variant of the streaming argmin/argmax pass for every later call in
  * the process (no counterpart in the paper, whose CPU kernel has one form):
- *   0  automatic (the default): per launch, by the bytes-weighted mean bin
- *      size: variant 3 below 768 bytes (8-byte y), 1.5 KB (4-byte), 1 KB
- *      (2-byte) or 512 bytes (1-byte), variant 2 otherwise;
+ *   0  automatic (the default).  Single-series calls: a warp per bin in one
+ *      launch for inputs of at most 256 MB with bins of at least 4 KB (or at
+ *      most 4096 bins) and for larger inputs with bins of at least 8 KB;
+ *      otherwise variant 4 when the mean bin is below 8 KB, variant 2 above.
+ *      Batches and served queries: series or queries are grouped by bin size
+ *      (variant 4 below 8 KB for batches without x and for queries, a warp
+ *      per bin up to 64 KB, variant 2 above; batches with x take variant 3
+ *      below 768 bytes (8-byte y), 1.5 KB (4-byte), 1 KB (2-byte) or 512
+ *      bytes (1-byte));
  *   1  shared-memory ring (bulk async copies into shared memory, one warp
  *      per bin);
  *   2  register streaming, one warp per bin;
  *   3  segmented: y staged through shared memory by per-lane async copies,
- *      bins split across lanes.
- * The environment variable TSDS_STREAM_VARIANT=ring|ldg|seg sets 1, 2 or 3
+ *      bins split across lanes;
+ *   4  lane groups: each bin reduced whole by a group of 1 to 32 lanes
+ *      (single-series calls; bins above 64 KB are handed to variant 2).
+ * The environment variable TSDS_STREAM_VARIANT=ring|ldg|seg|grp sets 1 to 4
  * when the library loads.  Results are identical; only speed differs.
  * Batched plans that were tuned keep the variant they chose.  Returns the
- * previous setting, or -1 (and sets nothing) when `variant` is not 0..3. */
+ * previous setting, or -1 (and sets nothing) when `variant` is not 0..4. */
 int tsds_stream_variant(int variant);
 
 /* Waits for the launches recorded since the previous read, writes the sum of

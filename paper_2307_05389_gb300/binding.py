@@ -49,6 +49,10 @@ def load(path: str = LIB_PATH):
         f.restype = c_int
     lib.tsds_minmaxlttb.argtypes = [p, c_int, p, c_int, i64, i64, i64, c_int, p, p, p]
     lib.tsds_minmaxlttb.restype = c_int
+    for name in ("tsds_minmax_bins", "tsds_m4_bins"):
+        f = getattr(lib, name)
+        f.argtypes = [p, c_int, p, c_int, i64, i64, i64, i64, c_int, p, p, p]
+        f.restype = c_int
     lib.tsds_last_error.argtypes = []
     lib.tsds_last_error.restype = ctypes.c_char_p
     lib.tsds_shutdown.argtypes = []
@@ -106,11 +110,11 @@ def tsds_timing_enable(on: bool) -> None:
     load().tsds_timing_enable(1 if on else 0)
 
 
-STREAM_VARIANTS = {"auto": 0, "ring": 1, "ldg": 2, "seg": 3}
+STREAM_VARIANTS = {"auto": 0, "ring": 1, "ldg": 2, "seg": 3, "grp": 4}
 
 
 def tsds_stream_variant(variant) -> str:
-    """Sets the streaming-pass kernel variant ("auto", "ring", "ldg", "seg" or 0..3)
+    """Sets the streaming-pass kernel variant ("auto", "ring", "ldg", "seg", "grp" or 0..4)
     for later calls; returns the previous one by name."""
     if isinstance(variant, str) and variant not in STREAM_VARIANTS:
         raise ValueError(f"unknown stream variant {variant!r}")
@@ -213,6 +217,14 @@ def tsds_minmaxlttb_values(x, x_dtype, y, y_dtype, n, n_out, minmax_ratio, nan, 
 
 def tsds_minmaxlttb(x, x_dtype, y, y_dtype, n, n_out, minmax_ratio, nan, out, out_count, stream):
     return load().tsds_minmaxlttb(x, x_dtype, y, y_dtype, n, n_out, minmax_ratio, nan, out, out_count, stream)
+
+
+def tsds_minmax_bins(x, x_dtype, y, y_dtype, n, n_out, bin_lo, bin_hi, nan, out, out_count, stream):
+    return load().tsds_minmax_bins(x, x_dtype, y, y_dtype, n, n_out, bin_lo, bin_hi, nan, out, out_count, stream)
+
+
+def tsds_m4_bins(x, x_dtype, y, y_dtype, n, n_out, bin_lo, bin_hi, nan, out, out_count, stream):
+    return load().tsds_m4_bins(x, x_dtype, y, y_dtype, n, n_out, bin_lo, bin_hi, nan, out, out_count, stream)
 
 
 def tsds_minmax_noalloc(x, x_dtype, y, y_dtype, n, n_out, nan, out, out_count, stream):
@@ -610,6 +622,35 @@ def downsample(algo, y, n_out, x=None, nan="propagate", minmax_ratio=4, out=None
     if not sync:
         return out, out_count
     k = int(out_count.item())
+    if k < 0:
+        raise TsdsError(-k, "the streaming pass reported a device-side failure")
+    return out[:k]
+
+
+def downsample_bins(algo, y, n_out, bin_lo, bin_hi, x=None, nan="propagate", stream=None):
+    """What bins [bin_lo, bin_hi) of MinMax or M4 select (tsds_minmax_bins / tsds_m4_bins),
+    the bins laid out over the whole series; a device int64 tensor of global indices."""
+    import torch
+    if algo not in ("minmax", "m4"):
+        raise ValueError(f"bin ranges cover MinMax and M4, not {algo!r}")
+    if not (y.is_cuda and y.dim() == 1 and y.is_contiguous()):
+        raise ValueError("y must be a contiguous 1-D CUDA tensor")
+    n = y.shape[0]
+    if x is not None and not (x.is_cuda and x.dim() == 1 and x.is_contiguous() and x.shape[0] == n):
+        raise ValueError("x must be a contiguous 1-D CUDA tensor as long as y")
+    per = 2 if algo == "minmax" else 4
+    dev = y.device
+    out = torch.empty(max(per * (bin_hi - bin_lo), 1), dtype=torch.int64, device=dev)
+    cnt = torch.empty(1, dtype=torch.int64, device=dev)
+    st = stream if stream is not None else torch.cuda.current_stream(dev)
+    fn = tsds_minmax_bins if algo == "minmax" else tsds_m4_bins
+    with torch.cuda.device(dev):
+        r = fn(x.data_ptr() if x is not None else None, DTYPES[_torch_dtype_name(x)] if x is not None else 0,
+               y.data_ptr(), DTYPES[_torch_dtype_name(y)], n, n_out, bin_lo, bin_hi, NAN_MODES[nan], out.data_ptr(),
+               cnt.data_ptr(), ctypes.c_void_p(st.cuda_stream))
+    if r != 0:
+        raise TsdsError(r, last_error())
+    k = int(cnt.item())
     if k < 0:
         raise TsdsError(-k, "the streaming pass reported a device-side failure")
     return out[:k]

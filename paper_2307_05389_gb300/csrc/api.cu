@@ -199,7 +199,7 @@ tsds_status check_sorted_x(const char* who, const void* x, tsds_dtype xd, int64_
 
 // Scratch layout of one binned call.
 struct BinnedLayout {
-  size_t edges, res, cnt, work, first, last, tiles, total, zero_begin, zero_bytes;
+  size_t edges, res, cnt, work, work2, first, last, tiles, total, zero_begin, zero_bytes;
 };
 
 static BinnedLayout binned_layout(int64_t nb, int64_t windows) {
@@ -210,6 +210,7 @@ static BinnedLayout binned_layout(int64_t nb, int64_t windows) {
   L.res = o;   o = align_up(o + (size_t)nb * 16, 256);
   L.cnt = o;   o = align_up(o + (size_t)nb * 4, 256);
   L.work = o;  o = align_up(o + sizeof(WorkCounters), 256);
+  L.work2 = o; o = align_up(o + sizeof(WorkCounters), 256);
   L.first = o; o = align_up(o + (size_t)windows * sizeof(Piece), 256);
   L.last = o;  o = align_up(o + (size_t)windows * sizeof(Piece), 256);
   L.total = o;
@@ -262,6 +263,7 @@ tsds_status run_binned_series(const void* x, tsds_dtype x_dtype, const void* y, 
   // warps would leave SMs idle.
   StreamConfig cfg;
   cfg.mean_bin_bytes = nb > 0 ? n / nb * dtype_size(y_dtype) : 0;
+  const bool grp = grp_call(cfg.mean_bin_bytes);
   {
     const int64_t bytes = n * dtype_size(y_dtype);
     const int64_t warps = (int64_t)device_sm_count() * 3 * 4;
@@ -293,13 +295,122 @@ tsds_status run_binned_series(const void* x, tsds_dtype x_dtype, const void* y, 
   TSDS_CK(launch_edges(nullptr, 1, &S, x != nullptr, x_dtype, nb, st));
   void* tok;
   timing_begin(st, &tok);
-  TSDS_CK(launch_argminmax(nullptr, 1, S, nullptr, windows, reinterpret_cast<Piece*>(base + L.first),
-                           reinterpret_cast<Piece*>(base + L.last), reinterpret_cast<WorkCounters*>(base + L.work),
-                           y_dtype, nan, st, cfg));
+  if (grp) {
+    // lanes-per-bin pass; bins far above the mean (possible with x) go to a
+    // register-streaming pass over the windows, which skips every other bin
+    // and exits at once when there is none
+    GrpShape shape = grp_shape(cfg.mean_bin_bytes, dtype_size(y_dtype));
+    const int64_t max_points = x ? n : (n - 1) / nb + 2;   // no x: bins differ by at most one point
+    const bool large_pass = max_points > shape.max_bin;
+    if (!large_pass) shape.max_bin = 0;
+    const int64_t tile_bins = (int64_t)(32 >> shape.g_log2) * shape.tile_rounds;
+    WorkCounters* w1 = reinterpret_cast<WorkCounters*>(base + L.work);
+    TSDS_CK(launch_argminmax_grp(nullptr, S, nullptr, (nb + tile_bins - 1) / tile_bins, w1, y_dtype, nan, shape, st));
+    if (large_pass) {
+      cfg.variant = STREAM_LDG;
+      cfg.mean_bin_bytes = kPrefetchOffBinBytes;   // the bins it reads are large: no L2 prefetch
+      cfg.min_bin = shape.max_bin;
+      cfg.large_dev = &w1->large;
+      TSDS_CK(launch_argminmax(nullptr, 1, S, nullptr, windows, reinterpret_cast<Piece*>(base + L.first),
+                               reinterpret_cast<Piece*>(base + L.last),
+                               reinterpret_cast<WorkCounters*>(base + L.work2), y_dtype, nan, st, cfg));
+    }
+  } else {
+    TSDS_CK(launch_argminmax(nullptr, 1, S, nullptr, windows, reinterpret_cast<Piece*>(base + L.first),
+                             reinterpret_cast<Piece*>(base + L.last), reinterpret_cast<WorkCounters*>(base + L.work),
+                             y_dtype, nan, st, cfg));
+  }
   timing_end(st, tok);
   if (nb >= kEmitTiledMinBins) TSDS_CK(launch_emit_tiled(S, algo, reinterpret_cast<int64_t*>(base + L.tiles), st));
   else TSDS_CK(launch_emit(nullptr, 1, S, algo, st));
   return TSDS_OK;
+}
+
+// Bins [b0, b1) of the whole-series layout of nb bins: the bin starts of the
+// whole series, then the lane-group pass over those bins only (bins above its
+// size limit go to a register-streaming pass over the windows that skips
+// every other bin and exits at once when there is none), then the emit of
+// those bins.  Output: what those bins select, in order.
+static tsds_status run_binned_range(const void* x, tsds_dtype x_dtype, const void* y, tsds_dtype y_dtype,
+                                    int64_t n, int64_t nb, int64_t b0, int64_t b1, tsds_nan_mode nan, Algo algo,
+                                    int64_t* out, int64_t* out_count, cudaStream_t st) {
+  const int64_t k = b1 - b0;
+  const int64_t elem = dtype_size(y_dtype);
+  const int64_t welems = kWindowBytes / elem;
+  const int64_t windows = (n + welems - 1) / welems;
+  size_t o = 0;
+  const size_t o_edges = o; o = align_up(o + (size_t)(nb + 1) * 8, 256);
+  const size_t o_res = o;   o = align_up(o + (size_t)k * 16, 256);
+  const size_t o_cnt = o;   o = align_up(o + (size_t)k * 4, 256);
+  const size_t o_work = o;  o = align_up(o + 2 * sizeof(WorkCounters), 256);
+  const size_t o_first = o; o = align_up(o + (size_t)windows * sizeof(Piece), 256);
+  const size_t o_last = o;  o = align_up(o + (size_t)windows * sizeof(Piece), 256);
+  const size_t o_tiles = o; o = align_up(o + (size_t)(k >= kEmitTiledMinBins ? emit_tiles(k) : 0) * 8, 256);
+  Scratch s;
+  TSDS_CK(scratch_alloc(s, o, st));
+  char* base = static_cast<char*>(s.p);
+  TSDS_CK(cudaMemsetAsync(base + o_cnt, 0, o_first - o_cnt, st));
+  SeriesDev S;
+  memset(&S, 0, sizeof S);
+  S.y = y;
+  S.x = x;
+  S.n = n;
+  S.nb = nb;
+  S.edges = reinterpret_cast<int64_t*>(base + o_edges);
+  TSDS_CK(launch_edges(nullptr, 1, &S, x != nullptr, x_dtype, nb, st));
+  // the range as a series of its own: its bins' starts are the whole series' starts b0..b1
+  WorkCounters* w = reinterpret_cast<WorkCounters*>(base + o_work);
+  S.nb = k;
+  S.edges += b0;
+  S.res = reinterpret_cast<int64_t*>(base + o_res);
+  S.cnt = reinterpret_cast<uint32_t*>(base + o_cnt);
+  S.out = out;
+  S.out_count = out_count;
+  S.status = &w->status;
+  StreamConfig cfg;
+  cfg.mean_bin_bytes = n / nb * elem;
+  GrpShape shape = grp_shape(cfg.mean_bin_bytes, elem);
+  const int64_t tile_bins = (int64_t)(32 >> shape.g_log2) * shape.tile_rounds;
+  void* tok;
+  timing_begin(st, &tok);
+  TSDS_CK(launch_argminmax_grp(nullptr, S, nullptr, (k + tile_bins - 1) / tile_bins, w, y_dtype, nan, shape, st));
+  cfg.variant = STREAM_LDG;
+  cfg.mean_bin_bytes = kPrefetchOffBinBytes;
+  cfg.min_bin = shape.max_bin;
+  cfg.large_dev = &w->large;
+  TSDS_CK(launch_argminmax(nullptr, 1, S, nullptr, windows, reinterpret_cast<Piece*>(base + o_first),
+                           reinterpret_cast<Piece*>(base + o_last), w + 1, y_dtype, nan, st, cfg));
+  timing_end(st, tok);
+  if (k >= kEmitTiledMinBins) TSDS_CK(launch_emit_tiled(S, algo, reinterpret_cast<int64_t*>(base + o_tiles), st));
+  else TSDS_CK(launch_emit(nullptr, 1, S, algo, st));
+  return TSDS_OK;
+}
+
+static tsds_status binned_range_entry(Algo algo, const void* x, tsds_dtype x_dtype, const void* y,
+                                      tsds_dtype y_dtype, int64_t n, int64_t n_out, int64_t bin_lo, int64_t bin_hi,
+                                      tsds_nan_mode nan, int64_t* out, int64_t* out_count, void* stream) {
+  g_err[0] = 0;
+  const char* who = algo == ALGO_MINMAX ? "tsds_minmax_bins" : "tsds_m4_bins";
+  tsds_status s = check_common(x, x_dtype, y, y_dtype, n, nan, out, out_count);
+  if (s != TSDS_OK) return s;
+  const int per_bin = algo == ALGO_MINMAX ? 2 : 4;
+  if (n_out < per_bin || n_out % per_bin != 0)
+    return fail(TSDS_EINVAL, "%s: n_out must be a positive multiple of %d (got %lld)", who, per_bin, (long long)n_out);
+  if (n_out >= n)
+    return fail(TSDS_EINVAL, "%s: n_out >= n selects every index and has no bins (n = %lld, n_out = %lld)", who,
+                (long long)n, (long long)n_out);
+  const int64_t nb = n_out / per_bin;
+  if (bin_lo < 0 || bin_hi < bin_lo || bin_hi > nb)
+    return fail(TSDS_EINVAL, "%s: bins [%lld, %lld) are not inside [0, %lld)", who, (long long)bin_lo,
+                (long long)bin_hi, (long long)nb);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  s = check_sorted_x(who, x, x_dtype, n, st);
+  if (s != TSDS_OK) return s;
+  if (bin_hi == bin_lo) {
+    TSDS_CK(cudaMemsetAsync(out_count, 0, sizeof(int64_t), st));
+    return TSDS_OK;
+  }
+  return run_binned_range(x, x_dtype, y, y_dtype, n, nb, bin_lo, bin_hi, nan, algo, out, out_count, st);
 }
 
 // EveryNth: the bin starts (index space or x space, as for MinMax/M4) with
@@ -444,6 +555,21 @@ tsds_status tsds_minmaxlttb(const void* x, tsds_dtype x_dtype, const void* y, ts
   NvtxRange nvtx_("tsds_minmaxlttb");
   return minmaxlttb_entry(x, x_dtype, y, y_dtype, n, n_out, minmax_ratio, nan, out, out_count, stream, nullptr,
                           nullptr);
+}
+
+tsds_status tsds_minmax_bins(const void* x, tsds_dtype x_dtype, const void* y, tsds_dtype y_dtype, int64_t n,
+                             int64_t n_out, int64_t bin_lo, int64_t bin_hi, tsds_nan_mode nan, int64_t* out,
+                             int64_t* out_count, void* stream) {
+  NvtxRange nvtx_("tsds_minmax_bins");
+  return binned_range_entry(ALGO_MINMAX, x, x_dtype, y, y_dtype, n, n_out, bin_lo, bin_hi, nan, out, out_count,
+                            stream);
+}
+
+tsds_status tsds_m4_bins(const void* x, tsds_dtype x_dtype, const void* y, tsds_dtype y_dtype, int64_t n,
+                         int64_t n_out, int64_t bin_lo, int64_t bin_hi, tsds_nan_mode nan, int64_t* out,
+                         int64_t* out_count, void* stream) {
+  NvtxRange nvtx_("tsds_m4_bins");
+  return binned_range_entry(ALGO_M4, x, x_dtype, y, y_dtype, n, n_out, bin_lo, bin_hi, nan, out, out_count, stream);
 }
 
 tsds_status tsds_everynth(const void* x, tsds_dtype x_dtype, const void* y, tsds_dtype y_dtype, int64_t n,

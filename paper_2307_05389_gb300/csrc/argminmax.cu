@@ -753,6 +753,7 @@ cudaError_t launch_wait_probe(unsigned long long* status, unsigned rounds, cudaS
 
 #include "stream_ldg.cuh"
 #include "stream_seg.cuh"
+#include "stream_grp.cuh"
 
 typedef unsigned __int128 u128;
 #include "stream_small.cuh"
@@ -811,6 +812,7 @@ static int variant_override() {
     const int env = (e && !strcmp(e, "ring")) ? STREAM_RING
                     : (e && !strcmp(e, "ldg")) ? STREAM_LDG
                     : (e && !strcmp(e, "seg")) ? STREAM_SEG
+                    : (e && !strcmp(e, "grp")) ? STREAM_GRP
                                                : STREAM_AUTO;
     int expect = -1;
     g_variant.compare_exchange_strong(expect, env);
@@ -821,8 +823,16 @@ static int variant_override() {
 
 int stream_variant_for(const StreamConfig& cfg, int64_t elem_bytes) {
   int v = cfg.variant != STREAM_AUTO ? cfg.variant : variant_override();
-  if (v == STREAM_AUTO) v = cfg.mean_bin_bytes < seg_max_bin_bytes(elem_bytes) ? STREAM_SEG : STREAM_LDG;
+  // the lane-group pass is not windowed: a windowed launch asked for it runs the automatic choice
+  if (v == STREAM_AUTO || v == STREAM_GRP)
+    v = cfg.mean_bin_bytes < seg_max_bin_bytes(elem_bytes) ? STREAM_SEG : STREAM_LDG;
   return v;
+}
+
+bool grp_call(int64_t mean_bin_bytes) {
+  const int v = variant_override();
+  if (v == STREAM_GRP) return true;
+  return v == STREAM_AUTO && mean_bin_bytes < kGrpAutoMaxBinBytes;
 }
 
 template <class P, int NM, int VAR, bool MULTI>
@@ -846,7 +856,7 @@ static cudaError_t launch_var(const SeriesDev* s_dev, const SeriesDev& single, c
     k_argminmax_ldg<P, NM, MULTI><<<(unsigned)blocks, threads, 0, st>>>(s_dev, single, win_series, total_windows, fp,
                                                                         lp, work, welems, cfg.total_windows_dev,
                                                                         cfg.window_first, cfg.window_first_dev,
-                                                                        prefetch);
+                                                                        prefetch, cfg.min_bin, cfg.large_dev);
   } else if constexpr (VAR == STREAM_SEG) {
     k_argminmax_seg<P, NM, MULTI><<<(unsigned)blocks, threads, 0, st>>>(s_dev, single, win_series, total_windows, fp,
                                                                         lp, work, welems, cfg.total_windows_dev,
@@ -926,10 +936,63 @@ cudaError_t launch_argminmax_sm(const SeriesDev& single, int64_t total_windows, 
 bool small_call(int64_t n, int64_t nb, tsds_dtype y_dtype) {
   const int64_t bytes = n * dtype_size(y_dtype);
   if (nb < 1 || bytes > kSmallMaxBinBytes * nb || variant_override() != STREAM_AUTO) return false;
-  // measured on GB300: up to 256 MB a warp per bin wins from 512-byte bins
-  // on; beyond, from 8 KB bins (below that the windowed pass keeps up)
-  if (bytes <= kSmallMaxBytes) return nb <= 4096 || bytes >= 512 * nb;
+  // measured on GB300: up to 256 MB a warp per bin wins from 4 KB bins on,
+  // beyond that from 8 KB bins (below, the lane-group pass is faster)
+  if (bytes <= kSmallMaxBytes) return nb <= 4096 || bytes >= 4096 * nb;
   return bytes >= 8192 * nb;
+}
+
+template <class P, int NM, bool MULTI>
+static cudaError_t launch_grp_var(const SeriesDev* s_dev, const SeriesDev& single, const int32_t* tile_series,
+                                  int64_t total_tiles, WorkCounters* work, const GrpShape& shape, cudaStream_t st,
+                                  const int64_t* total_dev, int sm_count) {
+  int d = 0;
+  cudaError_t e = cudaGetDevice(&d);
+  if (e != cudaSuccess) return e;
+  int occ = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_argminmax_grp<P, NM, MULTI>, kGrpThreads, 0);
+  if (e != cudaSuccess) return e;
+  if (occ < 1) occ = 1;
+  int64_t blocks = (total_tiles + kGrpThreads / 32 - 1) / (kGrpThreads / 32);
+  const int64_t cap = (int64_t)(sm_count > 0 ? sm_count : device_sm_count()) * occ;
+  if (blocks > cap || total_dev) blocks = cap;
+  if (blocks < 1) blocks = 1;
+  note_launch();
+  k_argminmax_grp<P, NM, MULTI><<<(unsigned)blocks, kGrpThreads, 0, st>>>(s_dev, single, tile_series, total_tiles, work,
+                                                                       shape.g_log2, shape.tile_rounds, shape.max_bin,
+                                                                       total_dev);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_argminmax_grp(const SeriesDev* s_dev, const SeriesDev& single, const int32_t* tile_series,
+                                 int64_t total_tiles, WorkCounters* work, tsds_dtype y_dtype, tsds_nan_mode nan,
+                                 const GrpShape& shape, cudaStream_t st, const int64_t* total_dev, int sm_count) {
+  if (total_tiles <= 0 && !total_dev) return cudaSuccess;
+  if (shape.g_log2 < 0 || shape.g_log2 > 5 || shape.tile_rounds < 1 ||
+      (int64_t)(32 >> shape.g_log2) * shape.tile_rounds > kGrpTileMaxBins)
+    return cudaErrorInvalidValue;
+  const bool ign = nan == TSDS_NAN_IGNORE;
+  const bool multi = s_dev != nullptr;
+#define TSDS_GRP(POL, NM)                                                                                     \
+  (multi ? launch_grp_var<POL, NM, true>(s_dev, single, tile_series, total_tiles, work, shape, st, total_dev,  \
+                                          sm_count)                                                           \
+         : launch_grp_var<POL, NM, false>(s_dev, single, tile_series, total_tiles, work, shape, st, total_dev, \
+                                           sm_count))
+  switch (y_dtype) {
+    case TSDS_I8: return TSDS_GRP(PolSmallInt<int8_t>, 0);
+    case TSDS_U8: return TSDS_GRP(PolSmallInt<uint8_t>, 0);
+    case TSDS_I16: return TSDS_GRP(PolSmallInt<int16_t>, 0);
+    case TSDS_U16: return TSDS_GRP(PolSmallInt<uint16_t>, 0);
+    case TSDS_I32: return TSDS_GRP(PolInt32<int32_t>, 0);
+    case TSDS_U32: return TSDS_GRP(PolInt32<uint32_t>, 0);
+    case TSDS_I64: return TSDS_GRP(PolI64, 0);
+    case TSDS_U64: return TSDS_GRP(PolU64, 0);
+    case TSDS_F16: return ign ? TSDS_GRP(PolF16<1>, 1) : TSDS_GRP(PolF16<0>, 0);
+    case TSDS_F32: return ign ? TSDS_GRP(PolF32<1>, 1) : TSDS_GRP(PolF32<0>, 0);
+    case TSDS_F64: return ign ? TSDS_GRP(PolF64Ign, 1) : TSDS_GRP(PolF64Prop, 0);
+    default: return cudaErrorInvalidValue;
+  }
+#undef TSDS_GRP
 }
 
 cudaError_t launch_bins_multi(const SeriesDev* s_dev, const int32_t* cta_series, int64_t ctas, tsds_dtype y_dtype,
@@ -978,7 +1041,7 @@ cudaError_t launch_small(const SeriesDev& S, tsds_dtype y_dtype, tsds_nan_mode n
 }  // namespace tsds
 
 extern "C" int tsds_stream_variant(int variant) {
-  if (variant < tsds::STREAM_AUTO || variant > tsds::STREAM_SEG) return -1;
+  if (variant < tsds::STREAM_AUTO || variant > tsds::STREAM_GRP) return -1;
   const int prev = tsds::variant_override();
   tsds::g_variant.store(variant, std::memory_order_relaxed);
   return prev;

@@ -49,12 +49,15 @@ struct BatchLayout {
   // numbered after group 0's, from split_windows on), 2 bins from there up to
   // kSmallMaxBinBytes (a warp per bin, mid_ctas CTAs, no windows).  With an
   // explicit variant every series is cut into windows.
+  // Group 3 (automatic variant, batches without x): bins below
+  // kGrpAutoMaxBinBytes run in the lane-group pass, grp_tiles tiles.
   std::vector<uint8_t> group;
-  int64_t split_windows = 0, mid_ctas = 0;
+  int64_t split_windows = 0, mid_ctas = 0, grp_tiles = 0;
+  int64_t elem = 1;
   bool auto_groups = true;     // how the current numbering was made
   bool any_full = false;       // some series returns every index
   size_t off_desc = 0, off_edges = 0, off_res = 0, off_cnt = 0, off_work = 0, off_map = 0, off_first = 0,
-         off_last = 0, off_ctas = 0, total = 0;
+         off_last = 0, off_ctas = 0, off_tiles = 0, total = 0;
   std::vector<SeriesDev> host; // descriptors (scratch pointers set by bind_layout)
   std::vector<int64_t> nb_before;  // bins of the series before each one
 };
@@ -113,15 +116,33 @@ tsds_status check_batch_sorted(const tsds_series* s, int64_t count, tsds_dtype x
 }
 
 // Window bases for windows of welems elements: group 0 first, then group 1
-// (from split_windows on); with auto_groups, group 2 gets CTA bases instead.
-static void number_windows(BatchLayout& L, int64_t welems, bool auto_groups) {
-  int64_t win = 0, cta = 0;
+// (from split_windows on); with auto_groups, group 2 gets CTA bases and group
+// 3 tile bases (its lane-group shape from the series' bin size, with G scaled
+// by 2^grp_scale) instead.
+static void number_windows(BatchLayout& L, int64_t welems, bool auto_groups, int grp_scale = 0) {
+  int64_t win = 0, cta = 0, tile = 0;
   L.auto_groups = auto_groups;
   for (int pass = 0; pass < 2; ++pass) {
     if (pass == 1) L.split_windows = win;
     for (size_t i = 0; i < L.host.size(); ++i) {
       SeriesDev& d = L.host[i];
       const int g = auto_groups ? L.group[i] : 0;
+      if (g == 3) {
+        if (pass == 0) {
+          GrpShape sh = grp_shape(d.n * L.elem / d.nb, L.elem);
+          int lg = sh.g_log2 + grp_scale;
+          lg = lg < 0 ? 0 : lg > 5 ? 5 : lg;
+          const int groups = 32 >> lg;
+          int rounds = (int)(sh.tile_rounds * (int64_t)(32 >> sh.g_log2) / groups);
+          if (rounds < 1) rounds = 1;
+          if (rounds * groups > kGrpTileMaxBins) rounds = kGrpTileMaxBins / groups;
+          d.mode = 2;
+          d.grp = grp_pack(lg, rounds);
+          d.tile_base = tile;
+          tile += (d.nb + (int64_t)groups * rounds - 1) / ((int64_t)groups * rounds);
+        }
+        continue;
+      }
       if (g == 2) {
         if (pass == 0) {
           d.mode = 1;
@@ -138,6 +159,7 @@ static void number_windows(BatchLayout& L, int64_t welems, bool auto_groups) {
   }
   L.total_windows = win;
   L.mid_ctas = cta;
+  L.grp_tiles = tile;
 }
 
 // Layout for the smallest window size a plan may try (most windows).
@@ -145,6 +167,9 @@ static BatchLayout make_layout(tsds_algo algo, const tsds_series* s, int64_t cou
                                int64_t window_bytes) {
   BatchLayout L;
   L.count = count;
+  L.elem = dtype_size(y_dtype);
+  // lane groups only without x: index bins never exceed the mean by more than a point
+  const bool grp_ok = !batch_has_x(s, count);
   const int per = algo == TSDS_ALGO_MINMAX ? 2 : 4;
   const int64_t welems = window_bytes / dtype_size(y_dtype);
   L.host.resize((size_t)count);
@@ -172,10 +197,13 @@ static BatchLayout make_layout(tsds_algo algo, const tsds_series* s, int64_t cou
       wsum += bytes;
       wbin += bytes * (bytes / (double)d.nb);
       const double bin = bytes / (double)d.nb;
-      const int g = bin < (double)seg_max_bin_bytes(dtype_size(y_dtype)) ? 1 : bin <= (double)kSmallMaxBinBytes ? 2 : 0;
+      int g = bin < (double)seg_max_bin_bytes(dtype_size(y_dtype)) ? 1 : bin <= (double)kSmallMaxBinBytes ? 2 : 0;
+      if (grp_ok && bin < (double)kGrpAutoMaxBinBytes) g = 3;
       L.group[(size_t)i] = (uint8_t)g;
-      gsum[g] += bytes;
-      gbin[g] += bytes * bin;
+      if (g < 3) {
+        gsum[g] += bytes;
+        gbin[g] += bytes * bin;
+      }
     }
     L.y_bytes += q.n * dtype_size(y_dtype);
   }
@@ -192,11 +220,12 @@ static BatchLayout make_layout(tsds_algo algo, const tsds_series* s, int64_t cou
   L.off_edges = o; o = up256(o + (size_t)(nb_sum + count) * 8);
   L.off_res = o;   o = up256(o + (size_t)nb_sum * 16);
   L.off_cnt = o;   o = up256(o + (size_t)nb_sum * 4);
-  L.off_work = o;  o = up256(o + 2 * sizeof(WorkCounters));   // one counter per launch of a split pass
+  L.off_work = o;  o = up256(o + 3 * sizeof(WorkCounters));   // one counter per launch of a split pass
   L.off_map = o;   o = up256(o + (size_t)win_sum * 4);
   L.off_first = o; o = up256(o + (size_t)win_sum * sizeof(Piece));
   L.off_last = o;  o = up256(o + (size_t)win_sum * sizeof(Piece));
   L.off_ctas = o;  o = up256(o + (size_t)ctas * 4);
+  L.off_tiles = o; o = up256(o + (size_t)(L.grp_tiles > 0 ? nb_sum : 0) * 4);   // at least one bin per tile
   L.total = o;
   return L;
 }
@@ -204,7 +233,8 @@ static BatchLayout make_layout(tsds_algo algo, const tsds_series* s, int64_t cou
 // Points the descriptors' scratch pointers into `base` and recomputes the
 // window bases for `window_bytes` (which must be >= the layout's) and the
 // launch shape's variant.
-static void bind_layout(BatchLayout& L, char* base, tsds_dtype y_dtype, int64_t window_bytes, int variant) {
+static void bind_layout(BatchLayout& L, char* base, tsds_dtype y_dtype, int64_t window_bytes, int variant,
+                        int grp_scale = 0) {
   for (size_t i = 0; i < L.host.size(); ++i) {
     SeriesDev& d = L.host[i];
     const int64_t before = L.nb_before[i];
@@ -214,11 +244,11 @@ static void bind_layout(BatchLayout& L, char* base, tsds_dtype y_dtype, int64_t 
     d.cnt = reinterpret_cast<uint32_t*>(base + L.off_cnt) + before;
     d.status = &reinterpret_cast<WorkCounters*>(base + L.off_work)->status;
   }
-  number_windows(L, window_bytes / dtype_size(y_dtype), variant == STREAM_AUTO);
+  number_windows(L, window_bytes / dtype_size(y_dtype), variant == STREAM_AUTO, grp_scale);
 }
 
-static void rebase_windows(BatchLayout& L, tsds_dtype y_dtype, int64_t window_bytes, int variant) {
-  number_windows(L, window_bytes / dtype_size(y_dtype), variant == STREAM_AUTO);
+static void rebase_windows(BatchLayout& L, tsds_dtype y_dtype, int64_t window_bytes, int variant, int grp_scale) {
+  number_windows(L, window_bytes / dtype_size(y_dtype), variant == STREAM_AUTO, grp_scale);
 }
 
 // The window map and (automatic variant) the CTA map of the current numbering.
@@ -230,6 +260,8 @@ static tsds_status launch_maps(const BatchLayout& L, char* base, tsds_dtype y_dt
                             window_bytes));
   if (L.auto_groups && L.mid_ctas > 0)
     BT_CK(launch_cta_map(sd, (int)L.count, reinterpret_cast<int32_t*>(base + L.off_ctas), st));
+  if (L.auto_groups && L.grp_tiles > 0)
+    BT_CK(launch_tile_map(sd, (int)L.count, reinterpret_cast<int32_t*>(base + L.off_tiles), st));
   return TSDS_OK;
 }
 
@@ -272,13 +304,17 @@ static tsds_status enqueue(const BatchLayout& L, char* base, tsds_algo algo, boo
       small.variant = STREAM_SEG;
       small.mean_bin_bytes = L.mean_bin_bytes1;
       small.window_first = L.split_windows;
-      const bool g0 = L.split_windows > 0, g1 = L.total_windows > L.split_windows, g2 = L.mid_ctas > 0;
+      const bool g0 = L.split_windows > 0, g1 = L.total_windows > L.split_windows, g2 = L.mid_ctas > 0,
+                 g3 = L.grp_tiles > 0;
       cudaStream_t st2 = st;
-      if (g1 && (g0 || g2) && fk.side) {
+      if ((g1 || g3) && (g0 || g2) && fk.side) {
         BT_CK(cudaEventRecord(fk.fork, st));
         BT_CK(cudaStreamWaitEvent(fk.side, fk.fork, 0));
         st2 = fk.side;
       }
+      if (g3)   // lane groups (small bins, no x): shape per series, no bin above the size limit
+        BT_CK(launch_argminmax_grp(sd, none, reinterpret_cast<const int32_t*>(base + L.off_tiles), L.grp_tiles,
+                                   work + 2, y_dtype, nan, GrpShape(), st2));
       if (g1)
         BT_CK(launch_argminmax(sd, (int)L.count, none, map, L.total_windows, fp, lp, work + 1, y_dtype, nan, st2,
                                small));
@@ -302,7 +338,7 @@ static tsds_status enqueue(const BatchLayout& L, char* base, tsds_algo algo, boo
 }
 
 static tsds_status upload(BatchLayout& L, char* base, tsds_dtype y_dtype, const StreamConfig& cfg, cudaStream_t st) {
-  rebase_windows(L, y_dtype, cfg.window_bytes, cfg.variant);
+  rebase_windows(L, y_dtype, cfg.window_bytes, cfg.variant, cfg.grp_scale);
   BT_CK(cudaMemcpyAsync(base + L.off_desc, L.host.data(), L.host.size() * sizeof(SeriesDev),
                         cudaMemcpyHostToDevice, st));
   const tsds_status s = launch_maps(L, base, y_dtype, cfg.window_bytes, st);
@@ -314,8 +350,15 @@ static tsds_status upload(BatchLayout& L, char* base, tsds_dtype y_dtype, const 
 
 // ---------------------------------------------------------------- autotuner
 
+static StreamConfig grp_candidate(int scale) {
+  StreamConfig c;
+  c.grp_scale = scale;
+  return c;
+}
+
 // Candidate launch shapes: window bytes, CTAs per SM, -, kernel variant
-// (automatic: split by series bin size).  The smallest window must come
+// (automatic: split by series bin size), lanes per bin of the lane-group
+// series (a power-of-two scale of the default).  The smallest window must come
 // first: the scratch is laid out for it (the most windows).  Without a tuned
 // choice a plan runs the default shape (64 KB windows, automatic variant).
 static const StreamConfig kCandidates[] = {
@@ -323,7 +366,9 @@ static const StreamConfig kCandidates[] = {
     {128 * 1024, 0, nullptr, STREAM_RING}, {64 * 1024, 2, nullptr, STREAM_RING}, {256 * 1024, 0, nullptr, STREAM_RING},
     {32 * 1024, 0, nullptr, STREAM_LDG},   {64 * 1024, 0, nullptr, STREAM_LDG},  {256 * 1024, 0, nullptr, STREAM_LDG},
     {32 * 1024, 0, nullptr, STREAM_SEG},   {64 * 1024, 0, nullptr, STREAM_SEG},  {256 * 1024, 0, nullptr, STREAM_SEG},
-    {64 * 1024, 0, nullptr, STREAM_AUTO},  {256 * 1024, 0, nullptr, STREAM_AUTO}};
+    {64 * 1024, 0, nullptr, STREAM_AUTO},  {256 * 1024, 0, nullptr, STREAM_AUTO},
+    // automatic split with half and twice the lanes per bin in the lane-group series
+    grp_candidate(-1), grp_candidate(1)};
 constexpr int kNumCandidates = sizeof(kCandidates) / sizeof(kCandidates[0]);
 
 static std::mutex g_tune_mu;

@@ -90,8 +90,8 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit(const SeriesDev* __restri
 }
 
 // Many bins in one series: tiles of kTileBins bins, one CTA each.  Pass 1
-// counts every tile's selections; pass 2 adds the counts of the tiles before
-// its own (at most a few thousand) to place the tile, scans within it and
+// counts every tile's selections, one CTA turns the counts into exclusive
+// prefix sums, pass 2 places each tile at its prefix, scans within it and
 // writes.  The last tile also writes the total.
 constexpr int kTileThreads = 256;
 constexpr int kTileItems = 4;
@@ -150,12 +150,8 @@ __global__ void __launch_bounds__(kTileThreads) k_emit_write(SeriesDev S, const 
     if (blockIdx.x == 0 && threadIdx.x == 0 && S.out_count) *S.out_count = -(int64_t)*S.status;
     return;
   }
-  // selections of the tiles before this one
-  int64_t before = 0;
-  for (int64_t t = threadIdx.x; t < blockIdx.x; t += kTileThreads) before += tile_count[t];
-  const int64_t b_off = tile_scan(before, warp_tot, &total);
-  (void)b_off;
-  if (threadIdx.x == 0) before_sh = total;
+  // selections of the tiles before this one (k_scan_tiles made tile_count exclusive)
+  if (threadIdx.x == 0) before_sh = tile_count[blockIdx.x];
   __syncthreads();
   const int64_t base = before_sh;
   const int64_t b0 = min((int64_t)blockIdx.x * kTileBins + (int64_t)threadIdx.x * kTileItems, S.nb);
@@ -171,20 +167,62 @@ __global__ void __launch_bounds__(kTileThreads) k_emit_write(SeriesDev S, const 
   if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0 && S.out_count) *S.out_count = base + total;
 }
 
+// Exclusive prefix sums of the tiles' counts, in place (one CTA; each thread
+// scans a contiguous run of tiles).
+constexpr int kScanThreads = 1024;
+__global__ void __launch_bounds__(kScanThreads) k_scan_tiles(int64_t* __restrict__ tile_count, int64_t tiles) {
+  __shared__ int64_t warp_tot[kScanThreads / 32];
+  __shared__ int64_t total;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t per = (tiles + kScanThreads - 1) / kScanThreads;
+  const int64_t t0 = min((int64_t)tid * per, tiles), t1 = min(t0 + per, tiles);
+  int64_t local = 0;
+  for (int64_t t = t0; t < t1; ++t) local += tile_count[t];
+  int64_t incl = local;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int64_t v = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += v;
+  }
+  if (lane == 31) warp_tot[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    const int64_t wv = warp_tot[lane];
+    int64_t wi = wv;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int64_t v = __shfl_up_sync(0xffffffffu, wi, o);
+      if (lane >= o) wi += v;
+    }
+    warp_tot[lane] = wi - wv;
+    if (lane == 31) total = wi;
+  }
+  __syncthreads();
+  int64_t run = warp_tot[warp] + incl - local;
+  for (int64_t t = t0; t < t1; ++t) {
+    const int64_t c = tile_count[t];
+    tile_count[t] = run;
+    run += c;
+  }
+}
+
 int64_t emit_tiles(int64_t nb) { return (nb + kTileBins - 1) / kTileBins; }
 
 cudaError_t launch_emit_tiled(const SeriesDev& single, Algo algo, int64_t* tile_count, cudaStream_t st) {
   const int64_t tiles = emit_tiles(single.nb);
   if (tiles <= 0) return cudaSuccess;
-  note_launch(2);
+  note_launch(3);
   if (algo == ALGO_MINMAX) {
     k_emit_count<ALGO_MINMAX><<<(unsigned)tiles, kTileThreads, 0, st>>>(single, tile_count);
+    k_scan_tiles<<<1, kScanThreads, 0, st>>>(tile_count, tiles);
     k_emit_write<ALGO_MINMAX><<<(unsigned)tiles, kTileThreads, 0, st>>>(single, tile_count);
   } else if (algo == ALGO_EVERYNTH) {
     k_emit_count<ALGO_EVERYNTH><<<(unsigned)tiles, kTileThreads, 0, st>>>(single, tile_count);
+    k_scan_tiles<<<1, kScanThreads, 0, st>>>(tile_count, tiles);
     k_emit_write<ALGO_EVERYNTH><<<(unsigned)tiles, kTileThreads, 0, st>>>(single, tile_count);
   } else {
     k_emit_count<ALGO_M4><<<(unsigned)tiles, kTileThreads, 0, st>>>(single, tile_count);
+    k_scan_tiles<<<1, kScanThreads, 0, st>>>(tile_count, tiles);
     k_emit_write<ALGO_M4><<<(unsigned)tiles, kTileThreads, 0, st>>>(single, tile_count);
   }
   return cudaGetLastError();

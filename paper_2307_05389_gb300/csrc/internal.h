@@ -42,7 +42,11 @@ struct SeriesDev {
                                      // non-zero makes emit report -status as the count
   Gather g;           // values written beside the indices (y[v], x[v] for index v + idx_bias)
   int32_t mode;       // batched: 0 the series is cut into windows; 1 a warp per bin, and
-                      // win_base is its first CTA in that launch (kBinsPerCta bins each)
+                      // win_base is its first CTA in that launch (kBinsPerCta bins each);
+                      // 2 lane groups (no windows); 3 lane groups, with windows for the
+                      // bins above the lane-group size limit
+  int32_t grp;        // modes 2 and 3: the lane-group shape, g_log2 | tile_rounds << 8
+  int64_t tile_base;  // modes 2 and 3: first tile of the series in the lane-group launch
 };
 
 // Partial argmin/argmax of one bin piece: ordered 64-bit keys plus indices.
@@ -56,7 +60,8 @@ struct Piece {
 struct WorkCounters {
   unsigned long long next_window;
   unsigned long long status;   // tsds_status of a device-side failure (TSDS_ETIMEOUT), 0 when fine
-  unsigned long long pad[6];
+  unsigned long long large;    // lane-group pass: bins it left to the windowed pass (too large)
+  unsigned long long pad[5];
 };
 
 inline int64_t dtype_size(tsds_dtype d) {
@@ -78,7 +83,7 @@ inline int64_t window_elems(tsds_dtype y_dtype) { return kWindowBytes / dtype_si
 // async copies and splits bins across lanes (cheapest per bin: small bins).  AUTO picks SEG when the bytes-weighted mean bin size is below
 // seg_max_bin_bytes(element size), LDG otherwise (crossovers measured on
 // GB300 over 1 GB and 40 MB inputs).
-enum StreamVariant : int { STREAM_AUTO = 0, STREAM_RING = 1, STREAM_LDG = 2, STREAM_SEG = 3 };
+enum StreamVariant : int { STREAM_AUTO = 0, STREAM_RING = 1, STREAM_LDG = 2, STREAM_SEG = 3, STREAM_GRP = 4 };
 inline int64_t seg_max_bin_bytes(int64_t elem_bytes) {
   return elem_bytes == 8 ? 768 : elem_bytes == 4 ? 1536 : elem_bytes == 2 ? 1024 : 512;
 }
@@ -95,7 +100,62 @@ struct StreamConfig {
   int64_t mean_bin_bytes = 0;           // bytes-weighted mean bin size of the launch
   int64_t window_first = 0;             // the launch takes windows [window_first, total_windows)
   const int64_t* window_first_dev = nullptr;   // when set, window_first is read here on the device
+  // Register streaming after the lane-group pass: only bins of more than
+  // min_bin points, and nothing at all when *large_dev is zero.
+  int64_t min_bin = 0;
+  const unsigned long long* large_dev = nullptr;
+  // Batched plans: lanes per bin of the lane-group series, 2^grp_scale times
+  // the default choice (an autotuner dimension).
+  int grp_scale = 0;
 };
+// A mean_bin_bytes at which the register-streaming pass never prefetches.
+constexpr int64_t kPrefetchOffBinBytes = 1ll << 40;
+
+// The lane-group pass (stream_grp.cuh): groups of 2^g_log2 lanes, tiles of
+// (32 >> g_log2) * tile_rounds consecutive bins claimed through
+// work->next_window.  Bins of more than max_bin points are left out and
+// counted in work->large (max_bin 0: none is left out).  Single series: s_dev
+// null; batched: tile_series maps tiles to series (win_base = first tile).
+constexpr int kGrpTileMaxBins = 128;   // bins per lane-group tile at most
+constexpr int kGrpU = 8;               // vectors per lane in flight
+// Bins above this size are left to the windowed register-streaming pass (a
+// group reads a bin at a few GB/s, so one huge x-space bin would otherwise
+// hold up the launch).
+constexpr int64_t kGrpMaxBinBytes = 64 * 1024;
+struct GrpShape {
+  int g_log2 = 0;
+  int tile_rounds = 1;
+  int64_t max_bin = 0;
+};
+// Lane-group shape for a launch whose bins average mean_bin_bytes: groups of
+// G lanes whose 2*G*kGrpU vectors cover a bin's interior (a bin's first and
+// last vector are taken apart; two rounds of loads per lane measured 8-21 %
+// faster on GB300 than one from 512-byte bins on, the same below), tiles of
+// about 32 KB.
+__host__ __device__ inline GrpShape grp_shape(int64_t mean_bin_bytes, int64_t elem_bytes) {
+  GrpShape g;
+  const int64_t inner = mean_bin_bytes / 16 - 1;
+  int lg = 0;
+  while (lg < 5 && ((int64_t)kGrpU << (lg + 1)) < inner) ++lg;
+  g.g_log2 = lg;
+  const int64_t groups = 32 >> lg;
+  int64_t rounds = (32 * 1024) / (groups * (mean_bin_bytes > 0 ? mean_bin_bytes : 1));
+  const int64_t max_rounds = kGrpTileMaxBins / groups;
+  g.tile_rounds = (int)(rounds < 1 ? 1 : rounds > max_rounds ? max_rounds : rounds);
+  g.max_bin = kGrpMaxBinBytes / elem_bytes;
+  return g;
+}
+// SeriesDev::grp of a shape.
+__host__ __device__ inline int32_t grp_pack(int g_log2, int tile_rounds) { return g_log2 | (tile_rounds << 8); }
+// Whether a single-series windowed call with this mean bin size takes the
+// lane-group pass (automatic choice below kGrpAutoMaxBinBytes, or forced by
+// tsds_stream_variant(STREAM_GRP)).
+constexpr int64_t kGrpAutoMaxBinBytes = 8 * 1024;
+bool grp_call(int64_t mean_bin_bytes);
+cudaError_t launch_argminmax_grp(const SeriesDev* s_dev, const SeriesDev& single, const int32_t* tile_series,
+                                 int64_t total_tiles, WorkCounters* work, tsds_dtype y_dtype, tsds_nan_mode nan,
+                                 const GrpShape& shape, cudaStream_t st, const int64_t* total_dev = nullptr,
+                                 int sm_count = 0);
 
 // The variant a launch with this shape runs for elements of elem_bytes.
 int stream_variant_for(const StreamConfig& cfg, int64_t elem_bytes);
@@ -127,7 +187,7 @@ cudaError_t launch_argminmax_sm(const SeriesDev& single, int64_t total_windows, 
 
 // Single-series calls with bins of at most 64 KB on average, no explicit
 // streaming variant, and either at most 256 MB of y (at most 4096 bins, or
-// bins of at least 512 bytes) or bins of at least 8 KB: a warp per bin in one
+// bins of at least 4 KB) or bins of at least 8 KB: a warp per bin in one
 // launch (index-bin starts in the kernel,
 // x-space starts from launch_edges first).  With emit (at most
 // kSmallEmitMaxBins bins) the last CTA also emits, with `done` a zeroed
@@ -147,6 +207,9 @@ cudaError_t launch_wait_probe(unsigned long long* status, unsigned rounds, cudaS
 // (cta_series maps each CTA to its series; launch_cta_map fills it).
 constexpr int kBinsPerCta = 8;
 cudaError_t launch_cta_map(const SeriesDev* s_dev, int count, int32_t* cta_series, cudaStream_t st);
+// Batched series in modes 2 and 3 (lane groups): tile_series[tile_base + t] = the
+// series, for each of its tiles (shape in SeriesDev::grp).
+cudaError_t launch_tile_map(const SeriesDev* s_dev, int count, int32_t* tile_series, cudaStream_t st);
 // ctas_dev (optional): the actual number of CTAs, read on the device (ctas is then a bound)
 cudaError_t launch_bins_multi(const SeriesDev* s_dev, const int32_t* cta_series, int64_t ctas, tsds_dtype y_dtype,
                               tsds_nan_mode nan, cudaStream_t st, const int64_t* ctas_dev = nullptr);

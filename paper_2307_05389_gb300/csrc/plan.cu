@@ -154,7 +154,7 @@ cudaError_t launch_edges(const SeriesDev* s_dev, int count, const SeriesDev* s_h
 
 __global__ void k_window_map(const SeriesDev* sd, int32_t* win_series, int64_t welems) {
   const SeriesDev S = sd[blockIdx.x];
-  if (S.nb <= 0 || S.mode != 0) return;
+  if (S.nb <= 0 || S.mode == 1 || S.mode == 2) return;
   int64_t k = (S.n + welems - 1) / welems;
   for (int64_t w = threadIdx.x; w < k; w += blockDim.x) win_series[S.win_base + w] = (int32_t)blockIdx.x;
 }
@@ -177,6 +177,21 @@ __global__ void k_cta_map(const SeriesDev* sd, int32_t* cta_series) {
 cudaError_t launch_cta_map(const SeriesDev* s_dev, int count, int32_t* cta_series, cudaStream_t st) {
   note_launch();
   k_cta_map<<<count, 256, 0, st>>>(s_dev, cta_series);
+  return cudaGetLastError();
+}
+
+// tile_series[tile_base + t] = the series, for each lane-group tile t of a series in mode 2 or 3.
+__global__ void k_tile_map(const SeriesDev* sd, int32_t* tile_series) {
+  const SeriesDev S = sd[blockIdx.x];
+  if (S.nb <= 0 || (S.mode != 2 && S.mode != 3)) return;
+  const int64_t tile_bins = (int64_t)(32 >> (S.grp & 0xff)) * (S.grp >> 8);
+  const int64_t tiles = (S.nb + tile_bins - 1) / tile_bins;
+  for (int64_t t = threadIdx.x; t < tiles; t += blockDim.x) tile_series[S.tile_base + t] = (int32_t)blockIdx.x;
+}
+
+cudaError_t launch_tile_map(const SeriesDev* s_dev, int count, int32_t* tile_series, cudaStream_t st) {
+  note_launch();
+  k_tile_map<<<count, 256, 0, st>>>(s_dev, tile_series);
   return cudaGetLastError();
 }
 

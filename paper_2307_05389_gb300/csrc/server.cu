@@ -128,32 +128,46 @@ __global__ void k_resolve(const QueryDev* __restrict__ qd, SeriesDev* __restrict
   D.idx_bias = S.idx_bias;
   D.out = S.out;
   D.out_count = S.out_count;
-  // bins under the small-bin size go to the segmented launch, bins from there
-  // to kSmallMaxBinBytes to a warp per bin (mode 1, no windows), larger ones
-  // to the register-streaming launch
+  // bins under the small-bin size go to the lane-group launch (mode 3: tiles
+  // of whole bins, plus windows for a register-streaming pass over the bins
+  // above the lane-group size limit), bins from there to kSmallMaxBinBytes to
+  // a warp per bin (mode 1, no windows), larger ones to the register-streaming
+  // launch
   const int64_t bytes = S.n * y_size;
   const int8_t g = S.nb <= 0 ? 0 : bytes < small_bin_bytes * S.nb ? 1 : bytes <= kSmallMaxBinBytes * S.nb ? 2 : 0;
   small[q] = g;
-  D.mode = g == 2 ? 1 : 0;
+  D.mode = g == 2 ? 1 : g == 1 ? 3 : 0;
+  if (g == 1) {
+    const GrpShape sh = grp_shape(bytes / S.nb, y_size);
+    D.grp = grp_pack(sh.g_log2, sh.tile_rounds);
+  }
   windows[q] = S.nb > 0 && g != 2 ? (S.n + welems - 1) / welems : 0;
   Q.info[1] = L;
   Q.info[2] = lo;
 }
 
+__device__ __forceinline__ int64_t grp_tiles_of(const SeriesDev& S) {
+  const int64_t tile_bins = (int64_t)(32 >> (S.grp & 0xff)) * (S.grp >> 8);
+  return (S.nb + tile_bins - 1) / tile_bins;
+}
+
 // Window bases of the queries: those with large bins first, then those with
 // small bins; total[0] = all windows, total[1] = the large-bin windows (where
 // the small-bin range starts).  Queries in mode 1 get CTA bases instead, and
-// total[2] = their CTAs.  One CTA.
+// total[2] = their CTAs; small-bin queries (mode 3) also get tile bases, and
+// total[3] = their tiles.  One CTA.
 __global__ void k_scan_windows(SeriesDev* __restrict__ sd, const int64_t* __restrict__ windows,
                                const int8_t* __restrict__ small, int count, int64_t* __restrict__ total) {
-  __shared__ int64_t part[3][1024];
+  __shared__ int64_t part[4][1024];
   const int t = threadIdx.x;
   const int per = (count + blockDim.x - 1) / blockDim.x;
   const int a = min(t * per, count), b = min(a + per, count);
-  int64_t s[3] = {0, 0, 0};
-  for (int i = a; i < b; ++i)
+  int64_t s[4] = {0, 0, 0, 0};
+  for (int i = a; i < b; ++i) {
     s[small[i]] += small[i] == 2 ? (sd[i].nb + kBinsPerCta - 1) / kBinsPerCta : windows[i];
-  for (int g = 0; g < 3; ++g) part[g][t] = s[g];
+    if (small[i] == 1) s[3] += grp_tiles_of(sd[i]);
+  }
+  for (int g = 0; g < 4; ++g) part[g][t] = s[g];
   __syncthreads();
   if (t == 0) {
     int64_t run = 0;
@@ -162,16 +176,22 @@ __global__ void k_scan_windows(SeriesDev* __restrict__ sd, const int64_t* __rest
       for (int i = 0; i < (int)blockDim.x; ++i) { const int64_t v = part[g][i]; part[g][i] = run; run += v; }
     }
     total[0] = run;
-    run = 0;
-    for (int i = 0; i < (int)blockDim.x; ++i) { const int64_t v = part[2][i]; part[2][i] = run; run += v; }
-    total[2] = run;
+    for (int g = 2; g < 4; ++g) {
+      run = 0;
+      for (int i = 0; i < (int)blockDim.x; ++i) { const int64_t v = part[g][i]; part[g][i] = run; run += v; }
+      total[g] = run;
+    }
   }
   __syncthreads();
-  int64_t r[3] = {part[0][t], part[1][t], part[2][t]};
+  int64_t r[4] = {part[0][t], part[1][t], part[2][t], part[3][t]};
   for (int i = a; i < b; ++i) {
     const int g = small[i];
     sd[i].win_base = r[g];
     r[g] += g == 2 ? (sd[i].nb + kBinsPerCta - 1) / kBinsPerCta : windows[i];
+    if (g == 1) {
+      sd[i].tile_base = r[3];
+      r[3] += grp_tiles_of(sd[i]);
+    }
   }
 }
 
@@ -342,14 +362,15 @@ tsds_status launch_batch(const Server& S, Slot& sl, const std::vector<tsds_query
   const size_t off_q = 0, off_sd = off_q + sz_q, off_ljobs = off_sd + sz_s, off_pjobs = off_ljobs + sz_l;
   const size_t in_bytes = off_pjobs + sz_p;
   size_t o = up256(in_bytes);
-  const size_t off_win = o; o = up256(o + (size_t)count * 8 + 24);   // windows; all, large-bin windows; CTAs
+  const size_t off_win = o; o = up256(o + (size_t)count * 8 + 32);   // windows; all, large-bin windows; CTAs; tiles
   const size_t off_small = o; o = up256(o + (size_t)count);
   std::vector<size_t> off_edges(count), off_res(count), off_cnt(count), off_R(count), off_lt(count);
-  int64_t max_nb = 0, win_ub = 0, cta_ub = 0;
+  int64_t max_nb = 0, win_ub = 0, cta_ub = 0, tile_ub = 0;
   for (int i = 0; i < count; ++i) {
     const int64_t nb = nb_of(qs[i]);
     max_nb = std::max(max_nb, nb);
     cta_ub += (nb + kBinsPerCta - 1) / kBinsPerCta;
+    tile_ub += nb;   // a tile holds at least one bin
     off_edges[i] = o; o = up256(o + (size_t)(nb + 1) * 8);
     off_res[i] = o;   o = up256(o + (size_t)nb * 16);
     win_ub += (ser[i].n * ys + window_bytes - 1) / window_bytes + 1;
@@ -357,12 +378,13 @@ tsds_status launch_batch(const Server& S, Slot& sl, const std::vector<tsds_query
   const size_t zero_begin = o;    // piece counters and the work counter start at zero
   for (int i = 0; i < count; ++i) { off_cnt[i] = o; o += (size_t)nb_of(qs[i]) * 4; }
   o = up256(o);
-  const size_t off_work = o; o = up256(o + 2 * sizeof(WorkCounters));   // one per launch of the split pass
+  const size_t off_work = o; o = up256(o + 3 * sizeof(WorkCounters));   // one per launch of the split pass
   const size_t zero_end = o;
   const size_t off_map = o;   o = up256(o + (size_t)win_ub * 4);
   const size_t off_first = o; o = up256(o + (size_t)win_ub * sizeof(Piece));
   const size_t off_last = o;  o = up256(o + (size_t)win_ub * sizeof(Piece));
   const size_t off_ctas = o;  o = up256(o + (size_t)cta_ub * 4);
+  const size_t off_tiles = o; o = up256(o + (size_t)tile_ub * 4);
   // results: per query n_out indices then kInfoSlots info words, contiguous for one copy back
   const size_t off_out = o;
   sl.out_off.assign(count, 0);
@@ -481,19 +503,20 @@ tsds_status launch_batch(const Server& S, Slot& sl, const std::vector<tsds_query
   SV_CK(cudaMemsetAsync(base + zero_begin, 0, zero_end - zero_begin, st));
   SV_CK(cudaMemsetAsync(outbase, 0, words * 8, st));
   int64_t* windows = reinterpret_cast<int64_t*>(base + off_win);
-  int64_t* total_dev = windows + count;   // [all windows, large-bin windows]
+  int64_t* total_dev = windows + count;   // [all windows, large-bin windows, CTAs, tiles]
   int8_t* small = reinterpret_cast<int8_t*>(base + off_small);
   const bool can_split = true;
   note_launch();
   k_resolve<<<(count + 7) / 8, 256, 0, st>>>(dq, dsd, windows, small, count, (int)S.x_dtype, (int)ys,
                                              has_x ? (int)dtype_size(S.x_dtype) : 0, welems,
-                                             can_split ? seg_max_bin_bytes(ys) : 0);
+                                             can_split ? kGrpAutoMaxBinBytes : 0);
   SV_CK(cudaGetLastError());
   note_launch();
   k_scan_windows<<<1, 1024, 0, st>>>(dsd, windows, small, count, total_dev);
   SV_CK(cudaGetLastError());
   SV_CK(launch_window_map(dsd, count, reinterpret_cast<int32_t*>(base + off_map), S.y_dtype, st, window_bytes));
   SV_CK(launch_cta_map(dsd, count, reinterpret_cast<int32_t*>(base + off_ctas), st));
+  SV_CK(launch_tile_map(dsd, count, reinterpret_cast<int32_t*>(base + off_tiles), st));
   SV_CK(launch_edges(dsd, count, nullptr, has_x, S.x_dtype, max_nb, st));
   SeriesDev none;
   memset(&none, 0, sizeof none);
@@ -515,11 +538,22 @@ tsds_status launch_batch(const Server& S, Slot& sl, const std::vector<tsds_query
   big.total_windows_dev = can_split ? total_dev + 1 : total_dev;
   SV_CK(launch_argminmax(dsd, count, none, map, std::max<int64_t>(win_ub, 1), fp, lp, work, S.y_dtype, nan, st, big));
   if (can_split) {
+    // small bins: lane groups over the tiles counted on the device, then a
+    // register-streaming pass over the small-bin queries' windows
+    // [total[1], total[0]) for the bins above the lane-group size limit (it
+    // exits at once when there is none)
+    GrpShape shp;
+    shp.max_bin = kGrpMaxBinBytes / ys;
+    SV_CK(launch_argminmax_grp(dsd, none, reinterpret_cast<const int32_t*>(base + off_tiles),
+                               std::max<int64_t>(tile_ub, 1), work + 1, S.y_dtype, nan, shp, st, total_dev + 3));
     StreamConfig sm;
-    sm.variant = STREAM_SEG;
+    sm.variant = STREAM_LDG;
     sm.total_windows_dev = total_dev;
     sm.window_first_dev = total_dev + 1;
-    SV_CK(launch_argminmax(dsd, count, none, map, std::max<int64_t>(win_ub, 1), fp, lp, work + 1, S.y_dtype, nan, st,
+    sm.mean_bin_bytes = kPrefetchOffBinBytes;
+    sm.min_bin = shp.max_bin;
+    sm.large_dev = &work[1].large;
+    SV_CK(launch_argminmax(dsd, count, none, map, std::max<int64_t>(win_ub, 1), fp, lp, work + 2, S.y_dtype, nan, st,
                            sm));
   }
   SV_CK(launch_emit(dsd, count, none, m4 ? ALGO_M4 : ALGO_MINMAX, st));

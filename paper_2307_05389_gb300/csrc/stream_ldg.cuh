@@ -200,9 +200,13 @@ __global__ void __launch_bounds__(kStreamThreadsLdg, MULTI ? 3 : 4)
 k_argminmax_ldg(const SeriesDev* __restrict__ sd, SeriesDev single, const int32_t* __restrict__ win_series,
             int64_t total_windows, Piece* __restrict__ first_piece, Piece* __restrict__ last_piece,
             WorkCounters* __restrict__ work, int64_t welems, const int64_t* __restrict__ total_dev,
-            int64_t w_first, const int64_t* __restrict__ first_dev, int prefetch) {
+            int64_t w_first, const int64_t* __restrict__ first_dev, int prefetch, int64_t min_bin,
+            const unsigned long long* __restrict__ large_dev) {
   using T = typename P::T;
   const int lane = threadIdx.x & 31;
+  // min_bin > 0: only bins of more than min_bin points (the lane-group pass
+  // did the others); nothing to do when it found none
+  if (large_dev && *large_dev == 0) return;
   if (total_dev) total_windows = *total_dev;
   if (first_dev) w_first = *first_dev;
   // a warp claims its next window as soon as it starts on one, so the claim's
@@ -236,7 +240,7 @@ k_argminmax_ldg(const SeriesDev* __restrict__ sd, SeriesDev single, const int32_
       const int64_t my_hi = (b + lane < nb) ? __ldg(edges + b + 1 + lane) : INT64_MAX;
       for (int q = 0; q < 32 && b < nb && lo < we; ++q, ++b) {
         const int64_t hi = __shfl_sync(0xffffffffu, my_hi, q);
-        if (hi > lo) {
+        if (hi - lo > min_bin) {
           const int64_t pa = max(lo, ws), pb = min(hi, we);
           Cand c = piece_ldg<P>(y, pa, pb, prefetch ? (int)((we - pa) * (int64_t)sizeof(T)) : 0);
           bin_result<P, NM>(S, b, lo, hi, k, welems, c, first_piece, last_piece, lane);

@@ -216,3 +216,16 @@ def test_binding_rejects_host_tensors_and_bad_shapes_before_any_call(lib):
     with pytest.raises(TypeError):
         binding.MinMaxDownsampler().downsample(y, y, y, n_out=4)
     assert pkg.tsds_kernel_launches() == before
+
+
+@pytest.mark.parametrize("fn", [binding.tsds_minmax_bins, binding.tsds_m4_bins])
+def test_bin_range_arguments_are_checked_on_the_host(lib, fn):
+    """tsds_minmax_bins / tsds_m4_bins refuse a range outside [0, nb), a reversed range, an n_out
+    that covers every index and an invalid n_out, before anything reaches the device."""
+    before = pkg.tsds_kernel_launches()
+    y, out, cnt = 1 << 20, 1 << 21, 1 << 22
+    nb = 400 // (2 if fn is binding.tsds_minmax_bins else 4)
+    for n_out, lo, hi in ((400, -1, 3), (400, 5, 4), (400, 0, nb + 1), (1000, 0, 1), (5, 0, 1), (0, 0, 0)):
+        assert fn(None, 0, y, 9, 1000, n_out, lo, hi, 0, out, cnt, None) == 1, (n_out, lo, hi)
+        assert pkg.last_error()
+    assert pkg.tsds_kernel_launches() == before

@@ -275,7 +275,7 @@ def stream_variant():
         binding.tsds_stream_variant(prev[0])
 
 
-@pytest.mark.parametrize("variant", ["ring", "ldg", "seg"])
+@pytest.mark.parametrize("variant", ["ring", "ldg", "seg", "grp"])
 @pytest.mark.parametrize("dtype", ALL_DTYPES)
 def test_each_stream_variant(variant, dtype, stream_variant):
     """Each variant on its own over bins far below and far above the automatic
@@ -290,7 +290,7 @@ def test_each_stream_variant(variant, dtype, stream_variant):
                 check("m4", None, y, n_out, nan)
 
 
-@pytest.mark.parametrize("variant", ["ring", "ldg", "seg"])
+@pytest.mark.parametrize("variant", ["ring", "ldg", "seg", "grp"])
 def test_each_variant_with_x_and_lttb_preselection(variant, stream_variant):
     stream_variant(variant)
     y = inputs.quantised_nan(300_000, seed=33)
@@ -300,14 +300,16 @@ def test_each_variant_with_x_and_lttb_preselection(variant, stream_variant):
         check("minmaxlttb", x, y, n_out, "propagate", 4)
 
 
+@pytest.mark.parametrize("variant", ["seg", "grp"])
 @pytest.mark.parametrize("dtype", ["float32", "int8", "uint16", "float16", "int32", "float64", "int64", "uint64"])
 @pytest.mark.parametrize("nan", ["propagate", "ignore"])
-def test_segmented_tiny_and_mixed_bins(dtype, nan, stream_variant):
-    """The segmented variant where bins are one to a few elements (many bin
-    starts per 512-byte sub-step, several refills of the prefetched starts),
-    around the sub-step size, and with x making empty bins and long runs of
-    equal bin starts."""
-    stream_variant("seg")
+def test_segmented_tiny_and_mixed_bins(variant, dtype, nan, stream_variant):
+    """The segmented and lane-group variants where bins are one to a few
+    elements (many bin starts per 512-byte sub-step, several refills of the
+    prefetched starts; lane groups of one lane), around the sub-step size, and
+    with x making empty bins, long runs of equal bin starts and bins far above
+    the lane-group size limit (the register-streaming pass takes those)."""
+    stream_variant(variant)
     rng = np.random.default_rng(61)
     n = 300_001
     y = series(dtype, n, seed=62, kind="ties")
@@ -345,3 +347,36 @@ def test_everynth(x_dtype):
     check("everynth", None if x is None else x[:500], y[:500], 500)
     check("everynth", None if x is None else x[:500], y[:500], 501)
     check("everynth", None if x is None else x[:0], y[:0], 10)
+
+
+@pytest.mark.parametrize("algo", ["minmax", "m4"])
+@pytest.mark.parametrize("xkind", ["none", "int64_gaps", "float64_skewed"])
+def test_bin_ranges_concatenate_to_the_whole_call(algo, xkind):
+    """tsds_minmax_bins / tsds_m4_bins over consecutive bin ranges (the split a set of ranks
+    uses, shard.shard_bins) concatenate to the single call's output and the oracle's.  The
+    skewed x puts most points in a few bins, far above the lane-group size limit."""
+    from paper_2307_05389_gb300 import binding, shard
+    import torch
+    rng = np.random.default_rng(71)
+    n = 600_001
+    y = inputs.random_walk(n, "float32", seed=72)
+    y[rng.choice(n, 50, replace=False)] = np.nan
+    if xkind == "none":
+        x = None
+    elif xkind == "int64_gaps":
+        x = np.concatenate([[0], np.cumsum(rng.choice([0, 1, 2, 40], size=n - 1))]).astype(np.int64)
+    else:
+        x = np.sort(np.concatenate([rng.uniform(0, 1, n - 1000), rng.uniform(0, 1e6, 1000)]))
+    dy = torch.from_numpy(y).cuda()
+    dx = torch.from_numpy(x).cuda() if x is not None else None
+    per = 2 if algo == "minmax" else 4
+    for n_out in (per * 7, per * 3000, per * 60_000):
+        for nan in ("propagate", "ignore"):
+            whole = oracle.downsample(algo, x, y, n_out, nan)
+            nb = n_out // per
+            for world in (1, 3, 8):
+                parts = [binding.downsample_bins(algo, dy, n_out, *shard.shard_bins(nb, r, world), x=dx, nan=nan)
+                         for r in range(world)]
+                got = torch.cat(parts).cpu().numpy()
+                np.testing.assert_array_equal(got, whole, err_msg=f"{algo} n_out={n_out} world={world} {nan}")
+            assert binding.downsample_bins(algo, dy, n_out, 3, 3, x=dx, nan=nan).numel() == 0
