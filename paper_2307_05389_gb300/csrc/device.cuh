@@ -160,6 +160,55 @@ __device__ __forceinline__ int64_t warp_lower_bound(int64_t lo, int64_t hi, Pred
   return hi;
 }
 
+// The same search with GL lanes per query (a warp serves 32/GL searches at
+// once), whose first round probes the window [a, b) around a guess instead of
+// all of [lo, hi).  Every lane of the warp calls it; lanes of groups without a
+// search pass act = false.  Rounds go on until every group is done, so the
+// warp stays converged and the probes of all groups of a round are in flight
+// together.  Invariant: pred is false on [.., lo), the answer lies in
+// [lo, hi], and pred(hi) is true or hi is the end.  Returns the answer on
+// every lane of the group (hi for a group that has no search).
+template <int GL, class Pred>
+__device__ __forceinline__ int64_t group_lower_bound(int64_t lo, int64_t hi, int64_t a, int64_t b, bool act,
+                                                     Pred pred) {
+  static_assert(GL >= 2 && GL <= 32 && (GL & (GL - 1)) == 0, "a power-of-two group");
+  const int lane = threadIdx.x & 31, sl = lane & (GL - 1);
+  const unsigned shift = (unsigned)(lane / GL * GL);
+  const unsigned gm = GL == 32 ? 0xffffffffu : ((1u << GL) - 1u);
+  a = a < lo ? lo : a;
+  b = b > hi ? hi : b;
+  bool first = a < b;
+  bool done = !act || lo >= hi;
+  while (__any_sync(0xffffffffu, !done)) {
+    const int64_t s = first ? a : lo, e = first ? b : hi;
+    const int64_t step = (e - s + GL - 1) / GL;
+    const int64_t q = s + (int64_t)sl * step;
+    const bool valid = !done && q < e;
+    const bool p = valid && pred(q);
+    const unsigned m = (__ballot_sync(0xffffffffu, p) >> shift) & gm;
+    const unsigned vm = (__ballot_sync(0xffffffffu, valid) >> shift) & gm;
+    if (!done) {
+      if (m == 0) {
+        // every probe false: so is everything up to the last one
+        lo = s + (int64_t)(31 - __clz(vm)) * step + 1;
+      } else {
+        const int f = __ffs(m) - 1;
+        const int64_t qf = s + (int64_t)f * step;
+        if (f == 0) {
+          if (s == lo) { lo = qf; hi = qf; }   // pred(lo) holds: lo is the answer
+          else hi = qf;                        // the window started past the answer
+        } else {
+          lo = s + (int64_t)(f - 1) * step + 1;
+          hi = qf;
+        }
+      }
+      if (lo >= hi) done = true;
+    }
+    first = false;
+  }
+  return hi;
+}
+
 // floor(a*b/c) and ceil(a*b/c) for non-negative a, b and positive c with a*b
 // below 2^127: one 64-bit division when a and b are below 2^32 (the product
 // then fits 64 bits), the 128-bit one otherwise.

@@ -61,6 +61,12 @@ __device__ __forceinline__ double x_as_f64<__half>(const __half* x, int64_t j) {
 constexpr int64_t kEdgeGroup = 32;
 constexpr int64_t kEdgesTwoLevelMinBins = 4096;
 constexpr int64_t kEdgesTwoLevelMaxBinPoints = 512;
+// The single launch with bins of at most this many points on average searches
+// with kEdgeLanes lanes per edge from a window around the edge's expected
+// position (four edges per warp, a few 8-way rounds) instead of a warp per
+// edge over all of x.
+constexpr int64_t kEdgesGuessMaxBinPoints = 8192;
+constexpr int kEdgeLanes = 8;
 
 template <class X, bool FLOATX, int PHASE>
 __global__ void k_edges_x(const SeriesDev* sd, SeriesDev single, int count) {
@@ -72,6 +78,62 @@ __global__ void k_edges_x(const SeriesDev* sd, SeriesDev single, int count) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t warps_total = (int64_t)gridDim.x * (blockDim.x >> 5);
   if (PHASE != 2 && blockIdx.x == 0 && threadIdx.x == 0) { S.edges[0] = 0; S.edges[nb] = n; }
+  if (PHASE != 0 || n <= kEdgesGuessMaxBinPoints * nb) {
+    // groups of kEdgeLanes lanes, one edge each, whose first round probes a
+    // window around the edge's expected position: its index position for
+    // evenly spread x over all of x (phases 0 and 1), or the position
+    // interpolated between the two group edges around it (phase 2, which
+    // searches only between them).  A miss costs a search over the rest.
+    constexpr int per = 32 / kEdgeLanes;
+    const int sub = lane / kEdgeLanes;
+    const int64_t stride = PHASE == 1 ? kEdgeGroup : 1;
+    const int64_t bin_pts = n / nb;
+    for (int64_t k0 = ((int64_t)blockIdx.x * (blockDim.x >> 5) + warp) * per;; k0 += warps_total * per) {
+      // this warp's edges: the k-th edge of the phase, i = stride * (k + 1)
+      // (phase 2 skips the group edges), per lanes group
+      int64_t i;
+      if (PHASE == 2) {
+        const int64_t k = k0 + sub;
+        i = k / (kEdgeGroup - 1) * kEdgeGroup + k % (kEdgeGroup - 1) + 1;
+        if (k0 / (kEdgeGroup - 1) * kEdgeGroup + k0 % (kEdgeGroup - 1) + 1 >= nb) break;
+      } else {
+        i = stride * (k0 + sub + 1);
+        if (stride * (k0 + 1) >= nb) break;
+      }
+      const bool act = i < nb;
+      int64_t lo = 0, hi = n, g = 0, radius = 0;
+      if (act) {
+        if (PHASE == 2) {
+          const int64_t gb = i - i % kEdgeGroup;
+          lo = S.edges[gb];
+          hi = gb + kEdgeGroup < nb ? S.edges[gb + kEdgeGroup] : n;
+          const int64_t span_bins = (gb + kEdgeGroup < nb ? kEdgeGroup : nb - gb);
+          g = lo + (int64_t)muldiv_floor((uint64_t)(i - gb), (uint64_t)(hi - lo), (uint64_t)span_bins);
+          radius = 4 * ((hi - lo) / span_bins) + 2 * (int64_t)sqrtf((float)(hi - lo)) + 32;
+        } else {
+          g = (int64_t)muldiv_floor((uint64_t)i, (uint64_t)(n - 1), (uint64_t)nb);
+          radius = 4 * bin_pts + 2 * (int64_t)sqrtf((float)n) + 32;
+        }
+      }
+      int64_t e;
+      if constexpr (FLOATX) {
+        const double x0 = x_as_f64<X>(x, 0);
+        const double xl = x_as_f64<X>(x, n - 1);
+        const double span = __dsub_rn(xl, x0);
+        const double edge = __dadd_rn(x0, __ddiv_rn(__dmul_rn(span, (double)i), (double)nb));
+        e = group_lower_bound<kEdgeLanes>(lo, hi, g - radius, g + radius, act,
+                                          [&](int64_t j) { return x_as_f64<X>(x, j) >= edge; });
+      } else {
+        const X x0 = __ldg(x);
+        const u128 span = XInt<X>::off(x, n - 1, x0);
+        const u128 rhs = (u128)i * span;
+        e = group_lower_bound<kEdgeLanes>(lo, hi, g - radius, g + radius, act,
+                                          [&](int64_t j) { return XInt<X>::off(x, j, x0) * (u128)nb >= rhs; });
+      }
+      if (act && lane % kEdgeLanes == 0) S.edges[i] = e;
+    }
+    return;
+  }
   const int64_t step = PHASE == 1 ? kEdgeGroup : 1;
   for (int64_t i = step + ((int64_t)blockIdx.x * (blockDim.x >> 5) + warp) * step; i < nb; i += warps_total * step) {
     if (PHASE == 2 && i % kEdgeGroup == 0) continue;
