@@ -45,22 +45,26 @@ WORKLOAD = ("single series n=1e9 float32 random walk with int64 sorted non-equid
             "(geometric(0.5) gaps), n_out=2000, MinMax + M4")
 
 
-def workload_name(n, n_out):
+def workload_name(n, n_out, no_x=False, dtype="float32"):
     """The default step's workload, or the same recipe at other sizes (profiling runs)."""
-    if n == N_DEFAULT and n_out == N_OUT:
+    if n == N_DEFAULT and n_out == N_OUT and not no_x and dtype == "float32":
         return WORKLOAD
-    return (f"single series n={n:.4g} float32 random walk with int64 sorted non-equidistant x "
-            f"(geometric(0.5) gaps), n_out={n_out}, MinMax + M4")
+    values = "float32 random walk" if dtype == "float32" else f"{dtype} uniform over a quarter of its range"
+    xs = "no x" if no_x else "int64 sorted non-equidistant x (geometric(0.5) gaps)"
+    return f"single series n={n:.4g} {values} with {xs}, n_out={n_out}, MinMax + M4"
 
 
-def l2_note(n):
-    gb = n * 4 / 1e9
-    if n * 4 > 129e6:
-        return f"inputs larger than L2 ({gb:.4g} GB y, {2 * gb:.4g} GB x); no flush"
+def l2_note(n, ysz=4, xsz=8):
+    gb = n * ysz / 1e9
+    if n * ysz > 129e6:
+        xs = f", {n * xsz / 1e9:.4g} GB x" if xsz else ""
+        return f"inputs larger than L2 ({gb:.4g} GB y{xs}); no flush"
     return f"y ({gb:.4g} GB) fits in L2: not an HBM measurement"
 
 
 FALLBACK_HBM = 6800.0
+DTYPE_SHORT = {"float32": "f32", "float64": "f64", "float16": "f16", "int8": "i8", "int16": "i16", "int32": "i32",
+               "int64": "i64", "uint8": "u8", "uint16": "u16", "uint32": "u32", "uint64": "u64"}
 
 
 def parse():
@@ -75,6 +79,15 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--n-out", type=int, default=N_OUT, help="n_out of the default step (profiling other bin sizes)")
+    ap.add_argument("--no-x", action="store_true", help="the default step without x (index bins; profiling runs)")
+    ap.add_argument("--dtype", default="float32",
+                    help="y dtype of the default step (float32: random walk; others: quarter-range values; profiling runs)")
+    ap.add_argument("--dtypes", default=None, help="dtypes suite: a comma-separated subset of the eleven dtypes")
+    ap.add_argument("--serve-series", type=int, default=32, help="resident series of the serve suite")
+    ap.add_argument("--serve-n", type=int, default=100_000_000, help="points per resident series of the serve suite")
+    ap.add_argument("--serve-algos", default="minmax,m4,minmaxlttb", help="algorithms the serve suite draws from")
+    ap.add_argument("--serve-burst-only", type=int, default=0,
+                    help="serve suite: only a warm-up and one burst of this many queries (profiling runs)")
     ap.add_argument("--batch-count", type=int, default=4096, help="series in the batched suite (smaller for profiling)")
     ap.add_argument("--stream-variant", default="auto", choices=["auto", "ring", "ldg", "seg", "grp"],
                     help="kernel variant of the streaming pass (tsds_stream_variant)")
@@ -130,7 +143,7 @@ def suite_dtypes(args):
     out = torch.empty(N_OUT, dtype=torch.int64, device=dev)
     cnt = torch.empty(1, dtype=torch.int64, device=dev)
     rpeak = None
-    for d in inputs.DTYPES:
+    for d in (args.dtypes.split(",") if args.dtypes else inputs.DTYPES):
         size = np.dtype(d).itemsize
         n = 4_000_000_000 // size
         y = inputs.quarter_range_cuda(n, d, seed=2, device=dev)
@@ -319,7 +332,8 @@ def suite_serve(args):
 
     from paper_2307_05389_gb300 import binding, inputs
     dev = torch.device("cuda", 0)
-    nser, n = 32, 100_000_000
+    nser, n = args.serve_series, args.serve_n
+    algos = args.serve_algos.split(",")
     ys = [inputs.random_walk_cuda(n, "float32", seed=500 + i, device=dev) for i in range(nser)]
     xs = [inputs.exponential_x_cuda(n, seed=600 + i, device=dev) for i in range(nser)]
     torch.cuda.synchronize()
@@ -331,11 +345,11 @@ def suite_serve(args):
         qs = []
         for _ in range(k):
             s = int(rng.integers(0, nser))
-            span = int(10 ** rng.uniform(4, 8))
+            span = int(10 ** rng.uniform(4, np.log10(n)))
             start = int(rng.integers(0, n - span + 1))
             lo_x = float(xh[s][min(start // 1000, len(xh[s]) - 1)])
             hi_x = float(xh[s][min((start + span) // 1000, len(xh[s]) - 1)])
-            qs.append((s, ["minmax", "m4", "minmaxlttb"][int(rng.integers(0, 3))],
+            qs.append((s, algos[int(rng.integers(0, len(algos)))],
                        int([500, 1000, 2000, 4000][int(rng.integers(0, 4))]), lo_x, hi_x))
         return qs
 
@@ -345,6 +359,20 @@ def suite_serve(args):
     # warm-up (autotune-free path; first batches allocate pinned buffers)
     for t in [srv.submit(ids[s], a, k, x_range=(l, h)) for s, a, k, l, h in draw(64)]:
         srv.result(t)
+    if args.serve_burst_only:
+        qs = draw(args.serve_burst_only)
+        srv.reset_stats()
+        tickets = [srv.submit(ids[s], a, k, x_range=(l, h)) for s, a, k, l, h in qs]
+        for t in tickets:
+            srv.result(t)
+        st = srv.stats()
+        srv.close()
+        return {"suite": "serve", "unit": "ms", "config": {
+            "workload": f"{nser} x {n:.3g} float32 random walks, float64 x; one burst of {len(qs)} viewport queries "
+                        f"({'/'.join(algos)})"},
+            "results": {"burst": {"achieved_qps": st["completed"] / st["span_s"], "p50_ms": st["p50_us"] / 1e3,
+                                  "p99_ms": st["p99_us"] / 1e3, "GBps": st["bytes"] / st["span_s"] / 1e9,
+                                  "batches": st["batches"]}}}
     for rate in (1e2, 1e3, 1e4, 1e5):
         count = int(min(max(200, rate * 2.0), 4000))
         qs = draw(count)
@@ -397,8 +425,9 @@ def suite_serve(args):
     res["one_call_per_query"] = {"queries": len(qs), "qps": len(qs) / dt, "GBps": tot_pts * 4 / dt / 1e9,
                                  "mean_ms": dt / len(qs) * 1e3}
     return {"suite": "serve", "unit": "ms", "config": {
-        "workload": "32 x 1e8 float32 random walks, float64 x = cumsum(exponential(1)); Poisson viewport queries, "
-                    "span log-uniform [1e4, 1e8] points, n_out in {500,1000,2000,4000}, MinMax/M4/MinMaxLTTB(4)",
+        "workload": f"{nser} x {n:.3g} float32 random walks, float64 x = cumsum(exponential(1)); Poisson viewport "
+                    f"queries, span log-uniform [1e4, {n:.3g}] points, n_out in {{500,1000,2000,4000}}, "
+                    f"{'/'.join(algos)} (MinMaxLTTB ratio 4)",
         "server": {"streams": 4, "max_batch": 256, "memory_budget_GiB": 8}}, "results": res}
 
 
@@ -491,11 +520,13 @@ def suite_lttb(args):
             "results": res}
 
 
-def step_bytes(n, n_out=N_OUT, x_itemsize=8):
+def step_bytes(n, n_out=N_OUT, x_itemsize=8, y_itemsize=4):
+    """Algorithmic input bytes of one MinMax and one M4 call: y read once, plus the x probes of the
+    bin searches (x_itemsize 0: no x)."""
     per = {}
     for algo in ALGOS:
         nb = n_out // (2 if algo == "minmax" else 4)
-        per[algo] = n * 4 + (nb + 1) * math.ceil(math.log2(max(n, 2))) * x_itemsize
+        per[algo] = n * y_itemsize + (nb + 1) * math.ceil(math.log2(max(n, 2))) * x_itemsize
     return per
 
 
@@ -536,14 +567,20 @@ def aggregate_ranks(ms_local, bytes_local, dist=None, device=None):
     return ms_max, total, total / (ms_max / 1e3) / 1e9
 
 
-def stream_kernel_name(n, n_out, forced):
-    """The streaming kernel a float32 MinMax launch of this shape runs (the
-    library's automatic rule: segmented below 1.5 KB mean bins)."""
+def stream_kernel_name(n, n_out, forced, itemsize=4):
+    """The streaming kernel a MinMax launch of this shape runs (the library's automatic rule for a
+    single series: a warp per bin up to 256 MB with bins of at least 4 KB and beyond with bins of at
+    least 8 KB, otherwise lane groups below 8 KB mean bins, register streaming above)."""
     v = forced
+    nb = max(n_out // 2, 1)
+    bytes_ = n * itemsize
     if v == "auto":
-        v = "seg" if n * 4 / max(n_out // 2, 1) < 1536 else "ldg"
+        small = bytes_ <= nb * 65536 and ((bytes_ <= 256 << 20 and (nb <= 4096 or bytes_ >= 4096 * nb))
+                                         or bytes_ >= 8192 * nb)
+        v = "small" if small else "grp" if bytes_ / nb < 8192 else "ldg"
     return {"ldg": "tsds::k_argminmax_ldg (register streaming)", "seg": "tsds::k_argminmax_seg (segmented)",
-            "ring": "tsds::k_argminmax (shared-memory ring)"}[v] + " — streaming per-bin argmin/argmax"
+            "ring": "tsds::k_argminmax (shared-memory ring)", "grp": "tsds::k_argminmax_grp (lane groups)",
+            "small": "tsds::k_small (a warp per bin)"}[v] + " — streaming per-bin argmin/argmax"
 
 
 def hbm_peak():
@@ -718,8 +755,13 @@ def main():
         binding.tsds_stream_variant(args.stream_variant)
 
     n = args.n
-    y = inputs.random_walk_cuda(n, "float32", seed=2 + rank, device=dev)
-    x = inputs.geometric_x_cuda(n, seed=2 + rank, device=dev)
+    if np.dtype(args.dtype).kind == "u":
+        args.no_e2e = True   # the host-buffer API takes torch tensors, which have no unsigned 16-64-bit types
+    if args.dtype == "float32":
+        y = inputs.random_walk_cuda(n, "float32", seed=2 + rank, device=dev)
+    else:
+        y = inputs.quarter_range_cuda(n, args.dtype, seed=2 + rank, device=dev)
+    x = None if args.no_x else inputs.geometric_x_cuda(n, seed=2 + rank, device=dev)
     outs = {a: torch.empty(args.n_out, dtype=torch.int64, device=dev) for a in ALGOS}
     cnts = {a: torch.empty(1, dtype=torch.int64, device=dev) for a in ALGOS}
     torch.cuda.synchronize()
@@ -729,7 +771,8 @@ def main():
     fns = {"minmax": binding.tsds_minmax, "m4": binding.tsds_m4}
 
     def call(algo):
-        r = fns[algo](x.data_ptr(), binding.DTYPES["int64"], y.data_ptr(), binding.DTYPES["float32"], n, args.n_out,
+        r = fns[algo](x.data_ptr() if x is not None else None, binding.DTYPES["int64"] if x is not None else 0,
+                      y.data_ptr(), binding.DTYPES[args.dtype], n, args.n_out,
                       0, outs[algo].data_ptr(), cnts[algo].data_ptr(), sp)
         if r != 0:
             raise RuntimeError(binding.last_error())
@@ -764,11 +807,13 @@ def main():
         dist.barrier()
     clk = clocks.stop()
     kern_ms, kern_launches = pkg.tsds_timing_read()
-    per = step_bytes(n, args.n_out)
+    ysz = np.dtype(args.dtype).itemsize
+    xsz = 0 if x is None else 8
+    per = step_bytes(n, args.n_out, xsz, ysz)
     ms_max, total_bytes, value = aggregate_ranks(ms, sum(per.values()) * args.steps, dist, dev)
     peak, peak_src = hbm_peak()
     kern_avg_ms = kern_ms / max(kern_launches, 1)
-    achieved = n * 4 / (kern_avg_ms / 1e3) / 1e9
+    achieved = n * ysz / (kern_avg_ms / 1e3) / 1e9
 
     # ---- per-algorithm breakdown (whole call and streaming kernel)
     per_algo = {}
@@ -786,7 +831,7 @@ def main():
         km, kl = pkg.tsds_timing_read()
         call_ms = e0.elapsed_time(e1) / reps
         per_algo[a] = {"call_ms": call_ms, "call_GBps": per[a] / (call_ms / 1e3) / 1e9,
-                       "kernel_ms": km / max(kl, 1), "kernel_GBps": n * 4 / (km / max(kl, 1) / 1e3) / 1e9,
+                       "kernel_ms": km / max(kl, 1), "kernel_GBps": n * ysz / (km / max(kl, 1) / 1e3) / 1e9,
                        "pct_of_hbm_peak": 100.0 * per[a] / (call_ms / 1e3) / 1e9 / peak}
 
     rpeak = read_peak(pkg, torch, y, stream)
@@ -795,8 +840,8 @@ def main():
     e2e = None
     if not args.no_e2e:
         yh = y.cpu().pin_memory()
-        xh = x.cpu().pin_memory()
-        yd, xd = torch.empty_like(y), torch.empty_like(x)
+        xh = x.cpu().pin_memory() if x is not None else None
+        yd, xd = torch.empty_like(y), (torch.empty_like(x) if x is not None else None)
         pkg.downsample_host(ALGOS, yh, args.n_out, x=xh, y_dev=yd, x_dev=xd)   # warm-up
         torch.cuda.synchronize()
         if dist:
@@ -814,9 +859,9 @@ def main():
         dt = float(tt.item())
         # y is copied to the device every step; the pinned x stays in host memory and the
         # bin search reads its probes in place ((nb+1) * ceil(log2 n) elements per call)
-        probes = sum(step_bytes(n, args.n_out).values()) - 2 * n * 4
+        probes = sum(per.values()) - 2 * n * ysz
         e2e = {"value": sum(per.values()) * args.e2e_steps * world / dt / 1e9, "unit": "GB/s",
-               "h2d_bytes_per_step": int(yh.numel() * 4), "d2h_bytes_per_step": int(d2h),
+               "h2d_bytes_per_step": int(yh.numel() * ysz), "d2h_bytes_per_step": int(d2h),
                "x_read_in_place_bytes_per_step": int(probes),
                "api": "paper_2307_05389_gb300.downsample_host (pinned y copied, pinned x searched in place)"}
         del yh, xh, yd, xd
@@ -828,12 +873,14 @@ def main():
         oracle.build()
         ns = min(args.cpu_sample, n)
         ys = y[:ns].cpu().numpy()
-        xs = x[:ns].cpu().numpy()
+        if args.dtype != "float32" and np.dtype(args.dtype).kind == "u":
+            ys = ys.view(np.dtype(args.dtype))
+        xs = x[:ns].cpu().numpy() if x is not None else None
         t0 = time.perf_counter()
         for a in ALGOS:
             oracle.downsample(a, xs, ys, args.n_out)
         dt = time.perf_counter() - t0
-        cpu = {"value": sum(step_bytes(ns, args.n_out).values()) / dt / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
+        cpu = {"value": sum(step_bytes(ns, args.n_out, xsz, ysz).values()) / dt / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
                "sample": f"first {ns} points of the same series and x, MinMax + M4 once each ({dt:.1f} s)"}
         cpu["all_cores"] = oracle_all_cores(oracle, xs, ys, args.n_out)
 
@@ -844,17 +891,19 @@ def main():
         line = {
             "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
             "warmup": max(3, args.warmup), "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": DTYPE_SHORT.get(args.dtype, args.dtype),
+            "data": "synthetic",
             "impl": "native",
-            "config": {"workload": workload_name(n, args.n_out), "n": n, "n_out": args.n_out,
-                       "algorithms": list(ALGOS), "x": "int64", "y": "float32", "l2": l2_note(n),
+            "config": {"workload": workload_name(n, args.n_out, x is None, args.dtype), "n": n, "n_out": args.n_out,
+                       "algorithms": list(ALGOS), "x": None if x is None else "int64", "y": args.dtype,
+                       "l2": l2_note(n, ysz, xsz),
                        "parallelism": f"{world} independent series (one per GPU)" if world > 1 else "single GPU"},
             "pct_of_hbm_peak": 100.0 * value / world / peak,
             "per_algo": per_algo,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": kernel_traffic(),
-                         "kernel": stream_kernel_name(n, args.n_out, args.stream_variant),
-                         "bytes_per_launch": n * 4, "launches_timed": kern_launches,
+                         "kernel": stream_kernel_name(n, args.n_out, args.stream_variant, ysz),
+                         "bytes_per_launch": n * ysz, "launches_timed": kern_launches,
                          "peak_source": f"{peak_src} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
                          "read_peak": None if rpeak is None else {
                              "value": rpeak, "frac": achieved / rpeak,

@@ -4,25 +4,26 @@
 //
 // The windowed variants give a bin to a whole warp, or walk bin boundaries
 // inside a warp-wide stream; both pay a fixed cost per bin that dominates when
-// bins are small.  Here a warp splits into 32/G groups of G lanes (G a power
-// of two chosen per launch from the mean bin size) and each group reduces one
-// whole bin at a time:
-//  * the bin's 16-byte vectors are dealt to the group's lanes round-robin, so
-//    every load instruction reads G*16 contiguous bytes per group, and each
-//    lane issues up to kGrpU loads before it uses any of them;
+// bins are small.  Here a warp claims a tile of up to kGrpTileMaxBins
+// consecutive whole bins, stages their starts in shared memory with one
+// coalesced load, asks L2 for the tile's bytes, and splits into 32/G groups of
+// G lanes (G a power of two chosen from the mean bin size), each group
+// reducing one whole bin at a time:
+//  * a bin's first and last 16-byte vector, which may hold elements of the
+//    neighbouring bins, are taken by one lane each, with the elements outside
+//    the bin replaced by one inside it (which changes neither extremum);
+//  * the interior vectors are dealt to the group's lanes round-robin, so every
+//    load instruction reads G*16 contiguous bytes per group, and each lane
+//    issues kGrpU loads before it uses any of them;
 //  * a vector reduces to one group minimum and maximum with the policy's
 //    packed instructions (value space, as in the other variants); a lane keeps
-//    its running extremum, the vector it came from (registers) and that
-//    vector's number, replacing them only on a strict improvement, so the
-//    earliest occurrence survives without any re-read;
-//  * elements of a bin's first and last vector that lie outside the bin are
-//    replaced by an element of the bin from the same vector, which changes
-//    neither extremum, and the index search at the end looks only at the
-//    bin's own positions;
-//  * the lanes then join packed (ordered key, offset) runs with log2(G)
-//    shuffle rounds, and the group's first lane writes the bin's selections.
-// No bin is cut, so nothing is published or merged across warps.  Warps claim
-// tiles of consecutive bins from an atomic counter.
+//    its running extremum and the number of the vector it came from, replacing
+//    them only on a strict improvement, so the earliest occurrence survives;
+//  * at the end a lane reads its winning vector again (an L1 hit) to find the
+//    first matching slot inside the bin, the lanes join packed (ordered key,
+//    offset) runs with log2(G) shuffle rounds, and the group's first lane
+//    writes the bin's selections.
+// No bin is cut, so nothing is published or merged across warps.
 #pragma once
 
 constexpr int kGrpThreads = 256;   // 8 warps per CTA
