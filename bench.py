@@ -83,6 +83,8 @@ def parse():
     ap.add_argument("--dtype", default="float32",
                     help="y dtype of the default step (float32: random walk; others: quarter-range values; profiling runs)")
     ap.add_argument("--dtypes", default=None, help="dtypes suite: a comma-separated subset of the eleven dtypes")
+    ap.add_argument("--batched-plan-only", action="store_true",
+                    help="batched suite: only the resident plan with its default shape (profiling runs)")
     ap.add_argument("--serve-series", type=int, default=32, help="resident series of the serve suite")
     ap.add_argument("--serve-n", type=int, default=100_000_000, help="points per resident series of the serve suite")
     ap.add_argument("--serve-algos", default="minmax,m4,minmaxlttb", help="algorithms the serve suite draws from")
@@ -218,6 +220,14 @@ def suite_batched(args):
             c = counts.clone()
             return c, [o[:int(k)].clone() for o, k in zip(outs, c.tolist())]
 
+        if args.batched_plan_only:
+            # profiling runs: the resident plan alone (default launch shape, CUDA graph)
+            plan = binding.Plan(algo, ys, n_outs, graph=True, autotune=False)
+            plan.execute()
+            t_p, _ = _timed_calls(torch, stream, plan.execute, max(3, args.steps // 10))
+            res[algo] = {"plan_graph_ms": t_p, "plan_GBps": total * 4 / (t_p / 1e3) / 1e9, "plan": plan.info()}
+            plan.close()
+            continue
         per_series()
         ref_c, ref_o = snapshot()
         t_ps, _ = _timed_calls(torch, stream, per_series, 3)

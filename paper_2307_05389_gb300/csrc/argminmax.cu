@@ -946,13 +946,23 @@ template <class P, int NM, bool MULTI>
 static cudaError_t launch_grp_var(const SeriesDev* s_dev, const SeriesDev& single, const int32_t* tile_series,
                                   int64_t total_tiles, WorkCounters* work, const GrpShape& shape, cudaStream_t st,
                                   const int64_t* total_dev, int sm_count) {
+  // resident CTAs per SM, cached per device like the windowed kernels' (cleared by tsds_shutdown)
+  static std::atomic<unsigned long long> cache[kOccDevices];
   int d = 0;
   cudaError_t e = cudaGetDevice(&d);
   if (e != cudaSuccess) return e;
+  const unsigned epoch = g_occ_epoch.load();
+  std::atomic<unsigned long long>* slot = (d >= 0 && d < kOccDevices) ? &cache[d] : nullptr;
   int occ = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_argminmax_grp<P, NM, MULTI>, kGrpThreads, 0);
-  if (e != cudaSuccess) return e;
-  if (occ < 1) occ = 1;
+  const unsigned long long c = slot ? slot->load() : 0ull;
+  if ((unsigned)(c >> 32) == epoch && (int)(c & 0xffffffffu) > 0) {
+    occ = (int)(c & 0xffffffffu);
+  } else {
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_argminmax_grp<P, NM, MULTI>, kGrpThreads, 0);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) occ = 1;
+    if (slot) slot->store(((unsigned long long)epoch << 32) | (unsigned)occ);
+  }
   int64_t blocks = (total_tiles + kGrpThreads / 32 - 1) / (kGrpThreads / 32);
   const int64_t cap = (int64_t)(sm_count > 0 ? sm_count : device_sm_count()) * occ;
   if (blocks > cap || total_dev) blocks = cap;

@@ -545,6 +545,13 @@ tsds_status tsds_plan_create(tsds_plan* plan, tsds_algo algo, const tsds_series*
   if (s != TSDS_OK) { tsds_plan_destroy(p); return s; }
 
   if (flags & TSDS_PLAN_GRAPH) {
+    // one run outside the capture first: every kernel of the sequence is
+    // loaded and its launch shape looked up before capturing, since a module
+    // load inside a capture invalidates it
+    s = enqueue(P->L, P->base, algo, P->has_x, x_dtype, y_dtype, nan, P->cfg, st, P->fork);
+    if (s != TSDS_OK) { tsds_plan_destroy(p); return s; }
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) { tsds_plan_destroy(p); return fail(TSDS_ECUDA, "plan warm-up: %s", cudaGetErrorString(e)); }
     cudaStream_t cap;
     e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
     if (e != cudaSuccess) { tsds_plan_destroy(p); return fail(TSDS_ECUDA, "graph capture stream: %s", cudaGetErrorString(e)); }

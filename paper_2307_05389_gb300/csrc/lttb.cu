@@ -19,7 +19,8 @@
 //  * Small buckets (at most 32 points, the MinMaxLTTB case): the pick of
 //    bucket j depends on the chain only through which point a of bucket j-1
 //    was picked.  A transition table best[j][a] is filled for every bucket in
-//    parallel (one warp per bucket, exact binary64 areas).
+//    parallel (a group of lanes per bucket, several buckets per warp, exact
+//    binary64 areas).
 //  * Larger buckets: the pick of bucket j is the largest |linear form| of its
 //    points, which a vertex of the bucket's convex hull attains, so the
 //    picks that can feed bucket j+1 are few (a random walk's hull has about
@@ -333,9 +334,44 @@ __device__ __forceinline__ bool exact_finish(const ExactSum& e, int cnt, double&
   return true;
 }
 
+// The same over each group of GS lanes (a power of two; lanes gs*GS ..
+// gs*GS+GS-1 hold one bucket): every lane of the warp calls it, and each gets
+// its group's result.
+__device__ __forceinline__ bool exact_finish_g(const ExactSum& e, int cnt, double& out, int GS) {
+  bool nan = e.nan;
+  int L = e.s, T = e.top;
+  for (int o = GS >> 1; o; o >>= 1) {
+    nan = __shfl_xor_sync(0xffffffffu, nan, o) || nan;
+    L = min(L, __shfl_xor_sync(0xffffffffu, L, o));
+    T = max(T, __shfl_xor_sync(0xffffffffu, T, o));
+  }
+  unsigned long long a = e.acc << min(e.s - L, 63);
+  if (e.s == 4096) a = 0ull;                             // lane saw no nonzero value
+  for (int o = GS >> 1; o; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+  if (nan) {
+    out = __longlong_as_double(0x7ff8000000000000ll);
+    return true;
+  }
+  if (T == -4096) {                                      // every value was zero
+    out = 0.0;
+    return true;
+  }
+  const int lg = cnt <= 1 ? 0 : 32 - __clz(cnt - 1);     // ceil(log2 cnt)
+  if (T + 1 + lg > 53 + L) return false;
+  double r = __ll2double_rn((long long)a);               // exact: |a| < 2^53
+  int e2 = L;
+  if (e2 < -1022) {                                      // scale in two exact steps
+    r = __dmul_rn(r, __longlong_as_double((long long)(-600 + 1023) << 52));
+    e2 += 600;
+  }
+  out = __dmul_rn(r, __longlong_as_double((long long)(e2 + 1023) << 52));
+  return true;
+}
+
 // means[j] for buckets 1..B-1 (the third vertex of steps 0..B-2): binary64
 // sums in index order divided once by the count.  Small buckets (table mode,
-// at most 32 points): a warp per bucket, a lane per point, the exact integer
+// at most 32 points): a group of lanes per bucket (32/GS buckets per warp for
+// buckets of at most GS points), a lane per point, the exact integer
 // sum (ExactSum) when no addition of the index-order sum can round; other
 // buckets are flagged for the sequential sums of k_sums_wide.
 __global__ void k_means(const LttbJob* __restrict__ jobs) {
@@ -343,16 +379,25 @@ __global__ void k_means(const LttbJob* __restrict__ jobs) {
   if (J.mode != 0) return;
   const int64_t m = job_m(J), B = J.B;
   if (m <= B + 2) return;
+  constexpr unsigned FULL = 0xffffffffu;
   const bool ign = J.nan == TSDS_NAN_IGNORE;
   const int lane = threadIdx.x & 31;
+  // buckets of at most GS points: 32/GS of them per warp, a lane per point
+  int gs = 1;
+  while (gs < J.K) gs <<= 1;
+  const int GS = gs, per = 32 / GS, gi = lane / GS, gl = lane % GS;
+  const unsigned shift = (unsigned)(gi * GS);
+  const unsigned gm = GS == 32 ? FULL : ((1u << GS) - 1u);
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t j = 1 + (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); j < B; j += warps) {
-    const int64_t lo = bucket_start(j, m, B), hi = bucket_start(j + 1, m, B);
-    const int n = (int)(hi - lo);          // at most 32 in table mode
-    const bool has = lane < n;
-    const double x = has ? J.px[lo + lane] : 0.0, y = has ? J.py[lo + lane] : 0.0;
+  for (int64_t j0 = 1 + ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * per; j0 < B;
+       j0 += warps * per) {
+    const int64_t j = j0 + gi;
+    const bool jact = j < B;
+    const int64_t lo = jact ? bucket_start(j, m, B) : 0, hi = jact ? bucket_start(j + 1, m, B) : 0;
+    const bool has = gl < hi - lo;          // at most GS points in table mode
+    const double x = has ? J.px[lo + gl] : 0.0, y = has ? J.py[lo + gl] : 0.0;
     const bool inc = has && !(ign && isnan(y));
-    const int cnt = __popc(__ballot_sync(0xffffffffu, inc));
+    const int cnt = __popc((__ballot_sync(FULL, inc) >> shift) & gm);
     ExactSum ex, ey;
     exact_init(ex);
     exact_init(ey);
@@ -361,12 +406,12 @@ __global__ void k_means(const LttbJob* __restrict__ jobs) {
       exact_add(ex, x, bad);
       exact_add(ey, y, bad);
     }
-    bad = __any_sync(0xffffffffu, bad);
+    bad = ((__ballot_sync(FULL, bad) >> shift) & gm) != 0u;
     double sx = 0.0, sy = 0.0;
-    const bool okx = exact_finish(ex, cnt, sx);
-    const bool oky = exact_finish(ey, cnt, sy);
+    const bool okx = exact_finish_g(ex, cnt, sx, GS);
+    const bool oky = exact_finish_g(ey, cnt, sy, GS);
     const bool exact = !bad && okx && oky;
-    if (lane == 0) {
+    if (jact && gl == 0) {
       J.chain[j] = exact ? 0 : 1;
       if (exact) J.means[j] = make_double2(__ddiv_rn(sx, (double)cnt), __ddiv_rn(sy, (double)cnt));
     }
@@ -533,31 +578,49 @@ __global__ void k_table(const LttbJob* __restrict__ jobs) {
   if (J.mode != 0) return;
   const int64_t m = job_m(J), B = J.B;
   if (m <= B + 2) return;
+  constexpr unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
+  // buckets of at most GS points: 32/GS of them per warp, GS lanes each, so
+  // the per-bucket binary64 work of several buckets shares one warp instruction
+  int gs = 1;
+  while (gs < J.K) gs <<= 1;
+  const int GS = gs, per = 32 / GS, gi = lane / GS, gl = lane % GS;
+  const unsigned shift = (unsigned)(gi * GS);
+  const unsigned gm = GS == 32 ? FULL : ((1u << GS) - 1u);
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t j = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); j < B; j += warps) {
-    const int64_t lo = bucket_start(j, m, B), hi = bucket_start(j + 1, m, B);
-    double xm, ym;
-    if (j == B - 1) { xm = J.px[m - 1]; ym = J.py[m - 1]; }
-    else { const double2 c = J.means[j + 1]; xm = c.x; ym = c.y; }
-    const double X0 = J.px[lo], Y0 = J.py[lo];
-    const int64_t b = lo + lane;
-    const bool has_b = b < hi;
+  for (int64_t j0 = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * per; j0 < B;
+       j0 += warps * per) {
+    const int64_t j = j0 + gi;
+    const bool jact = j < B;
+    int64_t lo = 0, hi = 0;
+    double xm = 0.0, ym = 0.0, X0 = 0.0, Y0 = 0.0;
+    if (jact) {
+      lo = bucket_start(j, m, B);
+      hi = bucket_start(j + 1, m, B);
+      if (j == B - 1) { xm = J.px[m - 1]; ym = J.py[m - 1]; }
+      else { const double2 c = J.means[j + 1]; xm = c.x; ym = c.y; }
+      X0 = J.px[lo];
+      Y0 = J.py[lo];
+    }
+    const int64_t b = lo + gl;
+    const bool has_b = jact && b < hi;
     const double xb = has_b ? J.px[b] : 0.0, yb = has_b ? J.py[b] : 0.0;
     const float2 pb = make_float2(__double2float_rn(__dsub_rn(xb, X0)), __double2float_rn(__dsub_rn(yb, Y0)));
     // NaN candidates have NaN areas; the others must suit the filter
     const bool nanb = has_b && (isnan(xb) || isnan(yb));
     const bool candb = has_b && !nanb;
-    const bool pts_ok = __all_sync(0xffffffffu, !candb || (filt_ok(pb.x) && filt_ok(pb.y)));
-    const unsigned nan_mask = __ballot_sync(0xffffffffu, nanb);
-    const unsigned cand_mask = __ballot_sync(0xffffffffu, candb);
+    const bool pts_ok = ((__ballot_sync(FULL, candb && !(filt_ok(pb.x) && filt_ok(pb.y))) >> shift) & gm) == 0u;
+    const unsigned nan_mask = (__ballot_sync(FULL, nanb) >> shift) & gm;
+    const unsigned cand_mask = (__ballot_sync(FULL, candb) >> shift) & gm;
     const bool prop = J.nan == TSDS_NAN_PROPAGATE;
-    int64_t alo, ahi;
-    if (j == 0) { alo = 0; ahi = 1; }
-    else { alo = bucket_start(j - 1, m, B); ahi = lo; }
-    // lane l: the previous pick a = alo + l
-    const bool has_a = alo + lane < ahi;
-    const double xa_l = has_a ? J.px[alo + lane] : 0.0, ya_l = has_a ? J.py[alo + lane] : 0.0;
+    int64_t alo = 0, ahi = 0;
+    if (jact) {
+      if (j == 0) { alo = 0; ahi = 1; }
+      else { alo = bucket_start(j - 1, m, B); ahi = lo; }
+    }
+    // lane gl of the group: the previous pick a = alo + gl
+    const bool has_a = alo + gl < ahi;
+    const double xa_l = has_a ? J.px[alo + gl] : 0.0, ya_l = has_a ? J.py[alo + gl] : 0.0;
     const double dxm_l = __dsub_rn(xa_l, xm), dym_l = __dsub_rn(ym, ya_l);
     const float al_l = __double2float_rn(dxm_l), be_l = __double2float_rn(dym_l);
     const float ax_l = __double2float_rn(__dsub_rn(xa_l, X0)), ay_l = __double2float_rn(__dsub_rn(ya_l, Y0));
@@ -567,41 +630,48 @@ __global__ void k_table(const LttbJob* __restrict__ jobs) {
     // candidate (NaN-propagate: first NaN; NaN-ignore: no winner, first index)
     const bool anan_l = isnan(dxm_l) || isnan(dym_l);
     const int ka = (int)(ahi - alo);
-    for (int ai = 0; ai < ka; ++ai) {
-      int32_t pick = -1;
-      if (__shfl_sync(0xffffffffu, anan_l, ai)) {
-        pick = 0;
-      } else if (__shfl_sync(0xffffffffu, fast_l, ai) && prop && nan_mask) {
-        pick = __ffs(nan_mask) - 1;   // every other area is finite here: the first NaN wins
-      } else if (__shfl_sync(0xffffffffu, fast_l, ai) && !cand_mask) {
-        pick = 0;                     // NaN-ignore, only NaN candidates: no winner
-      } else if (__shfl_sync(0xffffffffu, fast_l, ai)) {
-        const Filt F{__shfl_sync(0xffffffffu, al_l, ai), __shfl_sync(0xffffffffu, be_l, ai),
-                     __shfl_sync(0xffffffffu, ax_l, ai), __shfl_sync(0xffffffffu, ay_l, ai)};
-        float lowb = -INFINITY, upb = -INFINITY;
-        if (candb) {
-          const float est = fabsf(filt_signed(F, pb.x, pb.y));
-          const float err = filt_err(F, fabsf(pb.x), fabsf(pb.y), fabsf(__fsub_rn(pb.y, F.ay)),
-                                     fabsf(__fsub_rn(F.ax, pb.x)), est);
-          lowb = __fsub_rd(est, err);
-          upb = __fadd_rn(est, err);
-        }
-        float L = lowb;
+    int kw = ka;   // the warp's largest previous bucket
 #pragma unroll
-        for (int o = 16; o; o >>= 1) L = fmaxf(L, __shfl_xor_sync(0xffffffffu, L, o));
-        const unsigned pass = __ballot_sync(0xffffffffu, candb && upb >= L);
-        if (__popc(pass) == 1) pick = __ffs(pass) - 1;
+    for (int o = 16; o; o >>= 1) kw = max(kw, __shfl_xor_sync(FULL, kw, o));
+    for (int ai = 0; ai < kw; ++ai) {
+      // every shuffle and ballot below runs on the whole warp; each group uses its own lanes
+      const int src = (int)shift + ai;
+      const bool step = ai < ka;
+      const bool anan = __shfl_sync(FULL, anan_l, src);
+      const bool fast = __shfl_sync(FULL, fast_l, src);
+      const Filt F{__shfl_sync(FULL, al_l, src), __shfl_sync(FULL, be_l, src), __shfl_sync(FULL, ax_l, src),
+                   __shfl_sync(FULL, ay_l, src)};
+      float lowb = -INFINITY, upb = -INFINITY;
+      if (candb && fast) {
+        const float est = fabsf(filt_signed(F, pb.x, pb.y));
+        const float err = filt_err(F, fabsf(pb.x), fabsf(pb.y), fabsf(__fsub_rn(pb.y, F.ay)),
+                                   fabsf(__fsub_rn(F.ax, pb.x)), est);
+        lowb = __fsub_rd(est, err);
+        upb = __fadd_rn(est, err);
       }
-      if (pick < 0) {
-        const double xa = __shfl_sync(0xffffffffu, xa_l, ai), ya = __shfl_sync(0xffffffffu, ya_l, ai);
-        const double dxm = __shfl_sync(0xffffffffu, dxm_l, ai), dym = __shfl_sync(0xffffffffu, dym_l, ai);
+      float L = lowb;
+      for (int o = GS >> 1; o; o >>= 1) L = fmaxf(L, __shfl_xor_sync(FULL, L, o));
+      const unsigned pass = (__ballot_sync(FULL, candb && upb >= L) >> shift) & gm;
+      int32_t pick = -1;
+      if (anan) pick = 0;
+      else if (fast && prop && nan_mask) pick = __ffs(nan_mask) - 1;   // every other area is finite: first NaN wins
+      else if (fast && !cand_mask) pick = 0;                           // NaN-ignore, only NaN candidates: no winner
+      else if (fast && __popc(pass) == 1) pick = __ffs(pass) - 1;
+      const bool need = step && pick < 0;
+      if (__any_sync(FULL, need)) {
+        const double xa = __shfl_sync(FULL, xa_l, src), ya = __shfl_sync(FULL, ya_l, src);
+        const double dxm = __shfl_sync(FULL, dxm_l, src), dym = __shfl_sync(FULL, dym_l, src);
         uint64_t k = 0ull;
         int64_t idx = kIdxNone;
-        if (has_b) { k = area_key(exact_area(xa, ya, dxm, dym, xb, yb), J.nan); idx = b; }
-        amax_warp(k, idx);
-        pick = (int32_t)((k == 0ull ? lo : idx) - lo);
+        if (need && has_b) { k = area_key(exact_area(xa, ya, dxm, dym, xb, yb), J.nan); idx = b; }
+        for (int o = GS >> 1; o; o >>= 1) {
+          const uint64_t k2 = __shfl_xor_sync(FULL, k, o);
+          const int64_t i2 = __shfl_xor_sync(FULL, idx, o);
+          amax_merge(k, idx, k2, i2);
+        }
+        if (need) pick = (int32_t)((k == 0ull ? lo : idx) - lo);
       }
-      if (lane == 0) J.table[j * J.K + ai] = pick;
+      if (step && gl == 0) J.table[j * J.K + ai] = pick;
     }
   }
 }

@@ -4,6 +4,7 @@ several windows, n_out >= n series, and both algorithms; plans are executed
 more than once, with graphs and autotuning, and re-executed after the data
 changed in place (Section 2.2's consistency across threading configurations,
 here across launch shapes)."""
+import os
 import numpy as np
 import pytest
 
@@ -164,3 +165,29 @@ def test_batched_with_x_and_many_bins(algo):
     for i, y in enumerate(ys):
         exp = oracle.downsample(algo, xs[i], y, int(n_outs[i]))
         np.testing.assert_array_equal(got[i], exp, err_msg=f"series {i} n={len(y)} n_out={n_outs[i]}")
+
+
+def test_graph_plan_created_first_in_a_fresh_process(tmp_path):
+    """A graph plan made before any kernel of its sequence has run in the process (no autotune,
+    so nothing runs before the capture): the capture must not fail, and the replay must give
+    the one-shot batched call's output."""
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = (
+        "import sys; sys.path.insert(0, %r)\n"
+        "import torch\n"
+        "from paper_2307_05389_gb300 import binding, inputs\n"
+        "ys = [torch.from_numpy(inputs.random_walk(n, 'float32', seed=s)).cuda() for s, n in ((1, 200_000), (2, 5_000), (3, 2_000_000))]\n"
+        "n_outs = [4000, 400, 1000]\n"
+        "for algo in ('minmax', 'm4'):\n"
+        "    plan = binding.Plan(algo, ys, n_outs, graph=True, autotune=False)\n"
+        "    plan.execute(); torch.cuda.synchronize()\n"
+        "    outs, counts = binding.downsample_batched(algo, ys, n_outs); torch.cuda.synchronize()\n"
+        "    for i in range(3):\n"
+        "        k = int(counts[i]); assert int(plan.counts[i]) == k\n"
+        "        assert torch.equal(plan.outs[i][:k], outs[i][:k])\n"
+        "    plan.close()\n"
+        "print('ok')\n" % root)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0 and r.stdout.strip().endswith("ok"), r.stdout[-2000:] + r.stderr[-2000:]
