@@ -151,14 +151,45 @@ __device__ __forceinline__ int64_t grp_tiles_of(const SeriesDev& S) {
   return (S.nb + tile_bins - 1) / tile_bins;
 }
 
+// Exclusive prefix sum over the CTA's threads (blockDim.x a multiple of 32, at
+// most 1024); *total gets the sum.  Every thread calls it.
+__device__ __forceinline__ int64_t block_exclusive_scan(int64_t v, int64_t* warp_tot, int64_t* total) {
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5, nw = blockDim.x >> 5;
+  int64_t incl = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int64_t u = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += u;
+  }
+  if (lane == 31) warp_tot[w] = incl;
+  __syncthreads();
+  if (w == 0) {
+    const int64_t wv = lane < nw ? warp_tot[lane] : 0;
+    int64_t wi = wv;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int64_t u = __shfl_up_sync(0xffffffffu, wi, o);
+      if (lane >= o) wi += u;
+    }
+    if (lane < nw) warp_tot[lane] = wi - wv;
+    if (lane == 31) *total = wi;
+  }
+  __syncthreads();
+  const int64_t r = warp_tot[w] + incl - v;
+  __syncthreads();   // warp_tot is reused by the next scan
+  return r;
+}
+
 // Window bases of the queries: those with large bins first, then those with
 // small bins; total[0] = all windows, total[1] = the large-bin windows (where
 // the small-bin range starts).  Queries in mode 1 get CTA bases instead, and
 // total[2] = their CTAs; small-bin queries (mode 3) also get tile bases, and
-// total[3] = their tiles.  One CTA.
+// total[3] = their tiles.  One CTA: each thread takes a run of queries, and
+// the runs are placed with block-wide scans.
 __global__ void k_scan_windows(SeriesDev* __restrict__ sd, const int64_t* __restrict__ windows,
                                const int8_t* __restrict__ small, int count, int64_t* __restrict__ total) {
-  __shared__ int64_t part[4][1024];
+  __shared__ int64_t warp_tot[32];
+  __shared__ int64_t tot[4];
   const int t = threadIdx.x;
   const int per = (count + blockDim.x - 1) / blockDim.x;
   const int a = min(t * per, count), b = min(a + per, count);
@@ -167,23 +198,15 @@ __global__ void k_scan_windows(SeriesDev* __restrict__ sd, const int64_t* __rest
     s[small[i]] += small[i] == 2 ? (sd[i].nb + kBinsPerCta - 1) / kBinsPerCta : windows[i];
     if (small[i] == 1) s[3] += grp_tiles_of(sd[i]);
   }
-  for (int g = 0; g < 4; ++g) part[g][t] = s[g];
-  __syncthreads();
+  int64_t r[4];
+  for (int g = 0; g < 4; ++g) r[g] = block_exclusive_scan(s[g], warp_tot, &tot[g]);
+  r[1] += tot[0];   // the small-bin windows follow the large-bin ones
   if (t == 0) {
-    int64_t run = 0;
-    for (int g = 0; g < 2; ++g) {
-      if (g == 1) total[1] = run;
-      for (int i = 0; i < (int)blockDim.x; ++i) { const int64_t v = part[g][i]; part[g][i] = run; run += v; }
-    }
-    total[0] = run;
-    for (int g = 2; g < 4; ++g) {
-      run = 0;
-      for (int i = 0; i < (int)blockDim.x; ++i) { const int64_t v = part[g][i]; part[g][i] = run; run += v; }
-      total[g] = run;
-    }
+    total[0] = tot[0] + tot[1];
+    total[1] = tot[0];
+    total[2] = tot[2];
+    total[3] = tot[3];
   }
-  __syncthreads();
-  int64_t r[4] = {part[0][t], part[1][t], part[2][t], part[3][t]};
   for (int i = a; i < b; ++i) {
     const int g = small[i];
     sd[i].win_base = r[g];
