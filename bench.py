@@ -577,17 +577,20 @@ def aggregate_ranks(ms_local, bytes_local, dist=None, device=None):
     return ms_max, total, total / (ms_max / 1e3) / 1e9
 
 
-def stream_kernel_name(n, n_out, forced, itemsize=4):
+def stream_kernel_name(n, n_out, forced, itemsize=4, has_x=True):
     """The streaming kernel a MinMax launch of this shape runs (the library's automatic rule for a
-    single series: a warp per bin up to 256 MB with bins of at least 4 KB and beyond with bins of at
-    least 8 KB, otherwise lane groups below 8 KB mean bins, register streaming above)."""
+    single series: a warp per bin up to 256 MB with bins of at least 8 KB, and beyond with bins of
+    at least 8 KB with x or 32 KB without; otherwise lane groups below 8 KB mean bins (32 KB
+    without x beyond 256 MB), register streaming above)."""
     v = forced
     nb = max(n_out // 2, 1)
     bytes_ = n * itemsize
     if v == "auto":
-        small = bytes_ <= nb * 65536 and ((bytes_ <= 256 << 20 and (nb <= 4096 or bytes_ >= 4096 * nb))
-                                         or bytes_ >= 8192 * nb)
-        v = "small" if small else "grp" if bytes_ / nb < 8192 else "ldg"
+        big = bytes_ > 256 << 20
+        small = bytes_ <= nb * 65536 and ((not big and (nb <= 4096 or bytes_ >= 8192 * nb))
+                                         or (big and bytes_ >= (8192 if has_x else 32768) * nb))
+        limit = 32768 if (big and not has_x) else 8192
+        v = "small" if small else "grp" if bytes_ / nb < limit else "ldg"
     return {"ldg": "tsds::k_argminmax_ldg (register streaming)", "seg": "tsds::k_argminmax_seg (segmented)",
             "ring": "tsds::k_argminmax (shared-memory ring)", "grp": "tsds::k_argminmax_grp (lane groups)",
             "small": "tsds::k_small (a warp per bin)"}[v] + " — streaming per-bin argmin/argmax"
@@ -912,7 +915,7 @@ def main():
             "per_algo": per_algo,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": kernel_traffic(),
-                         "kernel": stream_kernel_name(n, args.n_out, args.stream_variant, ysz),
+                         "kernel": stream_kernel_name(n, args.n_out, args.stream_variant, ysz, x is not None),
                          "bytes_per_launch": n * ysz, "launches_timed": kern_launches,
                          "peak_source": f"{peak_src} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
                          "read_peak": None if rpeak is None else {

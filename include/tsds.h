@@ -369,9 +369,10 @@ tsds_status tsds_check_wait_timeout(unsigned rounds, void* stream);
 /* Kernel variant of the streaming argmin/argmax pass for every later call in
  * the process (no counterpart in the paper, whose CPU kernel has one form):
  *   0  automatic (the default).  Single-series calls: a warp per bin in one
- *      launch for inputs of at most 256 MB with bins of at least 4 KB (or at
- *      most 4096 bins) and for larger inputs with bins of at least 8 KB;
- *      otherwise variant 4 when the mean bin is below 8 KB, variant 2 above.
+ *      launch for inputs of at most 256 MB with bins of at least 8 KB (or at
+ *      most 4096 bins) and for larger inputs with bins of at least 8 KB (with
+ *      x) or 32 KB (without); otherwise variant 4 when the mean bin is below
+ *      8 KB (32 KB without x beyond 256 MB), variant 2 above.
  *      Batches and served queries: series or queries are grouped by bin size
  *      (variant 4 below 8 KB for batches without x and for queries, a warp
  *      per bin up to 64 KB, variant 2 above; batches with x take variant 3

@@ -224,7 +224,7 @@ static BinnedLayout binned_layout(int64_t nb, int64_t windows) {
 tsds_status run_binned_series(const void* x, tsds_dtype x_dtype, const void* y, tsds_dtype y_dtype,
                               int64_t n, int64_t nb, tsds_nan_mode nan, Algo algo, int64_t* out,
                               int64_t* out_count, int64_t idx_bias, cudaStream_t st, const Gather* g) {
-  if (small_call(n, nb, y_dtype)) {
+  if (small_call(n, nb, y_dtype, x != nullptr)) {
     // a warp per bin: one launch (after the edge search when x is given), then
     // the emit kernels when there are too many bins for the last CTA to emit
     const bool emit = nb <= kSmallEmitMaxBins;
@@ -263,7 +263,7 @@ tsds_status run_binned_series(const void* x, tsds_dtype x_dtype, const void* y, 
   // warps would leave SMs idle.
   StreamConfig cfg;
   cfg.mean_bin_bytes = nb > 0 ? n / nb * dtype_size(y_dtype) : 0;
-  const bool grp = grp_call(cfg.mean_bin_bytes);
+  const bool grp = grp_call(cfg.mean_bin_bytes, n * dtype_size(y_dtype), x != nullptr);
   {
     const int64_t bytes = n * dtype_size(y_dtype);
     const int64_t warps = (int64_t)device_sm_count() * 3 * 4;

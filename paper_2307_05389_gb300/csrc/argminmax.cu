@@ -829,10 +829,12 @@ int stream_variant_for(const StreamConfig& cfg, int64_t elem_bytes) {
   return v;
 }
 
-bool grp_call(int64_t mean_bin_bytes) {
+bool grp_call(int64_t mean_bin_bytes, int64_t bytes, bool has_x) {
   const int v = variant_override();
   if (v == STREAM_GRP) return true;
-  return v == STREAM_AUTO && mean_bin_bytes < kGrpAutoMaxBinBytes;
+  // without x and beyond 256 MB the lane groups also win at 8-16 KB bins
+  const int64_t limit = (!has_x && bytes > kSmallMaxBytes) ? kGrpAutoMaxBinBytesNoX : kGrpAutoMaxBinBytes;
+  return v == STREAM_AUTO && mean_bin_bytes < limit;
 }
 
 template <class P, int NM, int VAR, bool MULTI>
@@ -933,13 +935,14 @@ cudaError_t launch_argminmax_sm(const SeriesDev& single, int64_t total_windows, 
                     sm_count, st);
 }
 
-bool small_call(int64_t n, int64_t nb, tsds_dtype y_dtype) {
+bool small_call(int64_t n, int64_t nb, tsds_dtype y_dtype, bool has_x) {
   const int64_t bytes = n * dtype_size(y_dtype);
   if (nb < 1 || bytes > kSmallMaxBinBytes * nb || variant_override() != STREAM_AUTO) return false;
-  // measured on GB300: up to 256 MB a warp per bin wins from 4 KB bins on,
-  // beyond that from 8 KB bins (below, the lane-group pass is faster)
-  if (bytes <= kSmallMaxBytes) return nb <= 4096 || bytes >= 4096 * nb;
-  return bytes >= 8192 * nb;
+  // measured on GB300 (float32): up to 256 MB a warp per bin wins from 8 KB
+  // bins on; beyond, from 8 KB bins with x and from 32 KB without (below
+  // those the lane-group pass is faster)
+  if (bytes <= kSmallMaxBytes) return nb <= 4096 || bytes >= 8192 * nb;
+  return bytes >= (has_x ? 8192 : 32768) * nb;
 }
 
 template <class P, int NM, bool MULTI>

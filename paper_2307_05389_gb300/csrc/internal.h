@@ -128,9 +128,11 @@ struct GrpShape {
   int64_t max_bin = 0;
 };
 // Lane-group shape for a launch whose bins average mean_bin_bytes: groups of
-// G lanes whose 2*G*kGrpU vectors cover a bin's interior (a bin's first and
-// last vector are taken apart; two rounds of loads per lane measured 8-21 %
-// faster on GB300 than one from 512-byte bins on, the same below), tiles of
+// G lanes whose 4*G*kGrpU vectors cover a bin's interior (a bin's first and
+// last vector are taken apart; on GB300 four rounds of loads per lane
+// measured 10-20 % faster than two from 1 KB bins on, and two lanes per bin
+// 11 % faster than one at 512-byte bins; the per-bin work then weighs less
+// against the streaming), tiles of
 // about 16 KB (each tile's bytes are requested into L2 when it starts: with
 // 32 KB tiles the requests in flight outgrew L2 and 31 % of the lines were
 // fetched twice; 16 KB tiles measured 1.008x the bytes of y and 4.3 TB/s at
@@ -139,7 +141,8 @@ __host__ __device__ inline GrpShape grp_shape(int64_t mean_bin_bytes, int64_t el
   GrpShape g;
   const int64_t inner = mean_bin_bytes / 16 - 1;
   int lg = 0;
-  while (lg < 5 && ((int64_t)kGrpU << (lg + 1)) < inner) ++lg;
+  while (lg < 5 && ((int64_t)kGrpU << (lg + 2)) < inner) ++lg;
+  if (lg == 0 && inner > 16) lg = 1;   // bins of 384 bytes and more: at least two lanes
   g.g_log2 = lg;
   const int64_t groups = 32 >> lg;
   int64_t rounds = (16 * 1024) / (groups * (mean_bin_bytes > 0 ? mean_bin_bytes : 1));
@@ -154,7 +157,9 @@ __host__ __device__ inline int32_t grp_pack(int g_log2, int tile_rounds) { retur
 // lane-group pass (automatic choice below kGrpAutoMaxBinBytes, or forced by
 // tsds_stream_variant(STREAM_GRP)).
 constexpr int64_t kGrpAutoMaxBinBytes = 8 * 1024;
-bool grp_call(int64_t mean_bin_bytes);
+// (bytes: y of the call; without x beyond 256 MB the limit is kGrpAutoMaxBinBytesNoX)
+constexpr int64_t kGrpAutoMaxBinBytesNoX = 32 * 1024;
+bool grp_call(int64_t mean_bin_bytes, int64_t bytes, bool has_x);
 cudaError_t launch_argminmax_grp(const SeriesDev* s_dev, const SeriesDev& single, const int32_t* tile_series,
                                  int64_t total_tiles, WorkCounters* work, tsds_dtype y_dtype, tsds_nan_mode nan,
                                  const GrpShape& shape, cudaStream_t st, const int64_t* total_dev = nullptr,
@@ -190,7 +195,8 @@ cudaError_t launch_argminmax_sm(const SeriesDev& single, int64_t total_windows, 
 
 // Single-series calls with bins of at most 64 KB on average, no explicit
 // streaming variant, and either at most 256 MB of y (at most 4096 bins, or
-// bins of at least 4 KB) or bins of at least 8 KB: a warp per bin in one
+// bins of at least 8 KB) or bins of at least 8 KB (with x; 32 KB without): a
+// warp per bin in one
 // launch (index-bin starts in the kernel,
 // x-space starts from launch_edges first).  With emit (at most
 // kSmallEmitMaxBins bins) the last CTA also emits, with `done` a zeroed
@@ -198,7 +204,7 @@ cudaError_t launch_argminmax_sm(const SeriesDev& single, int64_t total_windows, 
 constexpr int64_t kSmallMaxBinBytes = 64 * 1024;
 constexpr int64_t kSmallMaxBytes = 256ll << 20;
 constexpr int64_t kSmallEmitMaxBins = 1024;
-bool small_call(int64_t n, int64_t nb, tsds_dtype y_dtype);
+bool small_call(int64_t n, int64_t nb, tsds_dtype y_dtype, bool has_x);
 cudaError_t launch_small(const SeriesDev& S, tsds_dtype y_dtype, tsds_nan_mode nan, Algo algo, bool has_x,
                          unsigned* done, bool emit, cudaStream_t st);
 

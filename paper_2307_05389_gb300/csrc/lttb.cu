@@ -134,9 +134,10 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-// Buckets whose mean needs the sequential sum (flagged by k_means or k_p32,
-// which give every other bucket its mean from exact sums, below) take it here, one
-// chain per bucket and coordinate.  A CTA covers 32 buckets with four warps,
+// Large buckets whose mean needs the sequential sum (flagged by k_p32, which
+// gives every other bucket its mean from exact sums, below) take it here, one
+// chain per bucket and coordinate (table mode's small buckets, flagged by
+// k_means, take k_sums_small).  A CTA covers 32 buckets with four warps,
 // one per SM sub-partition: two producer warps stream the flagged buckets'
 // x and y values through a ring of three 32-point chunks in shared memory
 // (lane i copies point i of each bucket's chunk: coalesced cp.async), and two
@@ -255,6 +256,33 @@ __global__ void __launch_bounds__(kSumThreads) k_sums_wide(const LttbJob* __rest
       if (!ign) cnt = n;
       if (n > 0) reinterpret_cast<double*>(J.means)[2 * j + warp] = __ddiv_rn(s, (double)cnt);
     }
+  }
+}
+
+// The same sequential sums for the small buckets of table mode (at most 32
+// points): a thread per flagged bucket adds its x and its y values in index
+// order, so the binary64 adds issued are the points' own (the ring above
+// issues a full 32-point chunk per bucket, and this GPU's FP64 pipe is
+// narrow).
+__global__ void k_sums_small(const LttbJob* __restrict__ jobs) {
+  const LttbJob J = jobs[blockIdx.y];
+  if (J.mode != 0) return;
+  const int64_t m = job_m(J), B = J.B;
+  if (m <= B + 2) return;
+  const bool ign = J.nan == TSDS_NAN_IGNORE;
+  for (int64_t j = 1 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < B; j += (int64_t)gridDim.x * blockDim.x) {
+    if (!J.chain[j]) continue;
+    const int64_t lo = bucket_start(j, m, B), hi = bucket_start(j + 1, m, B);
+    double sx = 0.0, sy = 0.0;
+    int64_t cnt = 0;
+    for (int64_t k = lo; k < hi; ++k) {
+      const double x = J.px[k], y = J.py[k];
+      if (ign && isnan(y)) continue;
+      sx = __dadd_rn(sx, x);
+      sy = __dadd_rn(sy, y);
+      ++cnt;
+    }
+    if (hi > lo) J.means[j] = make_double2(__ddiv_rn(sx, (double)cnt), __ddiv_rn(sy, (double)cnt));
   }
 }
 
@@ -1279,12 +1307,11 @@ tsds_status run_lttb_jobs(const LttbJob* jobs_host, const LttbJob* jobs_dev, int
   const int64_t cap = (int64_t)device_sm_count() * 16;
   if (any_table) {
     note_launch();
-    k_means<<<dim3(grid_for(max_B * 32, 8), (unsigned)count), 256, 0, st>>>(jobs_dev);   // a warp per bucket
+    k_means<<<dim3(grid_for(max_B * 32, 8), (unsigned)count), 256, 0, st>>>(jobs_dev);   // lane groups per bucket
     TSDS_CK(cudaGetLastError());
-    {
-      const tsds_status r = launch_sums(jobs_dev, count, max_B, 0, st);
-      if (r != TSDS_OK) return r;
-    }
+    note_launch();
+    k_sums_small<<<dim3(grid_for(max_B), (unsigned)count), 256, 0, st>>>(jobs_dev);   // flagged buckets
+    TSDS_CK(cudaGetLastError());
     int64_t blocks = (max_B + 7) / 8;
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;

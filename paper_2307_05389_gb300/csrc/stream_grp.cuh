@@ -202,7 +202,7 @@ k_argminmax_grp(const SeriesDev* __restrict__ sd, SeriesDev single, const int32_
         }
       }
       // the last vector, after the interior ones of the lane it falls to
-      if (nv >= 2 && (uint32_t)gj == (nv - 2) % (uint32_t)G) {
+      if (nv >= 2 && (uint32_t)gj == ((nv - 2) & (uint32_t)(G - 1))) {
         uint4 w = vec(nv - 1);
         if (e_last < E) w = grp_mask<T>(w, 0, e_last);
         grp_take(L, w, nv - 1);
