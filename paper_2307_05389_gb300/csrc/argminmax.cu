@@ -73,6 +73,20 @@ __device__ __forceinline__ float fmin_nan(float a, float b) {
 __device__ __forceinline__ float fmax_nan(float a, float b) {
   float r; asm("max.NaN.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b)); return r;
 }
+// three-input forms (sm_100 and later): NaN if any input is NaN (.NaN), else
+// the least / greatest of the non-NaN inputs
+__device__ __forceinline__ float fmin3_nan(float a, float b, float c) {
+  float r; asm("min.NaN.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c)); return r;
+}
+__device__ __forceinline__ float fmax3_nan(float a, float b, float c) {
+  float r; asm("max.NaN.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c)); return r;
+}
+__device__ __forceinline__ float fmin3_num(float a, float b, float c) {
+  float r; asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c)); return r;
+}
+__device__ __forceinline__ float fmax3_num(float a, float b, float c) {
+  float r; asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c)); return r;
+}
 
 template <class T, int E>
 __device__ __forceinline__ T vec_elem(const uint4& v, int e) {
@@ -110,14 +124,21 @@ struct PolF32 {
   __device__ static void group1(const uint4& v, Acc& gmin, Acc& gmax) {
     const float f0 = __uint_as_float(v.x), f1 = __uint_as_float(v.y);
     const float f2 = __uint_as_float(v.z), f3 = __uint_as_float(v.w);
-    gmin = mn(mn(f0, f1), mn(f2, f3));
-    gmax = mx(mx(f0, f1), mx(f2, f3));
+    if (NM == TSDS_NAN_PROPAGATE) {
+      gmin = fmin3_nan(f0, f1, fmin_nan(f2, f3));
+      gmax = fmax3_nan(f0, f1, fmax_nan(f2, f3));
+    } else {
+      gmin = fmin3_num(f0, f1, fminf(f2, f3));
+      gmax = fmax3_num(f0, f1, fmaxf(f2, f3));
+    }
   }
+  // propagate: g < r, or g NaN and r not; ignore: g < r, or r NaN and g not
+  // (!(g >= r) holds for g < r and whenever either is NaN)
   __device__ static bool better_min(Acc g, Acc r) {
-    return NM == TSDS_NAN_PROPAGATE ? (g < r || (isnan(g) && !isnan(r))) : (g < r || (isnan(r) && !isnan(g)));
+    return NM == TSDS_NAN_PROPAGATE ? (!(g >= r) && r == r) : (!(g >= r) && g == g);
   }
   __device__ static bool better_max(Acc g, Acc r) {
-    return NM == TSDS_NAN_PROPAGATE ? (g > r || (isnan(g) && !isnan(r))) : (g > r || (isnan(r) && !isnan(g)));
+    return NM == TSDS_NAN_PROPAGATE ? (!(g <= r) && r == r) : (!(g <= r) && g == g);
   }
   __device__ static bool match(T e, Acc t) { return isnan(t) ? isnan(e) : e == t; }
   __device__ static bool match_min(T e, Acc t) { return match(e, t); }

@@ -117,7 +117,11 @@ constexpr int64_t kPrefetchOffBinBytes = 1ll << 40;
 // counted in work->large (max_bin 0: none is left out).  Single series: s_dev
 // null; batched: tile_series maps tiles to series (win_base = first tile).
 constexpr int kGrpTileMaxBins = 128;   // bins per lane-group tile at most
-constexpr int kGrpU = 8;               // vectors per lane in flight
+// vectors a lane loads before it uses any of them: 16 for elements of up to
+// 4 bytes, 8 for 8-byte elements (whose 64-bit keys take twice the registers)
+constexpr int kGrpU = 16;
+constexpr int kGrpU64 = 8;
+__host__ __device__ constexpr int grp_unroll(int64_t elem_bytes) { return elem_bytes == 8 ? kGrpU64 : kGrpU; }
 // Bins above this size are left to the windowed register-streaming pass (a
 // group reads a bin at a few GB/s, so one huge x-space bin would otherwise
 // hold up the launch).
@@ -128,7 +132,7 @@ struct GrpShape {
   int64_t max_bin = 0;
 };
 // Lane-group shape for a launch whose bins average mean_bin_bytes: groups of
-// G lanes whose 4*G*kGrpU vectors cover a bin's interior (a bin's first and
+// G lanes whose 4*G*U vectors (U = grp_unroll) cover a bin's interior (a bin's first and
 // last vector are taken apart; on GB300 four rounds of loads per lane
 // measured 10-20 % faster than two from 1 KB bins on, and two lanes per bin
 // 11 % faster than one at 512-byte bins; the per-bin work then weighs less
@@ -141,7 +145,7 @@ __host__ __device__ inline GrpShape grp_shape(int64_t mean_bin_bytes, int64_t el
   GrpShape g;
   const int64_t inner = mean_bin_bytes / 16 - 1;
   int lg = 0;
-  while (lg < 5 && ((int64_t)kGrpU << (lg + 2)) < inner) ++lg;
+  while (lg < 5 && ((int64_t)grp_unroll(elem_bytes) << (lg + 2)) < inner) ++lg;
   if (lg == 0 && inner > 16) lg = 1;   // bins of 384 bytes and more: at least two lanes
   g.g_log2 = lg;
   const int64_t groups = 32 >> lg;

@@ -14,7 +14,7 @@
 //    the bin replaced by one inside it (which changes neither extremum);
 //  * the interior vectors are dealt to the group's lanes round-robin, so every
 //    load instruction reads G*16 contiguous bytes per group, and each lane
-//    issues kGrpU loads before it uses any of them;
+//    issues grp_unroll loads before it uses any of them;
 //  * a vector reduces to one group minimum and maximum with the policy's
 //    packed instructions (value space, as in the other variants); a lane keeps
 //    its running extremum and the number of the vector it came from, replacing
@@ -31,6 +31,10 @@ constexpr int kGrpThreads = 256;   // 8 warps per CTA
 // shared memory) and its first kGrpPrefetchBytes are requested into L2 when
 // it starts.
 constexpr int64_t kGrpPrefetchBytes = 64 * 1024;
+// Only tiles whose bins average less than this are requested into L2: larger
+// bins give each lane enough loads in flight on their own, and there the
+// requests measured 2-6 % slower.
+constexpr int64_t kGrpPrefetchMaxBin = 4 * 1024;
 
 // Replaces the elements of v outside positions [e_lo, e_hi) by element e_lo
 // (which lies inside).
@@ -96,19 +100,18 @@ template <class P>
 __device__ __forceinline__ void grp_take(GrpLane<P>& L, const uint4& w, uint32_t r) {
   typename P::Acc gmin, gmax;
   P::group1(w, gmin, gmax);
-  if (!L.valid || P::better_min(gmin, L.rmin)) {
+  if (P::better_min(gmin, L.rmin)) {
     L.rmin = gmin;
     L.pmin = r;
   }
-  if (!L.valid || P::better_max(gmax, L.rmax)) {
+  if (P::better_max(gmax, L.rmax)) {
     L.rmax = gmax;
     L.pmax = r;
   }
-  L.valid = true;
 }
 
 template <class P, int NM, bool MULTI>
-__global__ void __launch_bounds__(kGrpThreads, 3)
+__global__ void __launch_bounds__(kGrpThreads, 2)
 k_argminmax_grp(const SeriesDev* __restrict__ sd, SeriesDev single, const int32_t* __restrict__ tile_series,
                 int64_t total_tiles, WorkCounters* __restrict__ work, int g_log2, int tile_rounds,
                 int64_t max_bin, const int64_t* __restrict__ total_dev) {
@@ -151,7 +154,8 @@ k_argminmax_grp(const SeriesDev* __restrict__ sd, SeriesDev single, const int32_
     {
       const int64_t e0 = ts[0], e1 = ts[nts];
       const char* pa = reinterpret_cast<const char*>(y + e0);
-      const int64_t bytes = min((e1 - e0) * (int64_t)sizeof(T), kGrpPrefetchBytes);
+      const int64_t tb = (e1 - e0) * (int64_t)sizeof(T);
+      const int64_t bytes = tb < kGrpPrefetchMaxBin * nts ? min(tb, kGrpPrefetchBytes) : 0;
       for (int64_t q = 128 * (int64_t)lane; q < bytes; q += 32 * 128) asm volatile("prefetch.global.L2 [%0];" ::"l"(pa + q));
     }
     for (int64_t bb = b_first; bb < b_end; bb += groups) {
@@ -177,27 +181,63 @@ k_argminmax_grp(const SeriesDev* __restrict__ sd, SeriesDev single, const int32_
       const uint4* __restrict__ bp = gbase + v_lo;
       // vector r of the bin (the array-end form only when a vector of the bin can reach outside)
       auto vec = [&](uint32_t r) { return at_ends ? grp_load<T>(gbase, y, v_lo + r, d, S.n) : ldg_vec(bp + r); };
-      GrpLane<P> L;
-      L.valid = false;
-      // vector 0 (partly outside the bin unless the bin starts on a vector) on the group's first lane
-      if (gj == 0 && nv > 0) {
-        uint4 w = vec(0);
-        const int e_hi = nv == 1 ? e_last : E;
-        if (e_first > 0 || e_hi < E) w = grp_mask<T>(w, e_first, e_hi);
-        grp_take(L, w, 0u);
-      }
-      // interior vectors 1 .. nv-2, dealt round-robin: lane gj takes 1 + gj, 1 + gj + G, ...
+      // interior vectors 1 .. nv-2 (inside the bin, so inside the array) are
+      // dealt round-robin: lane gj takes 1 + gj, 1 + gj + G, ...  Every lane
+      // of the group also takes vector 0 (one broadcast load; partly outside
+      // the bin unless the bin starts on a vector), so no vector needs a
+      // first-take test.  Vector 0 and the first round's loads are issued
+      // before any of them is used; then the rounds of G*U vectors that
+      // lie wholly inside the bin run without a test per load, and one
+      // partial round ends the bin (the same split for every lane of the
+      // group, so the group stays converged).
       const uint32_t ni = nv >= 2 ? nv - 2 : 0u;
-      for (uint32_t q0 = (uint32_t)gj; q0 < ni; q0 += (uint32_t)(G * kGrpU)) {
-        uint4 v[kGrpU];
+      const uint4* __restrict__ ip = bp + 1;
+      const uint32_t step = (uint32_t)G;
+      constexpr int U = grp_unroll(sizeof(T));
+      const uint32_t round = step * U;
+      GrpLane<P> L;
+      L.valid = nv > 0;
+      {
+        uint4 w = make_uint4(0u, 0u, 0u, 0u);
+        if (L.valid) w = vec(0);
+        uint4 v[U];
 #pragma unroll
-        for (int u = 0; u < kGrpU; ++u) {
-          const uint32_t q = q0 + (uint32_t)(G * u);
-          v[u] = q < ni ? vec(1u + q) : make_uint4(0u, 0u, 0u, 0u);
+        for (int u = 0; u < U; ++u) {
+          const uint32_t q = (uint32_t)gj + step * u;
+          v[u] = q < ni ? ldg_vec(ip + q) : make_uint4(0u, 0u, 0u, 0u);
+        }
+        if (L.valid) {
+          const int e_hi = nv == 1 ? e_last : E;
+          if (e_first > 0 || e_hi < E) w = grp_mask<T>(w, e_first, e_hi);
+          P::group1(w, L.rmin, L.rmax);
+          L.pmin = L.pmax = 0u;
         }
 #pragma unroll
-        for (int u = 0; u < kGrpU; ++u) {
-          const uint32_t q = q0 + (uint32_t)(G * u);
+        for (int u = 0; u < U; ++u) {
+          const uint32_t q = (uint32_t)gj + step * u;
+          if (q < ni) grp_take(L, v[u], 1u + q);
+        }
+      }
+      uint32_t r0 = round;
+      for (; r0 + round <= ni; r0 += round) {
+        const uint32_t q0 = r0 + (uint32_t)gj;
+        uint4 v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) v[u] = ldg_vec(ip + q0 + step * u);
+#pragma unroll
+        for (int u = 0; u < U; ++u) grp_take(L, v[u], 1u + q0 + step * u);
+      }
+      if (r0 < ni) {
+        const uint32_t q0 = r0 + (uint32_t)gj;
+        uint4 v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const uint32_t q = q0 + step * u;
+          v[u] = q < ni ? ldg_vec(ip + q) : make_uint4(0u, 0u, 0u, 0u);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const uint32_t q = q0 + step * u;
           if (q < ni) grp_take(L, v[u], 1u + q);
         }
       }
