@@ -579,17 +579,16 @@ def aggregate_ranks(ms_local, bytes_local, dist=None, device=None):
 
 def stream_kernel_name(n, n_out, forced, itemsize=4, has_x=True):
     """The streaming kernel a MinMax launch of this shape runs (the library's automatic rule for a
-    single series: a warp per bin up to 256 MB with bins of at least 8 KB, and beyond with bins of
-    at least 8 KB with x or 32 KB without; otherwise lane groups below 8 KB mean bins (32 KB
-    without x beyond 256 MB), register streaming above)."""
+    single series: up to 256 MB a warp per bin with bins of at least 8 KB or at most 4096 bins of
+    at most 64 KB, else lane groups below 8 KB mean bins; beyond 256 MB lane groups below 64 KB
+    mean bins; register streaming above)."""
     v = forced
     nb = max(n_out // 2, 1)
     bytes_ = n * itemsize
     if v == "auto":
         big = bytes_ > 256 << 20
-        small = bytes_ <= nb * 65536 and ((not big and (nb <= 4096 or bytes_ >= 8192 * nb))
-                                         or (big and bytes_ >= (8192 if has_x else 32768) * nb))
-        limit = 32768 if (big and not has_x) else 8192
+        small = (not big) and bytes_ <= nb * 65536 and (nb <= 4096 or bytes_ >= 8192 * nb)
+        limit = 65536 if big else 8192
         v = "small" if small else "grp" if bytes_ / nb < limit else "ldg"
     return {"ldg": "tsds::k_argminmax_ldg (register streaming)", "seg": "tsds::k_argminmax_seg (segmented)",
             "ring": "tsds::k_argminmax (shared-memory ring)", "grp": "tsds::k_argminmax_grp (lane groups)",

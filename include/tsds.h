@@ -368,16 +368,17 @@ tsds_status tsds_check_wait_timeout(unsigned rounds, void* stream);
 
 /* Kernel variant of the streaming argmin/argmax pass for every later call in
  * the process (no counterpart in the paper, whose CPU kernel has one form):
- *   0  automatic (the default).  Single-series calls: a warp per bin in one
- *      launch for inputs of at most 256 MB with bins of at least 8 KB (or at
- *      most 4096 bins) and for larger inputs with bins of at least 8 KB (with
- *      x) or 32 KB (without); otherwise variant 4 when the mean bin is below
- *      8 KB (32 KB without x beyond 256 MB), variant 2 above.
+ *   0  automatic (the default).  Single-series calls of at most 256 MB: a
+ *      warp per bin in one launch with bins of at least 8 KB (or at most 4096
+ *      bins of at most 64 KB), else variant 4 below 8 KB mean bins and
+ *      variant 2 above; larger calls: variant 4 below 64 KB mean bins,
+ *      variant 2 above.
  *      Batches and served queries: series or queries are grouped by bin size
- *      (variant 4 below 8 KB for batches without x and for queries, a warp
- *      per bin up to 64 KB, variant 2 above; batches with x take variant 3
- *      below 768 bytes (8-byte y), 1.5 KB (4-byte), 1 KB (2-byte) or 512
- *      bytes (1-byte));
+ *      (variant 4 below 64 KB for batches without x and below 32 KB for
+ *      queries, a warp per bin from there up to 64 KB, variant 2 above;
+ *      batches with x take variant 3 below 768 bytes (8-byte y), 1.5 KB
+ *      (4-byte), 1 KB (2-byte) or 512 bytes (1-byte), a warp per bin up to
+ *      64 KB);
  *   1  shared-memory ring (bulk async copies into shared memory, one warp
  *      per bin);
  *   2  register streaming, one warp per bin;

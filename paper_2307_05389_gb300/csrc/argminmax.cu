@@ -853,8 +853,9 @@ int stream_variant_for(const StreamConfig& cfg, int64_t elem_bytes) {
 bool grp_call(int64_t mean_bin_bytes, int64_t bytes, bool has_x) {
   const int v = variant_override();
   if (v == STREAM_GRP) return true;
-  // without x and beyond 256 MB the lane groups also win at 8-16 KB bins
-  const int64_t limit = (!has_x && bytes > kSmallMaxBytes) ? kGrpAutoMaxBinBytesNoX : kGrpAutoMaxBinBytes;
+  // beyond 256 MB the lane groups also win at 8-32 KB bins (with x and without)
+  (void)has_x;
+  const int64_t limit = bytes > kSmallMaxBytes ? kGrpAutoMaxBinBytesLarge : kGrpAutoMaxBinBytes;
   return v == STREAM_AUTO && mean_bin_bytes < limit;
 }
 
@@ -960,10 +961,11 @@ bool small_call(int64_t n, int64_t nb, tsds_dtype y_dtype, bool has_x) {
   const int64_t bytes = n * dtype_size(y_dtype);
   if (nb < 1 || bytes > kSmallMaxBinBytes * nb || variant_override() != STREAM_AUTO) return false;
   // measured on GB300 (float32): up to 256 MB a warp per bin wins from 8 KB
-  // bins on; beyond, from 8 KB bins with x and from 32 KB without (below
-  // those the lane-group pass is faster)
+  // bins on (below, the lane-group pass is faster); beyond 256 MB the lane
+  // groups win up to 64 KB bins and the windowed pass from there
+  (void)has_x;
   if (bytes <= kSmallMaxBytes) return nb <= 4096 || bytes >= 8192 * nb;
-  return bytes >= (has_x ? 8192 : 32768) * nb;
+  return false;
 }
 
 template <class P, int NM, bool MULTI>

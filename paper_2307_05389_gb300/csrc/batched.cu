@@ -50,7 +50,7 @@ struct BatchLayout {
   // kSmallMaxBinBytes (a warp per bin, mid_ctas CTAs, no windows).  With an
   // explicit variant every series is cut into windows.
   // Group 3 (automatic variant, batches without x): bins below
-  // kGrpAutoMaxBinBytes run in the lane-group pass, grp_tiles tiles.
+  // kGrpBatchedMaxBinBytes run in the lane-group pass, grp_tiles tiles.
   std::vector<uint8_t> group;
   int64_t split_windows = 0, mid_ctas = 0, grp_tiles = 0;
   int64_t elem = 1;
@@ -198,7 +198,7 @@ static BatchLayout make_layout(tsds_algo algo, const tsds_series* s, int64_t cou
       wbin += bytes * (bytes / (double)d.nb);
       const double bin = bytes / (double)d.nb;
       int g = bin < (double)seg_max_bin_bytes(dtype_size(y_dtype)) ? 1 : bin <= (double)kSmallMaxBinBytes ? 2 : 0;
-      if (grp_ok && bin < (double)kGrpAutoMaxBinBytes) g = 3;
+      if (grp_ok && bin < (double)kGrpBatchedMaxBinBytes) g = 3;
       L.group[(size_t)i] = (uint8_t)g;
       if (g < 3) {
         gsum[g] += bytes;

@@ -137,10 +137,9 @@ struct GrpShape {
 // measured 10-20 % faster than two from 1 KB bins on, and two lanes per bin
 // 11 % faster than one at 512-byte bins; the per-bin work then weighs less
 // against the streaming), tiles of
-// about 16 KB (each tile's bytes are requested into L2 when it starts: with
-// 32 KB tiles the requests in flight outgrew L2 and 31 % of the lines were
-// fetched twice; 16 KB tiles measured 1.008x the bytes of y and 4.3 TB/s at
-// 1 KB bins against 3.9).
+// about 16 KB (a tile of bins below 4 KB has its bytes requested into L2 when
+// it starts: with 32 KB tiles the requests in flight outgrew L2 and 31 % of
+// the lines were fetched twice; 16 KB tiles measured 1.008x the bytes of y).
 __host__ __device__ inline GrpShape grp_shape(int64_t mean_bin_bytes, int64_t elem_bytes) {
   GrpShape g;
   const int64_t inner = mean_bin_bytes / 16 - 1;
@@ -161,8 +160,15 @@ __host__ __device__ inline int32_t grp_pack(int g_log2, int tile_rounds) { retur
 // lane-group pass (automatic choice below kGrpAutoMaxBinBytes, or forced by
 // tsds_stream_variant(STREAM_GRP)).
 constexpr int64_t kGrpAutoMaxBinBytes = 8 * 1024;
-// (bytes: y of the call; without x beyond 256 MB the limit is kGrpAutoMaxBinBytesNoX)
-constexpr int64_t kGrpAutoMaxBinBytesNoX = 32 * 1024;
+// (bytes: y of the call; beyond 256 MB the limit is kGrpAutoMaxBinBytesLarge)
+constexpr int64_t kGrpAutoMaxBinBytesLarge = 64 * 1024;
+// Batches without x: series whose bins average below this run in the
+// lane-group pass (the 4096-series batch measured 2.68 ms for MinMax on GB300
+// with this limit, 2.91 ms with 8 KB and a warp per bin above).
+constexpr int64_t kGrpBatchedMaxBinBytes = 64 * 1024;
+// Served queries: bins below this run in the lane-group pass (x-space bins;
+// larger bins of such a query go to the windowed pass).
+constexpr int64_t kGrpServedMaxBinBytes = 32 * 1024;
 bool grp_call(int64_t mean_bin_bytes, int64_t bytes, bool has_x);
 cudaError_t launch_argminmax_grp(const SeriesDev* s_dev, const SeriesDev& single, const int32_t* tile_series,
                                  int64_t total_tiles, WorkCounters* work, tsds_dtype y_dtype, tsds_nan_mode nan,

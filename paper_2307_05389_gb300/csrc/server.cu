@@ -532,7 +532,7 @@ tsds_status launch_batch(const Server& S, Slot& sl, const std::vector<tsds_query
   note_launch();
   k_resolve<<<(count + 7) / 8, 256, 0, st>>>(dq, dsd, windows, small, count, (int)S.x_dtype, (int)ys,
                                              has_x ? (int)dtype_size(S.x_dtype) : 0, welems,
-                                             can_split ? kGrpAutoMaxBinBytes : 0);
+                                             can_split ? kGrpServedMaxBinBytes : 0);
   SV_CK(cudaGetLastError());
   note_launch();
   k_scan_windows<<<1, 1024, 0, st>>>(dsd, windows, small, count, total_dev);

@@ -1,20 +1,23 @@
 // stream_grp.cuh -- the lane-group variant of the per-bin argmin/argmax pass
 // (included by argminmax.cu after the policies and stream_seg.cuh, whose
-// packed (key, offset) runs it reuses), for bins of a few bytes to a few KB.
+// packed (key, offset) runs it reuses), for bins of a few bytes to tens of KB.
 //
 // The windowed variants give a bin to a whole warp, or walk bin boundaries
 // inside a warp-wide stream; both pay a fixed cost per bin that dominates when
 // bins are small.  Here a warp claims a tile of up to kGrpTileMaxBins
 // consecutive whole bins, stages their starts in shared memory with one
-// coalesced load, asks L2 for the tile's bytes, and splits into 32/G groups of
-// G lanes (G a power of two chosen from the mean bin size), each group
-// reducing one whole bin at a time:
-//  * a bin's first and last 16-byte vector, which may hold elements of the
-//    neighbouring bins, are taken by one lane each, with the elements outside
-//    the bin replaced by one inside it (which changes neither extremum);
+// coalesced load, asks L2 for the tile's bytes when its bins are small, and
+// splits into 32/G groups of G lanes (G a power of two chosen from the mean
+// bin size), each group reducing one whole bin at a time:
+//  * a bin's first and last 16-byte vector may hold elements of the
+//    neighbouring bins; those are replaced by one inside the bin (which
+//    changes neither extremum).  Every lane of the group starts from the
+//    first vector (one broadcast load), so its running extremum is defined
+//    from the start; the last vector goes to one lane;
 //  * the interior vectors are dealt to the group's lanes round-robin, so every
 //    load instruction reads G*16 contiguous bytes per group, and each lane
-//    issues grp_unroll loads before it uses any of them;
+//    issues grp_unroll loads (16, or 8 for 8-byte elements) before it uses
+//    any of them; the first vector is loaded together with the first round;
 //  * a vector reduces to one group minimum and maximum with the policy's
 //    packed instructions (value space, as in the other variants); a lane keeps
 //    its running extremum and the number of the vector it came from, replacing
