@@ -875,7 +875,7 @@ def main():
         e2e = {"value": sum(per.values()) * args.e2e_steps * world / dt / 1e9, "unit": "GB/s",
                "h2d_bytes_per_step": int(yh.numel() * ysz), "d2h_bytes_per_step": int(d2h),
                "x_read_in_place_bytes_per_step": int(probes),
-               "api": "paper_2307_05389_gb300.downsample_host (pinned y copied, pinned x searched in place)"}
+               "api": "paper_2307_05389_gb300.downsample_host -> tsds_downsample_host (pinned y copied in chunks that overlap the reduction, pinned x searched in place)"}
         del yh, xh, yd, xd
 
     # ---- CPU oracle on a bounded sample (rank 0)

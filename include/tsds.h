@@ -130,6 +130,42 @@ tsds_status tsds_m4_bins(const void* x, tsds_dtype x_dtype, const void* y, tsds_
                          int64_t n, int64_t n_out, int64_t bin_lo, int64_t bin_hi, tsds_nan_mode nan,
                          int64_t* out, int64_t* out_count, void* stream);
 
+/* Host-buffer form of MinMax and M4 (the paper's downsample([x], y, n_out),
+ * Section 2.3, on a series in host memory), for one or more of them over the
+ * same series, returning the indices in host memory.
+ *   count                 number of algorithms, 1..16;
+ *   algos[i], n_outs[i]   TSDS_ALGO_MINMAX or TSDS_ALGO_M4 and its n_out (a
+ *                         positive multiple of 2 or 4; n_out >= n returns
+ *                         every index, as tsds_minmax/tsds_m4 do);
+ *   x, x_dtype            optional sorted x (NULL: index bins), either device
+ *                         memory or page-locked host memory; it is read in
+ *                         place by the bin search, which probes about log2(n)
+ *                         values per bin, so it is never copied;
+ *   y_host, y_dtype, n    y in host memory (page-locked memory lets the copies
+ *                         overlap the reduction; pageable memory works too);
+ *   y_dev                 optional device buffer of n * size(y_dtype) bytes,
+ *                         aligned to the element size, that receives y (it
+ *                         holds y on return); NULL: the library takes one from
+ *                         its pool for the call;
+ *   outs_host[i]          host buffer for min(n_outs[i], n) int64 indices;
+ *   counts_host[i]        receives how many were written.
+ * y goes to the device in chunks (an eighth of it, between 16 and 256 MB) on
+ * a private stream that first waits for the work already queued on `stream`;
+ * after each chunk, the bins whose points have all arrived are reduced on
+ * `stream` (bin ranges, as in tsds_minmax_bins), so the copy and the
+ * reduction overlap; the ranges' outputs are joined on the host in bin order.
+ * The result equals tsds_minmax / tsds_m4 on the same series.  Synchronous:
+ * returns when every output is in host memory (`stream` is synchronised).
+ * Errors: TSDS_EINVAL for the argument errors of tsds_minmax/tsds_m4, for a
+ * count, algorithm, NULL output or misaligned y_dev, and for an x that is
+ * pageable host memory (checked before any device work); CUDA failures as in
+ * the other calls; a device-side failure of the streaming pass is returned as
+ * its status. */
+tsds_status tsds_downsample_host(int count, const int* algos, const int64_t* n_outs, const void* x,
+                                 tsds_dtype x_dtype, const void* y_host, tsds_dtype y_dtype, int64_t n,
+                                 tsds_nan_mode nan, void* y_dev, int64_t* const* outs_host, int64_t* counts_host,
+                                 void* stream);
+
 /* EveryNth (Section 1 names it among the algorithms; reading): the n_out bins
  * MinMax/M4 lay out (index space without x: bin i starts at
  * ceil(i(n-1)/n_out); equal-width x ranges with x) and the first point of

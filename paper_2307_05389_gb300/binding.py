@@ -53,6 +53,9 @@ def load(path: str = LIB_PATH):
         f = getattr(lib, name)
         f.argtypes = [p, c_int, p, c_int, i64, i64, i64, i64, c_int, p, p, p]
         f.restype = c_int
+    lib.tsds_downsample_host.argtypes = [c_int, ctypes.POINTER(c_int), ctypes.POINTER(i64), p, c_int, p, c_int, i64,
+                                         c_int, p, ctypes.POINTER(p), ctypes.POINTER(i64), p]
+    lib.tsds_downsample_host.restype = c_int
     lib.tsds_last_error.argtypes = []
     lib.tsds_last_error.restype = ctypes.c_char_p
     lib.tsds_shutdown.argtypes = []
@@ -225,6 +228,14 @@ def tsds_minmax_bins(x, x_dtype, y, y_dtype, n, n_out, bin_lo, bin_hi, nan, out,
 
 def tsds_m4_bins(x, x_dtype, y, y_dtype, n, n_out, bin_lo, bin_hi, nan, out, out_count, stream):
     return load().tsds_m4_bins(x, x_dtype, y, y_dtype, n, n_out, bin_lo, bin_hi, nan, out, out_count, stream)
+
+
+def tsds_downsample_host(count, algos, n_outs, x, x_dtype, y_host, y_dtype, n, nan, y_dev, outs_host, counts_host,
+                         stream):
+    """algos, n_outs: ctypes int / int64 arrays; outs_host: ctypes array of host pointers;
+    counts_host: ctypes int64 array (see tsds.h)."""
+    return load().tsds_downsample_host(count, algos, n_outs, x, x_dtype, y_host, y_dtype, n, nan, y_dev, outs_host,
+                                       counts_host, stream)
 
 
 def tsds_minmax_noalloc(x, x_dtype, y, y_dtype, n, n_out, nan, out, out_count, stream):
@@ -658,15 +669,20 @@ def downsample_bins(algo, y, n_out, bin_lo, bin_hi, x=None, nan="propagate", str
 
 def downsample_host(algos, y, n_out, x=None, nan="propagate", minmax_ratio=4, device="cuda",
                     y_dev=None, x_dev=None):
-    """Host-buffer form: copies y from host memory to the device once
-    (asynchronously when the host tensor is pinned), runs each algorithm in
-    `algos` on the GPU and copies each index list back.  A pinned x is read in
-    place by the bin search of MinMax, M4 and EveryNth (which probes only
-    about log2(n) values per bin); otherwise x is copied too.  Returns a list
-    of CPU int64 tensors.  y_dev / x_dev may supply preallocated device
-    buffers to copy into."""
+    """Host-buffer form: y (a CPU tensor) goes to the device, each algorithm in
+    `algos` runs on the GPU and each index list comes back as a CPU int64
+    tensor.  When every algorithm is MinMax or M4 this is one
+    tsds_downsample_host call: y is copied in chunks that overlap the
+    reduction of the bins already on the device.  Otherwise y is copied once
+    and the single-series calls run on the copy.  A pinned (or device) x is
+    read in place by the bin search of MinMax, M4 and EveryNth (which probes
+    only about log2(n) values per bin); otherwise x is copied too.  y_dev /
+    x_dev may supply preallocated device buffers to copy into."""
     import torch
     st = torch.cuda.current_stream(device)
+    if (not y.is_cuda and y.is_contiguous() and len(algos) > 0
+            and all(a in ("minmax", "m4") for a in algos)):
+        return _downsample_host_native(algos, y, n_out, x, nan, device, y_dev, x_dev, st)
     yd = y_dev if y_dev is not None else torch.empty_like(y, device=device)
     yd.copy_(y, non_blocking=True)
     xp, xd = None, 0
@@ -703,6 +719,33 @@ def downsample_host(algos, y, n_out, x=None, nan="propagate", minmax_ratio=4, de
             raise TsdsError(-k, "the streaming pass reported a device-side failure")
         res.append(out[:k].cpu())
     return res
+
+
+def _downsample_host_native(algos, y, n_out, x, nan, device, y_dev, x_dev, st):
+    import torch
+    n = y.shape[0]
+    xp, xd = None, 0
+    if x is not None:
+        if x.is_cuda or x.is_pinned():
+            xp = x.data_ptr()
+        else:
+            xdev = x_dev if x_dev is not None else torch.empty_like(x, device=device)
+            xdev.copy_(x, non_blocking=False)
+            xp = xdev.data_ptr()
+        xd = DTYPES[_torch_dtype_name(x)]
+    k = len(algos)
+    codes = (ctypes.c_int * k)(*[{"minmax": 0, "m4": 1}[a] for a in algos])
+    n_outs = (ctypes.c_int64 * k)(*([int(n_out)] * k))
+    outs = [torch.empty(max(min(int(n_out), n), 1), dtype=torch.int64) for _ in algos]
+    ptrs = (ctypes.c_void_p * k)(*[o.data_ptr() for o in outs])
+    counts = (ctypes.c_int64 * k)()
+    with torch.cuda.device(device):
+        r = tsds_downsample_host(k, codes, n_outs, xp, xd, y.data_ptr(), DTYPES[_torch_dtype_name(y)], n,
+                                 NAN_MODES[nan], y_dev.data_ptr() if y_dev is not None else None, ptrs, counts,
+                                 ctypes.c_void_p(st.cuda_stream))
+    if r != 0:
+        raise TsdsError(r, last_error())
+    return [o[:int(c)] for o, c in zip(outs, counts)]
 
 
 class _Downsampler:

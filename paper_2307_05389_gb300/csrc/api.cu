@@ -6,6 +6,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <atomic>
 #include <map>
 #include <mutex>
@@ -331,15 +332,17 @@ tsds_status run_binned_series(const void* x, tsds_dtype x_dtype, const void* y, 
 // size limit go to a register-streaming pass over the windows that skips
 // every other bin and exits at once when there is none), then the emit of
 // those bins.  Output: what those bins select, in order.
+// edges: the whole series' bin starts already on the device, or null to
+// compute them here.
 static tsds_status run_binned_range(const void* x, tsds_dtype x_dtype, const void* y, tsds_dtype y_dtype,
                                     int64_t n, int64_t nb, int64_t b0, int64_t b1, tsds_nan_mode nan, Algo algo,
-                                    int64_t* out, int64_t* out_count, cudaStream_t st) {
+                                    int64_t* out, int64_t* out_count, cudaStream_t st, int64_t* edges = nullptr) {
   const int64_t k = b1 - b0;
   const int64_t elem = dtype_size(y_dtype);
   const int64_t welems = kWindowBytes / elem;
   const int64_t windows = (n + welems - 1) / welems;
   size_t o = 0;
-  const size_t o_edges = o; o = align_up(o + (size_t)(nb + 1) * 8, 256);
+  const size_t o_edges = o; o = align_up(o + (size_t)(edges ? 0 : nb + 1) * 8, 256);
   const size_t o_res = o;   o = align_up(o + (size_t)k * 16, 256);
   const size_t o_cnt = o;   o = align_up(o + (size_t)k * 4, 256);
   const size_t o_work = o;  o = align_up(o + 2 * sizeof(WorkCounters), 256);
@@ -356,8 +359,8 @@ static tsds_status run_binned_range(const void* x, tsds_dtype x_dtype, const voi
   S.x = x;
   S.n = n;
   S.nb = nb;
-  S.edges = reinterpret_cast<int64_t*>(base + o_edges);
-  TSDS_CK(launch_edges(nullptr, 1, &S, x != nullptr, x_dtype, nb, st));
+  S.edges = edges ? edges : reinterpret_cast<int64_t*>(base + o_edges);
+  if (!edges) TSDS_CK(launch_edges(nullptr, 1, &S, x != nullptr, x_dtype, nb, st));
   // the range as a series of its own: its bins' starts are the whole series' starts b0..b1
   WorkCounters* w = reinterpret_cast<WorkCounters*>(base + o_work);
   S.nb = k;
@@ -411,6 +414,191 @@ static tsds_status binned_range_entry(Algo algo, const void* x, tsds_dtype x_dty
     return TSDS_OK;
   }
   return run_binned_range(x, x_dtype, y, y_dtype, n, nb, bin_lo, bin_hi, nan, algo, out, out_count, st);
+}
+
+// Host-buffer form: y is copied to the device in chunks on a private stream;
+// after each chunk the bins whose points have all arrived are reduced on the
+// caller's stream (bin ranges over the whole series' bin starts, Section 2.2's
+// independent bins), so the copy and the reduction overlap; the range outputs
+// are compacted on the host in bin order.
+static int64_t host_chunk_bytes(int64_t total) {
+  int64_t c = total / 8;
+  const int64_t lo = 16ll << 20, hi = 256ll << 20;
+  c = c < lo ? lo : c > hi ? hi : c;
+  return c / 64 * 64;
+}
+
+struct HostJob {
+  Algo algo = ALGO_MINMAX;
+  int per = 2;
+  int64_t nb = 0;
+  int64_t* edges_dev = nullptr;
+  int64_t* out_dev = nullptr;
+  int64_t* cnt_dev = nullptr;
+  std::vector<int64_t> edges;
+  std::vector<int64_t> range_lo;   // first bin of each range (ranges in bin order)
+};
+
+static tsds_status host_entry(int count, const int* algos, const int64_t* n_outs, const void* x, tsds_dtype x_dtype,
+                              const void* y_host, tsds_dtype y_dtype, int64_t n, tsds_nan_mode nan, void* y_dev,
+                              int64_t* const* outs_host, int64_t* counts_host, void* stream) {
+  g_err[0] = 0;
+  const char* who = "tsds_downsample_host";
+  if (count < 1 || count > 16) return fail(TSDS_EINVAL, "%s: count must be in [1, 16] (got %d)", who, count);
+  if (!algos || !n_outs || !outs_host || !counts_host)
+    return fail(TSDS_EINVAL, "%s: algos, n_outs, outs_host and counts_host must not be NULL", who);
+  tsds_status s = check_common(x, x_dtype, y_host, y_dtype, n, nan, outs_host[0], counts_host);
+  if (s != TSDS_OK) return s;
+  for (int i = 0; i < count; ++i) {
+    if (algos[i] != TSDS_ALGO_MINMAX && algos[i] != TSDS_ALGO_M4)
+      return fail(TSDS_EINVAL, "%s: algos[%d] = %d is neither TSDS_ALGO_MINMAX nor TSDS_ALGO_M4", who, i, algos[i]);
+    const int per = algos[i] == TSDS_ALGO_MINMAX ? 2 : 4;
+    if (n_outs[i] < per || n_outs[i] % per != 0)
+      return fail(TSDS_EINVAL, "%s: n_outs[%d] must be a positive multiple of %d (got %lld)", who, i, per,
+                  (long long)n_outs[i]);
+    if (n > 0 && !outs_host[i]) return fail(TSDS_EINVAL, "%s: outs_host[%d] is NULL", who, i);
+  }
+  if (y_dev && reinterpret_cast<uintptr_t>(y_dev) % dtype_size(y_dtype) != 0)
+    return fail(TSDS_EINVAL, "%s: y_dev is not aligned to its element size", who);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // x: device memory, or page-locked host memory read in place through its
+  // device address
+  const void* xd = x;
+  if (x) {
+    cudaPointerAttributes pa;
+    const cudaError_t e = cudaPointerGetAttributes(&pa, x);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(TSDS_EINVAL, "%s: x is not an address CUDA knows (%s)", who, cudaGetErrorString(e));
+    }
+    if (pa.type == cudaMemoryTypeUnregistered || (pa.type == cudaMemoryTypeHost && !pa.devicePointer))
+      return fail(TSDS_EINVAL, "%s: x must be device memory or page-locked host memory", who);
+    if (pa.type == cudaMemoryTypeHost) xd = pa.devicePointer;
+  }
+  s = check_sorted_x(who, xd, x_dtype, n, st);
+  if (s != TSDS_OK) return s;
+  if (n == 0) {
+    for (int i = 0; i < count; ++i) counts_host[i] = 0;
+    return TSDS_OK;
+  }
+  const int64_t es = dtype_size(y_dtype);
+  const int64_t total = n * es;
+  const int64_t chunk = host_chunk_bytes(total);
+  const int64_t chunks = (total + chunk - 1) / chunk;
+  // scratch: y (unless the caller gives a buffer), then per binned job its
+  // bin starts, its range outputs at their largest and one count per chunk
+  std::vector<HostJob> jobs;
+  size_t o = align_up(y_dev ? 0 : (size_t)total, 256);
+  for (int i = 0; i < count; ++i) {
+    HostJob j;
+    j.algo = algos[i] == TSDS_ALGO_MINMAX ? ALGO_MINMAX : ALGO_M4;
+    j.per = algos[i] == TSDS_ALGO_MINMAX ? 2 : 4;
+    j.nb = n_outs[i] >= n ? 0 : n_outs[i] / j.per;
+    jobs.push_back(std::move(j));
+  }
+  std::vector<size_t> off(count * 3);
+  for (int i = 0; i < count; ++i) {
+    const int64_t nb = jobs[i].nb;
+    off[3 * i] = o;     o = align_up(o + (size_t)(nb > 0 ? nb + 1 : 0) * 8, 256);
+    off[3 * i + 1] = o; o = align_up(o + (size_t)(nb * jobs[i].per) * 8, 256);
+    off[3 * i + 2] = o; o = align_up(o + (size_t)chunks * 8, 256);
+  }
+  Scratch sc;
+  TSDS_CK(scratch_alloc(sc, o, st));
+  char* base = static_cast<char*>(sc.p);
+  char* yd = y_dev ? static_cast<char*>(y_dev) : base;
+  // bin starts of every binned job (x read in place), copied to the host to
+  // cut the bins into per-chunk ranges
+  for (int i = 0; i < count; ++i) {
+    HostJob& j = jobs[i];
+    if (j.nb == 0) continue;
+    j.edges_dev = reinterpret_cast<int64_t*>(base + off[3 * i]);
+    j.out_dev = reinterpret_cast<int64_t*>(base + off[3 * i + 1]);
+    j.cnt_dev = reinterpret_cast<int64_t*>(base + off[3 * i + 2]);
+    SeriesDev S;
+    memset(&S, 0, sizeof S);
+    S.x = xd;
+    S.n = n;
+    S.nb = j.nb;
+    S.edges = j.edges_dev;
+    TSDS_CK(launch_edges(nullptr, 1, &S, xd != nullptr, x_dtype, j.nb, st));
+    j.edges.resize((size_t)j.nb + 1);
+    TSDS_CK(cudaMemcpyAsync(j.edges.data(), j.edges_dev, (size_t)(j.nb + 1) * 8, cudaMemcpyDeviceToHost, st));
+  }
+  TSDS_CK(cudaStreamSynchronize(st));
+  // the copy stream starts after the caller's earlier work on `stream` (y_dev
+  // may still be read by it); one event per chunk.  On every way out the
+  // caller's stream waits for the last copy, so that nothing later on it (the
+  // scratch's release among them) overtakes a copy still in flight.
+  struct Events {
+    cudaStream_t cs = nullptr, st = nullptr;
+    std::vector<cudaEvent_t> ev;
+    int64_t last = -1;
+    ~Events() {
+      if (last >= 0) cudaStreamWaitEvent(st, ev[(size_t)last], 0);
+      for (cudaEvent_t e : ev) cudaEventDestroy(e);
+      if (cs) cudaStreamDestroy(cs);
+    }
+  } E;
+  E.st = st;
+  TSDS_CK(cudaStreamCreateWithFlags(&E.cs, cudaStreamNonBlocking));
+  E.ev.assign((size_t)chunks + 1, nullptr);
+  for (auto& e : E.ev) TSDS_CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  TSDS_CK(cudaEventRecord(E.ev[chunks], st));
+  TSDS_CK(cudaStreamWaitEvent(E.cs, E.ev[chunks], 0));
+  const char* yh = static_cast<const char*>(y_host);
+  for (int64_t c = 0; c < chunks; ++c) {
+    const int64_t b = c * chunk, len = (c + 1 == chunks ? total : b + chunk) - b;
+    TSDS_CK(cudaMemcpyAsync(yd + b, yh + b, (size_t)len, cudaMemcpyHostToDevice, E.cs));
+    TSDS_CK(cudaEventRecord(E.ev[c], E.cs));
+    E.last = c;
+  }
+  std::vector<int64_t> done((size_t)count, 0);
+  for (int64_t c = 0; c < chunks; ++c) {
+    TSDS_CK(cudaStreamWaitEvent(st, E.ev[c], 0));
+    const int64_t have = c + 1 == chunks ? n : (c + 1) * chunk / es;   // points on the device
+    for (int i = 0; i < count; ++i) {
+      HostJob& j = jobs[i];
+      if (j.nb == 0) continue;
+      // bins whose last point has arrived: edges[b + 1] <= have
+      const int64_t b1 = (int64_t)(std::upper_bound(j.edges.begin() + 1, j.edges.end(), have) - (j.edges.begin() + 1));
+      if (b1 <= done[i]) continue;
+      int64_t* cnt = j.cnt_dev + j.range_lo.size();
+      s = run_binned_range(xd, x_dtype, yd, y_dtype, n, j.nb, done[i], b1, nan, j.algo, j.out_dev + j.per * done[i],
+                           cnt, st, j.edges_dev);
+      if (s != TSDS_OK) return s;
+      j.range_lo.push_back(done[i]);
+      done[i] = b1;
+    }
+  }
+  // outputs: each job's ranges back to the host, compacted in bin order
+  std::vector<std::vector<int64_t>> stage((size_t)count), counts((size_t)count);
+  for (int i = 0; i < count; ++i) {
+    HostJob& j = jobs[i];
+    if (j.nb == 0) continue;
+    stage[i].resize((size_t)(j.nb * j.per));
+    counts[i].resize(j.range_lo.size());
+    TSDS_CK(cudaMemcpyAsync(stage[i].data(), j.out_dev, stage[i].size() * 8, cudaMemcpyDeviceToHost, st));
+    TSDS_CK(cudaMemcpyAsync(counts[i].data(), j.cnt_dev, counts[i].size() * 8, cudaMemcpyDeviceToHost, st));
+  }
+  TSDS_CK(cudaStreamSynchronize(st));
+  for (int i = 0; i < count; ++i) {
+    HostJob& j = jobs[i];
+    if (j.nb == 0) {
+      for (int64_t v = 0; v < n; ++v) outs_host[i][v] = v;   // n_out >= n: every index
+      counts_host[i] = n;
+      continue;
+    }
+    int64_t pos = 0;
+    for (size_t r = 0; r < j.range_lo.size(); ++r) {
+      const int64_t k = counts[i][r];
+      if (k < 0) return fail((tsds_status)(-k), "%s: the streaming pass reported a device-side failure", who);
+      memcpy(outs_host[i] + pos, stage[i].data() + j.per * j.range_lo[r], (size_t)k * 8);
+      pos += k;
+    }
+    counts_host[i] = pos;
+  }
+  return TSDS_OK;
 }
 
 // EveryNth: the bin starts (index space or x space, as for MinMax/M4) with
@@ -570,6 +758,15 @@ tsds_status tsds_m4_bins(const void* x, tsds_dtype x_dtype, const void* y, tsds_
                          int64_t* out_count, void* stream) {
   NvtxRange nvtx_("tsds_m4_bins");
   return binned_range_entry(ALGO_M4, x, x_dtype, y, y_dtype, n, n_out, bin_lo, bin_hi, nan, out, out_count, stream);
+}
+
+tsds_status tsds_downsample_host(int count, const int* algos, const int64_t* n_outs, const void* x,
+                                 tsds_dtype x_dtype, const void* y_host, tsds_dtype y_dtype, int64_t n,
+                                 tsds_nan_mode nan, void* y_dev, int64_t* const* outs_host, int64_t* counts_host,
+                                 void* stream) {
+  NvtxRange nvtx_("tsds_downsample_host");
+  return host_entry(count, algos, n_outs, x, x_dtype, y_host, y_dtype, n, nan, y_dev, outs_host, counts_host,
+                    stream);
 }
 
 tsds_status tsds_everynth(const void* x, tsds_dtype x_dtype, const void* y, tsds_dtype y_dtype, int64_t n,

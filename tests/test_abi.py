@@ -229,3 +229,30 @@ def test_bin_range_arguments_are_checked_on_the_host(lib, fn):
         assert fn(None, 0, y, 9, 1000, n_out, lo, hi, 0, out, cnt, None) == 1, (n_out, lo, hi)
         assert pkg.last_error()
     assert pkg.tsds_kernel_launches() == before
+
+
+def test_host_entry_arguments_are_checked_on_the_host(lib):
+    """tsds_downsample_host refuses a bad count, an unknown algorithm, an invalid n_out, a NULL
+    output and a misaligned y_dev before anything reaches the device."""
+    import ctypes
+    before = pkg.tsds_kernel_launches()
+    y = (ctypes.c_float * 1000)()
+    out = (ctypes.c_int64 * 1000)()
+    counts = (ctypes.c_int64 * 2)()
+    outs = (ctypes.c_void_p * 2)(ctypes.addressof(out), ctypes.addressof(out))
+    null_outs = (ctypes.c_void_p * 2)(None, None)
+
+    def call(count, algos, n_outs, outs_=outs, y_dev=None):
+        a = (ctypes.c_int * max(len(algos), 1))(*algos)
+        k = (ctypes.c_int64 * max(len(n_outs), 1))(*n_outs)
+        return binding.tsds_downsample_host(count, a, k, None, 0, ctypes.addressof(y), 9, 1000, 0, y_dev, outs_,
+                                            counts, None)
+
+    cases = [(0, [0], [100]), (17, [0], [100]), (1, [2], [100]), (1, [0], [101]), (1, [1], [102]),
+             (1, [1], [0]), (2, [0, 1], [100, 6])]
+    for count, algos, n_outs in cases:
+        assert call(count, algos, n_outs) == 1, (count, algos, n_outs)
+        assert pkg.last_error()
+    assert call(1, [0], [100], outs_=null_outs) == 1
+    assert call(1, [0], [100], y_dev=1 << 20 | 2) == 1
+    assert pkg.tsds_kernel_launches() == before

@@ -93,6 +93,30 @@ def test_dtype_workloads_whole_output(dtype):
     torch.cuda.empty_cache()
 
 
+@pytest.mark.parametrize("bin_bytes", [1024, 16384, 49152, 131072])
+@pytest.mark.parametrize("with_x", [False, True])
+def test_automatic_choice_beyond_256mb_whole_output(bin_bytes, with_x):
+    """1 GB of float32 random walk (seed 2), index bins or x-space bins over int64 geometric x:
+    beyond 256 MB the automatic choice runs lane groups below 64 KB mean bins and register
+    streaming above; every index of both outputs at bins of 1, 16, 48 and 128 KB."""
+    import torch
+    n = 250_000_000
+    y = inputs.random_walk_cuda(n, "float32", seed=2)
+    x = inputs.geometric_x_cuda(n, seed=2) if with_x else None
+    torch.cuda.synchronize()
+    yh = _host(y, "float32")
+    xh = _host(x, "int64") if with_x else None
+    for algo, per in (("minmax", 2), ("m4", 4)):
+        n_out = per * (n * 4 // bin_bytes)
+        g = _raw(algo, x, y, "float32", n, n_out)
+        want = oracle.binned_threads(algo, xh, yh, n_out)
+        assert len(want) == len(g), f"{algo} {bin_bytes} B bins: {len(g)} indices, oracle {len(want)}"
+        bad = np.flatnonzero(g != want)
+        assert bad.size == 0, f"{algo} {bin_bytes} B bins: first difference at output {bad[:1]}"
+    del x, y, xh, yh
+    torch.cuda.empty_cache()
+
+
 def test_batched_workload_sampled_series():
     """4096 float32 series, lengths round(10**U(3,7)) and n_out in [200, 4000] (seed 3), as a
     resident autotuned plan with a CUDA graph, MinMax and M4."""
