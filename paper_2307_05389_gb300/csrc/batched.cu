@@ -118,8 +118,9 @@ tsds_status check_batch_sorted(const tsds_series* s, int64_t count, tsds_dtype x
 // Window bases for windows of welems elements: group 0 first, then group 1
 // (from split_windows on); with auto_groups, group 2 gets CTA bases and group
 // 3 tile bases (its lane-group shape from the series' bin size, with G scaled
-// by 2^grp_scale) instead.
-static void number_windows(BatchLayout& L, int64_t welems, bool auto_groups, int grp_scale = 0) {
+// by 2^grp_scale and the bins per tile by 2^tile_scale) instead.
+static void number_windows(BatchLayout& L, int64_t welems, bool auto_groups, int grp_scale = 0,
+                           int tile_scale = 0) {
   int64_t win = 0, cta = 0, tile = 0;
   L.auto_groups = auto_groups;
   for (int pass = 0; pass < 2; ++pass) {
@@ -134,6 +135,7 @@ static void number_windows(BatchLayout& L, int64_t welems, bool auto_groups, int
           lg = lg < 0 ? 0 : lg > 5 ? 5 : lg;
           const int groups = 32 >> lg;
           int rounds = (int)(sh.tile_rounds * (int64_t)(32 >> sh.g_log2) / groups);
+          rounds = tile_scale >= 0 ? rounds << tile_scale : rounds >> -tile_scale;
           if (rounds < 1) rounds = 1;
           if (rounds * groups > kGrpTileMaxBins) rounds = kGrpTileMaxBins / groups;
           d.mode = 2;
@@ -247,8 +249,9 @@ static void bind_layout(BatchLayout& L, char* base, tsds_dtype y_dtype, int64_t 
   number_windows(L, window_bytes / dtype_size(y_dtype), variant == STREAM_AUTO, grp_scale);
 }
 
-static void rebase_windows(BatchLayout& L, tsds_dtype y_dtype, int64_t window_bytes, int variant, int grp_scale) {
-  number_windows(L, window_bytes / dtype_size(y_dtype), variant == STREAM_AUTO, grp_scale);
+static void rebase_windows(BatchLayout& L, tsds_dtype y_dtype, int64_t window_bytes, int variant, int grp_scale,
+                           int tile_scale) {
+  number_windows(L, window_bytes / dtype_size(y_dtype), variant == STREAM_AUTO, grp_scale, tile_scale);
 }
 
 // The window map and (automatic variant) the CTA map of the current numbering.
@@ -338,7 +341,7 @@ static tsds_status enqueue(const BatchLayout& L, char* base, tsds_algo algo, boo
 }
 
 static tsds_status upload(BatchLayout& L, char* base, tsds_dtype y_dtype, const StreamConfig& cfg, cudaStream_t st) {
-  rebase_windows(L, y_dtype, cfg.window_bytes, cfg.variant, cfg.grp_scale);
+  rebase_windows(L, y_dtype, cfg.window_bytes, cfg.variant, cfg.grp_scale, cfg.grp_tile_scale);
   BT_CK(cudaMemcpyAsync(base + L.off_desc, L.host.data(), L.host.size() * sizeof(SeriesDev),
                         cudaMemcpyHostToDevice, st));
   const tsds_status s = launch_maps(L, base, y_dtype, cfg.window_bytes, st);
@@ -350,25 +353,30 @@ static tsds_status upload(BatchLayout& L, char* base, tsds_dtype y_dtype, const 
 
 // ---------------------------------------------------------------- autotuner
 
-static StreamConfig grp_candidate(int scale) {
+static StreamConfig grp_candidate(int scale, int tile_scale = 0) {
   StreamConfig c;
   c.grp_scale = scale;
+  c.grp_tile_scale = tile_scale;
   return c;
 }
 
 // Candidate launch shapes: window bytes, CTAs per SM, -, kernel variant
-// (automatic: split by series bin size), lanes per bin of the lane-group
-// series (a power-of-two scale of the default).  The smallest window must come
-// first: the scratch is laid out for it (the most windows).  Without a tuned
-// choice a plan runs the default shape (64 KB windows, automatic variant).
+// (automatic: split by series bin size), lanes per bin and bins per tile of
+// the lane-group series (power-of-two scales of the default).  The smallest
+// window must come first: the scratch is laid out for it (the most windows).
+// Without a tuned choice a plan runs the default shape (64 KB windows,
+// automatic variant).  The vector width is not a dimension: every streaming
+// kernel loads 16 bytes per lane, which reaches the copy bandwidth on large
+// bins; below that the per-bin work, not the load width, sets the rate.
 static const StreamConfig kCandidates[] = {
     {16 * 1024, 0, nullptr, STREAM_RING},  {32 * 1024, 0, nullptr, STREAM_RING}, {64 * 1024, 0, nullptr, STREAM_RING},
     {128 * 1024, 0, nullptr, STREAM_RING}, {64 * 1024, 2, nullptr, STREAM_RING}, {256 * 1024, 0, nullptr, STREAM_RING},
     {32 * 1024, 0, nullptr, STREAM_LDG},   {64 * 1024, 0, nullptr, STREAM_LDG},  {256 * 1024, 0, nullptr, STREAM_LDG},
     {32 * 1024, 0, nullptr, STREAM_SEG},   {64 * 1024, 0, nullptr, STREAM_SEG},  {256 * 1024, 0, nullptr, STREAM_SEG},
     {64 * 1024, 0, nullptr, STREAM_AUTO},  {256 * 1024, 0, nullptr, STREAM_AUTO},
-    // automatic split with half and twice the lanes per bin in the lane-group series
-    grp_candidate(-1), grp_candidate(1)};
+    // automatic split with half and twice the lanes per bin in the lane-group series,
+    // then with half and twice the bins per lane-group tile
+    grp_candidate(-1), grp_candidate(1), grp_candidate(0, -1), grp_candidate(0, 1)};
 constexpr int kNumCandidates = sizeof(kCandidates) / sizeof(kCandidates[0]);
 
 static std::mutex g_tune_mu;

@@ -105,8 +105,10 @@ struct StreamConfig {
   int64_t min_bin = 0;
   const unsigned long long* large_dev = nullptr;
   // Batched plans: lanes per bin of the lane-group series, 2^grp_scale times
-  // the default choice (an autotuner dimension).
+  // the default choice, and bins per lane-group tile, 2^grp_tile_scale times
+  // the default (autotuner dimensions).
   int grp_scale = 0;
+  int grp_tile_scale = 0;
 };
 // A mean_bin_bytes at which the register-streaming pass never prefetches.
 constexpr int64_t kPrefetchOffBinBytes = 1ll << 40;
