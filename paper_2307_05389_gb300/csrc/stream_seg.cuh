@@ -471,7 +471,7 @@ k_argminmax_seg(const SeriesDev* __restrict__ sd, SeriesDev single, const int32_
         memcpy(el, &cv, 16);
         int r_lo = o_lo;
         for (;;) {
-          // this round: positions [r_lo, r_hi) and the bin starts cur[j] < qs + r_hi
+          // this pass of the loop: positions [r_lo, r_hi) and the bin starts cur[j] < qs + r_hi
           const int64_t n0 = __shfl_sync(FULL, nxt, 0);
           const int r_hi = n0 < s_hi ? (int)(n0 - qs) : o_hi;
           const bool in = lane >= ep && cur < qs + r_hi;
