@@ -328,12 +328,13 @@ struct Pol64 {
   }
   __device__ static void group1(const uint4& v, Acc& gmin, Acc& gmax) {
     const uint64_t k0 = raw(((uint64_t)v.y << 32) | v.x), k1 = raw(((uint64_t)v.w << 32) | v.z);
-    if (KIND == 2 && (raw_key_is_nan(k0) || raw_key_is_nan(k1))) {
+    gmin = min(k0, k1);
+    gmax = max(k0, k1);
+    // raw NaN keys lie outside [key(-inf), key(+inf)], so one of the two is a
+    // NaN exactly when the smaller lies below that range or the larger above
+    if (KIND == 2 && (gmin < kKeyNegInf || gmax > kKeyPosInf)) {
       gmin = min(kmin_of(k0), kmin_of(k1));
       gmax = max(kmax_of(k0), kmax_of(k1));
-    } else {
-      gmin = min(k0, k1);
-      gmax = max(k0, k1);
     }
   }
   __device__ static uint64_t bits(T e) {
